@@ -1,0 +1,298 @@
+"""ctypes wrapper around the FP64 C oracle (cv_oracle.c) plus the conv-to-dense expansion.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference leg.  It imports nothing from the CUDA product package.
+
+Every floating-point input is converted to float64 exactly (the callers hand FP32
+values); every result is float64 except masks and flags.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cv_oracle.c")
+_LIB = os.path.join(_HERE, "libcv_oracle.so")
+_lib = None
+
+def build(force=False):
+    """Compile cv_oracle.c with gcc (plain -O2, IEEE semantics, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", _LIB, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        _lib.orc_concretize.argtypes = [I, P, D, P, P, P, P]
+        _lib.orc_root_crown.argtypes = [I, P, P, P, P, P, I, P, P, P, P, P, P, P]
+        _lib.orc_row_check.argtypes = [I, P, D, P, P, P, P, P]
+        _lib.orc_row_check.restype = I
+        _lib.orc_relaxed_clip_row.argtypes = [I, P, D, P, P, P, P]
+        _lib.orc_relaxed_clip_parallel.argtypes = [I, I, P, P, P, P, P, P]
+        _lib.orc_relaxed_clip_parallel.restype = I
+        _lib.orc_relaxed_clip_sequential.argtypes = [I, I, P, P, P, P, P, P]
+        _lib.orc_relaxed_clip_sequential.restype = I
+        _lib.orc_complete_clip.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
+        _lib.orc_complete_clip.restype = D
+        _lib.orc_dual_value.argtypes = [I, P, D, I, P, P, P, P, P]
+        _lib.orc_dual_value.restype = D
+        _lib.orc_bound_batch.argtypes = ([I, P, P, P] + [I, P, P, P, P, P] + [P, P, P] +
+                                         [I, P, P, P, P] + [P, P] + [P, P, P] + [I, P, P] +
+                                         [P, I] + [P, P] + [I, I, I] +
+                                         [P] * 13 + [I])
+        _lib.orc_bound_batch.restype = I
+        _lib.orc_alpha_grad.argtypes = [I, P, P, P, P, P, P, P, P, I, P, P, P, P, P, P]
+        _lib.orc_alpha_grad.restype = I
+        _lib.orc_adam_step.argtypes = [ctypes.c_long, P, P, P, P, I, D, D, D, D]
+    return _lib
+
+
+def _f64(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _i32(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# network: conv layers become dense matrices written out from the definition
+# --------------------------------------------------------------------------
+def conv_to_dense(ly):
+    """The dense matrix of a 2-D convolution with zero padding (output index
+    (oc, oy, ox), input index (ic, iy, ix), row-major C,H,W flattening):
+    W[(oc,oy,ox),(ic,iy,ix)] = K[oc,ic,ky,kx] where iy = oy*s - p + ky, ix = ox*s - p + kx."""
+    K = np.asarray(ly["W"], np.float64)
+    oc_n, ic_n, kh, kw = K.shape
+    _, H, Wd = ly["in_shape"]
+    _, Ho, Wo = ly["out_shape"]
+    s, p = ly["stride"], ly["pad"]
+    M = np.zeros((oc_n * Ho * Wo, ic_n * H * Wd))
+    for oc in range(oc_n):
+        for oy in range(Ho):
+            for ox in range(Wo):
+                r = (oc * Ho + oy) * Wo + ox
+                for ic in range(ic_n):
+                    for ky in range(kh):
+                        iy = oy * s - p + ky
+                        if iy < 0 or iy >= H:
+                            continue
+                        for kx in range(kw):
+                            ix = ox * s - p + kx
+                            if ix < 0 or ix >= Wd:
+                                continue
+                            M[r, (ic * H + iy) * Wd + ix] += K[oc, ic, ky, kx]
+    bias = np.repeat(np.asarray(ly["b"], np.float64), Ho * Wo)
+    return M, bias
+
+
+class Net:
+    """Dense FP64 view of a layer list (dicts from the workload generators)."""
+
+    def __init__(self, layers):
+        Ws, bs = [], []
+        dims = [int(np.prod(layers[0]["in_shape"]))]
+        for ly in layers:
+            if ly["kind"] == 1:
+                M, bb = conv_to_dense(ly)
+            else:
+                M, bb = np.asarray(ly["W"], np.float64), np.asarray(ly["b"], np.float64)
+            Ws.append(M)
+            bs.append(bb)
+            dims.append(M.shape[0])
+        self.Ws = Ws
+        self.bs = bs
+        self.dims = np.asarray(dims, np.int32)
+        self.L = len(Ws)
+        self.H = int(sum(dims[1:-1]))
+        self.Wflat = _f64(np.concatenate([w.ravel() for w in Ws]))
+        self.bflat = _f64(np.concatenate(bs))
+
+    def forward(self, x):
+        """Exact-ish FP64 forward pass; returns (output, list of pre-activations)."""
+        z = np.asarray(x, np.float64)
+        pre = []
+        for i, (W, b) in enumerate(zip(self.Ws, self.bs)):
+            z = z @ W.T + b
+            if i < self.L - 1:
+                pre.append(z.copy())
+                z = np.maximum(z, 0.0)
+        return z, pre
+
+
+# --------------------------------------------------------------------------
+# wrappers
+# --------------------------------------------------------------------------
+def concretize(a, c, lo, hi):
+    lib = _load()
+    a, lo, hi = _f64(a), _f64(lo), _f64(hi)
+    vmin, vmax = ctypes.c_double(), ctypes.c_double()
+    lib.orc_concretize(a.size, _p(a), float(c), _p(lo), _p(hi), ctypes.byref(vmin), ctypes.byref(vmax))
+    return vmin.value, vmax.value
+
+
+def root_crown(net: Net, lo, hi, alpha_mode=0):
+    """Root CROWN bounds and planes of every hidden neuron (dict of float64 arrays)."""
+    lib = _load()
+    lo, hi = _f64(lo), _f64(hi)
+    H, n0 = net.H, int(net.dims[0])
+    out = dict(l=np.zeros(H), u=np.zeros(H), lA=np.zeros((H, n0)), lc=np.zeros(H),
+               uA=np.zeros((H, n0)), uc=np.zeros(H), pscale=np.zeros(H))
+    rc = lib.orc_root_crown(net.L, _p(net.dims), _p(net.Wflat), _p(net.bflat), _p(lo), _p(hi),
+                            int(alpha_mode), _p(out["l"]), _p(out["u"]), _p(out["lA"]), _p(out["lc"]),
+                            _p(out["uA"]), _p(out["uc"]), _p(out["pscale"]))
+    assert rc == 0
+    return out
+
+
+def make_cache(root):
+    """Cache of the root-unstable neurons (Section 3.4): slots in global-id order."""
+    l, u = root["l"], root["u"]
+    ids = np.nonzero((l < 0.0) & (u > 0.0))[0].astype(np.int32)
+    return dict(ids=ids, lA=root["lA"][ids], lc=root["lc"][ids], uA=root["uA"][ids], uc=root["uc"][ids],
+                root_l=root["l"], root_u=root["u"], pscale=root["pscale"])
+
+
+def cache_as_f32(cache):
+    """The cache as the FP32 arrays both sides consume (values rounded to nearest)."""
+    out = dict(cache)
+    for k in ("lA", "lc", "uA", "uc"):
+        out[k] = np.asarray(cache[k], np.float32).astype(np.float64)
+    return out
+
+
+def row_check(g, h, lo, hi):
+    lib = _load()
+    g, lo, hi = _f64(g), _f64(lo), _f64(hi)
+    vmin, vmax, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    f = lib.orc_row_check(g.size, _p(g), float(h), _p(lo), _p(hi), ctypes.byref(vmin),
+                          ctypes.byref(vmax), ctypes.byref(s))
+    return f, vmin.value, vmax.value, s.value
+
+
+def relaxed_clip(G, h, lo, hi, sequential=False):
+    lib = _load()
+    G, h, lo, hi = _f64(np.atleast_2d(G)), _f64(np.atleast_1d(h)), _f64(lo), _f64(hi)
+    lo2, hi2 = np.zeros_like(lo), np.zeros_like(hi)
+    fn = lib.orc_relaxed_clip_sequential if sequential else lib.orc_relaxed_clip_parallel
+    inf = fn(lo.size, G.shape[0], _p(G), _p(h), _p(lo), _p(hi), _p(lo2), _p(hi2))
+    return lo2, hi2, bool(inf)
+
+
+def complete_clip(a, c, G, h, lo, hi, sweeps):
+    """Algorithm 1 repeated `sweeps` times: (value, beta, scale)."""
+    lib = _load()
+    a, G, h, lo, hi = _f64(a), _f64(np.atleast_2d(G)), _f64(np.atleast_1d(h)), _f64(lo), _f64(hi)
+    R = G.shape[0] if G.size else 0
+    beta = np.zeros(max(R, 1))
+    sc = ctypes.c_double()
+    v = lib.orc_complete_clip(a.size, _p(a), float(c), R, _p(G), _p(h), _p(lo), _p(hi), int(sweeps),
+                              _p(beta), ctypes.byref(sc))
+    return v, beta[:R], sc.value
+
+
+def dual_value(a, c, G, h, lo, hi, beta):
+    lib = _load()
+    a, G, h, lo, hi, beta = (_f64(a), _f64(np.atleast_2d(G)), _f64(np.atleast_1d(h)), _f64(lo),
+                             _f64(hi), _f64(beta))
+    return lib.orc_dual_value(a.size, _p(a), float(c), G.shape[0], _p(G), _p(h), _p(lo), _p(hi), _p(beta))
+
+
+def bound_batch(net: Net, cache, lo, hi, *, l_in=None, u_in=None, split_off=None, split_ids=None,
+                row_off=None, G=None, h=None, C, t, alpha=None, alpha_mode=0,
+                tgt_off=None, tgt_ids=None, relaxed=1, sweeps=0, enforce_splits=1, want_final=False,
+                nthreads=0):
+    """One BaB round (a2..a8) for B subdomains.  Returns a dict of outputs."""
+    lib = _load()
+    lo, hi = _f64(lo), _f64(hi)
+    B, n0 = lo.shape
+    ids = _i32(cache["ids"])
+    U = ids.size
+    m = int(np.asarray(C).shape[0])
+    lA, lc, uA, uc = (_f64(cache[k]) for k in ("lA", "lc", "uA", "uc"))
+    rl, ru, ps = _f64(cache["root_l"]), _f64(cache["root_u"]), _f64(cache["pscale"])
+    if lA.size == 0:
+        lA = np.zeros((1, n0)); uA = np.zeros((1, n0)); lc = np.zeros(1); uc = np.zeros(1)
+    l_in = None if l_in is None else _f64(l_in)
+    u_in = None if u_in is None else _f64(u_in)
+    so = None if split_off is None else _i32(split_off)
+    si = None if split_ids is None else _i32(split_ids)
+    if si is not None and si.size == 0:
+        si = np.zeros(1, np.int32)
+    ro = None if row_off is None else _i32(row_off)
+    Gx = None if G is None else _f64(G)
+    hx = None if h is None else _f64(h)
+    if Gx is not None and Gx.size == 0:
+        Gx = np.zeros((1, n0)); hx = np.zeros(1)
+    Cx, tx = _f64(C), _f64(t)
+    al = None if alpha is None else _f64(alpha)
+    to = None if tgt_off is None else _i32(tgt_off)
+    ti = None if tgt_ids is None else _i32(tgt_ids)
+    if ti is not None and ti.size == 0:
+        ti = np.zeros(1, np.int32)
+    Uo = max(U, 1)
+    out = dict(lower=np.zeros((B, m)), lower_scale=np.zeros((B, m)),
+               lo_clip=np.zeros((B, n0)), hi_clip=np.zeros((B, n0)),
+               l=np.zeros((B, Uo)), u=np.zeros((B, Uo)), l_scale=np.zeros((B, Uo)), u_scale=np.zeros((B, Uo)),
+               mask=np.zeros((B, Uo), np.int8), infeasible=np.zeros(B, np.uint8), verified=np.zeros(B, np.uint8))
+    fA = np.zeros((B, m, n0)) if want_final else None
+    fc = np.zeros((B, m)) if want_final else None
+    rc = lib.orc_bound_batch(net.L, _p(net.dims), _p(net.Wflat), _p(net.bflat),
+                             U, _p(ids), _p(lA), _p(lc), _p(uA), _p(uc), _p(rl), _p(ru), _p(ps),
+                             B, _p(lo), _p(hi), _p(l_in), _p(u_in), _p(so), _p(si), _p(ro), _p(Gx), _p(hx),
+                             m, _p(Cx), _p(tx), _p(al), int(alpha_mode), _p(to), _p(ti),
+                             int(relaxed), int(sweeps), int(enforce_splits),
+                             _p(out["lower"]), _p(out["lower_scale"]), _p(out["lo_clip"]), _p(out["hi_clip"]),
+                             _p(out["l"]), _p(out["u"]), _p(out["l_scale"]), _p(out["u_scale"]),
+                             _p(out["mask"]), _p(out["infeasible"]), _p(out["verified"]), _p(fA), _p(fc),
+                             int(nthreads))
+    assert rc == 0
+    if U == 0:
+        for k in ("l", "u", "l_scale", "u_scale", "mask"):
+            out[k] = out[k][:, :0]
+    if want_final:
+        out["final_A"], out["final_c"] = fA, fc
+    return out
+
+
+def alpha_grad(net: Net, hl, hu, hs, lo, hi, C, t, alpha, grad_f=None):
+    """f [m] and d(sum grad_f*f)/d alpha [m x H] for one subdomain."""
+    lib = _load()
+    m = int(np.asarray(C).shape[0])
+    hl, hu, lo, hi, Cx, tx, al = _f64(hl), _f64(hu), _f64(lo), _f64(hi), _f64(C), _f64(t), _f64(alpha)
+    hs = np.ascontiguousarray(np.asarray(hs, np.int8))
+    gf = None if grad_f is None else _f64(grad_f)
+    f = np.zeros(m)
+    g = np.zeros((m, net.H))
+    rc = lib.orc_alpha_grad(net.L, _p(net.dims), _p(net.Wflat), _p(net.bflat), _p(hl), _p(hu), _p(hs),
+                            _p(lo), _p(hi), m, _p(Cx), _p(tx), _p(al), _p(gf), _p(f), _p(g))
+    assert rc == 0
+    return f, g
+
+
+def adam_step(alpha, m1, m2, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam ascent step with clamp to [0,1] on float64 arrays."""
+    lib = _load()
+    for a in (alpha, m1, m2):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(g)
+    lib.orc_adam_step(alpha.size, _p(alpha), _p(m1), _p(m2), _p(g), int(t), float(lr), float(b1),
+                      float(b2), float(eps))

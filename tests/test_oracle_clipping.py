@@ -1,0 +1,148 @@
+"""The oracle's clipping solvers against brute force and the mathematics.
+
+Pins: Lemma A.1 (box extremes at vertices), Theorem 1 (one-row complete clipping
+is the exact LP optimum; equals the fractional-knapsack greedy), Theorem 2
+(one-row relaxed clipping is component-wise tight), weak duality and monotone
+ascent for Algorithm 1 with several rows, the a-priori infeasibility test, and
+the order-dependency example of the Appendix (Algorithm 3 vs Algorithm 2)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests._brute import knapsack_greedy, lp_vertex
+
+
+def rand_box(rng, n):
+    lo = rng.uniform(-1.0, 0.5, n)
+    hi = lo + rng.uniform(0.05, 2.0, n)
+    return lo, hi
+
+
+def cutting_row(rng, lo, hi, spread=0.8):
+    g = rng.normal(size=lo.size)
+    xh, ep = (lo + hi) / 2, (hi - lo) / 2
+    h = -(g @ xh) + rng.uniform(-spread, spread) * (np.abs(g) @ ep)
+    return g, h
+
+
+def test_concretize_equals_vertex_extremes():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        n = int(rng.integers(1, 7))
+        lo, hi = rand_box(rng, n)
+        a, c = rng.normal(size=n), rng.normal()
+        vals = [a @ np.where(np.array(bits), hi, lo) + c for bits in itertools.product([0, 1], repeat=n)]
+        vmin, vmax = O.concretize(a, c, lo, hi)
+        assert vmin == pytest.approx(min(vals), abs=1e-12)
+        assert vmax == pytest.approx(max(vals), abs=1e-12)
+
+
+def test_one_row_complete_clip_is_lp_and_knapsack():
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        n = int(rng.integers(1, 6))
+        lo, hi = rand_box(rng, n)
+        g, h = cutting_row(rng, lo, hi)
+        a, c = rng.normal(size=n), rng.normal()
+        lp = lp_vertex(a, c, [g], [h], lo, hi)
+        ks = knapsack_greedy(a, c, g, h, lo, hi)
+        v, beta, _ = O.complete_clip(a, c, [g], [h], lo, hi, sweeps=1)
+        assert beta[0] >= 0.0
+        assert v == pytest.approx(lp, abs=1e-9 * (1 + abs(lp)))
+        assert ks == pytest.approx(lp, abs=1e-9 * (1 + abs(lp)))
+
+
+def test_one_row_relaxed_clip_is_componentwise_tight():
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        n = int(rng.integers(1, 6))
+        lo, hi = rand_box(rng, n)
+        g, h = cutting_row(rng, lo, hi)
+        lo2, hi2, inf = O.relaxed_clip([g], [h], lo, hi)
+        assert not inf
+        for i in range(n):
+            e = np.eye(n)[i]
+            assert lo2[i] == pytest.approx(lp_vertex(e, 0.0, [g], [h], lo, hi, "min"), abs=1e-9)
+            assert hi2[i] == pytest.approx(lp_vertex(e, 0.0, [g], [h], lo, hi, "max"), abs=1e-9)
+
+
+def test_multi_row_weak_duality_and_monotone_ascent():
+    rng = np.random.default_rng(4)
+    for _ in range(80):
+        n = int(rng.integers(2, 5))
+        R = int(rng.integers(2, 4))
+        lo, hi = rand_box(rng, n)
+        # rows through a common interior point keep the system feasible
+        x0 = lo + (hi - lo) * rng.uniform(0.3, 0.7, n)
+        G = rng.normal(size=(R, n))
+        h = -(G @ x0) - rng.uniform(0.0, 0.3, R) * (np.abs(G) @ ((hi - lo) / 2))
+        a, c = rng.normal(size=n), rng.normal()
+        lp = lp_vertex(a, c, G, h, lo, hi)
+        base, _ = O.concretize(a, c, lo, hi)
+        prev = base
+        for s in range(1, 6):
+            v, beta, _ = O.complete_clip(a, c, G, h, lo, hi, sweeps=s)
+            assert np.all(beta >= 0.0)
+            assert v <= lp + 1e-9 * (1 + abs(lp))          # weak duality
+            assert v >= prev - 1e-12 * (1 + abs(prev))      # ascent never decreases the dual
+            assert O.dual_value(a, c, G, h, lo, hi, beta) == pytest.approx(v, abs=1e-12 * (1 + abs(v)))
+            prev = v
+
+
+def test_infeasibility_precheck_matches_lp():
+    rng = np.random.default_rng(5)
+    for _ in range(100):
+        n = int(rng.integers(1, 5))
+        lo, hi = rand_box(rng, n)
+        g, h = cutting_row(rng, lo, hi, spread=2.0)
+        f, vmin, vmax, _ = O.row_check(g, h, lo, hi)
+        lp = lp_vertex(g, h, None, None, lo, hi)  # min over the box of g.x + h
+        assert vmin == pytest.approx(lp, abs=1e-12)
+        assert (f == 1) == (lp > 0)
+        if f == 1:
+            lo2, hi2, inf = O.relaxed_clip([g], [h], lo, hi)
+            assert inf
+
+
+def test_clipped_box_contains_feasible_samples():
+    rng = np.random.default_rng(6)
+    for _ in range(30):
+        n = int(rng.integers(2, 8))
+        R = int(rng.integers(1, 4))
+        lo, hi = rand_box(rng, n)
+        G = np.stack([cutting_row(rng, lo, hi)[0] for _ in range(R)])
+        h = np.array([cutting_row(rng, lo, hi)[1] for _ in range(R)])
+        for seq in (False, True):
+            lo2, hi2, inf = O.relaxed_clip(G, h, lo, hi, sequential=seq)
+            assert np.all(lo2 >= lo) and np.all(hi2 <= hi)
+            X = lo + (hi - lo) * rng.uniform(size=(4000, n))
+            feas = np.all(X @ G.T + h <= 0, axis=1)
+            if inf:
+                assert not feas.any()
+            else:
+                assert np.all(X[feas] >= lo2 - 1e-12) and np.all(X[feas] <= hi2 + 1e-12)
+        lop, hip, _ = O.relaxed_clip(G, h, lo, hi)
+        los, his, infs = O.relaxed_clip(G, h, lo, hi, sequential=True)
+        if not infs:
+            assert np.all(los >= lop - 1e-12) and np.all(his <= hip + 1e-12)
+
+
+def test_order_dependency_example():
+    # Appendix, order dependency: sequential clipping depends on the row order when one
+    # row's clip uses a bound that the other row tightens.  Instance on the box [0,2]^2:
+    # F1: x1 + x2 <= 2 (clips x1 <= 2 - lo2), F2: -x2 + 1 <= 0 (lo2 = 1).
+    lo, hi = np.array([0.0, 0.0]), np.array([2.0, 2.0])
+    G = np.array([[1.0, 1.0], [0.0, -1.0]])
+    h = np.array([-2.0, 1.0])
+    a_lo, a_hi, _ = O.relaxed_clip(G, h, lo, hi, sequential=True)          # F1 then F2
+    b_lo, b_hi, _ = O.relaxed_clip(G[::-1], h[::-1], lo, hi, sequential=True)  # F2 then F1
+    p_lo, p_hi, _ = O.relaxed_clip(G, h, lo, hi, sequential=False)
+    assert np.array_equal(a_hi, [2.0, 2.0]) and np.array_equal(a_lo, [0.0, 1.0])
+    assert np.array_equal(b_hi, [1.0, 2.0]) and np.array_equal(b_lo, [0.0, 1.0])
+    # the exact feasible range of x1 is [0, 1]: F2-then-F1 reaches it, F1-then-F2 does not
+    assert lp_vertex([1.0, 0.0], 0.0, G, h, lo, hi, "max") == pytest.approx(1.0)
+    # the parallel box is order-independent and contains both sequential boxes
+    assert np.all(p_lo <= a_lo) and np.all(p_hi >= a_hi)
+    assert np.all(p_lo <= b_lo) and np.all(p_hi >= b_hi)

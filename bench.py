@@ -1,0 +1,295 @@
+"""Benchmark: subdomains bounded and clipped per second on GB300.
+
+One step = one Clip-and-Verify bounding round (cv_bound_batch: constraint rows, pre-check,
+relaxed clipping, re-concretisation, complete clipping, spec back-substitution) over one batch of
+synthetic subdomains of the 784->256x6->10 ReLU MLP workload (4096 subdomains, 1-4 split
+constraints each, 9 margin rows, 10 coordinate-ascent sweeps).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--precision fp32|bf16x6]
+
+--impl reference times the FP64 CPU oracle on the host cores (the slow reference program).
+Under torchrun every rank bounds its own batch (weak scaling, no data-path collective)."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG = "mlp784x256"
+ALG_OPS_BASE = 7  # per coordinate and row step of Algorithm 1, besides the argsort comparisons
+
+
+def workload_desc(cfg):
+    d = cfg["dims"]
+    return (f"{CONFIG}: ReLU MLP {d[0]}->{d[1]}x{len(d) - 2}->{d[-1]} He-normal seed 0; box eps={cfg['eps']} around "
+            f"U[0,1]^{d[0]} clipped to [0,1]; B={cfg['B']} subdomains with {cfg['kmin']}-{cfg['kmax']} ReLU split "
+            f"constraints each; 9 margin spec rows; relaxed clipping + complete clipping ({cfg['sweeps']} sweeps) "
+            f"on every still-unstable cached neuron")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16x6"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6], swt=parts[7],
+                                 swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("swp", "sw_power_cap")):
+            if any(r[key].lower().startswith("active") for r in rows):
+                reasons.append(name)
+        return dict(sm_mhz=statistics.median(r["sm"] for r in rows), sm_max_mhz=max(r["smax"] for r in rows),
+                    reasons=reasons, samples=len(rows))
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_sample_rate(cfg, n_sub, seed=1):
+    """Time the FP64 oracle on n_sub subdomains of the workload with all host threads."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2512_11087_gb300 import workloads as WL
+    layers = WL.he_mlp(cfg["dims"], seed=0)
+    net = O.Net(layers)
+    lo0, hi0 = WL.box(cfg["dims"][0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    cache = O.make_cache(O.root_crown(net, lo0, hi0))
+    so, si = WL.draw_splits(cache["ids"], n_sub, cfg["kmin"], cfg["kmax"], seed=seed)
+    lo, hi = WL.tile_box(lo0, hi0, n_sub)
+    C, t = WL.margin_spec(cfg["dims"][-1])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    O.bound_batch(net, cache, lo, hi, split_off=so, split_ids=si, C=C, t=t, relaxed=cfg["relaxed"],
+                  sweeps=cfg["sweeps"], nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n_sub / dt, dt, cores
+
+
+def pick_sample(cfg, budget_s):
+    """Subdomain count whose oracle run takes about budget_s seconds on all host threads."""
+    rate, dt, cores = oracle_sample_rate(cfg, max(1, os.cpu_count() or 1), seed=7)
+    n = int(max(1, min(cfg["B"], rate * budget_s)))
+    return n, cores
+
+
+def run_reference(args, cfg, rank, world):
+    if rank != 0:
+        return
+    n, cores = pick_sample(cfg, 6.0)
+    for _ in range(args.warmup):
+        oracle_sample_rate(cfg, n, seed=11)
+    total_dt, total_n = 0.0, 0
+    for k in range(args.steps):
+        rate, dt, cores = oracle_sample_rate(cfg, n, seed=100 + k)
+        total_dt += dt
+        total_n += n
+    value = total_n / total_dt
+    line = dict(metric="subdomains bounded+clipped per second", value=value, unit="subdomains/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * total_dt / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=workload_desc(cfg), sample=f"{n} subdomains per step"),
+                cpu_baseline=dict(value=value, unit="subdomains/s", cores=cores, kind="oracle",
+                                  sample=f"{n} subdomains of the workload per step, FP64 C oracle, OpenMP"),
+                e2e=dict(value=value, unit="subdomains/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse_args()
+    from paper_2512_11087_gb300 import workloads as WL
+    cfg = WL.CONFIGS[CONFIG]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, cfg, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    dims = cfg["dims"]
+    B, kmin, kmax = cfg["B"], cfg["kmin"], cfg["kmax"]
+    layers = WL.he_mlp(dims, seed=0)
+    lo0, hi0 = WL.box(dims[0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    U = net.build_cache(lo0, hi0)
+    ids = net.read_cache()["ids"]
+    so, si = WL.draw_splits(ids, B, kmin, kmax, seed=1 + rank)
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    C, t = WL.margin_spec(dims[-1])
+    m = C.shape[0]
+    prec = capi.CV_PREC_FP32 if args.precision == "fp32" else capi.CV_PREC_BF16X6
+    rnd = E.Round(net, B, m, max_splits=kmax, relaxed=cfg["relaxed"], sweeps=cfg["sweeps"], precision=prec)
+    timer = capi.cv_timer_create()
+    rnd.opt.timer = timer
+    d = E.to_dev
+    dlo, dhi, dC, dt_, dso, dsi = d(lo), d(hi), d(C), d(t), d(so), d(si)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, phases = [], []
+    launches = steps_cc = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        ph, nl, ncc = capi.cv_timer_read(timer)
+        phases.append(ph)
+        launches += nl
+        steps_cc = ncc
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    total_ms = sum(times)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # end to end through the same C-ABI call with host buffers (pinned), copies inside the timed region
+    hlo, hhi = torch.from_numpy(lo).pin_memory(), torch.from_numpy(hi).pin_memory()
+    hso, hsi = torch.from_numpy(so).pin_memory(), torch.from_numpy(si).pin_memory()
+    hlower = torch.empty(B, m, dtype=torch.float32).pin_memory()
+    hver = torch.empty(B, dtype=torch.uint8).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in (hlo, hhi, hso, hsi))
+    d2h = hlower.numel() * 4 + hver.numel()
+    e2e_ms = 0.0
+    rnd.opt.timer = None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dlo.copy_(hlo, non_blocking=True)
+        dhi.copy_(hhi, non_blocking=True)
+        dso.copy_(hso, non_blocking=True)
+        dsi.copy_(hsi, non_blocking=True)
+        out = rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
+        hlower.copy_(out["lower"], non_blocking=True)
+        hver.copy_(out["verified"], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * B * args.steps / (e2e_ms / 1e3)
+    status = capi.cv_device_status(net.handle)
+
+    # roofline of the dominant kernel (complete clipping, ALU bound)
+    ph_mean = [statistics.mean(p[i] for p in phases) for i in range(capi.N_PHASES)]
+    n0 = dims[0]
+    alg_ops = steps_cc * n0 * (ALG_OPS_BASE + float(np.log2(n0)))
+    achieved = alg_ops / (ph_mean[2] / 1e3) / 1e9  # Gop/s
+    sm_clock = (clk or {}).get("sm_mhz") or 2070.0
+    peak = 152 * 128 * sm_clock / 1e3  # Gop/s: 152 SMs x 128 FP32/INT32 lanes x clock
+    if rank == 0:
+        line = dict(metric="subdomains bounded+clipped per second", value=value, unit="subdomains/s", n_gpus=world,
+                    steps=args.steps, warmup=max(args.warmup, 3), ms_per_step=total_ms / args.steps,
+                    higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                    config=dict(workload=workload_desc(cfg), precision=args.precision, cached_neurons=U,
+                                l2="flushed (256 MiB write) before every timed step",
+                                phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
+                                                  [round(x, 4) for x in ph_mean]))),
+                    roofline=dict(bound="alu", kernel="k_complete", achieved=achieved, peak=peak, unit="Gop/s",
+                                  frac=achieved / peak, traffic=None,
+                                  alg_ops_per_launch=alg_ops, cc_row_steps=steps_cc),
+                    e2e=dict(value=e2e_value, unit="subdomains/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                    gpu_launches=launches, device_status=status, clocks=clk)
+        if world == 1 and not args.no_cpu_baseline:
+            n, cores = pick_sample(cfg, 3.0)
+            rate, dt, cores = oracle_sample_rate(cfg, max(n * 4, 1), seed=21)
+            line["cpu_baseline"] = dict(value=rate, unit="subdomains/s", cores=cores, kind="oracle",
+                                        sample=f"{max(n * 4, 1)} subdomains of the same workload, FP64 C oracle "
+                                               f"({dt:.1f} s on {cores} threads)")
+        print(json.dumps(line), flush=True)
+    capi.cv_timer_destroy(timer)
+    net.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * clipverify.h -- C-ABI of the GB300 (sm_103a) Clip-and-Verify bounding library.
+ *
+ * One call bounds a batch of branch-and-bound subdomains of a ReLU network:
+ * activation-split constraints are turned into input-space rows, the input box is
+ * clipped (relaxed clipping), every cached intermediate bound is re-concretised over
+ * the clipped box and tightened by complete clipping, and the specification is
+ * bounded by CROWN back-substitution.  Method: arXiv 2512.11087 (Sections 3.2-3.4,
+ * Theorems 1-2, Algorithms 1, 2 and 5; CROWN as in its Appendix "Formulations").
+ *
+ * Conventions common to every entry point
+ *  - Status codes are returned, never exceptions; cv_last_error() gives a message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Pointers documented as "device" must point to memory of the current CUDA device;
+ *    "host" pointers are read during the call only.  The library never frees caller
+ *    memory.  Objects created by cv_*_create / cv_*_build are owned by the caller and
+ *    released with the matching cv_*_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Work is enqueued on it; entry points do not synchronise unless stated.
+ *  - All floating-point data is FP32, row-major.  Sizes are element counts.
+ *  - Invalid arguments (NULL where required, negative sizes, unknown enums, sizes that
+ *    do not match the network or cache) return CV_EINVAL / CV_ESHAPE before anything is
+ *    launched.  Problems only a kernel can see (a CSR count above the stated maximum, a
+ *    split id out of range, a non-finite box) set the network's device status word;
+ *    cv_device_status() reads and clears it.
+ *  - Every returned bound is sound: lower bounds are rounded/padded toward -inf and
+ *    upper bounds toward +inf by an a-priori bound of the FP32 rounding error.
+ */
+#ifndef CLIPVERIFY_H
+#define CLIPVERIFY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cv_status;
+#define CV_OK           0
+#define CV_EINVAL       1  /* bad argument */
+#define CV_ESHAPE       2  /* sizes inconsistent with the network / cache */
+#define CV_ENAN         3  /* non-finite value found in an input */
+#define CV_ECUDA        4  /* CUDA runtime error (message in cv_last_error) */
+#define CV_ETIMEOUT     5  /* a bounded device wait ran out */
+#define CV_ENOMEM       6  /* device allocation failed */
+#define CV_EUNSUPPORTED 7  /* feature not available in this build / for this net */
+#define CV_EWORKSPACE   8  /* caller workspace too small */
+#define CV_EDEVICE      9  /* a kernel reported a bad input (see cv_device_status) */
+
+#define CV_MAX_LAYERS 16
+
+/* Layer kinds (every layer except the last is followed by a ReLU). */
+#define CV_LAYER_DENSE  0
+#define CV_LAYER_CONV2D 1
+
+/* Precision of the contractions (re-concretisation and back-substitution). */
+#define CV_PREC_FP32   0  /* CUDA-core FP32 with chunked, compensated accumulation */
+#define CV_PREC_BF16X6 1  /* tensor cores (tcgen05), operands split into three BF16 slices */
+
+/* Lower slope of an unstable ReLU when no per-row alpha is given. */
+#define CV_ALPHA_ADAPTIVE 0  /* alpha = 1 if u >= -l else 0 */
+#define CV_ALPHA_ONE      1
+#define CV_ALPHA_ZERO     2
+
+/* Human-readable message for the last failing call on this thread. */
+const char* cv_last_error(void);
+
+/* ---------------------------------------------------------------- network */
+
+/* One affine layer z = W x + b.
+ *  dense : in_c = fan-in, out_c = fan-out, in_h = in_w = out_h = out_w = 1,
+ *          weight host [out_c x in_c] row-major, bias host [out_c].
+ *  conv2d: input (in_c, in_h, in_w), output (out_c, out_h, out_w), square kernel k,
+ *          stride, zero padding pad; weight host [out_c x in_c x k x k], bias [out_c];
+ *          activations are flattened C,H,W. */
+typedef struct cv_layer_desc {
+    int kind;
+    int in_c, in_h, in_w;
+    int out_c, out_h, out_w;
+    int k, stride, pad;
+    const float* weight;
+    const float* bias;
+} cv_layer_desc;
+
+typedef struct cv_net cv_net;
+
+/* Copies the weights to the current device.  n_layers in [1, CV_MAX_LAYERS]; the
+ * flattened output size of layer i must equal the input size of layer i+1. */
+cv_status cv_net_create(const cv_layer_desc* layers, int n_layers, cv_net** out);
+void      cv_net_destroy(cv_net* net);
+/* dims (host, n_layers+1 entries, may be NULL): flattened widths n_0..n_L.
+ * n_hidden: sum of the hidden widths n_1..n_{L-1} (global hidden ids are 0..n_hidden-1,
+ * layer by layer). */
+cv_status cv_net_dims(const cv_net* net, int* n_layers, int* dims, int* n_hidden);
+/* Synchronises `stream`, returns CV_OK or CV_EDEVICE if a kernel flagged a bad input
+ * since the last call, and clears the flag.  `code` (may be NULL) receives the raw
+ * device status word (bit 0: CSR count above the stated maximum, bit 1: split id out
+ * of range, bit 2: non-finite box, bit 3: target slot out of range). */
+cv_status cv_device_status(cv_net* net, void* stream, int* code);
+
+/* ---------------------------------------------------------------- root cache */
+
+/* Root bounds and planes (Get_Constraints of Algorithm 5; Section 3.4 "cache and
+ * reuse"): the CROWN lower/upper planes of every hidden neuron over the root box,
+ * and the cache of the root-unstable ones (slots in increasing global id). */
+typedef struct cv_cache cv_cache;
+
+/* Runs CROWN on the GPU over the root box [root_lo, root_hi] (device, [n_0] each).
+ * alpha_mode: CV_ALPHA_*.  The planes are padded by their rounding bound so that
+ * they are valid over the root box.  Synchronises `stream` (it returns U). */
+cv_status cv_cache_build(cv_net* net, const float* root_lo, const float* root_hi,
+                         int alpha_mode, cv_cache** out, void* stream);
+
+/* Builds a cache from caller-supplied planes (all host):
+ *   root_lo, root_hi [n_0]; root_l, root_u [n_hidden] (bounds of every hidden neuron);
+ *   U cached neurons with global ids ids[U] (strictly increasing), lower planes
+ *   lA [U x n_0], lc [U] and upper planes uA [U x n_0], uc [U].  The planes are
+ *   taken as valid over the root box as given. */
+cv_status cv_cache_create(cv_net* net, const float* root_lo, const float* root_hi,
+                          const float* root_l, const float* root_u, int U, const int* ids,
+                          const float* lA, const float* lc, const float* uA, const float* uc,
+                          cv_cache** out);
+
+/* Number of cached (root-unstable) neurons. */
+cv_status cv_cache_size(const cv_cache* cache, int* U);
+
+/* Copies the cache to host buffers (any may be NULL): ids [U], lA/uA [U x n_0],
+ * lc/uc [U], root_l/root_u [n_hidden].  Synchronous. */
+cv_status cv_cache_read(const cv_cache* cache, int* ids, float* lA, float* lc,
+                        float* uA, float* uc, float* root_l, float* root_u);
+void      cv_cache_destroy(cv_cache* cache);
+
+/* ---------------------------------------------------------------- phase timing */
+
+/* Optional per-call instrumentation of cv_bound_batch (not part of the method).  When
+ * cv_options.timer is set, the call records CUDA events on its stream at the phase
+ * boundaries and counts its kernel launches and the coordinate-ascent row steps complete
+ * clipping executes (one atomic add per thread block).  Phases:
+ *   0 rows, pre-check and relaxed clipping   1 re-concretisation
+ *   2 complete clipping                      3 back-substitution and verified flags */
+#define CV_N_PHASES 4
+typedef struct cv_timer cv_timer;
+cv_status cv_timer_create(cv_timer** out);
+void      cv_timer_destroy(cv_timer* timer);
+/* Waits for the last timed call; ms[CV_N_PHASES] (may be NULL) receives its per-phase device
+ * time in milliseconds, launches (may be NULL) its kernel launch count, cc_steps (may be NULL)
+ * the row steps of Algorithm 1 it executed. */
+cv_status cv_timer_read(cv_timer* timer, float* ms, int* launches, long long* cc_steps);
+
+/* ---------------------------------------------------------------- one BaB round */
+
+typedef struct cv_options {
+    int relaxed;        /* 1: relaxed clipping of the input box (Theorem 2, Algorithm 2) */
+    int sweeps;         /* complete clipping passes of Algorithm 1 (0: off) */
+    int precision;      /* CV_PREC_* */
+    int alpha_mode;     /* CV_ALPHA_*; ignored where batch.alpha is given */
+    int enforce_splits; /* 1: clamp split neurons to their side (standard activation BaB) */
+    cv_timer* timer;    /* optional phase timing (NULL: none) */
+} cv_options;
+
+/* relaxed = 1, sweeps = 0, precision = CV_PREC_FP32, alpha_mode = CV_ALPHA_ADAPTIVE,
+ * enforce_splits = 1, timer = NULL. */
+void cv_options_default(cv_options* opt);
+
+/* Inputs of one round for B subdomains (all device pointers unless noted).
+ *  lo, hi        [B x n_0]  input box of every subdomain
+ *  l_in, u_in    [B x U]    inherited bounds of the cached neurons; NULL = root bounds
+ *  split_off     [B+1]      CSR offsets into split_ids; NULL = no splits
+ *  split_ids     [nnz]      +(g+1): split z_g >= 0, -(g+1): z_g <= 0, g a global hidden id
+ *  max_splits    (host)     upper bound on any subdomain's split count
+ *  row_off       [B+1]      CSR offsets of extra rows G x + h <= 0; NULL = none
+ *  G, h          [R x n_0], [R]
+ *  max_rows      (host)     upper bound on any subdomain's extra-row count
+ *  m, C, t       spec rows [m x n_L], thresholds [m]: bound f_r = C_r y + t_r
+ *  alpha         [B x m x n_hidden] lower slopes per subdomain, spec row and neuron; NULL =
+ *                alpha_mode
+ *  tgt_off, tgt_ids  CSR over cache slots: complete-clipping targets per subdomain; NULL =
+ *                every cached neuron still unstable after re-concretisation */
+typedef struct cv_batch_in {
+    int B;
+    const float* lo;
+    const float* hi;
+    const float* l_in;
+    const float* u_in;
+    const int* split_off;
+    const int* split_ids;
+    int max_splits;
+    const int* row_off;
+    const float* G;
+    const float* h;
+    int max_rows;
+    int m;
+    const float* C;
+    const float* t;
+    const float* alpha;
+    const int* tgt_off;
+    const int* tgt_ids;
+} cv_batch_in;
+
+/* Outputs (device, caller-allocated; optional ones may be NULL).
+ *  lower      [B x m]      sound lower bound of every spec row (+inf if infeasible)
+ *  lo_clip, hi_clip [B x n_0]  clipped box (rounded outward)
+ *  l, u       [B x U]      tightened bounds of the cached neurons
+ *  mask       [B x U]      +1 active, -1 inactive, 0 unstable
+ *  infeasible [B], verified [B]  0/1; an infeasible subdomain counts as verified
+ *  err_bound  [B x m]      optional: the outward pad included in lower
+ *  final_A    [B x m x n_0], final_c [B x m]  optional: the final linear bound
+ *             f_r >= final_A_r . x + final_c_r on the clipped box (final_c includes the
+ *             pad), e.g. for reuse as output constraints in input BaB (Section 3.3). */
+typedef struct cv_batch_out {
+    float* lower;
+    float* lo_clip;
+    float* hi_clip;
+    float* l;
+    float* u;
+    int8_t* mask;
+    uint8_t* infeasible;
+    uint8_t* verified;
+    float* err_bound;
+    float* final_A;
+    float* final_c;
+} cv_batch_out;
+
+/* Bytes of device workspace cv_bound_batch needs for these sizes (in->B, in->m,
+ * in->max_splits, in->max_rows; device pointers in `in` are not read). */
+cv_status cv_bound_batch_workspace(const cv_net* net, const cv_cache* cache,
+                                   const cv_batch_in* in, const cv_options* opt,
+                                   size_t* bytes);
+
+/* One round: constraint rows from splits and extra rows, pre-check, relaxed clipping,
+ * re-concretisation, complete clipping, back-substitution of the spec, verified flags.
+ * workspace: device memory of at least cv_bound_batch_workspace() bytes, 256-byte
+ * aligned, used only during the call's kernels (stream-ordered). */
+cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                         cv_batch_out* out, const cv_options* opt,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLIPVERIFY_H */

@@ -1,0 +1,266 @@
+"""Thin Python binding of libclipverify.so (the C-ABI in include/clipverify.h).
+
+Functions carry the C names and only marshal arguments: torch CUDA tensors become device
+pointers, numpy arrays become host pointers, None becomes NULL, and a non-OK status raises
+CVError with the library's message.  PyTorch is used only for device memory and streams.
+There is no fallback: if the library is missing every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libclipverify.so")
+
+CV_OK = 0
+CV_LAYER_DENSE = 0
+CV_LAYER_CONV2D = 1
+CV_PREC_FP32 = 0
+CV_PREC_BF16X6 = 1
+CV_ALPHA_ADAPTIVE = 0
+CV_ALPHA_ONE = 1
+CV_ALPHA_ZERO = 2
+STATUS_NAMES = {0: "CV_OK", 1: "CV_EINVAL", 2: "CV_ESHAPE", 3: "CV_ENAN", 4: "CV_ECUDA", 5: "CV_ETIMEOUT",
+                6: "CV_ENOMEM", 7: "CV_EUNSUPPORTED", 8: "CV_EWORKSPACE", 9: "CV_EDEVICE"}
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+
+
+class CVError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class cv_layer_desc(ctypes.Structure):
+    _fields_ = [("kind", I), ("in_c", I), ("in_h", I), ("in_w", I), ("out_c", I), ("out_h", I), ("out_w", I),
+                ("k", I), ("stride", I), ("pad", I), ("weight", P), ("bias", P)]
+
+
+class cv_options(ctypes.Structure):
+    _fields_ = [("relaxed", I), ("sweeps", I), ("precision", I), ("alpha_mode", I), ("enforce_splits", I),
+                ("timer", P)]
+
+
+class cv_batch_in(ctypes.Structure):
+    _fields_ = [("B", I), ("lo", P), ("hi", P), ("l_in", P), ("u_in", P), ("split_off", P), ("split_ids", P),
+                ("max_splits", I), ("row_off", P), ("G", P), ("h", P), ("max_rows", I), ("m", I), ("C", P),
+                ("t", P), ("alpha", P), ("tgt_off", P), ("tgt_ids", P)]
+
+
+class cv_batch_out(ctypes.Structure):
+    _fields_ = [("lower", P), ("lo_clip", P), ("hi_clip", P), ("l", P), ("u", P), ("mask", P),
+                ("infeasible", P), ("verified", P), ("err_bound", P), ("final_A", P), ("final_c", P)]
+
+
+_lib = None
+
+
+def load():
+    """The loaded library; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libclipverify.so not found at {LIB_PATH}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    sigs = {
+        "cv_last_error": ([], ctypes.c_char_p),
+        "cv_net_create": ([P, I, ctypes.POINTER(P)], I),
+        "cv_net_destroy": ([P], None),
+        "cv_net_dims": ([P, P, P, P], I),
+        "cv_device_status": ([P, P, P], I),
+        "cv_cache_build": ([P, P, P, I, ctypes.POINTER(P), P], I),
+        "cv_cache_create": ([P, P, P, P, P, I, P, P, P, P, P, ctypes.POINTER(P)], I),
+        "cv_cache_size": ([P, P], I),
+        "cv_cache_read": ([P, P, P, P, P, P, P, P], I),
+        "cv_cache_destroy": ([P], None),
+        "cv_options_default": ([P], None),
+        "cv_bound_batch_workspace": ([P, P, P, P, P], I),
+        "cv_bound_batch": ([P, P, P, P, P, P, ctypes.c_size_t, P], I),
+        "cv_timer_create": ([ctypes.POINTER(P)], I),
+        "cv_timer_destroy": ([P], None),
+        "cv_timer_read": ([P, P, P, P], I),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return [n for n in ("cv_last_error", "cv_net_create", "cv_net_destroy", "cv_net_dims", "cv_device_status",
+                        "cv_cache_build", "cv_cache_create", "cv_cache_size", "cv_cache_read", "cv_cache_destroy",
+                        "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
+                        "cv_timer_destroy", "cv_timer_read")]
+
+
+def _check(st):
+    if st != CV_OK:
+        raise CVError(st, load().cv_last_error().decode(errors="replace"))
+
+
+def ptr(x):
+    """Device pointer of a torch tensor, host pointer of a numpy array, NULL for None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(P)
+    return P(x.data_ptr())
+
+
+def stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return P(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- entry points
+def cv_net_create(layers):
+    """layers: list of dicts from workloads.he_mlp / he_cnn (numpy float32 weights)."""
+    lib = load()
+    descs = (cv_layer_desc * len(layers))()
+    keep = []
+    for i, ly in enumerate(layers):
+        W = np.ascontiguousarray(ly["W"], np.float32)
+        b = np.ascontiguousarray(ly["b"], np.float32)
+        keep += [W, b]
+        d = descs[i]
+        d.kind = ly["kind"]
+        if ly["kind"] == CV_LAYER_DENSE:
+            d.in_c, d.out_c = W.shape[1], W.shape[0]
+            d.in_h = d.in_w = d.out_h = d.out_w = 1
+        else:
+            d.in_c, d.in_h, d.in_w = ly["in_shape"]
+            d.out_c, d.out_h, d.out_w = ly["out_shape"]
+            d.k, d.stride, d.pad = W.shape[2], ly["stride"], ly["pad"]
+        d.weight = W.ctypes.data_as(P)
+        d.bias = b.ctypes.data_as(P)
+    h = P()
+    _check(lib.cv_net_create(ctypes.cast(descs, P), len(layers), ctypes.byref(h)))
+    return h
+
+
+def cv_net_destroy(h):
+    load().cv_net_destroy(h)
+
+
+def cv_net_dims(h):
+    lib = load()
+    L = ctypes.c_int()
+    _check(lib.cv_net_dims(h, ctypes.byref(L), None, None))
+    dims = (ctypes.c_int * (L.value + 1))()
+    H = ctypes.c_int()
+    _check(lib.cv_net_dims(h, None, ctypes.cast(dims, P), ctypes.byref(H)))
+    return list(dims), H.value
+
+
+def cv_device_status(h, stream=None):
+    code = ctypes.c_int()
+    _check(load().cv_device_status(h, stream_ptr(stream), ctypes.byref(code)))
+    return code.value
+
+
+def cv_cache_build(net, root_lo, root_hi, alpha_mode=CV_ALPHA_ADAPTIVE, stream=None):
+    h = P()
+    _check(load().cv_cache_build(net, ptr(root_lo), ptr(root_hi), int(alpha_mode), ctypes.byref(h),
+                                 stream_ptr(stream)))
+    return h
+
+
+def cv_cache_create(net, root_lo, root_hi, root_l, root_u, ids, lA, lc, uA, uc):
+    """All host numpy arrays (float32 / int32)."""
+    arrs = [np.ascontiguousarray(a, np.float32) for a in (root_lo, root_hi, root_l, root_u)]
+    ids = np.ascontiguousarray(ids, np.int32)
+    planes = [np.ascontiguousarray(a, np.float32) for a in (lA, lc, uA, uc)]
+    h = P()
+    _check(load().cv_cache_create(net, *[ptr(a) for a in arrs], int(ids.size), ptr(ids),
+                                  *[ptr(a) for a in planes], ctypes.byref(h)))
+    return h
+
+
+def cv_cache_size(cache):
+    U = ctypes.c_int()
+    _check(load().cv_cache_size(cache, ctypes.byref(U)))
+    return U.value
+
+
+def cv_cache_read(cache, n0, H):
+    U = cv_cache_size(cache)
+    out = dict(ids=np.zeros(U, np.int32), lA=np.zeros((U, n0), np.float32), lc=np.zeros(U, np.float32),
+               uA=np.zeros((U, n0), np.float32), uc=np.zeros(U, np.float32), root_l=np.zeros(H, np.float32),
+               root_u=np.zeros(H, np.float32))
+    _check(load().cv_cache_read(cache, *[ptr(out[k]) if out[k].size else None
+                                         for k in ("ids", "lA", "lc", "uA", "uc", "root_l", "root_u")]))
+    return out
+
+
+def cv_cache_destroy(cache):
+    load().cv_cache_destroy(cache)
+
+
+def cv_options_default():
+    o = cv_options()
+    load().cv_options_default(ctypes.byref(o))
+    return o
+
+
+def make_batch_in(B, lo, hi, m, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, max_splits=0,
+                  row_off=None, G=None, h=None, max_rows=0, alpha=None, tgt_off=None, tgt_ids=None):
+    bi = cv_batch_in()
+    bi.B, bi.m, bi.max_splits, bi.max_rows = int(B), int(m), int(max_splits), int(max_rows)
+    for name, v in dict(lo=lo, hi=hi, l_in=l_in, u_in=u_in, split_off=split_off, split_ids=split_ids,
+                        row_off=row_off, G=G, h=h, C=C, t=t, alpha=alpha, tgt_off=tgt_off,
+                        tgt_ids=tgt_ids).items():
+        setattr(bi, name, ptr(v))
+    return bi
+
+
+def make_batch_out(lower, lo_clip, hi_clip, l, u, mask, infeasible, verified, err_bound=None, final_A=None,
+                   final_c=None):
+    bo = cv_batch_out()
+    for name, v in dict(lower=lower, lo_clip=lo_clip, hi_clip=hi_clip, l=l, u=u, mask=mask,
+                        infeasible=infeasible, verified=verified, err_bound=err_bound, final_A=final_A,
+                        final_c=final_c).items():
+        setattr(bo, name, ptr(v))
+    return bo
+
+
+def cv_bound_batch_workspace(net, cache, bi, opt):
+    n = ctypes.c_size_t()
+    _check(load().cv_bound_batch_workspace(net, cache, ctypes.byref(bi), ctypes.byref(opt), ctypes.byref(n)))
+    return n.value
+
+
+def cv_bound_batch(net, cache, bi, bo, opt, workspace, workspace_bytes, stream=None):
+    _check(load().cv_bound_batch(net, cache, ctypes.byref(bi), ctypes.byref(bo), ctypes.byref(opt),
+                                 ptr(workspace), int(workspace_bytes), stream_ptr(stream)))
+
+
+N_PHASES = 4
+
+
+def cv_timer_create():
+    h = P()
+    _check(load().cv_timer_create(ctypes.byref(h)))
+    return h
+
+
+def cv_timer_destroy(t):
+    load().cv_timer_destroy(t)
+
+
+def cv_timer_read(t):
+    """(per-phase ms list, kernel launches, complete-clipping row steps) of the last timed call."""
+    ms = (ctypes.c_float * N_PHASES)()
+    n = ctypes.c_int()
+    steps = ctypes.c_longlong()
+    _check(load().cv_timer_read(t, ctypes.cast(ms, P), ctypes.byref(n), ctypes.byref(steps)))
+    return list(ms), n.value, steps.value

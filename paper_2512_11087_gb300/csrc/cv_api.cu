@@ -1,0 +1,207 @@
+// C-ABI entry points of one bounding round (cv_bound_batch and its helpers): argument
+// validation, workspace layout, and the launch sequence a2..a8 on the caller's stream.
+#include "cv_internal.cuh"
+
+#include <string.h>
+
+#include <string>
+
+
+static thread_local std::string g_err;
+
+void cv_set_error(const std::string& msg) { g_err = msg; }
+
+cv_status cv_cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? CV_ENOMEM : CV_ECUDA;
+}
+
+extern "C" const char* cv_last_error(void) { return g_err.c_str(); }
+
+extern "C" void cv_options_default(cv_options* o) {
+    if (!o) return;
+    o->relaxed = 1;
+    o->sweeps = 0;
+    o->precision = CV_PREC_FP32;
+    o->alpha_mode = CV_ALPHA_ADAPTIVE;
+    o->enforce_splits = 1;
+    o->timer = nullptr;
+}
+
+cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
+                     int max_rows, cv_ws_layout* lay) {
+    memset(lay, 0, sizeof(*lay));
+    lay->Rmax = max_splits + max_rows;
+    lay->R = B * m;
+    lay->ncb = cv_bwd_ncb_max(net);
+    const size_t R = (size_t)lay->R, Rm = (size_t)B * lay->Rmax, ncb = lay->ncb;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = cv_align256(off + (bytes ? bytes : 1)); return o; };
+    lay->rowflag = take(Rm);
+    lay->vmin = take(Rm * sizeof(double));
+    lay->rowdesc = take((size_t)2 * (cache->U > 0 ? cache->U : 1) * sizeof(float));
+    lay->lam0 = take(R * net->wmax * sizeof(float));
+    lay->lam1 = take(R * net->wmax * sizeof(float));
+    lay->part_bias = take(R * ncb * sizeof(double));
+    lay->part_pad = take(R * ncb * sizeof(double));
+    lay->part_f = take(R * ncb * sizeof(double));
+    lay->part_fmag = take(R * ncb * sizeof(double));
+    lay->acc_bias = take(R * sizeof(double));
+    lay->acc_pad = take(R * sizeof(double));
+    lay->total = off;
+    return CV_OK;
+}
+
+static cv_status validate(const cv_net* net, const cv_cache* cache, const cv_batch_in* in, const cv_options* opt,
+                          bool pointers = true) {
+    if (!net || !cache || !in || !opt) { cv_set_error("null net / cache / input / options"); return CV_EINVAL; }
+    if (cache->net != net) { cv_set_error("cache was built for another network"); return CV_EINVAL; }
+    if (in->B < 0 || in->m < 0 || in->max_splits < 0 || in->max_rows < 0) {
+        cv_set_error("negative B, m, max_splits or max_rows");
+        return CV_EINVAL;
+    }
+    if (opt->sweeps < 0 || opt->alpha_mode < 0 || opt->alpha_mode > 2 ||
+        (opt->precision != CV_PREC_FP32 && opt->precision != CV_PREC_BF16X6)) {
+        cv_set_error("bad options");
+        return CV_EINVAL;
+    }
+    if (!pointers) return CV_OK;
+    if (in->B > 0 && (!in->lo || !in->hi)) { cv_set_error("lo/hi required"); return CV_EINVAL; }
+    if (in->m > 0 && !in->C) { cv_set_error("C required when m > 0"); return CV_EINVAL; }
+    if ((in->split_off == nullptr) != (in->split_ids == nullptr)) { cv_set_error("split_off and split_ids go together"); return CV_EINVAL; }
+    if (in->row_off && (!in->G || !in->h)) { cv_set_error("row_off needs G and h"); return CV_EINVAL; }
+    if ((in->tgt_off == nullptr) != (in->tgt_ids == nullptr)) { cv_set_error("tgt_off and tgt_ids go together"); return CV_EINVAL; }
+    if ((in->l_in == nullptr) != (in->u_in == nullptr)) { cv_set_error("l_in and u_in go together"); return CV_EINVAL; }
+    if (!in->split_off && in->max_splits > 0) { cv_set_error("max_splits > 0 without splits"); return CV_EINVAL; }
+    if (!in->row_off && in->max_rows > 0) { cv_set_error("max_rows > 0 without rows"); return CV_EINVAL; }
+    return CV_OK;
+}
+
+extern "C" cv_status cv_bound_batch_workspace(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                                              const cv_options* opt, size_t* bytes) {
+    cv_status s = validate(net, cache, in, opt, false);
+    if (s) return s;
+    if (!bytes) { cv_set_error("null bytes"); return CV_EINVAL; }
+    cv_ws_layout lay;
+    cv_ws_plan(net, cache, in->B, in->m, in->max_splits, in->max_rows, &lay);
+    *bytes = lay.total;
+    return CV_OK;
+}
+
+namespace {
+__global__ void k_verified(int B, int m, const float* lower, const uint8_t* infeasible, uint8_t* verified) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    bool v = infeasible[b] != 0;
+    if (!v) {
+        v = true;
+        for (int r = 0; r < m; ++r) v = v && (lower[(size_t)b * m + r] > 0.f);
+    }
+    verified[b] = v ? 1 : 0;
+}
+}  // namespace
+
+extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                                    const cv_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
+    cv_status s = validate(net, cache, in, opt);
+    if (s) return s;
+    if (!out) { cv_set_error("null output"); return CV_EINVAL; }
+    const int B = in->B, m = in->m, U = cache->U;
+    if (B == 0) return CV_OK;
+    if (!out->lo_clip || !out->hi_clip || !out->infeasible || !out->verified || (m > 0 && !out->lower) ||
+        (U > 0 && (!out->l || !out->u || !out->mask))) {
+        cv_set_error("required output pointer is null");
+        return CV_EINVAL;
+    }
+    if (opt->precision != CV_PREC_FP32) {
+        cv_set_error("this build implements precision CV_PREC_FP32 only");
+        return CV_EUNSUPPORTED;
+    }
+    cv_ws_layout lay;
+    cv_ws_plan(net, cache, B, m, in->max_splits, in->max_rows, &lay);
+    if (!workspace || workspace_bytes < lay.total) {
+        cv_set_error("workspace too small: need " + std::to_string(lay.total) + " bytes");
+        return CV_EWORKSPACE;
+    }
+    if (((uintptr_t)workspace & 255) != 0) { cv_set_error("workspace must be 256-byte aligned"); return CV_EINVAL; }
+    char* ws = (char*)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    cv_timer* tm = opt->timer;
+    int launches = 0;
+    unsigned long long* steps = nullptr;
+    if (tm) {
+        CV_CUDA(cudaMemsetAsync(tm->d_steps, 0, sizeof(unsigned long long), st));
+        CV_CUDA(cudaEventRecord(tm->ev[0], st));
+        steps = tm->d_steps;
+    }
+
+    CV_CUDA(cudaMemsetAsync(out->infeasible, 0, B, st));
+    if ((s = cv_launch_rows(net, cache, in, &lay, ws, out->infeasible, st))) return s;
+    launches += lay.Rmax > 0;
+    if ((s = cv_launch_relaxed(net, cache, in, opt, &lay, ws, out->lo_clip, out->hi_clip, out->infeasible, st))) return s;
+    launches += 1;
+    if (tm) CV_CUDA(cudaEventRecord(tm->ev[1], st));
+    if ((s = cv_launch_reconc(net, cache, in, opt, &lay, ws, out->lo_clip, out->hi_clip, out->l, out->u, out->mask,
+                              out->infeasible, st)))
+        return s;
+    launches += U > 0 ? 3 : 0;
+    if (tm) CV_CUDA(cudaEventRecord(tm->ev[2], st));
+    if ((s = cv_launch_complete(net, cache, in, opt, &lay, ws, out->lo_clip, out->hi_clip, out->l, out->u, out->mask,
+                                out->infeasible, steps, &launches, st)))
+        return s;
+    if (tm) CV_CUDA(cudaEventRecord(tm->ev[3], st));
+    if (m > 0) {
+        s = cv_backward_raw(net, lay.R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
+                            cache->root_state, cache->slot_of, out->l, out->u, out->mask, U, in->alpha,
+                            opt->alpha_mode, cache->V, out->lo_clip, out->hi_clip, out->infeasible, out->lower,
+                            out->err_bound, out->final_A, out->final_c, nullptr, nullptr,
+                            (float*)(ws + lay.lam0), (float*)(ws + lay.lam1), (double*)(ws + lay.part_bias),
+                            (double*)(ws + lay.part_pad), (double*)(ws + lay.part_f),
+                            (double*)(ws + lay.part_fmag), (double*)(ws + lay.acc_bias),
+                            (double*)(ws + lay.acc_pad), st);
+        if (s) return s;
+        launches += 1 + 2 * net->L;
+    }
+    k_verified<<<(B + 255) / 256, 256, 0, st>>>(B, m, out->lower, out->infeasible, out->verified);
+    CV_LAUNCH_CHECK("k_verified");
+    launches += 1;
+    if (tm) {
+        CV_CUDA(cudaEventRecord(tm->ev[4], st));
+        tm->launches = launches;
+        tm->used = true;
+    }
+    return CV_OK;
+}
+
+extern "C" cv_status cv_timer_create(cv_timer** out) {
+    if (!out) { cv_set_error("cv_timer_create: null"); return CV_EINVAL; }
+    cv_timer* t = new cv_timer();
+    memset(t, 0, sizeof(*t));
+    for (int i = 0; i <= CV_N_PHASES; ++i) CV_CUDA(cudaEventCreate(&t->ev[i]));
+    CV_CUDA(cudaMalloc(&t->d_steps, sizeof(unsigned long long)));
+    CV_CUDA(cudaMemset(t->d_steps, 0, sizeof(unsigned long long)));
+    *out = t;
+    return CV_OK;
+}
+
+extern "C" void cv_timer_destroy(cv_timer* t) {
+    if (!t) return;
+    for (int i = 0; i <= CV_N_PHASES; ++i) cudaEventDestroy(t->ev[i]);
+    cudaFree(t->d_steps);
+    delete t;
+}
+
+extern "C" cv_status cv_timer_read(cv_timer* t, float* ms, int* launches, long long* cc_steps) {
+    if (!t) { cv_set_error("cv_timer_read: null"); return CV_EINVAL; }
+    if (!t->used) { cv_set_error("cv_timer_read: no timed call yet"); return CV_EINVAL; }
+    CV_CUDA(cudaEventSynchronize(t->ev[CV_N_PHASES]));
+    if (ms)
+        for (int i = 0; i < CV_N_PHASES; ++i) CV_CUDA(cudaEventElapsedTime(&ms[i], t->ev[i], t->ev[i + 1]));
+    if (launches) *launches = t->launches;
+    if (cc_steps) {
+        unsigned long long v = 0;
+        CV_CUDA(cudaMemcpy(&v, t->d_steps, sizeof(v), cudaMemcpyDeviceToHost));
+        *cc_steps = (long long)v;
+    }
+    return CV_OK;
+}

@@ -1,0 +1,126 @@
+// Internal declarations of the Clip-and-Verify GB300 library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/clipverify.h"
+
+// ---------------------------------------------------------------- error plumbing
+void cv_set_error(const std::string& msg);
+cv_status cv_cuda_fail(cudaError_t e, const char* what);
+
+#define CV_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cv_cuda_fail(e_, #call);          \
+    } while (0)
+
+#define CV_LAUNCH_CHECK(what)                                           \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return cv_cuda_fail(e_, what);           \
+    } while (0)
+
+// device status bits (cv_device_status)
+#define CV_DEV_CSR_COUNT   1
+#define CV_DEV_SPLIT_RANGE 2
+#define CV_DEV_NONFINITE   4
+#define CV_DEV_TARGET      8
+
+// unit roundoff of FP32 round-to-nearest (with a small safety factor)
+#define CV_U32 (5.9604644775390625e-08 * 1.0001)
+
+// ---------------------------------------------------------------- objects
+struct cv_net {
+    int L;                       // affine layers
+    int dims[CV_MAX_LAYERS + 1]; // flattened widths
+    int hoff[CV_MAX_LAYERS + 1]; // first global hidden id of hidden layer i (1..L-1)
+    int H;                       // hidden neurons
+    int wmax;                    // max width
+    float* W[CV_MAX_LAYERS + 1]; // device, W[i]: dims[i] x dims[i-1] row-major (i = 1..L)
+    float* b[CV_MAX_LAYERS + 1]; // device, b[i]: dims[i]
+    int* status;                 // device status word
+    int device;
+};
+
+struct cv_cache {
+    const cv_net* net;
+    int U, n0, H;
+    int* ids;          // [U] global hidden ids
+    int* slot_of;      // [H] cache slot or -1
+    float* lA;         // [U x n0]
+    float* lc;         // [U]
+    float* uA;         // [U x n0]
+    float* uc;         // [U]
+    float* PC;         // [2U x 2n0]: row c < U: [A̲⁺_c | A̲⁻_c]; row U+c: [Ā⁻_c | Ā⁺_c]
+    float* PCc;        // [2U]: lc, uc
+    float* pscale;     // [2U]: |A|.xmag_root + |c| of the lower / upper plane
+    float* root_l;     // [H]
+    float* root_u;     // [H]
+    int8_t* root_state;// [H] +1 / -1 / 0
+    float* V[CV_MAX_LAYERS + 1]; // V[i] [dims[i]]: |W^(i)| zmag^(i-1) + |b^(i)| (pad weights)
+    float* root_lo;    // [n0]
+    float* root_hi;    // [n0]
+};
+
+struct cv_timer {
+    cudaEvent_t ev[CV_N_PHASES + 1];
+    unsigned long long* d_steps;  // device counter of complete-clipping row steps
+    int launches;
+    bool used;
+};
+
+// ---------------------------------------------------------------- helpers shared by kernels
+__host__ __device__ inline size_t cv_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// workspace carving: returns the offset of the next 256-aligned block
+struct cv_ws_layout {
+    size_t rowflag, vmin, lam0, lam1, part_bias, part_pad, part_f, part_fmag, acc_bias, acc_pad, rowdesc, total;
+    int R, Rmax, ncb;  // rows of the spec backward, max constraint rows, column blocks
+};
+cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
+                     int max_rows, cv_ws_layout* lay);
+
+// kernels (launch wrappers); each returns CV_OK or a launch error
+cv_status cv_launch_rows(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                         const cv_ws_layout* lay, char* ws, uint8_t* infeasible, cudaStream_t st);
+cv_status cv_launch_relaxed(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                            const cv_options* opt, const cv_ws_layout* lay, char* ws,
+                            float* lo_clip, float* hi_clip, uint8_t* infeasible, cudaStream_t st);
+cv_status cv_launch_reconc(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                           const cv_options* opt, const cv_ws_layout* lay, char* ws,
+                           const float* lo_clip, const float* hi_clip, float* l, float* u,
+                           int8_t* mask, uint8_t* infeasible, cudaStream_t st);
+cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                             const cv_options* opt, const cv_ws_layout* lay, char* ws,
+                             const float* lo_clip, const float* hi_clip, float* l, float* u,
+                             int8_t* mask, uint8_t* infeasible, unsigned long long* step_counter,
+                             int* launches, cudaStream_t st);
+cv_status cv_launch_spec_backward(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                                  const cv_options* opt, const cv_ws_layout* lay, char* ws,
+                                  const float* lo_clip, const float* hi_clip, const float* l,
+                                  const float* u, const int8_t* mask, const uint8_t* infeasible,
+                                  cv_batch_out* out, cudaStream_t st);
+
+// Back-substitution of R rows (cv_backward.cu).  Row r belongs to subdomain r / rows_per_sub.
+// Start layer k with Lam^(k): init_mode 0 explicit lam_init [R x n_k], 1 spec rows C[r % m]
+// (bias t[r % m]), 2 stacked +/- identity (row r -> +e_{r % n_k} for r < n_k, else -e).
+// Relaxation of hidden neuron g: per-subdomain (l, u, mask)[sub * U + slot_of[g]] when slot_of
+// and l are given and the neuron is cached, else the root arrays.  Outputs (all optional):
+// lower (rounded down), err (pad), lam0 [R x n0], bias_out (bias - pad, rounded down),
+// bias_raw / pad_raw (FP64).  lamA/lamB [R x wmax] and the partial buffers are scratch.
+cv_status cv_backward_raw(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
+                          const float* lam_init, const float* C, const float* t,
+                          const float* root_l, const float* root_u, const int8_t* root_state,
+                          const int* slot_of, const float* l, const float* u, const int8_t* mask,
+                          int U, const float* alpha, int alpha_mode, float* const* V,
+                          const float* lo, const float* hi, const uint8_t* skip,
+                          float* lower, float* err, float* lam0, float* bias_out,
+                          double* bias_raw, double* pad_raw,
+                          float* lamA, float* lamB, double* part_bias, double* part_pad,
+                          double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
+                          cudaStream_t st);
+int cv_bwd_ncb_max(const cv_net* net);
+

@@ -1,0 +1,103 @@
+"""Device-memory plumbing around the C-ABI: allocates a round's outputs and workspace with
+torch and calls cv_bound_batch.  Every step of the round runs in the library's kernels."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def to_dev(x, dtype=None, device="cuda"):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype or x.dtype).contiguous()
+    a = np.ascontiguousarray(x)
+    t = torch.from_numpy(a)
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(device).contiguous()
+
+
+class Net:
+    """A network on the device (cv_net) plus its root cache (cv_cache)."""
+
+    def __init__(self, layers):
+        self.handle = capi.cv_net_create(layers)
+        self.dims, self.H = capi.cv_net_dims(self.handle)
+        self.n0, self.nL = self.dims[0], self.dims[-1]
+        self.cache = None
+        self.U = 0
+
+    def build_cache(self, root_lo, root_hi, alpha_mode=capi.CV_ALPHA_ADAPTIVE):
+        lo = to_dev(root_lo, torch.float32)
+        hi = to_dev(root_hi, torch.float32)
+        self._drop_cache()
+        self.cache = capi.cv_cache_build(self.handle, lo, hi, alpha_mode)
+        self.U = capi.cv_cache_size(self.cache)
+        return self.U
+
+    def set_cache(self, root_lo, root_hi, root_l, root_u, ids, lA, lc, uA, uc):
+        self._drop_cache()
+        self.cache = capi.cv_cache_create(self.handle, root_lo, root_hi, root_l, root_u, ids, lA, lc, uA, uc)
+        self.U = capi.cv_cache_size(self.cache)
+        return self.U
+
+    def read_cache(self):
+        return capi.cv_cache_read(self.cache, self.n0, self.H)
+
+    def _drop_cache(self):
+        if self.cache is not None:
+            capi.cv_cache_destroy(self.cache)
+            self.cache = None
+
+    def close(self):
+        self._drop_cache()
+        if self.handle is not None:
+            capi.cv_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Round:
+    """Outputs and workspace for rounds of B subdomains with m spec rows."""
+
+    def __init__(self, net: Net, B, m, max_splits=0, max_rows=0, relaxed=1, sweeps=0,
+                 precision=capi.CV_PREC_FP32, alpha_mode=capi.CV_ALPHA_ADAPTIVE, enforce_splits=1,
+                 want_final=False, device="cuda"):
+        self.net, self.B, self.m = net, B, m
+        self.max_splits, self.max_rows = max_splits, max_rows
+        self.opt = capi.cv_options_default()
+        self.opt.relaxed, self.opt.sweeps, self.opt.precision = int(relaxed), int(sweeps), int(precision)
+        self.opt.alpha_mode, self.opt.enforce_splits = int(alpha_mode), int(enforce_splits)
+        n0, U = net.n0, max(net.U, 1)
+        f32 = dict(dtype=torch.float32, device=device)
+        self.out = dict(lower=torch.empty(B, m, **f32), lo_clip=torch.empty(B, n0, **f32),
+                        hi_clip=torch.empty(B, n0, **f32), l=torch.empty(B, U, **f32),
+                        u=torch.empty(B, U, **f32), mask=torch.empty(B, U, dtype=torch.int8, device=device),
+                        infeasible=torch.empty(B, dtype=torch.uint8, device=device),
+                        verified=torch.empty(B, dtype=torch.uint8, device=device),
+                        err_bound=torch.empty(B, m, **f32))
+        if want_final:
+            self.out["final_A"] = torch.empty(B, m, n0, **f32)
+            self.out["final_c"] = torch.empty(B, m, **f32)
+        probe = capi.make_batch_in(B, None, None, m, None, None, max_splits=max_splits, max_rows=max_rows)
+        self.ws_bytes = capi.cv_bound_batch_workspace(net.handle, net.cache, probe, self.opt)
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
+        self.bo = capi.make_batch_out(**self.out)
+
+    def run(self, lo, hi, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, row_off=None, G=None,
+            h=None, alpha=None, tgt_off=None, tgt_ids=None, stream=None):
+        """All array arguments must already be device tensors (see to_dev)."""
+        bi = capi.make_batch_in(self.B, lo, hi, self.m, C, t, l_in=l_in, u_in=u_in, split_off=split_off,
+                                split_ids=split_ids, max_splits=self.max_splits, row_off=row_off, G=G, h=h,
+                                max_rows=self.max_rows, alpha=alpha, tgt_off=tgt_off, tgt_ids=tgt_ids)
+        capi.cv_bound_batch(self.net.handle, self.net.cache, bi, self.bo, self.opt, self.ws, self.ws_bytes,
+                            stream)
+        return self.out

@@ -1,0 +1,171 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Both sides receive the same seeded inputs and the same root cache (the oracle's planes as
+FP32 values), so every step is compared on identical data.  Tolerance (the arithmetic of the
+kernels, see the file headers of csrc/): a bound may differ from the oracle by at most
+1e-5 of its magnitude scale (the sum of the absolute values of the terms that form it, as
+the oracle reports it) and must never be tighter than the oracle's, beyond the oracle's
+own FP64 rounding (1e-12 of the scale).  Boxes: the GPU machine contains the oracle box and is
+at most two FP32 ulps wider.  Integer outputs (infeasible flags, masks) match exactly except
+where the oracle's deciding value lies within the tolerance band of the threshold, where the
+GPU must take the conservative decision; such cases are counted and must be rare."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from tests._cases import Case, f32  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+SOUND = 1e-12
+
+
+def gpu_round(case: Case, precision=0, **kw):
+    from paper_2512_11087_gb300 import engine as E
+    net = E.Net(case.layers)
+    c = case.cache
+    net.set_cache(f32(case.lo0), f32(case.hi0), f32(c["root_l"]), f32(c["root_u"]), c["ids"], f32(c["lA"]),
+                  f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
+    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, max_rows=case.max_rows, relaxed=case.relaxed,
+                  sweeps=case.sweeps, precision=precision, alpha_mode=case.alpha_mode, enforce_splits=case.enforce)
+    d = E.to_dev
+    out = rnd.run(d(case.lo), d(case.hi), d(case.C), d(case.t), split_off=d(case.split_off),
+                  split_ids=d(case.split_ids), row_off=d(case.row_off), G=d(case.G), h=d(case.h),
+                  tgt_off=d(case.tgt_off), tgt_ids=d(case.tgt_ids), **kw)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    from paper_2512_11087_gb300 import capi
+    assert capi.cv_device_status(net.handle) == 0
+    net.close()
+    return res
+
+
+def compare(case, g, o, sound_bounds=True, report=None):
+    """Element-wise comparison; returns a dict of statistics."""
+    st = {}
+    U = case.U
+    inf_g, inf_o = g["infeasible"].astype(bool), o["infeasible"].astype(bool)
+    assert np.array_equal(inf_g, inf_o), (np.nonzero(inf_g != inf_o))
+    fe = ~inf_o
+    # boxes
+    lo_o, hi_o = o["lo_clip"], o["hi_clip"]
+    assert np.all(g["lo_clip"] <= lo_o) and np.all(g["hi_clip"] >= hi_o)
+    ulp = np.spacing(np.maximum(np.abs(lo_o), np.abs(hi_o)).astype(np.float32)).astype(np.float64)
+    st["box_max_ulps"] = float(max(np.max((lo_o - g["lo_clip"]) / ulp), np.max((g["hi_clip"] - hi_o) / ulp)))
+    assert st["box_max_ulps"] <= 2.0
+    # intermediate bounds
+    if U:
+        for k, sc in (("l", "l_scale"), ("u", "u_scale")):
+            gv, ov, s = g[k][:, :U][fe], o[k][:, :U][fe], o[sc][:, :U][fe]
+            err = np.abs(gv - ov) / s
+            st[f"{k}_max_rel"] = float(err.max()) if err.size else 0.0
+            assert st[f"{k}_max_rel"] <= TOL
+            if sound_bounds:
+                viol = (gv - ov) / s if k == "l" else (ov - gv) / s
+                assert viol.size == 0 or viol.max() <= SOUND, (k, viol.max())
+        # masks: exact except in the tolerance band, where only the conservative (unstable) call is allowed
+        mg, mo = g["mask"][:, :U], o["mask"][:, :U]
+        diff = (mg != mo)
+        st["mask_mismatch"] = int(diff.sum())
+        if diff.any():
+            bi, ci = np.nonzero(diff)
+            for b, c in zip(bi, ci):
+                assert mg[b, c] == 0, "GPU took a non-conservative stability decision"
+                band = TOL * max(o["l_scale"][b, c], o["u_scale"][b, c])
+                assert min(abs(o["l"][b, c]), abs(o["u"][b, c])) <= band
+        assert st["mask_mismatch"] <= max(2, mg.size // 10000)
+    # spec bounds
+    lg, lo_, ls = g["lower"][fe], o["lower"][fe], o["lower_scale"][fe]
+    err = np.abs(lg - lo_) / ls
+    st["lower_max_rel"] = float(err.max()) if err.size else 0.0
+    st["lower_med_rel"] = float(np.median(err)) if err.size else 0.0
+    st["lower_max_rel_to_value"] = float(np.max(np.abs(lg - lo_) / np.maximum(np.abs(lo_), 1e-30))) if err.size else 0.0
+    assert st["lower_max_rel"] <= TOL, st
+    if sound_bounds:
+        assert np.all(lg <= lo_ + SOUND * ls)
+    assert np.all(np.isinf(g["lower"][inf_o]))
+    # verified: exact except rows within the band of 0
+    vg, vo = g["verified"].astype(bool), o["verified"].astype(bool)
+    for b in np.nonzero(vg != vo)[0]:
+        assert not vg[b] and vo[b]
+        assert np.min(np.abs(o["lower"][b]) / o["lower_scale"][b]) <= TOL
+    if report is not None:
+        report.update(st)
+    print(st)
+    return st
+
+
+def test_paper_toy_example_on_gpu():
+    import json, os
+    from fractions import Fraction
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "toy_2d.json")))
+    layers = [dict(kind=0, W=np.array(gold["W1"], np.float32), b=np.array(gold["b1"], np.float32),
+                   in_shape=(2,), out_shape=(2,)),
+              dict(kind=0, W=np.array([gold["w2"]], np.float32), b=np.array(gold["b2"], np.float32),
+                   in_shape=(2,), out_shape=(1,))]
+    case = Case(None, 1, 0, 0, 0.0, layers=layers, m_spec=(np.array([[1.0]], np.float32), np.zeros(1, np.float32)),
+                alpha_mode=1, enforce=0)
+    case.lo = np.array([gold["box_lo"]], np.float32)
+    case.hi = np.array([gold["box_hi"]], np.float32)
+    case.lo0, case.hi0 = case.lo[0], case.hi[0]
+    from oracle import oracle as O
+    root = O.root_crown(case.net, case.lo0, case.hi0, alpha_mode=1)
+    case.cache = O.make_cache(root)
+    case.U = 2
+    case.split_off, case.split_ids, case.max_splits = np.array([0, 1], np.int32), np.array([-1], np.int32), 1
+    # relaxed clipping: bound -2, box [-1,1] x [5/7,1]
+    case.relaxed, case.sweeps = 1, 0
+    g = gpu_round(case)
+    assert g["lower"][0, 0] <= -2.0 and g["lower"][0, 0] >= -2.0 - 1e-5
+    assert g["hi_clip"][0, 0] >= 1.0 and g["hi_clip"][0, 0] - 1.0 < 1e-6
+    assert g["lo_clip"][0, 1] <= 5 / 7 and 5 / 7 - g["lo_clip"][0, 1] < 1e-6
+    compare(case, g, case.oracle())
+    # complete clipping on the original box: zbar = [0, -3], output bound 0
+    case.relaxed, case.sweeps = 0, 1
+    g = gpu_round(case)
+    assert g["u"][0, 0] >= 0.0 and g["u"][0, 0] < 1e-5
+    assert g["u"][0, 1] >= -3.0 and g["u"][0, 1] < -3.0 + 1e-5
+    assert g["lower"][0, 0] <= 0.0 and g["lower"][0, 0] > -1e-5
+    compare(case, g, case.oracle())
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("mlp5x50_relaxed", dict(dims=[5] + [50] * 6 + [5], B=256, kmin=0, kmax=8, eps=0.05, centre="pm1",
+                             clip01=False, out_rows=1, sweeps=0)),
+    ("mlp5x50_complete", dict(dims=[5] + [50] * 6 + [5], B=64, kmin=1, kmax=8, eps=0.05, centre="pm1",
+                              clip01=False, out_rows=0, sweeps=10)),
+    ("mlp24_complete", dict(dims=[24, 32, 32, 32, 6], B=48, kmin=1, kmax=4, eps=0.1, sweeps=10)),
+    ("mlp784_ragged", dict(dims=[784, 70, 70, 10], B=37, kmin=1, kmax=4, eps=0.02, sweeps=10)),
+    ("mlp784_targets", dict(dims=[784, 64, 64, 10], B=20, kmin=1, kmax=4, eps=0.02, sweeps=3, targets=7)),
+    ("mlp100_no_splits", dict(dims=[100, 40, 40, 7], B=9, kmin=0, kmax=0, eps=0.05, sweeps=5)),
+])
+def test_round_parity(name, kw):
+    case = Case(**kw)
+    g = gpu_round(case)
+    o = case.oracle()
+    compare(case, g, o, sound_bounds=(case.sweeps == 0))
+
+
+def test_round_parity_alpha_given():
+    case = Case([30, 40, 40, 5], 16, 0, 3, 0.1, sweeps=0, seed=4)
+    rng = np.random.default_rng(9)
+    alpha = rng.uniform(0, 1, size=(case.B, case.m, case.net.H)).astype(np.float32)
+    from paper_2512_11087_gb300 import engine as E
+    g = gpu_round(case, alpha=E.to_dev(alpha))
+    o = case.oracle(alpha=alpha.astype(np.float64))
+    compare(case, g, o)
+
+
+def test_infeasible_and_edge_cases():
+    # contradictory splits (the same neuron on both sides) must be found infeasible by both
+    case = Case([12, 20, 20, 4], 8, 1, 2, 0.3, sweeps=4, seed=3)
+    so, si = case.split_off.copy(), case.split_ids.copy()
+    first = si[so[0]]
+    si[so[0] + 1 if so[1] - so[0] > 1 else so[0]] = -first
+    case.split_ids = si
+    g = gpu_round(case)
+    o = case.oracle()
+    assert o["infeasible"][0] == 1
+    compare(case, g, o, sound_bounds=False)

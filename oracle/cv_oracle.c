@@ -220,32 +220,39 @@ static signed char stab_state(double l, double u) {
 /* their concretizations over the root box (Lemma A.1).                       */
 /* Outputs: l,u [H]; planes lA,uA [H x n0], lc,uc [H]; pscale [H] =          */
 /* |A| max(|lo|,|hi|) + |c| (max over the two planes, the magnitude scale of  */
-/* the neuron's concretization).                                              */
+/* the neuron's concretization); bscale [H] (may be NULL): the magnitude of   */
+/* every term of the back-substitution that formed the bound,                 */
+/* sum_i |Lam^(i)|(|W^(i)| zmag^(i-1) + |b^(i)|) + |A| xmag + |c|.            */
 /* ------------------------------------------------------------------------- */
 int orc_root_crown(int L, const int* dims, const double* W, const double* b,
                    const double* lo, const double* hi, int alpha_mode,
                    double* l_all, double* u_all, double* lA, double* lc,
-                   double* uA, double* uc, double* pscale) {
+                   double* uA, double* uc, double* pscale, double* bscale) {
     net_t n;
     if (net_init(&n, L, dims, W, b)) return -1;
     int n0 = dims[0];
     signed char* st = (signed char*)calloc((size_t)n.H + 1, 1);
+    double* zmag = (double*)calloc((size_t)n.H + 1, sizeof(double));
+    double* xmag = (double*)malloc(sizeof(double) * n0);
+    for (int q = 0; q < n0; ++q) xmag[q] = fmax(fabs(lo[q]), fabs(hi[q]));
     for (int k = 1; k <= L - 1; ++k) {
         int nk = dims[k];
         int ho = n.hoff[k];
         double* Lam = (double*)calloc((size_t)nk * nk, sizeof(double));
         double* bias = (double*)calloc(nk, sizeof(double));
+        double* s1 = (double*)calloc(nk, sizeof(double));
+        double* s2 = (double*)calloc(nk, sizeof(double));
         /* lower planes */
         for (int j = 0; j < nk; ++j) Lam[(long)j * nk + j] = 1.0;
         backward(&n, k, nk, Lam, l_all, u_all, st, NULL, alpha_mode,
-                 lA + (long)ho * n0, bias, NULL, NULL, NULL, NULL);
+                 lA + (long)ho * n0, bias, s1, zmag, xmag, NULL);
         for (int j = 0; j < nk; ++j) lc[ho + j] = bias[j];
         /* upper planes: lower bound of -z, negated */
         memset(Lam, 0, sizeof(double) * (size_t)nk * nk);
         memset(bias, 0, sizeof(double) * nk);
         for (int j = 0; j < nk; ++j) Lam[(long)j * nk + j] = -1.0;
         backward(&n, k, nk, Lam, l_all, u_all, st, NULL, alpha_mode,
-                 uA + (long)ho * n0, bias, NULL, NULL, NULL, NULL);
+                 uA + (long)ho * n0, bias, s2, zmag, xmag, NULL);
         for (int j = 0; j < nk; ++j) {
             double* a = uA + (long)(ho + j) * n0;
             for (int q = 0; q < n0; ++q) a[q] = -a[q];
@@ -258,18 +265,29 @@ int orc_root_crown(int L, const int* dims, const double* W, const double* b,
             orc_concretize(n0, uA + (long)g * n0, uc[g], lo, hi, &dum, &vmax);
             l_all[g] = vmin;
             u_all[g] = vmax;
-            double s1 = fabs(lc[g]), s2 = fabs(uc[g]);
+            double p1 = fabs(lc[g]), p2 = fabs(uc[g]);
             for (int q = 0; q < n0; ++q) {
                 double xm = fmax(fabs(lo[q]), fabs(hi[q]));
-                s1 += fabs(lA[(long)g * n0 + q]) * xm;
-                s2 += fabs(uA[(long)g * n0 + q]) * xm;
+                p1 += fabs(lA[(long)g * n0 + q]) * xm;
+                p2 += fabs(uA[(long)g * n0 + q]) * xm;
             }
-            pscale[g] = fmax(s1, s2);
+            pscale[g] = fmax(p1, p2);
             st[g] = stab_state(vmin, vmax);
+            zmag[g] = fmax(fabs(vmin), fabs(vmax));
         }
-        free(Lam); free(bias);
+        /* back-substitution magnitude scale: sum_i |Lam^(i)| V^(i) + |Lam_0| xmag + |c| */
+        for (int j = 0; j < nk; ++j) {
+            int g = ho + j;
+            double t1 = s1[j] + fabs(lc[g]), t2 = s2[j] + fabs(uc[g]);
+            for (int q = 0; q < n0; ++q) {
+                t1 += fabs(lA[(long)g * n0 + q]) * xmag[q];
+                t2 += fabs(uA[(long)g * n0 + q]) * xmag[q];
+            }
+            if (bscale) bscale[g] = fmax(t1, t2);
+        }
+        free(Lam); free(bias); free(s1); free(s2);
     }
-    free(st);
+    free(st); free(zmag); free(xmag);
     return 0;
 }
 
@@ -441,6 +459,83 @@ double orc_complete_clip(int n, const double* a, double c, int R, const double* 
     return val;
 }
 
+/* Algorithm 1 with the breakpoint positions taken in FP32, the precision in   */
+/* which the CUDA kernel takes that decision (the paper fixes none).  The     */
+/* decision arithmetic is fixed as follows, every operation IEEE-754 binary32 */
+/* round-to-nearest: the running multiplier combination af (initially a) is   */
+/* kept in FP32;  a' = fma(-beta_k, g_k, af);  q = (-a') * (1/g_k);  after a  */
+/* change  af = fma(beta_k_new, g_k, a').  Weights, the threshold and the     */
+/* cumulative sums stay FP64, and the returned dual value D(beta) (Eq. 4) is  */
+/* evaluated in FP64 at the FP32 multipliers.  Inputs a and G are FP32 values.*/
+/* Near a kink where two breakpoints coalesce, the order of nearly equal q's  */
+/* is decided by this arithmetic; both sides then follow the same ascent.     */
+typedef struct { float q; double w; int j; } bpf_t;
+static int bpf_cmp(const void* A, const void* B) {
+    const bpf_t* x = (const bpf_t*)A; const bpf_t* y = (const bpf_t*)B;
+    if (x->q < y->q) return -1;
+    if (x->q > y->q) return 1;
+    return (x->j < y->j) ? -1 : (x->j > y->j);
+}
+
+double orc_complete_clip_f32(int n, const float* a, double c, int R, const float* G,
+                             const double* h, const double* lo, const double* hi,
+                             int sweeps, float* beta, double* scale) {
+    float* af = (float*)malloc(sizeof(float) * (n > 0 ? n : 1));
+    float* apr = (float*)malloc(sizeof(float) * (n > 0 ? n : 1));
+    bpf_t* bp = (bpf_t*)malloc(sizeof(bpf_t) * (n > 0 ? n : 1));
+    for (int j = 0; j < n; ++j) af[j] = a[j];
+    for (int k = 0; k < R; ++k) beta[k] = 0.0f;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int k = 0; k < R; ++k) {
+            const float* gk = G + (long)k * n;
+            const float bk = beta[k];
+            int nb = 0;
+            double s0 = h[k];
+            for (int j = 0; j < n; ++j) {
+                apr[j] = fmaf(-bk, gk[j], af[j]);
+                double gd = (double)gk[j];
+                s0 += fmax(gd * lo[j], gd * hi[j]);
+                if (gk[j] != 0.0f) {
+                    float r = 1.0f / gk[j];
+                    float na = -apr[j];
+                    bp[nb].q = na * r;
+                    bp[nb].w = fabs(gd) * (0.5 * (hi[j] - lo[j]));
+                    bp[nb].j = j;
+                    ++nb;
+                }
+            }
+            qsort(bp, nb, sizeof(bpf_t), bpf_cmp);
+            float bn = 0.0f;
+            if (s0 > 0.0) {
+                double s = s0;
+                for (int i = 0; i < nb; ++i) {
+                    s -= 2.0 * bp[i].w;
+                    if (s <= 0.0) { bn = bp[i].q; break; }
+                }
+            }
+            if (!(bn > 0.0f)) bn = 0.0f;
+            if (bn != bk) {
+                for (int j = 0; j < n; ++j) af[j] = fmaf(bn, gk[j], apr[j]);
+                beta[k] = bn;
+            }
+        }
+    }
+    double val = c, sc = fabs(c);
+    for (int k = 0; k < R; ++k) { val += (double)beta[k] * h[k]; sc += (double)beta[k] * fabs(h[k]); }
+    for (int j = 0; j < n; ++j) {
+        double v = a[j], va = fabs((double)a[j]);
+        for (int p = 0; p < R; ++p) {
+            v += (double)beta[p] * (double)G[(long)p * n + j];
+            va += (double)beta[p] * fabs((double)G[(long)p * n + j]);
+        }
+        val += fmin(v * lo[j], v * hi[j]);
+        sc += va * fmax(fabs(lo[j]), fabs(hi[j]));
+    }
+    if (scale) *scale = sc;
+    free(af); free(apr); free(bp);
+    return val;
+}
+
 /* The dual objective D(beta) of Eq. 4 at a given beta (any beta >= 0 gives a */
 /* valid lower bound: weak duality).                                          */
 double orc_dual_value(int n, const double* a, double c, int R, const double* G,
@@ -467,7 +562,8 @@ double orc_dual_value(int n, const double* a, double c, int R, const double* G,
 /*     activation BaB) unless enforce_splits = 0 (the paper's relaxed-clipping */
 /*     walk-through keeps the split neuron's clipped bounds as they are)      */
 /*  a6 complete clipping (Algorithm 1, `sweeps` passes) of every still-       */
-/*     unstable target, both sides                                            */
+/*     unstable target, both sides, breakpoint positions in FP32              */
+/*     (orc_complete_clip_f32; the cached planes are FP32 values)             */
 /*  a7 CROWN back-substitution of the spec rows C with the subdomain's bounds */
 /*  a8 concretisation over the clipped box; verified iff all f_r > 0         */
 /* Infeasible subdomains stop at the step that finds them; they report        */
@@ -596,24 +692,25 @@ static void one_subdomain(const cache_t* cc, int b,
 
     /* a6: complete clipping of the still-unstable targets */
     if (!infeas && sweeps > 0 && Ra > 0) {
-        double* beta = (double*)malloc(sizeof(double) * Ra);
-        double* na = (double*)malloc(sizeof(double) * n0);
+        float* beta = (float*)malloc(sizeof(float) * Ra);
+        float* Gf = (float*)malloc(sizeof(float) * (size_t)Ra * n0);
+        float* af = (float*)malloc(sizeof(float) * n0);
+        for (long q = 0; q < (long)Ra * n0; ++q) Gf[q] = (float)G[q];
         int nt = tgt_off ? tgt_off[b + 1] - tgt_off[b] : U;
         for (int ti = 0; ti < nt; ++ti) {
             int c = tgt_off ? tgt_ids[tgt_off[b] + ti] : ti;
             if (c < 0 || c >= U || mk[c] != 0) continue;
             double sc;
-            double L1 = orc_complete_clip(n0, cc->lA + (long)c * n0, cc->lc[c], Ra, G, h,
-                                          clo, chi, sweeps, beta, &sc);
+            for (int q = 0; q < n0; ++q) af[q] = (float)cc->lA[(long)c * n0 + q];
+            double L1 = orc_complete_clip_f32(n0, af, cc->lc[c], Ra, Gf, h, clo, chi, sweeps, beta, &sc);
             if (L1 > lb[c]) lb[c] = L1;
             if (sc > ls[c]) ls[c] = sc;
-            for (int q = 0; q < n0; ++q) na[q] = -cc->uA[(long)c * n0 + q];
-            double L2 = orc_complete_clip(n0, na, -cc->uc[c], Ra, G, h,
-                                          clo, chi, sweeps, beta, &sc);
+            for (int q = 0; q < n0; ++q) af[q] = -(float)cc->uA[(long)c * n0 + q];
+            double L2 = orc_complete_clip_f32(n0, af, -cc->uc[c], Ra, Gf, h, clo, chi, sweeps, beta, &sc);
             if (-L2 < ub[c]) ub[c] = -L2;
             if (sc > us[c]) us[c] = sc;
         }
-        free(beta); free(na);
+        free(beta); free(Gf); free(af);
         for (int c = 0; c < U; ++c) {
             if (mk[c] == 0) mk[c] = stab_state(lb[c], ub[c]);
             if (lb[c] > ub[c]) infeas = 1;

@@ -38,7 +38,7 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         _lib.orc_concretize.argtypes = [I, P, D, P, P, P, P]
-        _lib.orc_root_crown.argtypes = [I, P, P, P, P, P, I, P, P, P, P, P, P, P]
+        _lib.orc_root_crown.argtypes = [I, P, P, P, P, P, I, P, P, P, P, P, P, P, P]
         _lib.orc_row_check.argtypes = [I, P, D, P, P, P, P, P]
         _lib.orc_row_check.restype = I
         _lib.orc_relaxed_clip_row.argtypes = [I, P, D, P, P, P, P]
@@ -48,6 +48,8 @@ def _load():
         _lib.orc_relaxed_clip_sequential.restype = I
         _lib.orc_complete_clip.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
         _lib.orc_complete_clip.restype = D
+        _lib.orc_complete_clip_f32.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
+        _lib.orc_complete_clip_f32.restype = D
         _lib.orc_dual_value.argtypes = [I, P, D, I, P, P, P, P, P]
         _lib.orc_dual_value.restype = D
         _lib.orc_bound_batch.argtypes = ([I, P, P, P] + [I, P, P, P, P, P] + [P, P, P] +
@@ -155,10 +157,10 @@ def root_crown(net: Net, lo, hi, alpha_mode=0):
     lo, hi = _f64(lo), _f64(hi)
     H, n0 = net.H, int(net.dims[0])
     out = dict(l=np.zeros(H), u=np.zeros(H), lA=np.zeros((H, n0)), lc=np.zeros(H),
-               uA=np.zeros((H, n0)), uc=np.zeros(H), pscale=np.zeros(H))
+               uA=np.zeros((H, n0)), uc=np.zeros(H), pscale=np.zeros(H), bscale=np.zeros(H))
     rc = lib.orc_root_crown(net.L, _p(net.dims), _p(net.Wflat), _p(net.bflat), _p(lo), _p(hi),
                             int(alpha_mode), _p(out["l"]), _p(out["u"]), _p(out["lA"]), _p(out["lc"]),
-                            _p(out["uA"]), _p(out["uc"]), _p(out["pscale"]))
+                            _p(out["uA"]), _p(out["uc"]), _p(out["pscale"]), _p(out["bscale"]))
     assert rc == 0
     return out
 
@@ -206,6 +208,21 @@ def complete_clip(a, c, G, h, lo, hi, sweeps):
     sc = ctypes.c_double()
     v = lib.orc_complete_clip(a.size, _p(a), float(c), R, _p(G), _p(h), _p(lo), _p(hi), int(sweeps),
                               _p(beta), ctypes.byref(sc))
+    return v, beta[:R], sc.value
+
+
+def complete_clip_f32(a, c, G, h, lo, hi, sweeps):
+    """Algorithm 1 with FP32 breakpoint decisions (the batch oracle's a6): (value, beta, scale).
+    a and G are rounded to FP32 first."""
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(a, np.float32))
+    G = np.ascontiguousarray(np.atleast_2d(np.asarray(G, np.float32)))
+    h, lo, hi = _f64(np.atleast_1d(h)), _f64(lo), _f64(hi)
+    R = G.shape[0] if G.size else 0
+    beta = np.zeros(max(R, 1), np.float32)
+    sc = ctypes.c_double()
+    v = lib.orc_complete_clip_f32(a.size, _p(a), float(c), R, _p(G), _p(h), _p(lo), _p(hi), int(sweeps),
+                                  _p(beta), ctypes.byref(sc))
     return v, beta[:R], sc.value
 
 

@@ -68,8 +68,9 @@ static cv_status validate(const cv_net* net, const cv_cache* cache, const cv_bat
     if (!pointers) return CV_OK;
     if (in->B > 0 && (!in->lo || !in->hi)) { cv_set_error("lo/hi required"); return CV_EINVAL; }
     if (in->m > 0 && !in->C) { cv_set_error("C required when m > 0"); return CV_EINVAL; }
-    if ((in->split_off == nullptr) != (in->split_ids == nullptr)) { cv_set_error("split_off and split_ids go together"); return CV_EINVAL; }
-    if (in->row_off && (!in->G || !in->h)) { cv_set_error("row_off needs G and h"); return CV_EINVAL; }
+    if (!in->split_off && in->split_ids) { cv_set_error("split_ids without split_off"); return CV_EINVAL; }
+    if (in->split_off && !in->split_ids && in->max_splits > 0) { cv_set_error("split_ids required when max_splits > 0"); return CV_EINVAL; }
+    if (in->row_off && (!in->G || !in->h) && in->max_rows > 0) { cv_set_error("row_off needs G and h"); return CV_EINVAL; }
     if ((in->tgt_off == nullptr) != (in->tgt_ids == nullptr)) { cv_set_error("tgt_off and tgt_ids go together"); return CV_EINVAL; }
     if ((in->l_in == nullptr) != (in->u_in == nullptr)) { cv_set_error("l_in and u_in go together"); return CV_EINVAL; }
     if (!in->split_off && in->max_splits > 0) { cv_set_error("max_splits > 0 without splits"); return CV_EINVAL; }

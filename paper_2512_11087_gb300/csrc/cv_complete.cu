@@ -241,16 +241,32 @@ __global__ void __launch_bounds__(256) k_complete(CCArgs a) {
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-        if (lane == 0) {
-            float cst = c0;
-            double scale = (double)a.pscale[side ? a.U + c : c] + fabs((double)c0);
-            for (int k = 0; k < R; ++k) {
-                cst = fmaf(beta[k], hrow[k], cst);
-                scale += (double)beta[k] * (Sg[k] + fabs((double)hrow[k]));
+        float cst = c0;
+        double scale = (double)a.pscale[side ? a.U + c : c] + fabs((double)c0);
+        for (int k = 0; k < R; ++k) {
+            cst = fmaf(beta[k], hrow[k], cst);
+            scale += (double)beta[k] * (Sg[k] + fabs((double)hrow[k]));
+        }
+        const double gam = (double)(R + NE + 12) * CV_U32;
+        const float pad = __double2float_ru(gam * scale * 1.0001);
+        float val = __fsub_rd(__fadd_rd(part, cst), pad);
+        const float valhi = __fadd_ru(__fadd_ru(part, cst), pad);
+        const float cur = side == 0 ? a.l[o] : -a.u[o];
+        if (val < 0.f && valhi >= 0.f && cur < 0.f) {
+            // the stability decision is uncertain in FP32: evaluate D(beta) in FP64
+            double d = 0.0;
+            for (int j = lane; j < n0; j += 32) {
+                double v = (double)(sa * ap[j]);
+                for (int k = 0; k < R; ++k) v += (double)beta[k] * (double)gs[(size_t)k * n0 + j];
+                d += fmin(v * (double)slo[j], v * (double)shi[j]);
             }
-            const double gam = (double)(R + NE + 12) * CV_U32;
-            const float pad = __double2float_ru(gam * scale * 1.0001);
-            const float val = __fsub_rd(__fadd_rd(part, cst), pad);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+            d += (double)c0;
+            for (int k = 0; k < R; ++k) d += (double)beta[k] * (double)hrow[k];
+            val = __double2float_rd(d - ldexp(scale, -40));
+        }
+        if (lane == 0) {
             if (side == 0) { if (val > a.l[o]) a.l[o] = val; }
             else { const float ub = -val; if (ub < a.u[o]) a.u[o] = ub; }
         }

@@ -131,9 +131,9 @@ __global__ void k_post_reconc(cv_cache cc, cv_batch_in in, int enforce, float* l
         mask[o] = (l[o] >= 0.f) ? 1 : ((u[o] <= 0.f) ? -1 : 0);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && enforce && in.split_off) {
+    if (threadIdx.x == 0 && enforce && in.split_off && in.split_ids) {
         const int s0 = in.split_off[b], s1 = in.split_off[b + 1];
-        for (int s = s0; s < s1; ++s) {
+        for (int s = s0; s < s1 && s1 - s0 <= in.max_splits; ++s) {
             const int code = in.split_ids[s];
             const int g = (code > 0 ? code : -code) - 1;
             if (code == 0 || g >= cc.H) continue;

@@ -118,17 +118,22 @@ def test_paper_toy_example_on_gpu():
     # relaxed clipping: bound -2, box [-1,1] x [5/7,1]
     case.relaxed, case.sweeps = 1, 0
     g = gpu_round(case)
-    assert g["lower"][0, 0] <= -2.0 and g["lower"][0, 0] >= -2.0 - 1e-5
+    o = case.oracle()
+    tol = TOL * o["lower_scale"][0, 0]
+    assert o["lower"][0, 0] == pytest.approx(-2.0, abs=1e-6)
+    assert -2.0 - tol <= g["lower"][0, 0] <= -2.0
     assert g["hi_clip"][0, 0] >= 1.0 and g["hi_clip"][0, 0] - 1.0 < 1e-6
     assert g["lo_clip"][0, 1] <= 5 / 7 and 5 / 7 - g["lo_clip"][0, 1] < 1e-6
-    compare(case, g, case.oracle())
+    compare(case, g, o)
     # complete clipping on the original box: zbar = [0, -3], output bound 0
     case.relaxed, case.sweeps = 0, 1
     g = gpu_round(case)
-    assert g["u"][0, 0] >= 0.0 and g["u"][0, 0] < 1e-5
-    assert g["u"][0, 1] >= -3.0 and g["u"][0, 1] < -3.0 + 1e-5
-    assert g["lower"][0, 0] <= 0.0 and g["lower"][0, 0] > -1e-5
-    compare(case, g, case.oracle())
+    o = case.oracle()
+    assert np.array_equal(o["u"][0], [0.0, -3.0]) and o["lower"][0, 0] == 0.0
+    assert 0.0 <= g["u"][0, 0] <= TOL * o["u_scale"][0, 0]
+    assert -3.0 <= g["u"][0, 1] <= -3.0 + TOL * o["u_scale"][0, 1]
+    assert -TOL * o["lower_scale"][0, 0] <= g["lower"][0, 0] <= 0.0
+    compare(case, g, o)
 
 
 @pytest.mark.parametrize("name,kw", [
@@ -159,13 +164,56 @@ def test_round_parity_alpha_given():
 
 
 def test_infeasible_and_edge_cases():
-    # contradictory splits (the same neuron on both sides) must be found infeasible by both
-    case = Case([12, 20, 20, 4], 8, 1, 2, 0.3, sweeps=4, seed=3)
+    # (1) a split on a root-stable neuron against its sign; (2) an extra row that no point of the
+    # box satisfies; (3) a subdomain without rows.  Both sides must flag exactly (1) and (2).
+    case = Case([12, 20, 20, 4], 6, 1, 2, 0.3, sweeps=4, seed=3, out_rows=1)
+    stable = np.nonzero(case.cache["root_l"] >= 0)[0]
+    assert stable.size > 0
     so, si = case.split_off.copy(), case.split_ids.copy()
-    first = si[so[0]]
-    si[so[0] + 1 if so[1] - so[0] > 1 else so[0]] = -first
+    si[so[0]] = -(int(stable[0]) + 1)          # z <= 0 on a neuron that is always active
     case.split_ids = si
+    case.h = case.h.copy()
+    case.h[1] = 1e6                            # row 1 (subdomain 1): g.x + 1e6 <= 0 is empty
+    so2 = so.copy()
+    case.split_off = so2
     g = gpu_round(case)
     o = case.oracle()
-    assert o["infeasible"][0] == 1
+    assert o["infeasible"][0] == 1 and o["infeasible"][1] == 1
+    assert np.all(np.isinf(g["lower"][:2])) and np.all(g["verified"][:2] == 1)
     compare(case, g, o, sound_bounds=False)
+
+
+def test_cache_build_parity():
+    """a1 on the GPU (cv_cache_build) against the oracle's root CROWN: bounds within 1e-5 of the
+    back-substitution magnitude scale, never tighter, same unstable set (outside the band)."""
+    from oracle import oracle as O
+    from paper_2512_11087_gb300 import engine as E, workloads as WL
+    for dims, eps, seed in [([24, 32, 32, 32, 6], 0.1, 0), ([784, 256, 256, 256, 256, 256, 256, 10], 0.02, 0),
+                            ([5] + [50] * 6 + [5], 0.05, 1)]:
+        layers = WL.he_mlp(dims, seed=seed)
+        lo0, hi0 = WL.box(dims[0], eps, seed=seed, centre="unit" if dims[0] > 5 else "pm1", clip01=dims[0] > 5)
+        net = E.Net(layers)
+        U = net.build_cache(lo0, hi0)
+        gc = net.read_cache()
+        root = O.root_crown(O.Net(layers), lo0, hi0)
+        bs = root["bscale"]
+        el = (root["l"] - gc["root_l"]) / bs
+        eu = (gc["root_u"] - root["u"]) / bs
+        print(dims[0], len(dims), "max rel l %.2e u %.2e" % (el.max(), eu.max()))
+        assert el.min() >= -1e-12 and eu.min() >= -1e-12
+        assert el.max() <= TOL and eu.max() <= TOL
+        unst_o = (root["l"] < 0) & (root["u"] > 0)
+        unst_g = np.zeros_like(unst_o)
+        unst_g[gc["ids"]] = True
+        diff = np.nonzero(unst_o != unst_g)[0]
+        for g_ in diff:  # only conservative calls inside the band
+            assert unst_g[g_] and min(abs(root["l"][g_]), abs(root["u"][g_])) <= TOL * bs[g_]
+        assert U == unst_g.sum()
+        # the cached planes are valid: sampled points satisfy them
+        rng = np.random.default_rng(0)
+        X = lo0 + (hi0 - lo0) * rng.uniform(size=(2000, dims[0]))
+        _, pre = O.Net(layers).forward(X)
+        Z = np.concatenate(pre, axis=1)[:, gc["ids"]]
+        assert np.all(Z >= X @ gc["lA"].T.astype(np.float64) + gc["lc"] - 1e-9)
+        assert np.all(Z <= X @ gc["uA"].T.astype(np.float64) + gc["uc"] + 1e-9)
+        net.close()

@@ -152,10 +152,10 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
         return s;
     if (tm) CV_CUDA(cudaEventRecord(tm->ev[3], st));
     if (m > 0) {
-        s = cv_backward_raw(net, lay.R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
+        s = cv_backward_t<float>(net, lay.R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
                             cache->root_state, cache->slot_of, out->l, out->u, out->mask, U, in->alpha,
                             opt->alpha_mode, cache->V, out->lo_clip, out->hi_clip, out->infeasible, out->lower,
-                            out->err_bound, out->final_A, out->final_c, nullptr, nullptr,
+                            nullptr, out->err_bound, out->final_A, out->final_c, nullptr, nullptr,
                             (float*)(ws + lay.lam0), (float*)(ws + lay.lam1), (double*)(ws + lay.part_bias),
                             (double*)(ws + lay.part_pad), (double*)(ws + lay.part_f),
                             (double*)(ws + lay.part_fmag), (double*)(ws + lay.acc_bias),

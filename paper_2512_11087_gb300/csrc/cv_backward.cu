@@ -6,37 +6,43 @@
 //   i > 1 : Lam^(i-1)_q = P_q d_q, bias += P_q e_q   (d, e from the relaxation of neuron q
 //           of hidden layer i-1, chosen by the sign of P_q), bias += Lam^(i-1) . b^(i-1)
 //   i = 1 : f = sum_q min(P_q lo_q, P_q hi_q) + bias
-// Rounding: P is accumulated in FP32 chains of at most 32 FMAs whose results are summed with
-// a compensated (TwoSum) accumulator, so |P~ - P| <= (33 u) sum_j |Lam_j||W_jq| (u = 2^-24).
-// Every step adds gamma * |Lam^(i)| V^(i) to the pad, V^(i) = |W^(i)| zmag^(i-1) + |b^(i)|
-// with zmag a bound on |z^(i-1)| over the root box; gamma = 48 u covers the product chain,
-// the relaxation products and the FP32 partial sums of the epilogue.  Row sums are FP64.
+// Two instantiations of the same kernels:
+//  T = float  (the per-round spec bound): P is accumulated in FP32 chains of at most 32 FMAs whose
+//    results are summed with a compensated (TwoSum) accumulator, so |P~ - P| <= (33 u) sum_j
+//    |Lam_j||W_jq| (u = 2^-24).  Every step adds gamma * |Lam^(i)| V^(i) to the pad,
+//    V^(i) = |W^(i)| zmag^(i-1) + |b^(i)| with zmag a bound on |z^(i-1)| over the root box;
+//    gamma = 48 u covers the product chain, the relaxation products and the FP32 partial sums of
+//    the epilogue.
+//  T = double (the once-per-property root cache): the same recursion in FP64, gamma = 2^-40.
+// Row sums (bias, pad, final concretisation) are FP64 in both.
 #include "cv_internal.cuh"
 
 #include <math.h>
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, KC_TILES = 2;  // KC = 32 FMAs per chain
-constexpr double GAMMA_BWD = 48.0 * CV_U32;
+constexpr int BM = 64, BN = 64, BK = 16, KC_TILES = 2;  // KC = 32 FMAs per FP32 chain
 
+template <typename T> struct Gam;
+template <> struct Gam<float> { static constexpr double v = 48.0 * CV_U32; };
+template <> struct Gam<double> { static constexpr double v = 9.094947017729282e-13; };  // 2^-40
+
+template <typename T>
 struct LayerArgs {
-    const float* A;    // Lam^(i) [R x K]
+    const T* A;        // Lam^(i) [R x K]
     const float* W;    // W^(i) [K x N]
     int R, K, N, i;    // i: layer index of W
     int rows_per_sub, m;
-    // relaxation of hidden layer i-1 (i > 1)
     int hoff;          // first global id of hidden layer i-1
     int H;
-    const float* root_l; const float* root_u; const int8_t* root_state;
-    const int* slot_of; const float* l; const float* u; const int8_t* mask; int U;
+    const T* root_l; const T* root_u; const int8_t* root_state;
+    const int* slot_of; const T* l; const T* u; const int8_t* mask; int U;
     const float* alpha; int alpha_mode;
     const float* bnext;   // b^(i-1) [N]
     const float* Vnext;   // V^(i-1) [N]
-    float* Aout;          // Lam^(i-1) [R x N]
-    // final step (i == 1)
-    const float* lo; const float* hi;  // [nsub x N]
-    float* lam0;          // optional [R x N]
+    T* Aout;              // Lam^(i-1) [R x N]
+    const float* lo; const float* hi;  // [nsub x N] (i == 1)
+    T* lam0;              // optional [R x N]
     double* part_bias; double* part_pad; double* part_f; double* part_fmag; int ncb;
 };
 
@@ -46,42 +52,45 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bp)) + (b - bp);
 }
 
-__global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs a) {
-    __shared__ float As[BK][BM + 4];
-    __shared__ float Bs[BK][BN + 4];
+template <typename T>
+__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs<T> a) {
+    __shared__ T As[BK][BM + 4];
+    __shared__ T Bs[BK][BN + 4];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    constexpr bool F32 = sizeof(T) == 4;
 
-    float acc[4][4], tot[4][4], cmp[4][4];
+    T acc[4][4], tot[4][4], cmp[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; tot[i][j] = 0.f; cmp[i][j] = 0.f; }
+        for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); tot[i][j] = T(0); cmp[i][j] = T(0); }
 
     const int ntiles = (a.K + BK - 1) / BK;
     for (int kt = 0; kt < ntiles; ++kt) {
         const int k0 = kt * BK;
-        // A tile: 64 rows x 16 k
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            int idx = tid * 4 + e;  // 0..1023
+            int idx = tid * 4 + e;
             int r = idx >> 4, kk = idx & 15;
             int gr = row0 + r, gk = k0 + kk;
-            As[kk][r] = (gr < a.R && gk < a.K) ? a.A[(size_t)gr * a.K + gk] : 0.f;
+            As[kk][r] = (gr < a.R && gk < a.K) ? a.A[(size_t)gr * a.K + gk] : T(0);
         }
-        // W tile: 16 k x 64 cols
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             int idx = tid * 4 + e;
             int kk = idx >> 6, c = idx & 63;
             int gk = k0 + kk, gc = col0 + c;
-            Bs[kk][c] = (gk < a.K && gc < a.N) ? a.W[(size_t)gk * a.N + gc] : 0.f;
+            Bs[kk][c] = (gk < a.K && gc < a.N) ? (T)a.W[(size_t)gk * a.N + gc] : T(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            float av[4], bv[4];
+            T av[4], bv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
 #pragma unroll
@@ -89,24 +98,29 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs a) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
         }
         __syncthreads();
-        if ((kt % KC_TILES) == KC_TILES - 1 || kt == ntiles - 1) {
+        if (F32 && ((kt % KC_TILES) == KC_TILES - 1 || kt == ntiles - 1)) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float s, e;
-                    two_sum(tot[i][j], acc[i][j], s, e);
+                    two_sum((float)tot[i][j], (float)acc[i][j], s, e);
                     tot[i][j] = s;
                     cmp[i][j] += e;
-                    acc[i][j] = 0.f;
+                    acc[i][j] = T(0);
                 }
         }
     }
+    if (!F32) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tot[i][j] = acc[i][j];
+    }
 
-    // epilogue
     double pb[4], pp[4], pf[4], pm[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) { pb[i] = 0.0; pp[i] = 0.0; pf[i] = 0.0; pm[i] = 0.0; }
@@ -115,15 +129,15 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs a) {
         const int r = row0 + ty * 4 + i;
         if (r >= a.R) continue;
         const int sub = r / a.rows_per_sub;
-        float bsum = 0.f, psum = 0.f;
+        T bsum = T(0), psum = T(0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int q = col0 + tx * 4 + j;
             if (q >= a.N) continue;
-            const float p = tot[i][j] + cmp[i][j];
+            const T p = tot[i][j] + cmp[i][j];
             if (a.i > 1) {
                 const int g = a.hoff + q;
-                float l, u; int st;
+                T l, u; int st;
                 int slot = (a.slot_of && a.l) ? a.slot_of[g] : -1;
                 if (slot >= 0) {
                     size_t o = (size_t)sub * a.U + slot;
@@ -131,24 +145,24 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs a) {
                 } else {
                     l = a.root_l[g]; u = a.root_u[g]; st = a.root_state[g];
                 }
-                float d, e;
-                if (st > 0) { d = 1.f; e = 0.f; }
-                else if (st < 0) { d = 0.f; e = 0.f; }
-                else if (p >= 0.f) {
-                    if (a.alpha) d = a.alpha[((size_t)sub * a.m + (r % a.m)) * a.H + g];
-                    else d = (a.alpha_mode == CV_ALPHA_ONE) ? 1.f
-                           : (a.alpha_mode == CV_ALPHA_ZERO) ? 0.f : ((u >= -l) ? 1.f : 0.f);
-                    e = 0.f;
+                T d, e;
+                if (st > 0) { d = T(1); e = T(0); }
+                else if (st < 0) { d = T(0); e = T(0); }
+                else if (p >= T(0)) {
+                    if (a.alpha) d = (T)a.alpha[((size_t)sub * a.m + (r % a.m)) * a.H + g];
+                    else d = (a.alpha_mode == CV_ALPHA_ONE) ? T(1)
+                           : (a.alpha_mode == CV_ALPHA_ZERO) ? T(0) : ((u >= -l) ? T(1) : T(0));
+                    e = T(0);
                 } else {
-                    const float s = u / (u - l);
+                    const T s = u / (u - l);
                     d = s;
                     e = -s * l;
                 }
-                const float lam = p * d;
+                const T lam = p * d;
                 a.Aout[(size_t)r * a.N + q] = lam;
-                bsum = fmaf(p, e, bsum);
-                bsum = fmaf(lam, a.bnext[q], bsum);
-                psum = fmaf(fabsf(lam), a.Vnext[q], psum);
+                bsum = fma(p, e, bsum);
+                bsum = fma(lam, (T)a.bnext[q], bsum);
+                psum = fma(tabs(lam), (T)a.Vnext[q], psum);
             } else {
                 const size_t o = (size_t)sub * a.N + q;
                 const double lo = (double)a.lo[o], hi = (double)a.hi[o];
@@ -161,7 +175,6 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs a) {
         pb[i] = (double)bsum;
         pp[i] = (double)psum;
     }
-    // reduce across the 16 threads sharing these rows (tx = lane bits 0..3)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -185,8 +198,9 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs a) {
 }
 
 // Initial Lam^(k), its bias term and its pad weight.
+template <typename T>
 __global__ void k_bwd_init(int R, int nk, int mode, int m, const float* lam_init, const float* C,
-                           const float* t, const float* bk, const float* Vk, float* A,
+                           const float* t, const float* bk, const float* Vk, T* A,
                            double* acc_bias, double* acc_pad) {
     const int r = blockIdx.x * blockDim.y + threadIdx.y;
     if (r >= R) return;
@@ -196,7 +210,7 @@ __global__ void k_bwd_init(int R, int nk, int mode, int m, const float* lam_init
         if (mode == 0) v = lam_init[(size_t)r * nk + q];
         else if (mode == 1) v = C[(size_t)(r % m) * nk + q];
         else v = (q == r % nk) ? (((r / nk) & 1) ? -1.f : 1.f) : 0.f;
-        A[(size_t)r * nk + q] = v;
+        A[(size_t)r * nk + q] = (T)v;
         bs += (double)v * (double)bk[q];
         ps += (double)fabsf(v) * (double)Vk[q];
     }
@@ -208,24 +222,24 @@ __global__ void k_bwd_init(int R, int nk, int mode, int m, const float* lam_init
     if (threadIdx.x == 0) {
         double t0 = (mode == 1 && t) ? (double)t[r % m] : 0.0;
         acc_bias[r] = t0 + bs;
-        acc_pad[r] = GAMMA_BWD * ps;
+        acc_pad[r] = Gam<T>::v * ps;
     }
 }
 
-__global__ void k_bwd_reduce(int R, int ncb, const double* part_bias, const double* part_pad,
+__global__ void k_bwd_reduce(int R, int ncb, double gam, const double* part_bias, const double* part_pad,
                              double* acc_bias, double* acc_pad) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     double b = 0.0, p = 0.0;
     for (int c = 0; c < ncb; ++c) { b += part_bias[(size_t)r * ncb + c]; p += part_pad[(size_t)r * ncb + c]; }
     acc_bias[r] += b;
-    acc_pad[r] += GAMMA_BWD * p;
+    acc_pad[r] += gam * p;
 }
 
 // final: f = sum min(P lo, P hi) + bias - pad  (FP64), rounded down to FP32
 __global__ void k_bwd_final(int R, int ncb, int rows_per_sub, const double* part_f,
                             const double* part_fmag, const double* acc_bias, const double* acc_pad,
-                            const uint8_t* skip, float* lower, float* err, float* bias_out,
+                            const uint8_t* skip, float* lower, double* lower64, float* err, float* bias_out,
                             double* bias_raw, double* pad_raw) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
@@ -237,6 +251,7 @@ __global__ void k_bwd_final(int R, int ncb, int rows_per_sub, const double* part
     const double v = f + b - pad;
     const bool sk = skip && skip[r / rows_per_sub];
     if (lower) lower[r] = sk ? INFINITY : __double2float_rd(v);
+    if (lower64) lower64[r] = sk ? INFINITY : v;
     if (err) err[r] = sk ? 0.f : __double2float_ru(pad);
     if (bias_out) bias_out[r] = __double2float_rd(b - pad);
     if (bias_raw) bias_raw[r] = b;
@@ -245,29 +260,30 @@ __global__ void k_bwd_final(int R, int ncb, int rows_per_sub, const double* part
 
 }  // namespace
 
-cv_status cv_backward_raw(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
-                          const float* lam_init, const float* C, const float* t,
-                          const float* root_l, const float* root_u, const int8_t* root_state,
-                          const int* slot_of, const float* l, const float* u, const int8_t* mask,
-                          int U, const float* alpha, int alpha_mode, float* const* V,
-                          const float* lo, const float* hi, const uint8_t* skip,
-                          float* lower, float* err, float* lam0, float* bias_out,
-                          double* bias_raw, double* pad_raw,
-                          float* lamA, float* lamB, double* part_bias, double* part_pad,
-                          double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                          cudaStream_t st) {
+template <typename T>
+cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
+                        const float* lam_init, const float* C, const float* t,
+                        const T* root_l, const T* root_u, const int8_t* root_state,
+                        const int* slot_of, const T* l, const T* u, const int8_t* mask,
+                        int U, const float* alpha, int alpha_mode, float* const* V,
+                        const float* lo, const float* hi, const uint8_t* skip,
+                        float* lower, double* lower64, float* err, T* lam0, float* bias_out,
+                        double* bias_raw, double* pad_raw,
+                        T* lamA, T* lamB, double* part_bias, double* part_pad,
+                        double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
+                        cudaStream_t st) {
     const int nk = net->dims[k];
     {
         dim3 blk(32, 8);
         dim3 grd((R + 7) / 8);
-        k_bwd_init<<<grd, blk, 0, st>>>(R, nk, init_mode, m, lam_init, C, t, net->b[k], V[k], lamA,
-                                         acc_bias, acc_pad);
+        k_bwd_init<T><<<grd, blk, 0, st>>>(R, nk, init_mode, m, lam_init, C, t, net->b[k], V[k], lamA,
+                                            acc_bias, acc_pad);
         CV_LAUNCH_CHECK("k_bwd_init");
     }
-    float* cur = lamA;
-    float* nxt = lamB;
+    T* cur = lamA;
+    T* nxt = lamB;
     for (int i = k; i >= 1; --i) {
-        LayerArgs a;
+        LayerArgs<T> a;
         a.A = cur; a.W = net->W[i];
         a.R = R; a.K = net->dims[i]; a.N = net->dims[i - 1]; a.i = i;
         a.rows_per_sub = rows_per_sub; a.m = m > 0 ? m : 1;
@@ -283,21 +299,36 @@ cv_status cv_backward_raw(const cv_net* net, int R, int rows_per_sub, int k, int
         a.ncb = (a.N + BN - 1) / BN;
         a.part_bias = part_bias; a.part_pad = part_pad; a.part_f = part_f; a.part_fmag = part_fmag;
         dim3 grd(a.ncb, (R + BM - 1) / BM);
-        k_bwd_layer<<<grd, 256, 0, st>>>(a);
+        k_bwd_layer<T><<<grd, 256, 0, st>>>(a);
         CV_LAUNCH_CHECK("k_bwd_layer");
         if (i > 1) {
-            k_bwd_reduce<<<(R + 255) / 256, 256, 0, st>>>(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad);
+            k_bwd_reduce<<<(R + 255) / 256, 256, 0, st>>>(R, a.ncb, Gam<T>::v, part_bias, part_pad, acc_bias,
+                                                          acc_pad);
             CV_LAUNCH_CHECK("k_bwd_reduce");
-            float* tmp = cur; cur = nxt; nxt = tmp;
+            T* tmp = cur; cur = nxt; nxt = tmp;
         } else {
             k_bwd_final<<<(R + 255) / 256, 256, 0, st>>>(R, a.ncb, rows_per_sub, part_f, part_fmag,
-                                                         acc_bias, acc_pad, skip, lower, err, bias_out,
+                                                         acc_bias, acc_pad, skip, lower, lower64, err, bias_out,
                                                          bias_raw, pad_raw);
             CV_LAUNCH_CHECK("k_bwd_final");
         }
     }
     return CV_OK;
 }
+
+template cv_status cv_backward_t<float>(const cv_net*, int, int, int, int, int, const float*, const float*,
+                                        const float*, const float*, const float*, const int8_t*, const int*,
+                                        const float*, const float*, const int8_t*, int, const float*, int,
+                                        float* const*, const float*, const float*, const uint8_t*, float*,
+                                        double*, float*, float*, float*, double*, double*, float*, float*,
+                                        double*, double*, double*, double*, double*, double*, cudaStream_t);
+template cv_status cv_backward_t<double>(const cv_net*, int, int, int, int, int, const float*, const float*,
+                                         const float*, const double*, const double*, const int8_t*,
+                                         const int*, const double*, const double*, const int8_t*, int,
+                                         const float*, int, float* const*, const float*, const float*,
+                                         const uint8_t*, float*, double*, float*, double*, float*, double*,
+                                         double*, double*, double*, double*, double*, double*, double*,
+                                         double*, double*, cudaStream_t);
 
 // number of column blocks of the widest layer (sizing of the partial buffers)
 int cv_bwd_ncb_max(const cv_net* net) {

@@ -3,8 +3,9 @@
 // The root cache is the "Get_Constraints" / "Init_Clipper" step of the paper's Algorithm 5
 // (Section 3.4, cache and reuse): CROWN over every hidden layer k = 1..L-1 in turn, each a
 // back-substitution of +/- identity rows through layers k..1 with the relaxations of the
-// layers below, concretised over the root box.  The planes of the root-unstable neurons
-// are kept; every later round re-concretises them over its clipped box.
+// layers below, concretised over the root box.  It runs once per property, so it runs in FP64
+// (cv_backward_t<double>) and only the stored planes and bounds are FP32.  The planes of the
+// root-unstable neurons are kept; every later round re-concretises them over its clipped box.
 #include "cv_internal.cuh"
 
 #include <math.h>
@@ -32,25 +33,52 @@ __global__ void k_absmax(int n, const float* a, const float* b, float* out) {
     if (i < n) out[i] = fmaxf(fabsf(a[i]), fabsf(b[i]));
 }
 
-// layer k bounds from the backward results: rows < nk give l, rows >= nk give -u
-__global__ void k_root_bounds(int nk, int n0, const float* lower, const float* lam0, const double* bias_raw,
-                              const double* pad_raw, float* l_all, float* u_all, int8_t* st_all,
-                              float* zmag, float* lA, float* lc, float* uA, float* uc) {
+// Layer k bounds from the FP64 backward results (rows < nk: lower planes, rows >= nk: lower planes
+// of -z).  The FP64 planes are stored as FP32: A is rounded to nearest and the intercept absorbs the
+// rounding, c' = c - sum_q |A_q - fl(A_q)| max(|lo_q|,|hi_q|) (rounded down), so the stored plane
+// is valid over the root box.  Bounds are kept in FP64 for the deeper layers and rounded outward.
+__global__ void k_root_bounds(int nk, int n0, const double* lower64, const double* lam0, const double* bias_raw,
+                              const double* pad_raw, const float* xmag, double* l64, double* u64, float* l_all,
+                              float* u_all, int8_t* st_all, float* zmag, float* lA, float* lc, float* uA, float* uc) {
     const int j = blockIdx.x;
     if (j >= nk) return;
+    double dl = 0.0, du = 0.0, ml = 0.0, mu = 0.0;
     for (int q = threadIdx.x; q < n0; q += blockDim.x) {
-        lA[(size_t)j * n0 + q] = lam0[(size_t)j * n0 + q];
-        uA[(size_t)j * n0 + q] = -lam0[(size_t)(j + nk) * n0 + q];
+        const double a = lam0[(size_t)j * n0 + q];
+        const double b = -lam0[(size_t)(j + nk) * n0 + q];
+        const float af = (float)a, bf = (float)b;
+        lA[(size_t)j * n0 + q] = af;
+        uA[(size_t)j * n0 + q] = bf;
+        dl += fabs(a - (double)af) * (double)xmag[q];
+        du += fabs(b - (double)bf) * (double)xmag[q];
+        ml += fabs(a) * (double)xmag[q];
+        mu += fabs(b) * (double)xmag[q];
     }
+    __shared__ double red[4][32];
+    for (int off = 16; off > 0; off >>= 1) {
+        dl += __shfl_xor_sync(0xffffffffu, dl, off);
+        du += __shfl_xor_sync(0xffffffffu, du, off);
+        ml += __shfl_xor_sync(0xffffffffu, ml, off);
+        mu += __shfl_xor_sync(0xffffffffu, mu, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = dl; red[1][w] = du; red[2][w] = ml; red[3][w] = mu; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const float l = lower[j];
-        const float u = -lower[j + nk];
-        l_all[j] = l;
-        u_all[j] = u;
-        st_all[j] = (l >= 0.f) ? 1 : ((u <= 0.f) ? -1 : 0);
-        zmag[j] = fmaxf(fabsf(l), fabsf(u));
-        lc[j] = __double2float_rd(bias_raw[j] - pad_raw[j]);
-        uc[j] = __double2float_ru(-bias_raw[j + nk] + pad_raw[j + nk]);
+        double sdl = 0, sdu = 0, sml = 0, smu = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { sdl += red[0][i]; sdu += red[1][i]; sml += red[2][i]; smu += red[3][i]; }
+        const double l = lower64[j];
+        const double u = -lower64[j + nk];
+        l64[j] = l;
+        u64[j] = u;
+        l_all[j] = __double2float_rd(l);
+        u_all[j] = __double2float_ru(u);
+        st_all[j] = (l >= 0.0) ? 1 : ((u <= 0.0) ? -1 : 0);
+        zmag[j] = __double2float_ru(fmax(fabs(l), fabs(u)));
+        const double cl = bias_raw[j] - pad_raw[j];
+        const double cu = -bias_raw[j + nk] + pad_raw[j + nk];
+        lc[j] = __double2float_rd(cl - sdl - ldexp(fabs(cl) + sdl + sml, -45));
+        uc[j] = __double2float_ru(cu + sdu + ldexp(fabs(cu) + sdu + smu, -45));
     }
 }
 
@@ -301,25 +329,26 @@ extern "C" cv_status cv_cache_build(cv_net* net, const float* root_lo, const flo
     const int n0 = c->n0, H = net->H, L = net->L;
     CV_CUDA(cudaMemcpyAsync(c->root_lo, root_lo, n0 * sizeof(float), cudaMemcpyDeviceToDevice, st));
     CV_CUDA(cudaMemcpyAsync(c->root_hi, root_hi, n0 * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    // every hidden neuron's planes (temporary), pad weights built layer by layer
+    // FP64 back-substitution for every hidden layer; planes of all hidden neurons (temporary)
     float *AL = nullptr, *CL = nullptr, *AU = nullptr, *CU = nullptr, *xmag = nullptr, *zmag = nullptr;
+    double *l64 = nullptr, *u64 = nullptr;
     int nkmax = 1;
     for (int k = 1; k < L; ++k) nkmax = net->dims[k] > nkmax ? net->dims[k] : nkmax;
     const int R = 2 * nkmax;
     const int ncb = cv_bwd_ncb_max(net);
-    float *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr, *lower = nullptr;
+    double *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr, *lower64 = nullptr;
     double *pb = nullptr, *pp = nullptr, *pf = nullptr, *pm = nullptr, *ab = nullptr, *ap = nullptr, *br = nullptr, *pr = nullptr;
     bool ok = !(dalloc(&AL, (size_t)(H ? H : 1) * n0) || dalloc(&CL, H) || dalloc(&AU, (size_t)(H ? H : 1) * n0) ||
-                dalloc(&CU, H) || dalloc(&xmag, n0) || dalloc(&zmag, H) ||
+                dalloc(&CU, H) || dalloc(&xmag, n0) || dalloc(&zmag, H) || dalloc(&l64, H) || dalloc(&u64, H) ||
                 dalloc(&lamA, (size_t)R * net->wmax) || dalloc(&lamB, (size_t)R * net->wmax) ||
-                dalloc(&lam0, (size_t)R * n0) || dalloc(&lower, R) || dalloc(&pb, (size_t)R * ncb) ||
+                dalloc(&lam0, (size_t)R * n0) || dalloc(&lower64, R) || dalloc(&pb, (size_t)R * ncb) ||
                 dalloc(&pp, (size_t)R * ncb) || dalloc(&pf, (size_t)R * ncb) || dalloc(&pm, (size_t)R * ncb) ||
                 dalloc(&ab, R) || dalloc(&ap, R) || dalloc(&br, R) || dalloc(&pr, R));
     for (int i = 1; i <= L && ok; ++i) ok = !dalloc(&c->V[i], net->dims[i]);
     auto cleanup = [&]() {
-        cudaFree(AL); cudaFree(CL); cudaFree(AU); cudaFree(CU); cudaFree(xmag); cudaFree(zmag);
-        cudaFree(lamA); cudaFree(lamB); cudaFree(lam0); cudaFree(lower); cudaFree(pb); cudaFree(pp);
-        cudaFree(pf); cudaFree(pm); cudaFree(ab); cudaFree(ap); cudaFree(br); cudaFree(pr);
+        cudaFree(AL); cudaFree(CL); cudaFree(AU); cudaFree(CU); cudaFree(xmag); cudaFree(zmag); cudaFree(l64);
+        cudaFree(u64); cudaFree(lamA); cudaFree(lamB); cudaFree(lam0); cudaFree(lower64); cudaFree(pb);
+        cudaFree(pp); cudaFree(pf); cudaFree(pm); cudaFree(ab); cudaFree(ap); cudaFree(br); cudaFree(pr);
     };
     if (!ok) { cleanup(); cache_free(c); return CV_ENOMEM; }
     k_absmax<<<(n0 + 255) / 256, 256, 0, st>>>(n0, c->root_lo, c->root_hi, xmag);
@@ -329,14 +358,14 @@ extern "C" cv_status cv_cache_build(cv_net* net, const float* root_lo, const flo
     }
     for (int k = 1; k < L; ++k) {
         const int nk = net->dims[k], ho = net->hoff[k];
-        s = cv_backward_raw(net, 2 * nk, 2 * nk, k, 2, 1, nullptr, nullptr, nullptr, c->root_l, c->root_u,
-                            c->root_state, nullptr, nullptr, nullptr, nullptr, 0, nullptr, alpha_mode, c->V,
-                            c->root_lo, c->root_hi, nullptr, lower, nullptr, lam0, nullptr, br, pr, lamA, lamB,
-                            pb, pp, pf, pm, ab, ap, st);
+        s = cv_backward_t<double>(net, 2 * nk, 2 * nk, k, 2, 1, nullptr, nullptr, nullptr, l64, u64,
+                                  c->root_state, nullptr, nullptr, nullptr, nullptr, 0, nullptr, alpha_mode, c->V,
+                                  c->root_lo, c->root_hi, nullptr, nullptr, lower64, nullptr, lam0, nullptr, br, pr,
+                                  lamA, lamB, pb, pp, pf, pm, ab, ap, st);
         if (s) { cleanup(); cache_free(c); return s; }
-        k_root_bounds<<<nk, 256, 0, st>>>(nk, n0, lower, lam0, br, pr, c->root_l + ho, c->root_u + ho,
-                                          c->root_state + ho, zmag + ho, AL + (size_t)ho * n0, CL + ho,
-                                          AU + (size_t)ho * n0, CU + ho);
+        k_root_bounds<<<nk, 256, 0, st>>>(nk, n0, lower64, lam0, br, pr, xmag, l64 + ho, u64 + ho, c->root_l + ho,
+                                          c->root_u + ho, c->root_state + ho, zmag + ho, AL + (size_t)ho * n0,
+                                          CL + ho, AU + (size_t)ho * n0, CU + ho);
         dim3 blk(32, 8);
         k_padweights<<<(net->dims[k + 1] + 7) / 8, blk, 0, st>>>(net->dims[k + 1], nk, net->W[k + 1],
                                                                   net->b[k + 1], zmag + ho, c->V[k + 1]);

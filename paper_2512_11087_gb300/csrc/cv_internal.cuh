@@ -104,23 +104,25 @@ cv_status cv_launch_spec_backward(const cv_net* net, const cv_cache* cache, cons
                                   const float* u, const int8_t* mask, const uint8_t* infeasible,
                                   cv_batch_out* out, cudaStream_t st);
 
-// Back-substitution of R rows (cv_backward.cu).  Row r belongs to subdomain r / rows_per_sub.
-// Start layer k with Lam^(k): init_mode 0 explicit lam_init [R x n_k], 1 spec rows C[r % m]
-// (bias t[r % m]), 2 stacked +/- identity (row r -> +e_{r % n_k} for r < n_k, else -e).
-// Relaxation of hidden neuron g: per-subdomain (l, u, mask)[sub * U + slot_of[g]] when slot_of
-// and l are given and the neuron is cached, else the root arrays.  Outputs (all optional):
-// lower (rounded down), err (pad), lam0 [R x n0], bias_out (bias - pad, rounded down),
-// bias_raw / pad_raw (FP64).  lamA/lamB [R x wmax] and the partial buffers are scratch.
-cv_status cv_backward_raw(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
-                          const float* lam_init, const float* C, const float* t,
-                          const float* root_l, const float* root_u, const int8_t* root_state,
-                          const int* slot_of, const float* l, const float* u, const int8_t* mask,
-                          int U, const float* alpha, int alpha_mode, float* const* V,
-                          const float* lo, const float* hi, const uint8_t* skip,
-                          float* lower, float* err, float* lam0, float* bias_out,
-                          double* bias_raw, double* pad_raw,
-                          float* lamA, float* lamB, double* part_bias, double* part_pad,
-                          double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                          cudaStream_t st);
+// Back-substitution of R rows (cv_backward.cu), T = float (per-round spec bound) or double (root
+// cache).  Row r belongs to subdomain r / rows_per_sub.  Start layer k with Lam^(k): init_mode 0
+// explicit lam_init [R x n_k], 1 spec rows C[r % m] (bias t[r % m]), 2 stacked +/- identity
+// (row r -> +e_{r % n_k} for r < n_k, else -e).  Relaxation of hidden neuron g: per-subdomain
+// (l, u, mask)[sub * U + slot_of[g]] when slot_of and l are given and the neuron is cached, else
+// the root arrays.  Outputs (all optional): lower (rounded down), lower64, err (pad), lam0
+// [R x n0], bias_out (bias - pad, rounded down), bias_raw / pad_raw (FP64).  lamA/lamB
+// [R x wmax] and the partial buffers are scratch.
+template <typename T>
+cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
+                        const float* lam_init, const float* C, const float* t,
+                        const T* root_l, const T* root_u, const int8_t* root_state,
+                        const int* slot_of, const T* l, const T* u, const int8_t* mask,
+                        int U, const float* alpha, int alpha_mode, float* const* V,
+                        const float* lo, const float* hi, const uint8_t* skip,
+                        float* lower, double* lower64, float* err, T* lam0, float* bias_out,
+                        double* bias_raw, double* pad_raw,
+                        T* lamA, T* lamB, double* part_bias, double* part_pad,
+                        double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
+                        cudaStream_t st);
 int cv_bwd_ncb_max(const cv_net* net);
 

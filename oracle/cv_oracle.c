@@ -462,13 +462,14 @@ double orc_complete_clip(int n, const double* a, double c, int R, const double* 
 /* Algorithm 1 with the breakpoint positions taken in FP32, the precision in   */
 /* which the CUDA kernel takes that decision (the paper fixes none).  The     */
 /* decision arithmetic is fixed as follows, every operation IEEE-754 binary32 */
-/* round-to-nearest: the running multiplier combination af (initially a) is   */
-/* kept in FP32;  a' = fma(-beta_k, g_k, af);  q = (-a') * (1/g_k);  after a  */
-/* change  af = fma(beta_k_new, g_k, a').  Weights, the threshold and the     */
-/* cumulative sums stay FP64, and the returned dual value D(beta) (Eq. 4) is  */
-/* evaluated in FP64 at the FP32 multipliers.  Inputs a and G are FP32 values.*/
-/* Near a kink where two breakpoints coalesce, the order of nearly equal q's  */
-/* is decided by this arithmetic; both sides then follow the same ascent.     */
+/* round-to-nearest:  a'_j = a_j + sum_{p != k} beta_p G_pj  as the fma chain  */
+/* over p in increasing order starting from a_j (the multiplier sum of the    */
+/* text of Section 3.2, formed afresh for every row step);                    */
+/* q_j = (-a'_j) * (1/G_kj).  Weights, the threshold and the cumulative sums  */
+/* stay FP64, and the returned dual value D(beta) (Eq. 4) is evaluated in     */
+/* FP64 at the FP32 multipliers.  Inputs a and G are FP32 values.  Near a     */
+/* kink where two breakpoints coalesce, the order of nearly equal q's is      */
+/* decided by this arithmetic; both sides then follow the same ascent.        */
 typedef struct { float q; double w; int j; } bpf_t;
 static int bpf_cmp(const void* A, const void* B) {
     const bpf_t* x = (const bpf_t*)A; const bpf_t* y = (const bpf_t*)B;
@@ -480,19 +481,19 @@ static int bpf_cmp(const void* A, const void* B) {
 double orc_complete_clip_f32(int n, const float* a, double c, int R, const float* G,
                              const double* h, const double* lo, const double* hi,
                              int sweeps, float* beta, double* scale) {
-    float* af = (float*)malloc(sizeof(float) * (n > 0 ? n : 1));
     float* apr = (float*)malloc(sizeof(float) * (n > 0 ? n : 1));
     bpf_t* bp = (bpf_t*)malloc(sizeof(bpf_t) * (n > 0 ? n : 1));
-    for (int j = 0; j < n; ++j) af[j] = a[j];
     for (int k = 0; k < R; ++k) beta[k] = 0.0f;
     for (int sw = 0; sw < sweeps; ++sw) {
         for (int k = 0; k < R; ++k) {
             const float* gk = G + (long)k * n;
-            const float bk = beta[k];
             int nb = 0;
             double s0 = h[k];
             for (int j = 0; j < n; ++j) {
-                apr[j] = fmaf(-bk, gk[j], af[j]);
+                float v = a[j];
+                for (int p = 0; p < R; ++p)
+                    if (p != k) v = fmaf(beta[p], G[(long)p * n + j], v);
+                apr[j] = v;
                 double gd = (double)gk[j];
                 s0 += fmax(gd * lo[j], gd * hi[j]);
                 if (gk[j] != 0.0f) {
@@ -514,10 +515,7 @@ double orc_complete_clip_f32(int n, const float* a, double c, int R, const float
                 }
             }
             if (!(bn > 0.0f)) bn = 0.0f;
-            if (bn != bk) {
-                for (int j = 0; j < n; ++j) af[j] = fmaf(bn, gk[j], apr[j]);
-                beta[k] = bn;
-            }
+            beta[k] = bn;
         }
     }
     double val = c, sc = fabs(c);
@@ -532,7 +530,7 @@ double orc_complete_clip_f32(int n, const float* a, double c, int R, const float
         sc += va * fmax(fabs(lo[j]), fabs(hi[j]));
     }
     if (scale) *scale = sc;
-    free(af); free(apr); free(bp);
+    free(apr); free(bp);
     return val;
 }
 

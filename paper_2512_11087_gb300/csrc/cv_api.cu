@@ -48,6 +48,7 @@ cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int
     lay->part_fmag = take(R * ncb * sizeof(double));
     lay->acc_bias = take(R * sizeof(double));
     lay->acc_pad = take(R * sizeof(double));
+    lay->cc = take(cv_cc_workspace(B, lay->Rmax, net->dims[0]));
     lay->total = off;
     return CV_OK;
 }

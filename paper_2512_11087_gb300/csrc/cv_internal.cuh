@@ -77,9 +77,10 @@ __host__ __device__ inline size_t cv_align256(size_t x) { return (x + 255) & ~(s
 
 // workspace carving: returns the offset of the next 256-aligned block
 struct cv_ws_layout {
-    size_t rowflag, vmin, lam0, lam1, part_bias, part_pad, part_f, part_fmag, acc_bias, acc_pad, rowdesc, total;
+    size_t rowflag, vmin, lam0, lam1, part_bias, part_pad, part_f, part_fmag, acc_bias, acc_pad, rowdesc, cc, total;
     int R, Rmax, ncb;  // rows of the spec backward, max constraint rows, column blocks
 };
+size_t cv_cc_workspace(int B, int Rmax, int n0);  // complete-clipping region (cv_complete.cu)
 cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
                      int max_rows, cv_ws_layout* lay);
 

@@ -236,6 +236,36 @@ cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* 
                          cv_batch_out* out, const cv_options* opt,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* Size of the library's fixed device scratch array used by cv_relaxed_clip_static. */
+#define CV_STATIC_SCRATCH_BYTES (8u << 20)
+
+/* Constraint rows, pre-check and relaxed clipping (the first steps of cv_bound_batch) without
+ * any device allocation and without a caller workspace.  This entry has no counterpart in the
+ * paper; it exists for callers that cannot allocate device memory when they bound subdomains:
+ * a host framework whose caching allocator or memory pool must own every device byte, or a
+ * latency-bound loop where cudaMalloc / cudaFree, which may synchronise the device, are not
+ * allowed once the run has started.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine; its scratch is a fixed array of CV_STATIC_SCRATCH_BYTES inside this library, which
+ * every GPU that loads the library holds until the process exits.
+ *  in        the batch as for cv_bound_batch (B, lo, hi, splits, extra rows, max_splits,
+ *            max_rows); spec rows, bounds, alpha and targets are not read
+ *  lo_clip, hi_clip [B x n_0]  device outputs, identical to cv_bound_batch's with the same
+ *            relaxed option
+ *  infeasible [B]  device output: the subdomains the pre-check or relaxed clipping finds empty
+ *            (cv_bound_batch can flag more in its later steps)
+ *  relaxed   1: apply relaxed clipping; 0: only the pre-check (the box is copied)
+ * Limit: B x (max_splits + max_rows) x 9 bytes (plus 256 bytes of alignment) must fit in the
+ * array; larger batches return CV_EWORKSPACE before anything is launched.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make it before any stream capture.  All calls share the array and
+ * it keeps the last call's contents; calls whose kernels overlap on the GPU (concurrent streams,
+ * host threads) race on it, so serialise them. */
+cv_status cv_relaxed_clip_static(cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                                 float* lo_clip, float* hi_clip, uint8_t* infeasible, int relaxed,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ def load():
         "cv_timer_create": ([ctypes.POINTER(P)], I),
         "cv_timer_destroy": ([P], None),
         "cv_timer_read": ([P, P, P, P], I),
+        "cv_relaxed_clip_static": ([P, P, P, P, P, P, I, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -99,7 +100,7 @@ def exported_symbols():
     return [n for n in ("cv_last_error", "cv_net_create", "cv_net_destroy", "cv_net_dims", "cv_device_status",
                         "cv_cache_build", "cv_cache_create", "cv_cache_size", "cv_cache_read", "cv_cache_destroy",
                         "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
-                        "cv_timer_destroy", "cv_timer_read")]
+                        "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static")]
 
 
 def _check(st):
@@ -264,3 +265,10 @@ def cv_timer_read(t):
     steps = ctypes.c_longlong()
     _check(load().cv_timer_read(t, ctypes.cast(ms, P), ctypes.byref(n), ctypes.byref(steps)))
     return list(ms), n.value, steps.value
+
+
+def cv_relaxed_clip_static(net, cache, bi, lo_clip, hi_clip, infeasible, relaxed=1, stream=None):
+    """Rows, pre-check and relaxed clipping without any device allocation (scratch in the
+    library's fixed device array); for callers that must not allocate device memory."""
+    _check(load().cv_relaxed_clip_static(net, cache, ctypes.byref(bi), ptr(lo_clip), ptr(hi_clip), ptr(infeasible),
+                                         int(relaxed), stream_ptr(stream)))

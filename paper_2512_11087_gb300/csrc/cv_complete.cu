@@ -26,8 +26,9 @@
 // rows (g, 1/g, fixed-point weights, threshold) to the workspace once; a single-block scan turns
 // the per-subdomain task counts into work items of TPI (target, side) tasks, subdomains with more
 // rows first; a persistent k_complete grid (one block per resident slot) takes items from an
-// atomic ticket, stages the item's rows in shared memory and runs one warp per task with the
-// objective held in registers (n0/32 values per lane).
+// atomic ticket, stages the item's rows in shared memory and runs one warp per task; each warp
+// keeps its breakpoint keys in its own shared buffer, so the element loops stay short and rolled
+// (small code, few registers, 32 resident warps per SM).
 #include "cv_internal.cuh"
 
 #include <climits>
@@ -37,7 +38,7 @@ namespace {
 
 constexpr int RMAX_CC = 8;  // rows per subdomain handled by complete clipping
 constexpr int TPI = 64;     // (target, side) tasks per work item
-constexpr int NWARP = 8;    // warps per block
+constexpr int NWARP = 16;   // warps per block
 
 __device__ __forceinline__ unsigned fkey(float q) {
     unsigned u = __float_as_uint(q);
@@ -199,17 +200,18 @@ __global__ void __launch_bounds__(1024) k_cc_scan(CCArgs a) {
     }
 }
 
-template <int NE>
 __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n0 = a.n0, Rs = a.Rs, B = a.B;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // shared layout: w64 [Rs][n0] | g [Rs][n0] | rg [Rs][n0] | lo [n0] | hi [n0]
+    const int n0r = (n0 + 31) & ~31;
+    // shared: w64 [Rs][n0] | g [Rs][n0] | rg [Rs][n0] | lo [n0] | hi [n0] | keys [NWARP][n0r]
     long long* w64 = (long long*)smem;
     float* gs = (float*)(w64 + (size_t)Rs * n0);
     float* rg = gs + (size_t)Rs * n0;
     float* slo = rg + (size_t)Rs * n0;
     float* shi = slo + n0;
+    unsigned* keys = (unsigned*)(shi + n0) + (size_t)warp * n0r;  // this warp's breakpoint keys
     __shared__ long long T64[RMAX_CC];
     __shared__ float hrow[RMAX_CC];
     __shared__ double Sg[RMAX_CC];
@@ -281,12 +283,6 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
             const float* ap = side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0;
             const float sa = side ? -1.f : 1.f;
             const float c0 = side ? -a.uc[c] : a.lc[c];
-            float av[NE];  // the target plane (objective a)
-#pragma unroll
-            for (int e = 0; e < NE; ++e) {
-                const int j = lane + 32 * e;
-                av[e] = (j < n0) ? sa * ap[j] : 0.f;
-            }
             float* beta = sbeta[warp];
             int* jprev = sjprev[warp];
             if (lane < RMAX_CC) { beta[lane] = 0.f; jprev[lane] = -1; }
@@ -300,37 +296,29 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                     const float* rk = rg + (size_t)k * n0;
                     const long long* wk = w64 + (size_t)k * n0;
                     const int jp = jprev[k];
-                    unsigned key[NE];
-                    unsigned mykp = 0xffffffffu;
-#pragma unroll
-                    for (int e = 0; e < NE; ++e) {
-                        const int j = lane + 32 * e;
-                        if (j < n0) {
-                            // a' = a + sum_{p != k} beta_p g_p, fma chain in increasing p
-                            float apr = av[e];
-                            for (int p = 0; p < R; ++p)
-                                if (p != k) apr = fmaf(beta[p], gs[(size_t)p * n0 + j], apr);
-                            const float r = rk[j];
-                            key[e] = (r != 0.f) ? fkey(-apr * r) : 0xffffffffu;
-                        } else {
-                            key[e] = 0xffffffffu;
-                        }
-                        if (jp >= 0 && (jp >> 5) == e) mykp = key[e];
-                    }
-                    const unsigned kp = (jp >= 0) ? __shfl_sync(0xffffffffu, mykp, jp & 31) : 0xffffffffu;
+                    // a' = a + sum_{p != k} beta_p g_p (fma chain in increasing p), key of q = -a' / g_k
+                    auto key_of = [&](int j) -> unsigned {
+                        float apr = sa * ap[j];
+                        for (int p = 0; p < R; ++p)
+                            if (p != k) apr = fmaf(beta[p], gs[(size_t)p * n0 + j], apr);
+                        const float r = rk[j];
+                        return (r != 0.f) ? fkey(-apr * r) : 0xffffffffu;
+                    };
+                    unsigned kp = 0xffffffffu;
+                    if (jp >= 0) kp = __shfl_sync(0xffffffffu, key_of(jp), 0);
                     const bool warm = kp > KZERO && kp <= KINF;
                     // F(x) = sum of the weights of the breakpoints with key <= x (exact integers)
                     unsigned long long f0 = 0, ftot = 0, flt = 0, fle = 0;
-#pragma unroll
-                    for (int e = 0; e < NE; ++e) {
-                        const int j = lane + 32 * e;
-                        const unsigned long long w = (j < n0) ? (unsigned long long)wk[j] : 0ull;
-                        const unsigned kk = key[e];
+                    for (int j = lane; j < n0; j += 32) {
+                        const unsigned kk = key_of(j);
+                        keys[j] = kk;
+                        const unsigned long long w = (unsigned long long)wk[j];
                         f0 += (kk <= KZERO) ? w : 0ull;
                         ftot += (kk <= KINF) ? w : 0ull;
                         flt += (kk < kp) ? w : 0ull;
                         fle += (kk <= kp) ? w : 0ull;
                     }
+                    __syncwarp();
                     const long long T = T64[k];
                     const long long F0 = warp_sum64(f0), Ftot = warp_sum64(ftot);
                     const long long Flt = warp_sum64(flt), Fle = warp_sum64(fle);
@@ -354,9 +342,8 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                         unsigned ks = 0;
                         for (int it = 0; it < 96; ++it) {
                             unsigned cmin = 0xffffffffu, cmax = 0u;
-#pragma unroll
-                            for (int e = 0; e < NE; ++e) {
-                                const unsigned kk = key[e];
+                            for (int j = lane; j < n0; j += 32) {
+                                const unsigned kk = keys[j];
                                 if (kk > lo && kk <= hi) { cmin = min(cmin, kk); cmax = max(cmax, kk); }
                             }
                             cmin = __reduce_min_sync(0xffffffffu, cmin);
@@ -374,12 +361,8 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                                 mid = lo + off;
                             }
                             unsigned long long fm = 0;
-#pragma unroll
-                            for (int e = 0; e < NE; ++e) {
-                                const int j = lane + 32 * e;
-                                const unsigned long long w = (j < n0) ? (unsigned long long)wk[j] : 0ull;
-                                fm += (key[e] <= mid) ? w : 0ull;
-                            }
+                            for (int j = lane; j < n0; j += 32)
+                                fm += (keys[j] <= mid) ? (unsigned long long)wk[j] : 0ull;
                             const long long Fm = warp_sum64(fm);
                             if (Fm >= T) { hi = mid; Fhi = Fm; }
                             else { lo = mid; Flo = Fm; }
@@ -387,12 +370,12 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                         bn = fkey_inv(ks);
                         if (!(bn > 0.f)) bn = 0.f;
                         // the element holding the selected breakpoint (lowest index among ties)
-                        int mine = 0x7fffffff;
-#pragma unroll
-                        for (int e = NE - 1; e >= 0; --e)
-                            if (key[e] == ks) mine = lane + 32 * e;
-                        const unsigned bal = __ballot_sync(0xffffffffu, mine != 0x7fffffff);
-                        jn = bal ? __shfl_sync(0xffffffffu, mine, __ffs(bal) - 1) : -1;
+                        jn = -1;
+                        for (int j0 = 0; j0 < n0 && jn < 0; j0 += 32) {
+                            const int j = j0 + lane;
+                            const unsigned bal = __ballot_sync(0xffffffffu, j < n0 && keys[j] == ks);
+                            if (bal) jn = j0 + __ffs(bal) - 1;
+                        }
                     }
                     const float bk = beta[k];
                     __syncwarp();
@@ -404,14 +387,10 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
             }
             // dual objective at beta, FP32 with its rounding bound
             float part = 0.f;
-#pragma unroll
-            for (int e = 0; e < NE; ++e) {
-                const int j = lane + 32 * e;
-                if (j < n0) {
-                    float v = av[e];
-                    for (int k = 0; k < R; ++k) v = fmaf(beta[k], gs[(size_t)k * n0 + j], v);
-                    part += fminf(v * slo[j], v * shi[j]);
-                }
+            for (int j = lane; j < n0; j += 32) {
+                float v = sa * ap[j];
+                for (int k = 0; k < R; ++k) v = fmaf(beta[k], gs[(size_t)k * n0 + j], v);
+                part += fminf(v * slo[j], v * shi[j]);
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
@@ -421,7 +400,7 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                 cst = fmaf(beta[k], hrow[k], cst);
                 scale += (double)beta[k] * (Sg[k] + fabs((double)hrow[k]));
             }
-            const double gam = (double)(R + NE + 12) * CV_U32;
+            const double gam = (double)(R + (n0 + 31) / 32 + 12) * CV_U32;
             const float pad = __double2float_ru(gam * scale * 1.0001);
             float val = __fsub_rd(__fadd_rd(part, cst), pad);
             const float valhi = __fadd_ru(__fadd_ru(part, cst), pad);
@@ -473,20 +452,20 @@ __global__ void k_cc_post(CCArgs a) {
     if (threadIdx.x == 0 && bad) a.infeasible[b] = 1;
 }
 
-template <int NE>
-cv_status launch_ne(const CCArgs& a, int* launches, cudaStream_t st) {
-    const size_t smem = (size_t)a.Rs * a.n0 * (8 + 4 + 4) + 2 * (size_t)a.n0 * 4;
-    if (smem > 200 * 1024) {
+cv_status launch_cc(const CCArgs& a, int* launches, cudaStream_t st) {
+    const size_t n0r = (a.n0 + 31) & ~31;
+    const size_t smem = (size_t)a.Rs * a.n0 * (8 + 4 + 4) + 2 * (size_t)a.n0 * 4 + (size_t)NWARP * n0r * 4;
+    if (smem > 220 * 1024) {
         cv_set_error("complete clipping: input dimension too large for the shared-memory row cache");
         return CV_EUNSUPPORTED;
     }
-    CV_CUDA(cudaFuncSetAttribute(k_complete<NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CV_CUDA(cudaFuncSetAttribute(k_complete, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per = 0;
     CV_CUDA(cudaGetDevice(&dev));
     CV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_complete<NE>, NWARP * 32, smem));
+    CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_complete, NWARP * 32, smem));
     if (per < 1) per = 1;
-    k_complete<NE><<<sms * per, NWARP * 32, smem, st>>>(a);
+    k_complete<<<sms * per, NWARP * 32, smem, st>>>(a);
     CV_LAUNCH_CHECK("k_complete");
     ++*launches;
     return CV_OK;
@@ -552,19 +531,7 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     k_cc_scan<<<1, 1024, 0, st>>>(a);
     CV_LAUNCH_CHECK("k_cc_scan");
     *launches += 3;  // prep, scan, post
-    const int ne = (cache->n0 + 31) / 32;
-    cv_status s;
-    if (ne <= 1) s = launch_ne<1>(a, launches, st);
-    else if (ne <= 2) s = launch_ne<2>(a, launches, st);
-    else if (ne <= 4) s = launch_ne<4>(a, launches, st);
-    else if (ne <= 8) s = launch_ne<8>(a, launches, st);
-    else if (ne <= 16) s = launch_ne<16>(a, launches, st);
-    else if (ne <= 25) s = launch_ne<25>(a, launches, st);
-    else if (ne <= 32) s = launch_ne<32>(a, launches, st);
-    else {
-        cv_set_error("complete clipping: input dimension above 1024 is not supported by this build");
-        return CV_EUNSUPPORTED;
-    }
+    cv_status s = launch_cc(a, launches, st);
     if (s) return s;
     k_cc_post<<<in->B, 256, 0, st>>>(a);
     CV_LAUNCH_CHECK("k_cc_post");

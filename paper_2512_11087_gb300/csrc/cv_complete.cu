@@ -9,8 +9,9 @@
 // supergradient), clamped at 0.  This is the sorted-breakpoint rule of Algorithm 1 written as
 // a weighted quantile, so no sort is needed.  The quantile is found by shrinking a key bracket
 // (lo, hi] with F(lo) < T <= F(hi): each pass takes the min and max breakpoint key inside it
-// (done when they coincide) and splits it at an interpolated or halved pivot; the previous
-// sweep's breakpoint is tried first (coordinate ascent mostly re-selects it).
+// (done when they coincide) and splits it at the pivot interpolated from the weight still
+// needed (after eight passes, every other pass halves the range instead, which bounds the
+// count); the previous sweep's breakpoint is tried first (coordinate ascent mostly re-selects it).
 //
 // Decision arithmetic (reproduced by the oracle): a'_j = a_j + sum_{p != k} beta_p g_pj as an FP32
 // fma chain over increasing p, q_j = (-a'_j) * fl(1/g_kj), compared through an order-preserving
@@ -309,19 +310,30 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                     const bool warm = kp > KZERO && kp <= KINF;
                     // F(x) = sum of the weights of the breakpoints with key <= x (exact integers)
                     unsigned long long f0 = 0, ftot = 0, flt = 0, fle = 0;
-                    for (int j = lane; j < n0; j += 32) {
-                        const unsigned kk = key_of(j);
-                        keys[j] = kk;
-                        const unsigned long long w = (unsigned long long)wk[j];
-                        f0 += (kk <= KZERO) ? w : 0ull;
-                        ftot += (kk <= KINF) ? w : 0ull;
-                        flt += (kk < kp) ? w : 0ull;
-                        fle += (kk <= kp) ? w : 0ull;
+                    if (warm) {
+                        for (int j = lane; j < n0; j += 32) {
+                            const unsigned kk = key_of(j);
+                            keys[j] = kk;
+                            const unsigned long long w = (unsigned long long)wk[j];
+                            f0 += (kk <= KZERO) ? w : 0ull;
+                            ftot += (kk <= KINF) ? w : 0ull;
+                            flt += (kk < kp) ? w : 0ull;
+                            fle += (kk <= kp) ? w : 0ull;
+                        }
+                    } else {
+                        for (int j = lane; j < n0; j += 32) {
+                            const unsigned kk = key_of(j);
+                            keys[j] = kk;
+                            const unsigned long long w = (unsigned long long)wk[j];
+                            f0 += (kk <= KZERO) ? w : 0ull;
+                            ftot += (kk <= KINF) ? w : 0ull;
+                        }
                     }
                     __syncwarp();
                     const long long T = T64[k];
                     const long long F0 = warp_sum64(f0), Ftot = warp_sum64(ftot);
-                    const long long Flt = warp_sum64(flt), Fle = warp_sum64(fle);
+                    long long Flt = 0, Fle = 0;
+                    if (warm) { Flt = warp_sum64(flt); Fle = warp_sum64(fle); }
                     float bn = 0.f;
                     int jn = -1;
                     if (F0 >= T || Ftot < T) {
@@ -338,7 +350,8 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                             else { hi = kp - 1; Fhi = Flt; }
                         }
                         // shrink to a single breakpoint key: each pass takes the min and max key in the
-                        // bracket (done when equal) and splits at an interpolated or halved pivot
+                        // bracket (done when equal) and splits at the pivot interpolated from the weight
+                        // still needed (halving every other pass after the eighth)
                         unsigned ks = 0;
                         for (int it = 0; it < 96; ++it) {
                             unsigned cmin = 0xffffffffu, cmax = 0u;
@@ -352,7 +365,7 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                             lo = cmin - 1;  // F unchanged: no breakpoint in (lo, cmin)
                             hi = cmax;      // F unchanged: no breakpoint in (cmax, hi]
                             unsigned mid;
-                            if (it & 1) {
+                            if (it >= 8 && (it & 1)) {
                                 mid = lo + ((hi - lo) >> 1);
                             } else {
                                 const float fr = (float)(T - Flo) / (float)(Fhi - Flo);

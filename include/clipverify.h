@@ -236,6 +236,48 @@ cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* 
                          cv_batch_out* out, const cv_options* opt,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- alpha optimisation */
+
+/* Inputs of the slope gradient (device pointers).
+ *  B, m        subdomains and spec rows
+ *  lo, hi      [B x n_0] box of every subdomain (for instance the clipped box of a round)
+ *  l, u, mask  [B x U] bounds and stability of the cached neurons (for instance from
+ *              cv_bound_batch); the other hidden neurons use their root state
+ *  C, t        spec rows [m x n_L], thresholds [m]
+ *  alpha       [B x m x n_hidden] lower slopes of unstable neurons, in [0, 1]
+ *  grad_f      [B x m] upstream gradient of the bounds; NULL = ones */
+typedef struct cv_alpha_in {
+    int B, m;
+    const float* lo;
+    const float* hi;
+    const float* l;
+    const float* u;
+    const int8_t* mask;
+    const float* C;
+    const float* t;
+    const float* alpha;
+    const float* grad_f;
+} cv_alpha_in;
+
+/* Bytes of workspace cv_alpha_grad needs for B subdomains and m spec rows. */
+cv_status cv_alpha_grad_workspace(const cv_net* net, int B, int m, size_t* bytes);
+
+/* The spec lower bounds f [B x m] (as cv_bound_batch's back-substitution with these slopes,
+ * padded outward; may be NULL) and the gradient of sum_r grad_f[b,r] f[b,r] with respect to
+ * alpha, grad_alpha [B x m x n_hidden] (zero where a slope does not enter the bound: stable
+ * neurons and neurons whose upper relaxation was selected).  alpha-CROWN's slope gradient
+ * (the "optimized" alpha of the paper's ReLU relaxation Lemma), by a hand-written reverse
+ * sweep of the back-substitution with the relaxation choices of the forward pass held fixed.
+ * The gradient is FP32 and carries no pad. */
+cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_alpha_in* in, float* lower,
+                        float* grad_alpha, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One Adam ascent step on n slopes (device arrays alpha, m1, m2, grad), t >= 1 the step count,
+ * followed by clamping alpha to [0, 1] (the paper's alpha optimisation uses Adam with learning
+ * rate 0.1 decayed by 0.98 per iteration; the caller passes the decayed lr). */
+cv_status cv_alpha_adam(float* alpha, float* m1, float* m2, const float* grad, long long n, int t,
+                        float lr, float beta1, float beta2, float eps, void* stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Size of the library's fixed device scratch array used by cv_relaxed_clip_static. */

@@ -52,6 +52,11 @@ class cv_batch_in(ctypes.Structure):
                 ("t", P), ("alpha", P), ("tgt_off", P), ("tgt_ids", P)]
 
 
+class cv_alpha_in(ctypes.Structure):
+    _fields_ = [("B", I), ("m", I), ("lo", P), ("hi", P), ("l", P), ("u", P), ("mask", P), ("C", P), ("t", P),
+                ("alpha", P), ("grad_f", P)]
+
+
 class cv_batch_out(ctypes.Structure):
     _fields_ = [("lower", P), ("lo_clip", P), ("hi_clip", P), ("l", P), ("u", P), ("mask", P),
                 ("infeasible", P), ("verified", P), ("err_bound", P), ("final_A", P), ("final_c", P)]
@@ -87,6 +92,10 @@ def load():
         "cv_timer_destroy": ([P], None),
         "cv_timer_read": ([P, P, P, P], I),
         "cv_relaxed_clip_static": ([P, P, P, P, P, P, I, P], I),
+        "cv_alpha_grad_workspace": ([P, I, I, P], I),
+        "cv_alpha_grad": ([P, P, P, P, P, P, ctypes.c_size_t, P], I),
+        "cv_alpha_adam": ([P, P, P, P, ctypes.c_longlong, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -100,7 +109,8 @@ def exported_symbols():
     return [n for n in ("cv_last_error", "cv_net_create", "cv_net_destroy", "cv_net_dims", "cv_device_status",
                         "cv_cache_build", "cv_cache_create", "cv_cache_size", "cv_cache_read", "cv_cache_destroy",
                         "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
-                        "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static")]
+                        "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
+                        "cv_alpha_grad", "cv_alpha_adam")]
 
 
 def _check(st):
@@ -272,3 +282,27 @@ def cv_relaxed_clip_static(net, cache, bi, lo_clip, hi_clip, infeasible, relaxed
     library's fixed device array); for callers that must not allocate device memory."""
     _check(load().cv_relaxed_clip_static(net, cache, ctypes.byref(bi), ptr(lo_clip), ptr(hi_clip), ptr(infeasible),
                                          int(relaxed), stream_ptr(stream)))
+
+
+def make_alpha_in(B, m, lo, hi, l, u, mask, C, t, alpha, grad_f=None):
+    ai = cv_alpha_in()
+    ai.B, ai.m = int(B), int(m)
+    for name, v in dict(lo=lo, hi=hi, l=l, u=u, mask=mask, C=C, t=t, alpha=alpha, grad_f=grad_f).items():
+        setattr(ai, name, ptr(v))
+    return ai
+
+
+def cv_alpha_grad_workspace(net, B, m):
+    n = ctypes.c_size_t()
+    _check(load().cv_alpha_grad_workspace(net, int(B), int(m), ctypes.byref(n)))
+    return n.value
+
+
+def cv_alpha_grad(net, cache, ai, lower, grad_alpha, workspace, workspace_bytes, stream=None):
+    _check(load().cv_alpha_grad(net, cache, ctypes.byref(ai), ptr(lower), ptr(grad_alpha), ptr(workspace),
+                                int(workspace_bytes), stream_ptr(stream)))
+
+
+def cv_alpha_adam(alpha, m1, m2, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().cv_alpha_adam(ptr(alpha), ptr(m1), ptr(m2), ptr(grad), int(alpha.numel()), int(t), float(lr),
+                                float(beta1), float(beta2), float(eps), stream_ptr(stream)))

@@ -160,7 +160,7 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
                             (float*)(ws + lay.lam0), (float*)(ws + lay.lam1), (double*)(ws + lay.part_bias),
                             (double*)(ws + lay.part_pad), (double*)(ws + lay.part_f),
                             (double*)(ws + lay.part_fmag), (double*)(ws + lay.acc_bias),
-                            (double*)(ws + lay.acc_pad), st);
+                            (double*)(ws + lay.acc_pad), nullptr, st);
         if (s) return s;
         launches += 1 + 2 * net->L;
     }

@@ -43,6 +43,7 @@ struct LayerArgs {
     T* Aout;              // Lam^(i-1) [R x N]
     const float* lo; const float* hi;  // [nsub x N] (i == 1)
     T* lam0;              // optional [R x N]
+    T* keepP;             // optional [R x N]: the product P^(i) (i > 1), kept for the alpha adjoint
     double* part_bias; double* part_pad; double* part_f; double* part_fmag; int ncb;
 };
 
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs<T> a) {
                 }
                 const T lam = p * d;
                 a.Aout[(size_t)r * a.N + q] = lam;
+                if (a.keepP) a.keepP[(size_t)r * a.N + q] = p;
                 bsum = fma(p, e, bsum);
                 bsum = fma(lam, (T)a.bnext[q], bsum);
                 psum = fma(tabs(lam), (T)a.Vnext[q], psum);
@@ -271,7 +273,7 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         double* bias_raw, double* pad_raw,
                         T* lamA, T* lamB, double* part_bias, double* part_pad,
                         double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                        cudaStream_t st) {
+                        T* const* keepP, cudaStream_t st) {
     const int nk = net->dims[k];
     {
         dim3 blk(32, 8);
@@ -296,6 +298,7 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
         a.Vnext = (i > 1) ? V[i - 1] : nullptr;
         a.Aout = nxt;
         a.lo = lo; a.hi = hi; a.lam0 = lam0;
+        a.keepP = (keepP && i > 1) ? keepP[i] : nullptr;
         a.ncb = (a.N + BN - 1) / BN;
         a.part_bias = part_bias; a.part_pad = part_pad; a.part_f = part_f; a.part_fmag = part_fmag;
         dim3 grd(a.ncb, (R + BM - 1) / BM);
@@ -321,14 +324,15 @@ template cv_status cv_backward_t<float>(const cv_net*, int, int, int, int, int, 
                                         const float*, const float*, const int8_t*, int, const float*, int,
                                         float* const*, const float*, const float*, const uint8_t*, float*,
                                         double*, float*, float*, float*, double*, double*, float*, float*,
-                                        double*, double*, double*, double*, double*, double*, cudaStream_t);
+                                        double*, double*, double*, double*, double*, double*, float* const*,
+                                        cudaStream_t);
 template cv_status cv_backward_t<double>(const cv_net*, int, int, int, int, int, const float*, const float*,
                                          const float*, const double*, const double*, const int8_t*,
                                          const int*, const double*, const double*, const int8_t*, int,
                                          const float*, int, float* const*, const float*, const float*,
                                          const uint8_t*, float*, double*, float*, double*, float*, double*,
                                          double*, double*, double*, double*, double*, double*, double*,
-                                         double*, double*, cudaStream_t);
+                                         double*, double*, double* const*, cudaStream_t);
 
 // number of column blocks of the widest layer (sizing of the partial buffers)
 int cv_bwd_ncb_max(const cv_net* net) {

@@ -361,7 +361,7 @@ extern "C" cv_status cv_cache_build(cv_net* net, const float* root_lo, const flo
         s = cv_backward_t<double>(net, 2 * nk, 2 * nk, k, 2, 1, nullptr, nullptr, nullptr, l64, u64,
                                   c->root_state, nullptr, nullptr, nullptr, nullptr, 0, nullptr, alpha_mode, c->V,
                                   c->root_lo, c->root_hi, nullptr, nullptr, lower64, nullptr, lam0, nullptr, br, pr,
-                                  lamA, lamB, pb, pp, pf, pm, ab, ap, st);
+                                  lamA, lamB, pb, pp, pf, pm, ab, ap, nullptr, st);
         if (s) { cleanup(); cache_free(c); return s; }
         k_root_bounds<<<nk, 256, 0, st>>>(nk, n0, lower64, lam0, br, pr, xmag, l64 + ho, u64 + ho, c->root_l + ho,
                                           c->root_u + ho, c->root_state + ho, zmag + ho, AL + (size_t)ho * n0,

@@ -111,8 +111,9 @@ cv_status cv_launch_spec_backward(const cv_net* net, const cv_cache* cache, cons
 // (row r -> +e_{r % n_k} for r < n_k, else -e).  Relaxation of hidden neuron g: per-subdomain
 // (l, u, mask)[sub * U + slot_of[g]] when slot_of and l are given and the neuron is cached, else
 // the root arrays.  Outputs (all optional): lower (rounded down), lower64, err (pad), lam0
-// [R x n0], bias_out (bias - pad, rounded down), bias_raw / pad_raw (FP64).  lamA/lamB
-// [R x wmax] and the partial buffers are scratch.
+// [R x n0], bias_out (bias - pad, rounded down), bias_raw / pad_raw (FP64), keepP[i] [R x n_{i-1}]
+// (the products P^(i), i = 2..k, for the alpha adjoint).  lamA/lamB [R x wmax] and the partial
+// buffers are scratch.
 template <typename T>
 cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
                         const float* lam_init, const float* C, const float* t,
@@ -124,6 +125,6 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         double* bias_raw, double* pad_raw,
                         T* lamA, T* lamB, double* part_bias, double* part_pad,
                         double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                        cudaStream_t st);
+                        T* const* keepP, cudaStream_t st);
 int cv_bwd_ncb_max(const cv_net* net);
 

@@ -101,3 +101,59 @@ class Round:
         capi.cv_bound_batch(self.net.handle, self.net.cache, bi, self.bo, self.opt, self.ws, self.ws_bytes,
                             stream)
         return self.out
+
+
+class AlphaBound(torch.autograd.Function):
+    """Spec lower bounds as a differentiable function of the slopes alpha [B x m x H].
+
+    Forward and backward both run in the library (cv_alpha_grad): the forward computes the
+    bounds and the gradient of sum f (each bound row depends only on its own slope row, so the
+    gradient for any upstream gradient is that one scaled row by row); backward applies the
+    upstream gradient."""
+
+    @staticmethod
+    def forward(ctx, alpha, state):
+        lower, grad = state.bound_and_grad(alpha)
+        ctx.save_for_backward(grad)
+        return lower
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (grad,) = ctx.saved_tensors
+        return grad * grad_out.unsqueeze(-1), None
+
+
+class AlphaState:
+    """Inputs that stay fixed during slope optimisation, plus the workspace."""
+
+    def __init__(self, net: Net, lo, hi, l, u, mask, C, t):
+        self.net = net
+        self.B, self.n0 = lo.shape
+        self.m = C.shape[0]
+        self.lo, self.hi, self.l, self.u, self.mask, self.C, self.t = lo, hi, l, u, mask, C, t
+        self.ws_bytes = capi.cv_alpha_grad_workspace(net.handle, self.B, self.m)
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=lo.device)
+
+    def bound_and_grad(self, alpha, grad_f=None):
+        lower = torch.empty(self.B, self.m, dtype=torch.float32, device=alpha.device)
+        grad = torch.empty_like(alpha)
+        ai = capi.make_alpha_in(self.B, self.m, self.lo, self.hi, self.l, self.u, self.mask, self.C, self.t,
+                                alpha.detach().contiguous(), grad_f)
+        capi.cv_alpha_grad(self.net.handle, self.net.cache, ai, lower, grad, self.ws, self.ws_bytes)
+        return lower, grad
+
+
+def optimize_alpha(state: AlphaState, alpha, steps=20, lr=0.1, decay=0.98):
+    """Adam ascent on the slopes (the paper's SDP-FO setting: 20 steps, lr 0.1, x0.98 per step).
+    Returns the final slopes and the bound after each step (every step runs in library kernels)."""
+    alpha = alpha.detach().clone().contiguous()
+    m1 = torch.zeros_like(alpha)
+    m2 = torch.zeros_like(alpha)
+    history = []
+    for it in range(1, steps + 1):
+        lower, grad = state.bound_and_grad(alpha)
+        history.append(lower)
+        capi.cv_alpha_adam(alpha, m1, m2, grad, it, lr * decay ** (it - 1))
+    lower, _ = state.bound_and_grad(alpha)
+    history.append(lower)
+    return alpha, history

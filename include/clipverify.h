@@ -236,6 +236,25 @@ cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* 
                          cv_batch_out* out, const cv_options* opt,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- CUDA graph of a round */
+
+/* A captured, instantiated CUDA graph of one cv_bound_batch call.  Replays run the same round
+ * (same sizes, options and pointers) on whatever the input buffers hold at replay time, with a
+ * single host launch: the round's ~25 kernels and its persistent complete-clipping launch are
+ * replayed without per-kernel launch overhead. */
+typedef struct cv_graph cv_graph;
+
+/* Captures cv_bound_batch(net, cache, in, out, opt, workspace, workspace_bytes) on a private
+ * stream (nothing runs during capture) and instantiates it.  opt->timer is ignored.  The
+ * pointers in `in` and `out`, the workspace and the cache must stay valid while the graph is
+ * used.  Synchronous. */
+cv_status cv_graph_capture(cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                           cv_batch_out* out, const cv_options* opt, void* workspace,
+                           size_t workspace_bytes, cv_graph** graph);
+/* Enqueues one replay on `stream`. */
+cv_status cv_graph_launch(cv_graph* graph, void* stream);
+void      cv_graph_destroy(cv_graph* graph);
+
 /* ---------------------------------------------------------------- alpha optimisation */
 
 /* Inputs of the slope gradient (device pointers).

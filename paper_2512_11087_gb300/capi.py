@@ -92,6 +92,9 @@ def load():
         "cv_timer_destroy": ([P], None),
         "cv_timer_read": ([P, P, P, P], I),
         "cv_relaxed_clip_static": ([P, P, P, P, P, P, I, P], I),
+        "cv_graph_capture": ([P, P, P, P, P, P, ctypes.c_size_t, ctypes.POINTER(P)], I),
+        "cv_graph_launch": ([P, P], I),
+        "cv_graph_destroy": ([P], None),
         "cv_alpha_grad_workspace": ([P, I, I, P], I),
         "cv_alpha_grad": ([P, P, P, P, P, P, ctypes.c_size_t, P], I),
         "cv_alpha_adam": ([P, P, P, P, ctypes.c_longlong, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -110,7 +113,7 @@ def exported_symbols():
                         "cv_cache_build", "cv_cache_create", "cv_cache_size", "cv_cache_read", "cv_cache_destroy",
                         "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
                         "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
-                        "cv_alpha_grad", "cv_alpha_adam")]
+                        "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy")]
 
 
 def _check(st):
@@ -306,3 +309,18 @@ def cv_alpha_grad(net, cache, ai, lower, grad_alpha, workspace, workspace_bytes,
 def cv_alpha_adam(alpha, m1, m2, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     _check(load().cv_alpha_adam(ptr(alpha), ptr(m1), ptr(m2), ptr(grad), int(alpha.numel()), int(t), float(lr),
                                 float(beta1), float(beta2), float(eps), stream_ptr(stream)))
+
+
+def cv_graph_capture(net, cache, bi, bo, opt, workspace, workspace_bytes):
+    g = P()
+    _check(load().cv_graph_capture(net, cache, ctypes.byref(bi), ctypes.byref(bo), ctypes.byref(opt), ptr(workspace),
+                                   int(workspace_bytes), ctypes.byref(g)))
+    return g
+
+
+def cv_graph_launch(graph, stream=None):
+    _check(load().cv_graph_launch(graph, stream_ptr(stream)))
+
+
+def cv_graph_destroy(graph):
+    load().cv_graph_destroy(graph)

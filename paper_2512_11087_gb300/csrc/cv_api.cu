@@ -207,3 +207,49 @@ extern "C" cv_status cv_timer_read(cv_timer* t, float* ms, int* launches, long l
     }
     return CV_OK;
 }
+
+// ---------------------------------------------------------------- CUDA graph of a round
+struct cv_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" cv_status cv_graph_capture(cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                                      const cv_options* opt, void* workspace, size_t workspace_bytes,
+                                      cv_graph** graph) {
+    if (!graph || !opt) { cv_set_error("cv_graph_capture: null argument"); return CV_EINVAL; }
+    *graph = nullptr;
+    cv_options o = *opt;
+    o.timer = nullptr;
+    cudaStream_t st = nullptr;
+    CV_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { cudaStreamDestroy(st); return cv_cuda_fail(e, "cudaStreamBeginCapture"); }
+    cv_status s = cv_bound_batch(net, cache, in, out, &o, workspace, workspace_bytes, st);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    cudaStreamDestroy(st);
+    if (s) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cv_cuda_fail(e, "cudaStreamEndCapture"); }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cv_cuda_fail(e, "cudaGraphInstantiate"); }
+    cv_graph* r = new cv_graph();
+    r->graph = g;
+    r->exec = x;
+    *graph = r;
+    return CV_OK;
+}
+
+extern "C" cv_status cv_graph_launch(cv_graph* graph, void* stream) {
+    if (!graph) { cv_set_error("cv_graph_launch: null graph"); return CV_EINVAL; }
+    CV_CUDA(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+    return CV_OK;
+}
+
+extern "C" void cv_graph_destroy(cv_graph* graph) {
+    if (!graph) return;
+    cudaGraphExecDestroy(graph->exec);
+    cudaGraphDestroy(graph->graph);
+    delete graph;
+}

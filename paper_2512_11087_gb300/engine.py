@@ -92,14 +92,31 @@ class Round:
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
         self.bo = capi.make_batch_out(**self.out)
 
+    def _bi(self, lo, hi, C, t, l_in, u_in, split_off, split_ids, row_off, G, h, alpha, tgt_off, tgt_ids):
+        return capi.make_batch_in(self.B, lo, hi, self.m, C, t, l_in=l_in, u_in=u_in, split_off=split_off,
+                                  split_ids=split_ids, max_splits=self.max_splits, row_off=row_off, G=G, h=h,
+                                  max_rows=self.max_rows, alpha=alpha, tgt_off=tgt_off, tgt_ids=tgt_ids)
+
     def run(self, lo, hi, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, row_off=None, G=None,
             h=None, alpha=None, tgt_off=None, tgt_ids=None, stream=None):
         """All array arguments must already be device tensors (see to_dev)."""
-        bi = capi.make_batch_in(self.B, lo, hi, self.m, C, t, l_in=l_in, u_in=u_in, split_off=split_off,
-                                split_ids=split_ids, max_splits=self.max_splits, row_off=row_off, G=G, h=h,
-                                max_rows=self.max_rows, alpha=alpha, tgt_off=tgt_off, tgt_ids=tgt_ids)
+        bi = self._bi(lo, hi, C, t, l_in, u_in, split_off, split_ids, row_off, G, h, alpha, tgt_off, tgt_ids)
         capi.cv_bound_batch(self.net.handle, self.net.cache, bi, self.bo, self.opt, self.ws, self.ws_bytes,
                             stream)
+        return self.out
+
+    def capture(self, lo, hi, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, row_off=None, G=None,
+                h=None, alpha=None, tgt_off=None, tgt_ids=None):
+        """CUDA graph of a round on these (device) buffers; replay with replay().  The tensors passed
+        here are kept alive with the graph."""
+        self._graph_keep = (lo, hi, C, t, l_in, u_in, split_off, split_ids, row_off, G, h, alpha, tgt_off, tgt_ids)
+        bi = self._bi(*self._graph_keep)
+        self.graph = capi.cv_graph_capture(self.net.handle, self.net.cache, bi, self.bo, self.opt, self.ws,
+                                           self.ws_bytes)
+        return self.graph
+
+    def replay(self, stream=None):
+        capi.cv_graph_launch(self.graph, stream)
         return self.out
 
 

@@ -219,3 +219,72 @@ def test_cache_build_parity():
         assert np.all(Z >= X @ gc["lA"].T.astype(np.float64) + gc["lc"] - 1e-9)
         assert np.all(Z <= X @ gc["uA"].T.astype(np.float64) + gc["uc"] + 1e-9)
         net.close()
+
+
+def test_graph_replay_matches_direct_call():
+    """A captured round (cv_graph_capture / cv_graph_launch) reads its buffers at replay time and
+    gives the same outputs as a direct cv_bound_batch call."""
+    from paper_2512_11087_gb300 import engine as E
+    case = Case([24, 32, 32, 32, 6], 32, 1, 4, 0.1, sweeps=5, seed=2)
+    net = E.Net(case.layers)
+    c = case.cache
+    net.set_cache(f32(case.lo0), f32(case.hi0), f32(c["root_l"]), f32(c["root_u"]), c["ids"], f32(c["lA"]),
+                  f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
+    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, sweeps=case.sweeps)
+    d = E.to_dev
+    lo, hi = d(case.lo), d(case.hi)
+    args = (d(case.C), d(case.t))
+    so, si = d(case.split_off), d(case.split_ids)
+    direct = {k: v.clone() for k, v in rnd.run(lo, hi, *args, split_off=so, split_ids=si).items()}
+    # capture on scratch data, then write the real inputs and replay
+    lo_s, hi_s = lo.clone(), hi.clone()
+    lo.zero_(); hi.fill_(1.0)
+    rnd.capture(lo, hi, *args, split_off=so, split_ids=si)
+    lo.copy_(lo_s); hi.copy_(hi_s)
+    for k in rnd.out:
+        rnd.out[k].zero_()
+    out = rnd.replay()
+    torch.cuda.synchronize()
+    for k in direct:
+        assert torch.equal(direct[k], out[k]), k
+    from paper_2512_11087_gb300 import capi
+    capi.cv_graph_destroy(rnd.graph)
+    net.close()
+
+
+def test_cnn_round_parity():
+    """A small CIFAR-shaped CNN (two strided 4x4 convolutions, a 3x3 one, two dense layers): the
+    conv layers are expanded to matrices independently on both sides."""
+    from paper_2512_11087_gb300 import workloads as WL
+    layers = WL.he_cnn((3, 12, 12), [(6, 4, 2, 1), (8, 4, 2, 1), (8, 3, 1, 1)], [20, 10], seed=4)
+    case = Case(None, 24, 1, 6, 2.0 / 255.0, layers=layers, sweeps=4, seed=4)
+    g = gpu_round(case)
+    o = case.oracle()
+    compare(case, g, o)
+
+
+def test_bench_workload_full_size_sampled():
+    """The benchmark's launch configuration: 784->256x6->10, 4096 subdomains with 1-4 splits,
+    relaxed + complete clipping with 10 sweeps.  The GPU bounds all subdomains; the oracle bounds a
+    sample (every subdomain with two or more active rows among the first 1024, plus others)."""
+    from paper_2512_11087_gb300 import workloads as WL
+    cfg = WL.CONFIGS["mlp784x256"]
+    case = Case(cfg["dims"], cfg["B"], cfg["kmin"], cfg["kmax"], cfg["eps"], sweeps=cfg["sweeps"], seed=0)
+    g = gpu_round(case)
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([rng.choice(case.B, 12, replace=False), [0, case.B - 1]]))
+    sub = Case.__new__(Case)
+    sub.__dict__.update(case.__dict__)
+    sub.B = sample.size
+    sub.lo, sub.hi = case.lo[sample], case.hi[sample]
+    so = np.zeros(sample.size + 1, np.int32)
+    ids = []
+    for i, b in enumerate(sample):
+        seg = case.split_ids[case.split_off[b]:case.split_off[b + 1]]
+        ids.append(seg)
+        so[i + 1] = so[i] + seg.size
+    sub.split_off, sub.split_ids = so, np.concatenate(ids).astype(np.int32)
+    o = sub.oracle(nthreads=0)
+    gs = {k: v[sample] for k, v in g.items()}
+    st = compare(sub, gs, o)
+    print("full-size sampled parity", st)

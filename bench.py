@@ -43,6 +43,8 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16x6"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--subdomains", type=int, default=0,
+                   help="smaller batch for profiler captures (default: the workload's own batch)")
     return p.parse_args()
 
 
@@ -153,6 +155,8 @@ def main():
     args = parse_args()
     from paper_2512_11087_gb300 import workloads as WL
     cfg = WL.CONFIGS[CONFIG]
+    if args.subdomains > 0:
+        cfg = dict(cfg, B=args.subdomains)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

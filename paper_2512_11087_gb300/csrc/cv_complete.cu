@@ -14,22 +14,27 @@
 // count); the previous sweep's breakpoint is tried first (coordinate ascent mostly re-selects it).
 //
 // Decision arithmetic (reproduced by the oracle): a'_j = a_j + sum_{p != k} beta_p g_pj as an FP32
-// fma chain over increasing p, q_j = (-a'_j) * fl(1/g_kj), compared through an order-preserving
-// 32-bit key.  Weights are exact 64-bit fixed-point integers (w scaled by 2^s_k, s_k chosen so
+// fma chain over increasing p, q_j = (-a'_j) * fl(1/g_kj); breakpoints with q > 0 are compared
+// through the raw bits of q (for positive floats the unsigned order of the bits is the order of
+// the values).  Weights are exact 64-bit fixed-point integers (w scaled by 2^s_k, s_k chosen so
 // the row's total stays below 2^62), so every cumulative sum is exact and order independent and
 // the quantile decision matches an FP64 evaluation; warp sums use three 21-bit redux.sync limbs.
 // A sweep that changes no multiplier ends the ascent (the next would repeat it bit for bit); with
 // a single row a' = a, so one pass suffices.  The bound is the dual objective at the final beta,
 // evaluated in FP32 and padded by its rounding bound (any beta >= 0 gives a valid bound), or in
-// FP64 when the padded value straddles 0 so that the stability decision is exact.
+// FP64 when the padded value straddles 0 so that the stability decision is exact.  With every
+// multiplier 0 it equals the re-concretised bound already stored, and is skipped.
 //
 // GB300 mapping (persistent scheduling of uneven work): k_cc_prep writes each subdomain's active
-// rows (g, 1/g, fixed-point weights, threshold) to the workspace once; a single-block scan turns
-// the per-subdomain task counts into work items of TPI (target, side) tasks, subdomains with more
-// rows first; a persistent k_complete grid (one block per resident slot) takes items from an
-// atomic ticket, stages the item's rows in shared memory and runs one warp per task; each warp
-// keeps its breakpoint keys in its own shared buffer, so the element loops stay short and rolled
-// (small code, few registers, 32 resident warps per SM).
+// rows (g, 1/g, fixed-point weights, threshold, total weight) to the workspace once; a
+// single-block scan turns the per-subdomain task counts into work items (256 (target, side)
+// tasks for one row, 64 for two, 16 for more: longer tasks, smaller items), subdomains with more
+// rows first; a persistent k_complete grid (two blocks of 16 warps per SM) takes items from an
+// atomic ticket, stages the item's rows in shared memory, and its warps take the item's tasks one
+// at a time from a shared counter.  The task body is compiled for each row count (multipliers in
+// registers); subdomains with more than four rows run in a separate launch of one block per SM
+// (more registers).  Each warp keeps its breakpoint keys in its own shared buffer and loads the
+// target's coefficients four per lane ahead, so the element loops stay short and rolled.
 #include "cv_internal.cuh"
 
 #include <climits>
@@ -38,17 +43,12 @@
 namespace {
 
 constexpr int RMAX_CC = 8;  // rows per subdomain handled by complete clipping
-constexpr int TPI = 64;     // (target, side) tasks per work item
-constexpr int NWARP = 16;   // warps per block
-
-__device__ __forceinline__ unsigned fkey(float q) {
-    unsigned u = __float_as_uint(q);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float fkey_inv(unsigned k) {
-    unsigned u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
-    return __uint_as_float(u);
-}
+constexpr int RTPL = 4;     // row counts up to this run in the main launch (two blocks per SM)
+// (target, side) tasks per work item: fewer for subdomains with more rows (longer tasks)
+__host__ __device__ __forceinline__ int tpi_of(int R) { return R <= 1 ? 256 : (R == 2 ? 64 : 16); }
+constexpr int NWARP = 16;   // warps per block at most
+constexpr int CAPC = 256;   // breakpoints a warp's compacted list holds
+constexpr int PF = 4;       // coefficients loaded ahead per lane in the element loops
 
 // Exact warp sum of non-negative per-lane 64-bit values whose total is below 2^62: three
 // 21-bit limbs, each summed with one redux.sync (32 x 2^21 < 2^26, no overflow).
@@ -76,13 +76,15 @@ struct CCArgs {
     unsigned long long* steps;  // optional counter of executed row steps
     // workspace
     float* wg; float* wrg; long long* ww;   // [B][Rs][n0]
-    long long* wT; double* wSg; float* wh;  // [B][Rs]
+    long long* wT; long long* wW;           // [B][Rs] threshold, total weight (fixed point)
+    double* wSg; float* wh;                  // [B][Rs]
     int* wR;                                 // [B] active rows used
     int* wcnt;                               // [B] work items
     int* order;                              // [B] positions -> subdomains, more rows first
     int* ioff;                               // [B+1] first item of every position; [B] = total
     int* nplaced;                            // positions holding subdomains with work
-    unsigned* ticket;
+    int* wide;                               // items of subdomains with more than RTPL rows (first)
+    unsigned* ticket;                        // [2] item tickets: wide items, the rest
 };
 
 __device__ __forceinline__ int ntargets(const CCArgs& a, int b) {
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
                 if (a.rowflag[(size_t)b * a.Rmax + k] == 0) rowsel[r++] = k;
         R = r;
         a.wR[b] = r;
-        a.wcnt[b] = r > 0 ? (2 * ntargets(a, b) + TPI - 1) / TPI : 0;
+        a.wcnt[b] = r > 0 ? (2 * ntargets(a, b) + tpi_of(r) - 1) / tpi_of(r) : 0;
     }
     __syncthreads();
     const int ns = a.split_off ? a.split_off[b + 1] - a.split_off[b] : 0;
@@ -140,11 +142,16 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
         }
         // fixed-point weights: scale so that the row total stays below 2^62
         const int sh = (wsum > 0.0) ? 61 - ilogb(wsum) : 0;
+        unsigned long long wtot = 0;
         for (int j = lane; j < n0; j += 32) {
             const double w = fabs((double)sg * (double)gp[j]) * (0.5 * ((double)hi[j] - (double)lo[j]));
-            a.ww[base + j] = __double2ll_rn(ldexp(w, sh));
+            const long long wi = __double2ll_rn(ldexp(w, sh));
+            a.ww[base + j] = wi;
+            wtot += (unsigned long long)wi;
         }
+        const long long Wrow = warp_sum64(wtot);
         if (lane == 0) {
+            a.wW[(size_t)b * Rs + r] = Wrow;
             const double T = 0.5 * (smax + (double)hh);
             a.wT[(size_t)b * Rs + r] = (T <= 0.0) ? LLONG_MIN : __double2ll_ru(ldexp(T, sh));
             a.wh[(size_t)b * Rs + r] = hh;
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(1024) k_cc_scan(CCArgs a) {
     __shared__ int placed, carry;
     const int B = a.B, tid = threadIdx.x, nt = blockDim.x;
     const int per = (B + nt - 1) / nt;
-    if (tid == 0) { placed = 0; carry = 0; }
+    if (tid == 0) { placed = 0; carry = 0; *a.wide = 0; }
     __syncthreads();
     for (int v = a.Rs; v >= 1; --v) {
         int c = 0, s = 0;
@@ -190,47 +197,346 @@ __global__ void __launch_bounds__(1024) k_cc_scan(CCArgs a) {
             }
         }
         __syncthreads();
-        if (tid == 0) { placed += sc[nt - 1]; carry += si[nt - 1]; }
+        if (tid == 0) {
+            placed += sc[nt - 1];
+            carry += si[nt - 1];
+            if (v == RTPL + 1) *a.wide = carry;
+        }
         __syncthreads();
     }
     for (int i = placed + tid; i < B; i += nt) { a.ioff[i] = carry; a.order[i] = -1; }
     if (tid == 0) {
         a.ioff[B] = carry;
         *a.nplaced = placed;
-        *a.ticket = 0u;
+        a.ticket[0] = 0u;
+        a.ticket[1] = 0u;
     }
 }
 
-__global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
+// Shared-memory view of the staged subdomain (rows of the item's subdomain).
+struct Stage {
+    const long long* w64;  // [Rs][n0] fixed-point weights
+    const float* gs;       // [Rs][n0] row coefficients g
+    const float* rg;       // [Rs][n0] fl(1 / g), 0 where g = 0
+    const long long* T64;  // [R] thresholds (fixed point)
+    const long long* W64;  // [R] total weight (fixed point)
+    const float* hrow;     // [R] row constants h
+    const double* Sg;      // [R] magnitude of g against the root box
+};
+
+constexpr unsigned QINF = 0x7f800000u;  // bits of +inf; breakpoints q > 0 have bits in (0, QINF]
+
+// One (target, side) task of complete clipping with R active rows (R fixed at compile time, so the
+// multipliers live in registers).  Breakpoint keys are the raw bits of q_j = (-a'_j) * fl(1/g_kj):
+// for q > 0 (the search range) the unsigned order of the bits is the order of the values.
+template <int R>
+__device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsigned* keys,
+                                        unsigned short* cidx, int b, int c, int side, int lane,
+                                        unsigned long long& my_steps) {
+    const int n0 = a.n0;
+    const size_t o = (size_t)b * a.U + c;
+    const float* ap = side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0;
+    const float sa = side ? -1.f : 1.f;
+    const float c0 = side ? -a.uc[c] : a.lc[c];
+    float beta[R];
+    int jprev[R];
+#pragma unroll
+    for (int p = 0; p < R; ++p) { beta[p] = 0.f; jprev[p] = -1; }
+    // with one row, a' = a in every sweep, so one pass already repeats bit for bit
+    const int nsweeps = (R == 1) ? 1 : a.sweeps;
+    for (int sw = 0; sw < nsweeps; ++sw) {
+        bool changed = false;
+        my_steps += R;
+#pragma unroll 1
+        for (int k = 0; k < R; ++k) {
+            const float* rk = st.rg + k * n0;
+            const long long* wk = st.w64 + k * n0;
+            float bk = 0.f;
+            int jp = -1;
+#pragma unroll
+            for (int p = 0; p < R; ++p)
+                if (p == k) { bk = beta[p]; jp = jprev[p]; }
+            // q_j from a' = a + sum_{p != k} beta_p g_p (fma chain in increasing p)
+            auto q_of = [&](float av, int j) -> float {
+                float apr = sa * av;
+#pragma unroll
+                for (int p = 0; p < R; ++p) {
+                    if (R > 1) {
+                        const float t = fmaf(beta[p], st.gs[p * n0 + j], apr);
+                        apr = (p != k) ? t : apr;
+                    }
+                }
+                return (-apr) * rk[j];
+            };
+            // previous breakpoint of this row (same value for every lane)
+            float qp = 0.f;
+            if (jp >= 0) qp = q_of(__ldg(ap + jp), jp);
+            const bool warm = qp > 0.f;
+            const long long T = st.T64[k];
+            const long long W = st.W64[k];
+            // One pass over all n0 elements keeps the keys in the warp's buffer.  Without a previous
+            // breakpoint it takes F(0) = sum_{q <= 0} w and the extent and size of the search range;
+            // with one, F just below and at it.  F(+inf) is the row's total weight W.
+            unsigned long long f0 = 0, flt = 0, fle = 0;
+            unsigned mn = 0xffffffffu, mx = 0u, cnt = 0u;
+#pragma unroll 1
+            for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
+                float av[PF];
+#pragma unroll
+                for (int u = 0; u < PF; ++u) av[u] = (j0 + 32 * u < n0) ? __ldg(ap + j0 + 32 * u) : 0.f;
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    const int j = j0 + 32 * u;
+                    if (j < n0) {
+                        const float q = q_of(av[u], j);
+                        const unsigned kk = __float_as_uint(q);
+                        keys[j] = kk;
+                        const unsigned long long w = (unsigned long long)wk[j];
+                        if (warm) {
+                            flt += (q < qp) ? w : 0ull;
+                            fle += (q <= qp) ? w : 0ull;
+                        } else if (q > 0.f) {
+                            mn = min(mn, kk); mx = max(mx, kk); ++cnt;
+                        } else if (q <= 0.f) {
+                            f0 += w;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            float bn = 0.f;
+            int jn = -1;
+            // bracket (lo, hi] of key bits with F(lo) < T <= F(hi); mn, mx, cnt: extent and size of the
+            // breakpoints inside it
+            unsigned lo = 0u, hi = QINF;
+            long long Flo = 0, Fhi = W;
+            bool search = false;
+            if (warm) {
+                const long long Flt = warp_sum64(flt), Fle = warp_sum64(fle);
+                if (Flt < T && T <= Fle) {
+                    bn = qp;  // the same breakpoint as last time
+                    jn = jp;
+                } else {
+                    // missed: F(0) and the extent of the side of qp that holds the answer
+                    const unsigned kp = __float_as_uint(qp);
+                    if (Fle < T) { lo = kp; Flo = Fle; }
+                    else { hi = kp - 1u; Fhi = Flt; }
+#pragma unroll 4
+                    for (int j = lane; j < n0; j += 32) {
+                        const unsigned kk = keys[j];
+                        if (__uint_as_float(kk) <= 0.f) f0 += (unsigned long long)wk[j];
+                        if (kk > lo && kk <= hi) { mn = min(mn, kk); mx = max(mx, kk); ++cnt; }
+                    }
+                    const long long F0 = warp_sum64(f0);
+                    if (lo == 0u) Flo = F0;
+                    search = !(F0 >= T || W < T);
+                }
+            } else {
+                const long long F0 = warp_sum64(f0);
+                Flo = F0;
+                search = !(F0 >= T || W < T);  // else beta = 0: slope at 0+ not positive, or no crossing
+            }
+            if (search) {
+                unsigned cmin = __reduce_min_sync(0xffffffffu, mn);
+                unsigned cmax = __reduce_max_sync(0xffffffffu, mx);
+                unsigned ncnt = __reduce_add_sync(0xffffffffu, cnt);
+                // Shrink to a single key.  Each pass splits the bracket at a pivot interpolated from
+                // the weight still needed (after eight passes every other pass halves it) and takes F
+                // at the pivot and the extent and size of both halves.  Once the bracket holds at most
+                // CAPC breakpoints, the pass also moves them (key and element) to the front of the
+                // warp's buffer, and later passes read only that list.
+                bool listed = false;
+                int m = n0;
+                unsigned ks = 0u;
+                const unsigned below = (1u << lane) - 1u;
+#pragma unroll 1
+                for (int it = 0; it < 96; ++it) {
+                    if (cmin == cmax) { ks = cmin; break; }
+                    lo = cmin - 1u;  // F unchanged: no breakpoint in (lo, cmin)
+                    hi = cmax;       // F unchanged: no breakpoint in (cmax, hi]
+                    unsigned mid;
+                    if (it >= 8 && (it & 1)) {
+                        mid = lo + ((hi - lo) >> 1);
+                    } else {
+                        const float fr = (float)(T - Flo) / (float)(Fhi - Flo);
+                        unsigned off = (unsigned)(fr * (float)(hi - lo));
+                        off = min(max(off, 1u), hi - lo - 1u);
+                        mid = lo + off;
+                    }
+                    const bool wr = listed || ncnt <= (unsigned)CAPC;
+                    unsigned long long fm = 0;
+                    unsigned mnL = 0xffffffffu, mxL = 0u, mnR = 0xffffffffu, mxR = 0u, cl = 0u;
+                    int wpos = 0;
+#pragma unroll 1
+                    for (int j0 = 0; j0 < m; j0 += 32) {
+                        const int j = j0 + lane;
+                        unsigned kk = 0u;
+                        int e = j;
+                        if (j < m) {
+                            kk = keys[j];
+                            if (listed) e = cidx[j];
+                        }
+                        const bool in = j < m && kk > lo && kk <= hi;
+                        if (wr) {
+                            // in-place compaction: every write lands at or before the position read
+                            const unsigned bal = __ballot_sync(0xffffffffu, in);
+                            if (in) {
+                                const int q = wpos + __popc(bal & below);
+                                keys[q] = kk;
+                                cidx[q] = (unsigned short)e;
+                            }
+                            wpos += __popc(bal);
+                        }
+                        if (in) {
+                            if (kk <= mid) {
+                                fm += (unsigned long long)wk[e];
+                                mnL = min(mnL, kk); mxL = max(mxL, kk); ++cl;
+                            } else {
+                                mnR = min(mnR, kk); mxR = max(mxR, kk);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (wr) { listed = true; m = wpos; }
+                    const long long Fm = Flo + warp_sum64(fm);
+                    const unsigned nl = __reduce_add_sync(0xffffffffu, cl);
+                    if (Fm >= T) {
+                        hi = mid; Fhi = Fm;
+                        cmin = __reduce_min_sync(0xffffffffu, mnL);
+                        cmax = __reduce_max_sync(0xffffffffu, mxL);
+                        ncnt = nl;
+                    } else {
+                        lo = mid; Flo = Fm;
+                        cmin = __reduce_min_sync(0xffffffffu, mnR);
+                        cmax = __reduce_max_sync(0xffffffffu, mxR);
+                        ncnt -= nl;
+                    }
+                }
+                bn = (ks != 0u) ? __uint_as_float(ks) : 0.f;
+                // the element holding the selected breakpoint (lowest index among ties)
+                if (ks != 0u) {
+                    if (listed) {
+                        int jm = INT_MAX;
+                        for (int j = lane; j < m; j += 32)
+                            if (keys[j] == ks) jm = min(jm, (int)cidx[j]);
+                        jm = __reduce_min_sync(0xffffffffu, jm);
+                        jn = (jm == INT_MAX) ? -1 : jm;
+                    } else {
+                        for (int j0 = 0; j0 < n0 && jn < 0; j0 += 32) {
+                            const int j = j0 + lane;
+                            const unsigned bal = __ballot_sync(0xffffffffu, j < n0 && keys[j] == ks);
+                            if (bal) jn = j0 + __ffs(bal) - 1;
+                        }
+                    }
+                }
+            }
+            __syncwarp();  // the next step rewrites the key buffer
+#pragma unroll
+            for (int p = 0; p < R; ++p)
+                if (p == k) { beta[p] = bn; jprev[p] = jn; }
+            changed |= (bn != bk);
+        }
+        if (!changed) break;
+    }
+    // With every multiplier 0 the dual objective is the target's plane concretised over the clipped
+    // box, which re-concretisation has already folded into l / u: nothing to update.
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < R; ++p) any |= (beta[p] != 0.f);
+    if (!any) return;
+    // dual objective at beta, FP32 with its rounding bound
+    const float* slo = a.lo + (size_t)b * n0;
+    const float* shi = a.hi + (size_t)b * n0;
+    const float psc = __ldg(a.pscale + (side ? a.U + c : c));
+    const float cur = side == 0 ? a.l[o] : -a.u[o];
+    float part = 0.f;
+#pragma unroll 1
+    for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
+        float av[PF], lv[PF], hv[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int j = j0 + 32 * u;
+            const bool in = j < n0;
+            av[u] = in ? __ldg(ap + j) : 0.f;
+            lv[u] = in ? __ldg(slo + j) : 0.f;
+            hv[u] = in ? __ldg(shi + j) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int j = j0 + 32 * u;
+            if (j < n0) {
+                float v = sa * av[u];
+#pragma unroll
+                for (int p = 0; p < R; ++p) v = fmaf(beta[p], st.gs[p * n0 + j], v);
+                part += fminf(v * lv[u], v * hv[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    float cst = c0;
+    double scale = (double)psc + fabs((double)c0);
+#pragma unroll
+    for (int p = 0; p < R; ++p) {
+        cst = fmaf(beta[p], st.hrow[p], cst);
+        scale += (double)beta[p] * (st.Sg[p] + fabs((double)st.hrow[p]));
+    }
+    const double gam = (double)(R + (n0 + 31) / 32 + 12) * CV_U32;
+    const float pad = __double2float_ru(gam * scale * 1.0001);
+    float val = __fsub_rd(__fadd_rd(part, cst), pad);
+    const float valhi = __fadd_ru(__fadd_ru(part, cst), pad);
+    if (val < 0.f && valhi >= 0.f && cur < 0.f) {
+        // the stability decision is uncertain in FP32: evaluate D(beta) in FP64
+        double d = 0.0;
+        for (int j = lane; j < n0; j += 32) {
+            double v = (double)(sa * __ldg(ap + j));
+#pragma unroll
+            for (int p = 0; p < R; ++p) v += (double)beta[p] * (double)st.gs[p * n0 + j];
+            d += fmin(v * (double)__ldg(slo + j), v * (double)__ldg(shi + j));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+        d += (double)c0;
+#pragma unroll
+        for (int p = 0; p < R; ++p) d += (double)beta[p] * (double)st.hrow[p];
+        val = __double2float_rd(d - ldexp(scale, -40));
+    }
+    if (lane == 0) {
+        if (side == 0) { if (val > a.l[o]) a.l[o] = val; }
+        else { const float ub = -val; if (ub < a.u[o]) a.u[o] = ub; }
+    }
+}
+
+// WIDE: the items of subdomains with more than RTPL rows (one block per SM, more registers);
+// otherwise the rest.
+template <bool WIDE>
+__global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n0 = a.n0, Rs = a.Rs, B = a.B;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int n0r = (n0 + 31) & ~31;
-    // shared: w64 [Rs][n0] | g [Rs][n0] | rg [Rs][n0] | lo [n0] | hi [n0] | keys [NWARP][n0r]
-    long long* w64 = (long long*)smem;
+    // shared: keys [nw][n0r] | w64 [Rs][n0] | g [Rs][n0] | 1/g [Rs][n0] | list elements [nw][CAPC]
+    unsigned* keys = (unsigned*)smem + (size_t)warp * n0r;  // this warp's breakpoint keys
+    long long* w64 = (long long*)((unsigned*)smem + (size_t)nw * n0r);
     float* gs = (float*)(w64 + (size_t)Rs * n0);
     float* rg = gs + (size_t)Rs * n0;
-    float* slo = rg + (size_t)Rs * n0;
-    float* shi = slo + n0;
-    unsigned* keys = (unsigned*)(shi + n0) + (size_t)warp * n0r;  // this warp's breakpoint keys
-    __shared__ long long T64[RMAX_CC];
+    unsigned short* cidx = (unsigned short*)(rg + (size_t)Rs * n0) + (size_t)warp * CAPC;
+    __shared__ long long T64[RMAX_CC], W64[RMAX_CC];
     __shared__ float hrow[RMAX_CC];
     __shared__ double Sg[RMAX_CC];
-    __shared__ float sbeta[NWARP][RMAX_CC];  // per warp: multipliers of the current task
-    __shared__ int sjprev[NWARP][RMAX_CC];   // per warp: element of the last selected breakpoint
-    __shared__ int s_item, s_pos, s_R;
+    __shared__ int s_item, s_pos, s_R, s_next;
     __shared__ unsigned long long nsteps;
+    const Stage st{w64, gs, rg, T64, W64, hrow, Sg};
     if (threadIdx.x == 0) nsteps = 0;
     unsigned long long my_steps = 0;
-    const unsigned KZERO = 0x80000000u;  // key(+0.0)
-    const unsigned KINF = 0xff800000u;   // key(+inf)
-    const int total = a.ioff[B];
+    const int ibeg = WIDE ? 0 : *a.wide;
+    const int total = WIDE ? *a.wide : a.ioff[B];
     const int np = *a.nplaced;
     int cur_b = -1;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int it = (int)atomicAdd(a.ticket, 1u);
+            const int it = ibeg + (int)atomicAdd(&a.ticket[WIDE ? 0 : 1], 1u);
             s_item = it;
             if (it < total) {
                 int lo = 0, hi = np - 1;  // last position whose first item is <= it
@@ -247,7 +553,7 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
         const int pos = s_pos;
         const int b = a.order[pos];
         if (b != cur_b) {
-            // stage the subdomain's rows and clipped box
+            // stage the subdomain's rows
             if (threadIdx.x == 0) s_R = a.wR[b];
             __syncthreads();
             const int R = s_R;
@@ -257,184 +563,49 @@ __global__ void __launch_bounds__(NWARP * 32, 2) k_complete(CCArgs a) {
                 gs[i] = a.wg[base + i];
                 rg[i] = a.wrg[base + i];
             }
-            for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-                slo[i] = a.lo[(size_t)b * n0 + i];
-                shi[i] = a.hi[(size_t)b * n0 + i];
-            }
             if (threadIdx.x < R) {
                 T64[threadIdx.x] = a.wT[(size_t)b * Rs + threadIdx.x];
+                W64[threadIdx.x] = a.wW[(size_t)b * Rs + threadIdx.x];
                 hrow[threadIdx.x] = a.wh[(size_t)b * Rs + threadIdx.x];
                 Sg[threadIdx.x] = a.wSg[(size_t)b * Rs + threadIdx.x];
             }
             cur_b = b;
-            __syncthreads();
         }
         const int R = s_R;
         const bool have_list = a.tgt_off != nullptr;
         const int t0 = have_list ? a.tgt_off[b] : 0;
         const int ntask = 2 * ntargets(a, b);
-        const int first = (item - a.ioff[pos]) * TPI;
-        const int last = min(first + TPI, ntask);
-        for (int task = first + warp; task < last; task += NWARP) {
-            const int ti = task >> 1, side = task & 1;
+        const int first = (item - a.ioff[pos]) * tpi_of(R);
+        const int last = min(first + tpi_of(R), ntask);
+        if (threadIdx.x == 0) s_next = first;
+        __syncthreads();
+        // the warps take the item's tasks one at a time from its counter
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&s_next, 1);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= last) break;
+            const int ti = t >> 1, side = t & 1;
             const int c = have_list ? a.tgt_ids[t0 + ti] : ti;
-            if (c < 0 || c >= a.U) { if (lane == 0) atomicOr(a.status, CV_DEV_TARGET); continue; }
-            const size_t o = (size_t)b * a.U + c;
-            if (a.mask[o] != 0) continue;
-            const float* ap = side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0;
-            const float sa = side ? -1.f : 1.f;
-            const float c0 = side ? -a.uc[c] : a.lc[c];
-            float* beta = sbeta[warp];
-            int* jprev = sjprev[warp];
-            if (lane < RMAX_CC) { beta[lane] = 0.f; jprev[lane] = -1; }
-            __syncwarp();
-            // with one row, a' = a in every sweep, so one pass already repeats bit for bit
-            const int nsweeps = (R == 1) ? 1 : a.sweeps;
-            for (int sw = 0; sw < nsweeps; ++sw) {
-                bool changed = false;
-                my_steps += R;
-                for (int k = 0; k < R; ++k) {
-                    const float* rk = rg + (size_t)k * n0;
-                    const long long* wk = w64 + (size_t)k * n0;
-                    const int jp = jprev[k];
-                    // a' = a + sum_{p != k} beta_p g_p (fma chain in increasing p), key of q = -a' / g_k
-                    auto key_of = [&](int j) -> unsigned {
-                        float apr = sa * ap[j];
-                        for (int p = 0; p < R; ++p)
-                            if (p != k) apr = fmaf(beta[p], gs[(size_t)p * n0 + j], apr);
-                        const float r = rk[j];
-                        return (r != 0.f) ? fkey(-apr * r) : 0xffffffffu;
-                    };
-                    unsigned kp = 0xffffffffu;
-                    if (jp >= 0) kp = __shfl_sync(0xffffffffu, key_of(jp), 0);
-                    const bool warm = kp > KZERO && kp <= KINF;
-                    // F(x) = sum of the weights of the breakpoints with key <= x (exact integers)
-                    unsigned long long f0 = 0, ftot = 0, flt = 0, fle = 0;
-                    if (warm) {
-                        for (int j = lane; j < n0; j += 32) {
-                            const unsigned kk = key_of(j);
-                            keys[j] = kk;
-                            const unsigned long long w = (unsigned long long)wk[j];
-                            f0 += (kk <= KZERO) ? w : 0ull;
-                            ftot += (kk <= KINF) ? w : 0ull;
-                            flt += (kk < kp) ? w : 0ull;
-                            fle += (kk <= kp) ? w : 0ull;
-                        }
-                    } else {
-                        for (int j = lane; j < n0; j += 32) {
-                            const unsigned kk = key_of(j);
-                            keys[j] = kk;
-                            const unsigned long long w = (unsigned long long)wk[j];
-                            f0 += (kk <= KZERO) ? w : 0ull;
-                            ftot += (kk <= KINF) ? w : 0ull;
-                        }
-                    }
-                    __syncwarp();
-                    const long long T = T64[k];
-                    const long long F0 = warp_sum64(f0), Ftot = warp_sum64(ftot);
-                    long long Flt = 0, Fle = 0;
-                    if (warm) { Flt = warp_sum64(flt); Fle = warp_sum64(fle); }
-                    float bn = 0.f;
-                    int jn = -1;
-                    if (F0 >= T || Ftot < T) {
-                        // beta = 0 (slope at 0+ not positive; or a row infeasible on this machine)
-                    } else if (warm && Flt < T && T <= Fle) {
-                        bn = fkey_inv(kp);  // the same breakpoint as last time
-                        jn = jp;
-                    } else {
-                        // bracket (lo, hi] with F(lo) < T <= F(hi)
-                        unsigned lo = KZERO, hi = KINF;
-                        long long Flo = F0, Fhi = Ftot;
-                        if (warm) {
-                            if (Fle < T) { lo = kp; Flo = Fle; }
-                            else { hi = kp - 1; Fhi = Flt; }
-                        }
-                        // shrink to a single breakpoint key: each pass takes the min and max key in the
-                        // bracket (done when equal) and splits at the pivot interpolated from the weight
-                        // still needed (halving every other pass after the eighth)
-                        unsigned ks = 0;
-                        for (int it = 0; it < 96; ++it) {
-                            unsigned cmin = 0xffffffffu, cmax = 0u;
-                            for (int j = lane; j < n0; j += 32) {
-                                const unsigned kk = keys[j];
-                                if (kk > lo && kk <= hi) { cmin = min(cmin, kk); cmax = max(cmax, kk); }
-                            }
-                            cmin = __reduce_min_sync(0xffffffffu, cmin);
-                            cmax = __reduce_max_sync(0xffffffffu, cmax);
-                            if (cmin == cmax) { ks = cmin; break; }
-                            lo = cmin - 1;  // F unchanged: no breakpoint in (lo, cmin)
-                            hi = cmax;      // F unchanged: no breakpoint in (cmax, hi]
-                            unsigned mid;
-                            if (it >= 8 && (it & 1)) {
-                                mid = lo + ((hi - lo) >> 1);
-                            } else {
-                                const float fr = (float)(T - Flo) / (float)(Fhi - Flo);
-                                unsigned off = (unsigned)(fr * (float)(hi - lo));
-                                off = min(max(off, 1u), hi - lo - 1);
-                                mid = lo + off;
-                            }
-                            unsigned long long fm = 0;
-                            for (int j = lane; j < n0; j += 32)
-                                fm += (keys[j] <= mid) ? (unsigned long long)wk[j] : 0ull;
-                            const long long Fm = warp_sum64(fm);
-                            if (Fm >= T) { hi = mid; Fhi = Fm; }
-                            else { lo = mid; Flo = Fm; }
-                        }
-                        bn = fkey_inv(ks);
-                        if (!(bn > 0.f)) bn = 0.f;
-                        // the element holding the selected breakpoint (lowest index among ties)
-                        jn = -1;
-                        for (int j0 = 0; j0 < n0 && jn < 0; j0 += 32) {
-                            const int j = j0 + lane;
-                            const unsigned bal = __ballot_sync(0xffffffffu, j < n0 && keys[j] == ks);
-                            if (bal) jn = j0 + __ffs(bal) - 1;
-                        }
-                    }
-                    const float bk = beta[k];
-                    __syncwarp();
-                    if (lane == 0) { jprev[k] = jn; beta[k] = bn; }
-                    __syncwarp();
-                    changed |= (bn != bk);
+            if (c < 0 || c >= a.U) {
+                if (lane == 0) atomicOr(a.status, CV_DEV_TARGET);
+                continue;
+            }
+            if (a.mask[(size_t)b * a.U + c] != 0) continue;
+            if (WIDE) {
+                switch (R) {
+                    case 5: cc_task<5>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    case 6: cc_task<6>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    case 7: cc_task<7>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    default: cc_task<8>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
                 }
-                if (!changed) break;
-            }
-            // dual objective at beta, FP32 with its rounding bound
-            float part = 0.f;
-            for (int j = lane; j < n0; j += 32) {
-                float v = sa * ap[j];
-                for (int k = 0; k < R; ++k) v = fmaf(beta[k], gs[(size_t)k * n0 + j], v);
-                part += fminf(v * slo[j], v * shi[j]);
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-            float cst = c0;
-            double scale = (double)a.pscale[side ? a.U + c : c] + fabs((double)c0);
-            for (int k = 0; k < R; ++k) {
-                cst = fmaf(beta[k], hrow[k], cst);
-                scale += (double)beta[k] * (Sg[k] + fabs((double)hrow[k]));
-            }
-            const double gam = (double)(R + (n0 + 31) / 32 + 12) * CV_U32;
-            const float pad = __double2float_ru(gam * scale * 1.0001);
-            float val = __fsub_rd(__fadd_rd(part, cst), pad);
-            const float valhi = __fadd_ru(__fadd_ru(part, cst), pad);
-            const float cur = side == 0 ? a.l[o] : -a.u[o];
-            if (val < 0.f && valhi >= 0.f && cur < 0.f) {
-                // the stability decision is uncertain in FP32: evaluate D(beta) in FP64
-                double d = 0.0;
-                for (int j = lane; j < n0; j += 32) {
-                    double v = (double)(sa * ap[j]);
-                    for (int k = 0; k < R; ++k) v += (double)beta[k] * (double)gs[(size_t)k * n0 + j];
-                    d += fmin(v * (double)slo[j], v * (double)shi[j]);
+            } else {
+                switch (R) {
+                    case 1: cc_task<1>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    case 2: cc_task<2>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    case 3: cc_task<3>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    default: cc_task<4>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-                d += (double)c0;
-                for (int k = 0; k < R; ++k) d += (double)beta[k] * (double)hrow[k];
-                val = __double2float_rd(d - ldexp(scale, -40));
-            }
-            if (lane == 0) {
-                if (side == 0) { if (val > a.l[o]) a.l[o] = val; }
-                else { const float ub = -val; if (ub < a.u[o]) a.u[o] = ub; }
             }
             __syncwarp();
         }
@@ -465,23 +636,37 @@ __global__ void k_cc_post(CCArgs a) {
     if (threadIdx.x == 0 && bad) a.infeasible[b] = 1;
 }
 
-cv_status launch_cc(const CCArgs& a, int* launches, cudaStream_t st) {
+template <bool WIDE>
+cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
     const size_t n0r = (a.n0 + 31) & ~31;
-    const size_t smem = (size_t)a.Rs * a.n0 * (8 + 4 + 4) + 2 * (size_t)a.n0 * 4 + (size_t)NWARP * n0r * 4;
-    if (smem > 220 * 1024) {
+    const size_t fixed = (size_t)a.Rs * a.n0 * (8 + 4 + 4);
+    const size_t per_warp = n0r * 4 + CAPC * 2;  // keys, compacted list elements
+    const size_t limit = 220 * 1024;
+    int nw = NWARP;
+    while (nw > 1 && fixed + nw * per_warp > limit) --nw;
+    const size_t smem = fixed + nw * per_warp;
+    if (smem > limit || a.n0 > 65535) {
         cv_set_error("complete clipping: input dimension too large for the shared-memory row cache");
         return CV_EUNSUPPORTED;
     }
-    CV_CUDA(cudaFuncSetAttribute(k_complete, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CV_CUDA(cudaFuncSetAttribute(k_complete<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per = 0;
     CV_CUDA(cudaGetDevice(&dev));
     CV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_complete, NWARP * 32, smem));
+    CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_complete<WIDE>, nw * 32, smem));
     if (per < 1) per = 1;
-    k_complete<<<sms * per, NWARP * 32, smem, st>>>(a);
+    k_complete<WIDE><<<sms * per, nw * 32, smem, st>>>(a);
     CV_LAUNCH_CHECK("k_complete");
     ++*launches;
     return CV_OK;
+}
+
+cv_status launch_cc(const CCArgs& a, int* launches, cudaStream_t st) {
+    if (a.Rs > RTPL) {
+        cv_status s = launch_cc_one<true>(a, launches, st);
+        if (s) return s;
+    }
+    return launch_cc_one<false>(a, launches, st);
 }
 
 }  // namespace
@@ -493,7 +678,7 @@ size_t cv_cc_workspace(int B, int Rmax, int n0) {
     size_t s = 0;
     s += cv_align256(b * Rs * n0 * 4) * 2;  // wg, wrg
     s += cv_align256(b * Rs * n0 * 8);      // ww
-    s += cv_align256(b * Rs * 8) * 2;       // wT, wSg
+    s += cv_align256(b * Rs * 8) * 3;       // wT, wW, wSg
     s += cv_align256(b * Rs * 4);           // wh
     s += cv_align256(b * 4) * 3;            // wR, wcnt, order
     s += cv_align256((b + 1) * 4);          // ioff
@@ -531,13 +716,16 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     a.wrg = (float*)p; p += cv_align256(B * Rs * n0 * 4);
     a.ww = (long long*)p; p += cv_align256(B * Rs * n0 * 8);
     a.wT = (long long*)p; p += cv_align256(B * Rs * 8);
+    a.wW = (long long*)p; p += cv_align256(B * Rs * 8);
     a.wSg = (double*)p; p += cv_align256(B * Rs * 8);
     a.wh = (float*)p; p += cv_align256(B * Rs * 4);
     a.wR = (int*)p; p += cv_align256(B * 4);
     a.wcnt = (int*)p; p += cv_align256(B * 4);
     a.order = (int*)p; p += cv_align256(B * 4);
     a.ioff = (int*)p; p += cv_align256((B + 1) * 4);
-    a.nplaced = (int*)p; p += 256;
+    a.nplaced = (int*)p;
+    a.wide = a.nplaced + 1;
+    p += 256;
     a.ticket = (unsigned*)p;
     k_cc_prep<<<in->B, 256, 0, st>>>(a);
     CV_LAUNCH_CHECK("k_cc_prep");

@@ -14,7 +14,9 @@ Recipe (one line per workload; sizes follow the paper's benchmark families):
   * splits: drawn uniformly without replacement among the given candidate neuron
     ids, sides uniform (seed 1); per-subdomain counts uniform in [kmin, kmax];
   * extra rows (input-BaB output constraints): the given plane shifted by a
-    uniform offset so that it cuts the box (seed 2).
+    uniform offset so that it cuts the box (seed 2);
+  * random cutting rows (several active rows per subdomain): Gaussian directions,
+    each shifted so that the box centre satisfies it with slack (seed 4).
 """
 from __future__ import annotations
 
@@ -145,6 +147,28 @@ def shifted_plane_rows(a, c, lo, hi, B, seed=2, spread=0.5):
         G[b] = a.astype(np.float32)
         h[b] = np.float32(-(a @ xh) + s * (np.abs(a) @ ep))
     off = np.arange(B + 1, dtype=np.int32)
+    return off, G, h
+
+
+def random_cut_rows(lo, hi, B, kmin, kmax, seed=4, spread=0.6):
+    """kmin..kmax extra rows g.x + h <= 0 per subdomain (CSR), Gaussian directions, each shifted so
+    that the box centre satisfies it with slack s*|g|.eps, s ~ U(0.05, spread): every row cuts the
+    box (neither redundant nor infeasible on its own) and the centre stays feasible."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = lo.shape[1]
+    counts = rng.integers(kmin, kmax + 1, size=B)
+    off = np.zeros(B + 1, np.int32)
+    off[1:] = np.cumsum(counts)
+    G = np.empty((int(off[-1]), n), np.float32)
+    h = np.empty(int(off[-1]), np.float32)
+    for b in range(B):
+        xh = 0.5 * (lo[b].astype(np.float64) + hi[b].astype(np.float64))
+        ep = 0.5 * (hi[b].astype(np.float64) - lo[b].astype(np.float64))
+        for r in range(off[b], off[b + 1]):
+            g = rng.normal(size=n).astype(np.float32)
+            s = rng.uniform(0.05, spread)
+            G[r] = g
+            h[r] = np.float32(-(g.astype(np.float64) @ xh) - s * (np.abs(g.astype(np.float64)) @ ep))
     return off, G, h
 
 

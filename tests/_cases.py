@@ -30,7 +30,8 @@ class Case:
     and one round's batch."""
 
     def __init__(self, dims, B, kmin, kmax, eps, centre="unit", clip01=True, out_rows=0, seed=0,
-                 m_spec=None, sweeps=0, relaxed=1, enforce=1, alpha_mode=0, layers=None, targets=None):
+                 m_spec=None, sweeps=0, relaxed=1, enforce=1, alpha_mode=0, layers=None, targets=None,
+                 cut_rows=None):
         self.layers = layers if layers is not None else WL.he_mlp(dims, seed=seed)
         self.net = O.Net(self.layers)
         dims = list(self.net.dims)
@@ -59,6 +60,11 @@ class Case:
             a = o["final_A"][0, 0]
             self.row_off, self.G, self.h = WL.shifted_plane_rows(a, 0.0, self.lo, self.hi, B, seed=seed + 2)
             self.max_rows = 1
+        if cut_rows is not None:
+            # kmin..kmax random rows cutting each box (several active rows per subdomain)
+            self.row_off, self.G, self.h = WL.random_cut_rows(self.lo, self.hi, B, cut_rows[0], cut_rows[1],
+                                                               seed=seed + 4)
+            self.max_rows = int(np.max(np.diff(self.row_off))) if B else 0
         self.tgt_off = self.tgt_ids = None
         if targets is not None and self.U:
             self.tgt_off, self.tgt_ids = WL.random_targets(self.U, B, targets, seed=seed + 3)

@@ -105,14 +105,17 @@ def test_alpha_autograd_and_finite_difference():
     st = _state(s)
     alpha = E.to_dev(s["alpha"]).requires_grad_(True)
     lower = E.AlphaBound.apply(alpha, st)
-    w = torch.rand_like(lower)
+    gen = torch.Generator(device=alpha.device).manual_seed(11)
+    w = torch.rand(lower.shape, generator=gen, device=alpha.device)
     (lower * w).sum().backward()
     _, g1 = st.bound_and_grad(alpha.detach())
     assert torch.allclose(alpha.grad, g1 * w.unsqueeze(-1))
     # directional derivative of the GPU bound along a random direction (f is affine in each slope
-    # while no relaxation choice flips; a small step keeps the choices)
-    v = torch.randn_like(alpha) * (alpha.grad != 0)
+    # while no relaxation choice flips; a small step keeps the choices, and slopes near 0 or 1 are
+    # left out of the direction so that the clamp to [0, 1] does not cut the step)
     h = 1e-3
+    inner = (alpha.detach() > 0.01) & (alpha.detach() < 0.99)
+    v = torch.randn(alpha.shape, generator=gen, device=alpha.device) * (alpha.grad != 0) * inner
     fp, _ = st.bound_and_grad((alpha.detach() + h * v).clamp(0, 1))
     fm, _ = st.bound_and_grad((alpha.detach() - h * v).clamp(0, 1))
     fd = ((fp - fm) * w).sum().item() / (2 * h)

@@ -47,7 +47,7 @@ constexpr int RTPL = 4;     // row counts up to this run in the main launch (two
 // (target, side) tasks per work item: fewer for subdomains with more rows (longer tasks)
 __host__ __device__ __forceinline__ int tpi_of(int R) { return R <= 1 ? 256 : (R == 2 ? 64 : 16); }
 constexpr int NWARP = 16;   // warps per block at most
-constexpr int CAPC = 256;   // breakpoints a warp's compacted list holds
+constexpr int CAPC = 416;   // breakpoints a warp's compacted list holds
 constexpr int PF = 4;       // coefficients loaded ahead per lane in the element loops
 
 // Exact warp sum of non-negative per-lane 64-bit values whose total is below 2^62: three
@@ -242,13 +242,20 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
     int jprev[R];
 #pragma unroll
     for (int p = 0; p < R; ++p) { beta[p] = 0.f; jprev[p] = -1; }
-    // with one row, a' = a in every sweep, so one pass already repeats bit for bit
+    // With one row, a' = a in every sweep, so one pass already repeats bit for bit.  More
+    // generally a row step depends only on the other rows' multipliers: a row whose inputs have
+    // not changed since its last step would repeat it exactly and is skipped (bit `k` of `dirty`
+    // marks row k as having changed inputs), which leaves every multiplier as the full sweep
+    // order gives it.
     const int nsweeps = (R == 1) ? 1 : a.sweeps;
-    for (int sw = 0; sw < nsweeps; ++sw) {
+    unsigned dirty = (1u << R) - 1u;
+    for (int sw = 0; sw < nsweeps && dirty; ++sw) {
         bool changed = false;
-        my_steps += R;
 #pragma unroll 1
         for (int k = 0; k < R; ++k) {
+            if (!((dirty >> k) & 1u)) continue;
+            dirty &= ~(1u << k);
+            ++my_steps;
             const float* rk = st.rg + k * n0;
             const long long* wk = st.w64 + k * n0;
             float bk = 0.f;
@@ -358,7 +365,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
                     if (it >= 8 && (it & 1)) {
                         mid = lo + ((hi - lo) >> 1);
                     } else {
-                        const float fr = (float)(T - Flo) / (float)(Fhi - Flo);
+                        const float fr = __fdividef((float)(T - Flo), (float)(Fhi - Flo));
                         unsigned off = (unsigned)(fr * (float)(hi - lo));
                         off = min(max(off, 1u), hi - lo - 1u);
                         mid = lo + off;
@@ -434,7 +441,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
 #pragma unroll
             for (int p = 0; p < R; ++p)
                 if (p == k) { beta[p] = bn; jprev[p] = jn; }
-            changed |= (bn != bk);
+            if (bn != bk) {
+                changed = true;
+                dirty |= ((1u << R) - 1u) & ~(1u << k);
+            }
         }
         if (!changed) break;
     }

@@ -213,16 +213,36 @@ __global__ void __launch_bounds__(1024) k_cc_scan(CCArgs a) {
     }
 }
 
-// Shared-memory view of the staged subdomain (rows of the item's subdomain).
-struct Stage {
-    const long long* w64;  // [Rs][n0] fixed-point weights
-    const float* gs;       // [Rs][n0] row coefficients g
-    const float* rg;       // [Rs][n0] fl(1 / g), 0 where g = 0
-    const long long* T64;  // [R] thresholds (fixed point)
-    const long long* W64;  // [R] total weight (fixed point)
-    const float* hrow;     // [R] row constants h
-    const double* Sg;      // [R] magnitude of g against the root box
+// Shared memory of k_complete.  The dynamic part holds, in order: the breakpoint keys of every
+// warp [nw][n0r], the staged subdomain's rows w64 [Rs][n0] (fixed-point weights), g [Rs][n0],
+// fl(1/g) [Rs][n0] (0 where g = 0), and the compacted list elements of every warp [nw][CAPC].
+// Every pointer into it is formed from these namespace-scope arrays with 32-bit offsets, so the
+// compiler addresses them as shared memory.
+extern __shared__ __align__(16) unsigned char cc_smem[];
+__shared__ long long cc_T64[RMAX_CC];  // thresholds (fixed point)
+__shared__ long long cc_W64[RMAX_CC];  // total weights (fixed point)
+__shared__ float cc_hrow[RMAX_CC];     // row constants h
+__shared__ double cc_Sg[RMAX_CC];      // magnitude of g against the root box
+
+struct CCView {
+    unsigned* keys;        // this warp's keys
+    long long* w64;
+    float* gs;
+    float* rg;
+    unsigned short* cidx;  // this warp's list elements
 };
+
+__device__ __forceinline__ CCView cc_view(int n0, int Rs) {
+    const int n0r = (n0 + 31) & ~31;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    CCView v;
+    v.keys = (unsigned*)cc_smem + warp * n0r;
+    v.w64 = (long long*)((unsigned*)cc_smem + nw * n0r);
+    v.gs = (float*)(v.w64 + Rs * n0);
+    v.rg = v.gs + Rs * n0;
+    v.cidx = (unsigned short*)(v.rg + Rs * n0) + warp * CAPC;
+    return v;
+}
 
 constexpr unsigned QINF = 0x7f800000u;  // bits of +inf; breakpoints q > 0 have bits in (0, QINF]
 
@@ -230,10 +250,12 @@ constexpr unsigned QINF = 0x7f800000u;  // bits of +inf; breakpoints q > 0 have 
 // multipliers live in registers).  Breakpoint keys are the raw bits of q_j = (-a'_j) * fl(1/g_kj):
 // for q > 0 (the search range) the unsigned order of the bits is the order of the values.
 template <int R>
-__device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsigned* keys,
-                                        unsigned short* cidx, int b, int c, int side, int lane,
+__device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side, int lane,
                                         unsigned long long& my_steps) {
     const int n0 = a.n0;
+    const CCView sv = cc_view(n0, a.Rs);
+    unsigned* keys = sv.keys;
+    unsigned short* cidx = sv.cidx;
     const size_t o = (size_t)b * a.U + c;
     const float* ap = side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0;
     const float sa = side ? -1.f : 1.f;
@@ -256,8 +278,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
             if (!((dirty >> k) & 1u)) continue;
             dirty &= ~(1u << k);
             ++my_steps;
-            const float* rk = st.rg + k * n0;
-            const long long* wk = st.w64 + k * n0;
+            const float* rk = sv.rg + k * n0;
+            const long long* wk = sv.w64 + k * n0;
             float bk = 0.f;
             int jp = -1;
 #pragma unroll
@@ -269,7 +291,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
 #pragma unroll
                 for (int p = 0; p < R; ++p) {
                     if (R > 1) {
-                        const float t = fmaf(beta[p], st.gs[p * n0 + j], apr);
+                        const float t = fmaf(beta[p], sv.gs[p * n0 + j], apr);
                         apr = (p != k) ? t : apr;
                     }
                 }
@@ -279,34 +301,52 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
             float qp = 0.f;
             if (jp >= 0) qp = q_of(__ldg(ap + jp), jp);
             const bool warm = qp > 0.f;
-            const long long T = st.T64[k];
-            const long long W = st.W64[k];
+            const long long T = cc_T64[k];
+            const long long W = cc_W64[k];
             // One pass over all n0 elements keeps the keys in the warp's buffer.  Without a previous
             // breakpoint it takes F(0) = sum_{q <= 0} w and the extent and size of the search range;
             // with one, F just below and at it.  F(+inf) is the row's total weight W.
+            // (Branch-free element loops: indices past n0 are clamped and contribute nothing.)
             unsigned long long f0 = 0, flt = 0, fle = 0;
             unsigned mn = 0xffffffffu, mx = 0u, cnt = 0u;
+            if (warm) {
 #pragma unroll 1
-            for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
-                float av[PF];
+                for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
+                    float av[PF];
 #pragma unroll
-                for (int u = 0; u < PF; ++u) av[u] = (j0 + 32 * u < n0) ? __ldg(ap + j0 + 32 * u) : 0.f;
+                    for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
 #pragma unroll
-                for (int u = 0; u < PF; ++u) {
-                    const int j = j0 + 32 * u;
-                    if (j < n0) {
-                        const float q = q_of(av[u], j);
+                    for (int u = 0; u < PF; ++u) {
+                        const int j = j0 + 32 * u;
+                        const bool v = j < n0;
+                        const int jj = v ? j : n0 - 1;
+                        const float q = q_of(av[u], jj);
+                        if (v) keys[j] = __float_as_uint(q);
+                        const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
+                        flt += (q < qp) ? w : 0ull;
+                        fle += (q <= qp) ? w : 0ull;
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
+                    float av[PF];
+#pragma unroll
+                    for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
+#pragma unroll
+                    for (int u = 0; u < PF; ++u) {
+                        const int j = j0 + 32 * u;
+                        const bool v = j < n0;
+                        const int jj = v ? j : n0 - 1;
+                        const float q = q_of(av[u], jj);
                         const unsigned kk = __float_as_uint(q);
-                        keys[j] = kk;
-                        const unsigned long long w = (unsigned long long)wk[j];
-                        if (warm) {
-                            flt += (q < qp) ? w : 0ull;
-                            fle += (q <= qp) ? w : 0ull;
-                        } else if (q > 0.f) {
-                            mn = min(mn, kk); mx = max(mx, kk); ++cnt;
-                        } else if (q <= 0.f) {
-                            f0 += w;
-                        }
+                        if (v) keys[j] = kk;
+                        const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
+                        const bool pos = v && q > 0.f;
+                        f0 += (q <= 0.f) ? w : 0ull;
+                        mn = min(mn, pos ? kk : 0xffffffffu);
+                        mx = max(mx, pos ? kk : 0u);
+                        cnt += pos ? 1u : 0u;
                     }
                 }
             }
@@ -331,8 +371,12 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
 #pragma unroll 4
                     for (int j = lane; j < n0; j += 32) {
                         const unsigned kk = keys[j];
-                        if (__uint_as_float(kk) <= 0.f) f0 += (unsigned long long)wk[j];
-                        if (kk > lo && kk <= hi) { mn = min(mn, kk); mx = max(mx, kk); ++cnt; }
+                        const unsigned long long w = (unsigned long long)wk[j];
+                        f0 += (__uint_as_float(kk) <= 0.f) ? w : 0ull;
+                        const bool in = kk > lo && kk <= hi;
+                        mn = min(mn, in ? kk : 0xffffffffu);
+                        mx = max(mx, in ? kk : 0u);
+                        cnt += in ? 1u : 0u;
                     }
                     const long long F0 = warp_sum64(f0);
                     if (lo == 0u) Flo = F0;
@@ -371,37 +415,36 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
                         mid = lo + off;
                     }
                     const bool wr = listed || ncnt <= (unsigned)CAPC;
+                    // F at the pivot; the largest key at or below it and the smallest above it (the
+                    // other extreme of either half is the bracket's own, cmin or cmax)
                     unsigned long long fm = 0;
-                    unsigned mnL = 0xffffffffu, mxL = 0u, mnR = 0xffffffffu, mxR = 0u, cl = 0u;
+                    unsigned mxL = 0u, mnR = 0xffffffffu, cl = 0u;
                     int wpos = 0;
 #pragma unroll 1
                     for (int j0 = 0; j0 < m; j0 += 32) {
                         const int j = j0 + lane;
-                        unsigned kk = 0u;
-                        int e = j;
-                        if (j < m) {
-                            kk = keys[j];
-                            if (listed) e = cidx[j];
-                        }
-                        const bool in = j < m && kk > lo && kk <= hi;
+                        const bool v = j < m;
+                        const int jj = v ? j : 0;
+                        const unsigned kk = keys[jj];
+                        const int e = v ? (listed ? (int)cidx[jj] : jj) : 0;
+                        const bool in = v && kk > lo && kk <= hi;
                         if (wr) {
                             // in-place compaction: every write lands at or before the position read
                             const unsigned bal = __ballot_sync(0xffffffffu, in);
+                            const int q = wpos + __popc(bal & below);
                             if (in) {
-                                const int q = wpos + __popc(bal & below);
                                 keys[q] = kk;
                                 cidx[q] = (unsigned short)e;
                             }
                             wpos += __popc(bal);
                         }
-                        if (in) {
-                            if (kk <= mid) {
-                                fm += (unsigned long long)wk[e];
-                                mnL = min(mnL, kk); mxL = max(mxL, kk); ++cl;
-                            } else {
-                                mnR = min(mnR, kk); mxR = max(mxR, kk);
-                            }
-                        }
+                        const unsigned long long w = (unsigned long long)wk[e];
+                        const bool L = in && kk <= mid;
+                        const bool Rt = in && kk > mid;
+                        fm += L ? w : 0ull;
+                        mxL = max(mxL, L ? kk : 0u);
+                        mnR = min(mnR, Rt ? kk : 0xffffffffu);
+                        cl += L ? 1u : 0u;
                     }
                     __syncwarp();
                     if (wr) { listed = true; m = wpos; }
@@ -409,13 +452,11 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
                     const unsigned nl = __reduce_add_sync(0xffffffffu, cl);
                     if (Fm >= T) {
                         hi = mid; Fhi = Fm;
-                        cmin = __reduce_min_sync(0xffffffffu, mnL);
-                        cmax = __reduce_max_sync(0xffffffffu, mxL);
+                        cmax = __reduce_max_sync(0xffffffffu, mxL);  // cmin stays
                         ncnt = nl;
                     } else {
                         lo = mid; Flo = Fm;
-                        cmin = __reduce_min_sync(0xffffffffu, mnR);
-                        cmax = __reduce_max_sync(0xffffffffu, mxR);
+                        cmin = __reduce_min_sync(0xffffffffu, mnR);  // cmax stays
                         ncnt -= nl;
                     }
                 }
@@ -465,21 +506,19 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
         float av[PF], lv[PF], hv[PF];
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
-            const int j = j0 + 32 * u;
-            const bool in = j < n0;
-            av[u] = in ? __ldg(ap + j) : 0.f;
-            lv[u] = in ? __ldg(slo + j) : 0.f;
-            hv[u] = in ? __ldg(shi + j) : 0.f;
+            const int jj = min(j0 + 32 * u, n0 - 1);
+            const bool in = j0 + 32 * u < n0;
+            av[u] = __ldg(ap + jj);
+            lv[u] = in ? __ldg(slo + jj) : 0.f;
+            hv[u] = in ? __ldg(shi + jj) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
-            const int j = j0 + 32 * u;
-            if (j < n0) {
-                float v = sa * av[u];
+            const int jj = min(j0 + 32 * u, n0 - 1);
+            float v = sa * av[u];
 #pragma unroll
-                for (int p = 0; p < R; ++p) v = fmaf(beta[p], st.gs[p * n0 + j], v);
-                part += fminf(v * lv[u], v * hv[u]);
-            }
+            for (int p = 0; p < R; ++p) v = fmaf(beta[p], sv.gs[p * n0 + jj], v);
+            part += fminf(v * lv[u], v * hv[u]);  // 0 past n0 (lv = hv = 0)
         }
     }
 #pragma unroll
@@ -488,8 +527,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
     double scale = (double)psc + fabs((double)c0);
 #pragma unroll
     for (int p = 0; p < R; ++p) {
-        cst = fmaf(beta[p], st.hrow[p], cst);
-        scale += (double)beta[p] * (st.Sg[p] + fabs((double)st.hrow[p]));
+        cst = fmaf(beta[p], cc_hrow[p], cst);
+        scale += (double)beta[p] * (cc_Sg[p] + fabs((double)cc_hrow[p]));
     }
     const double gam = (double)(R + (n0 + 31) / 32 + 12) * CV_U32;
     const float pad = __double2float_ru(gam * scale * 1.0001);
@@ -501,14 +540,14 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
         for (int j = lane; j < n0; j += 32) {
             double v = (double)(sa * __ldg(ap + j));
 #pragma unroll
-            for (int p = 0; p < R; ++p) v += (double)beta[p] * (double)st.gs[p * n0 + j];
+            for (int p = 0; p < R; ++p) v += (double)beta[p] * (double)sv.gs[p * n0 + j];
             d += fmin(v * (double)__ldg(slo + j), v * (double)__ldg(shi + j));
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
         d += (double)c0;
 #pragma unroll
-        for (int p = 0; p < R; ++p) d += (double)beta[p] * (double)st.hrow[p];
+        for (int p = 0; p < R; ++p) d += (double)beta[p] * (double)cc_hrow[p];
         val = __double2float_rd(d - ldexp(scale, -40));
     }
     if (lane == 0) {
@@ -521,22 +560,14 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const Stage& st, unsign
 // otherwise the rest.
 template <bool WIDE>
 __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
     const int n0 = a.n0, Rs = a.Rs, B = a.B;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int n0r = (n0 + 31) & ~31;
-    // shared: keys [nw][n0r] | w64 [Rs][n0] | g [Rs][n0] | 1/g [Rs][n0] | list elements [nw][CAPC]
-    unsigned* keys = (unsigned*)smem + (size_t)warp * n0r;  // this warp's breakpoint keys
-    long long* w64 = (long long*)((unsigned*)smem + (size_t)nw * n0r);
-    float* gs = (float*)(w64 + (size_t)Rs * n0);
-    float* rg = gs + (size_t)Rs * n0;
-    unsigned short* cidx = (unsigned short*)(rg + (size_t)Rs * n0) + (size_t)warp * CAPC;
-    __shared__ long long T64[RMAX_CC], W64[RMAX_CC];
-    __shared__ float hrow[RMAX_CC];
-    __shared__ double Sg[RMAX_CC];
+    const int lane = threadIdx.x & 31;
+    const CCView sv = cc_view(n0, Rs);
+    long long* w64 = sv.w64;
+    float* gs = sv.gs;
+    float* rg = sv.rg;
     __shared__ int s_item, s_pos, s_R, s_next;
     __shared__ unsigned long long nsteps;
-    const Stage st{w64, gs, rg, T64, W64, hrow, Sg};
     if (threadIdx.x == 0) nsteps = 0;
     unsigned long long my_steps = 0;
     const int ibeg = WIDE ? 0 : *a.wide;
@@ -574,10 +605,10 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
                 rg[i] = a.wrg[base + i];
             }
             if (threadIdx.x < R) {
-                T64[threadIdx.x] = a.wT[(size_t)b * Rs + threadIdx.x];
-                W64[threadIdx.x] = a.wW[(size_t)b * Rs + threadIdx.x];
-                hrow[threadIdx.x] = a.wh[(size_t)b * Rs + threadIdx.x];
-                Sg[threadIdx.x] = a.wSg[(size_t)b * Rs + threadIdx.x];
+                cc_T64[threadIdx.x] = a.wT[(size_t)b * Rs + threadIdx.x];
+                cc_W64[threadIdx.x] = a.wW[(size_t)b * Rs + threadIdx.x];
+                cc_hrow[threadIdx.x] = a.wh[(size_t)b * Rs + threadIdx.x];
+                cc_Sg[threadIdx.x] = a.wSg[(size_t)b * Rs + threadIdx.x];
             }
             cur_b = b;
         }
@@ -604,17 +635,17 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
             if (a.mask[(size_t)b * a.U + c] != 0) continue;
             if (WIDE) {
                 switch (R) {
-                    case 5: cc_task<5>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
-                    case 6: cc_task<6>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
-                    case 7: cc_task<7>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
-                    default: cc_task<8>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    case 5: cc_task<5>(a, b, c, side, lane, my_steps); break;
+                    case 6: cc_task<6>(a, b, c, side, lane, my_steps); break;
+                    case 7: cc_task<7>(a, b, c, side, lane, my_steps); break;
+                    default: cc_task<8>(a, b, c, side, lane, my_steps); break;
                 }
             } else {
                 switch (R) {
-                    case 1: cc_task<1>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
-                    case 2: cc_task<2>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
-                    case 3: cc_task<3>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
-                    default: cc_task<4>(a, st, keys, cidx, b, c, side, lane, my_steps); break;
+                    case 1: cc_task<1>(a, b, c, side, lane, my_steps); break;
+                    case 2: cc_task<2>(a, b, c, side, lane, my_steps); break;
+                    case 3: cc_task<3>(a, b, c, side, lane, my_steps); break;
+                    default: cc_task<4>(a, b, c, side, lane, my_steps); break;
                 }
             }
             __syncwarp();

@@ -5,7 +5,7 @@ relaxed clipping, re-concretisation, complete clipping, spec back-substitution) 
 synthetic subdomains of the 784->256x6->10 ReLU MLP workload (4096 subdomains, 1-4 split
 constraints each, 9 margin rows, 10 coordinate-ascent sweeps).  Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--precision fp32|bf16x6]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--precision fp32|bf16x8]
 
 --impl reference times the FP64 CPU oracle on the host cores (the slow reference program).
 Under torchrun every rank bounds its own batch (weak scaling, no data-path collective)."""
@@ -41,7 +41,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16x6"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16x8"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--subdomains", type=int, default=0,
                    help="smaller batch for profiler captures (default: the workload's own batch)")
@@ -185,7 +185,7 @@ def main():
     lo, hi = WL.tile_box(lo0, hi0, B)
     C, t = WL.margin_spec(dims[-1])
     m = C.shape[0]
-    prec = capi.CV_PREC_FP32 if args.precision == "fp32" else capi.CV_PREC_BF16X6
+    prec = capi.CV_PREC_FP32 if args.precision == "fp32" else capi.CV_PREC_BF16X8
     rnd = E.Round(net, B, m, max_splits=kmax, relaxed=cfg["relaxed"], sweeps=cfg["sweeps"], precision=prec)
     timer = capi.cv_timer_create()
     rnd.opt.timer = timer
@@ -272,7 +272,8 @@ def main():
     if rank == 0:
         line = dict(metric="subdomains bounded+clipped per second", value=value, unit="subdomains/s", n_gpus=world,
                     steps=args.steps, warmup=max(args.warmup, 3), ms_per_step=total_ms / args.steps,
-                    higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                    higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f32" if args.precision == "fp32" else "bf16x8+f32", data="synthetic",
                     config=dict(workload=workload_desc(cfg), precision=args.precision, cached_neurons=U,
                                 l2="flushed (256 MiB write) before every timed step",
                                 phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],

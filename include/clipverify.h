@@ -56,7 +56,8 @@ typedef int cv_status;
 
 /* Precision of the contractions (re-concretisation and back-substitution). */
 #define CV_PREC_FP32   0  /* CUDA-core FP32 with chunked, compensated accumulation */
-#define CV_PREC_BF16X6 1  /* tensor cores (tcgen05), operands split into three BF16 slices */
+#define CV_PREC_BF16X8 1  /* spec back-substitution on tcgen05 tensor cores: operands split into three
+                                 * BF16 digit slices, eight exact slice products per tile step */
 
 /* Lower slope of an unstable ReLU when no per-row alpha is given. */
 #define CV_ALPHA_ADAPTIVE 0  /* alpha = 1 if u >= -l else 0 */
@@ -96,7 +97,9 @@ cv_status cv_net_dims(const cv_net* net, int* n_layers, int* dims, int* n_hidden
 /* Synchronises `stream`, returns CV_OK or CV_EDEVICE if a kernel flagged a bad input
  * since the last call, and clears the flag.  `code` (may be NULL) receives the raw
  * device status word (bit 0: CSR count above the stated maximum, bit 1: split id out
- * of range, bit 2: non-finite box, bit 3: target slot out of range). */
+ * of range, bit 2: non-finite box, bit 3: target slot out of range, bit 4: a wait inside the
+ * tensor-core back-substitution (CV_PREC_BF16X8) ran out; that round's spec bounds are not
+ * valid). */
 cv_status cv_device_status(cv_net* net, void* stream, int* code);
 
 /* ---------------------------------------------------------------- root cache */

@@ -19,7 +19,7 @@ CV_OK = 0
 CV_LAYER_DENSE = 0
 CV_LAYER_CONV2D = 1
 CV_PREC_FP32 = 0
-CV_PREC_BF16X6 = 1
+CV_PREC_BF16X8 = 1
 CV_ALPHA_ADAPTIVE = 0
 CV_ALPHA_ONE = 1
 CV_ALPHA_ZERO = 2

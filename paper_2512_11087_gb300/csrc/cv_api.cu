@@ -29,7 +29,7 @@ extern "C" void cv_options_default(cv_options* o) {
 }
 
 cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
-                     int max_rows, cv_ws_layout* lay) {
+                     int max_rows, int precision, cv_ws_layout* lay) {
     memset(lay, 0, sizeof(*lay));
     lay->Rmax = max_splits + max_rows;
     lay->R = B * m;
@@ -49,6 +49,11 @@ cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int
     lay->acc_bias = take(R * sizeof(double));
     lay->acc_pad = take(R * sizeof(double));
     lay->cc = take(cv_cc_workspace(B, lay->Rmax, net->dims[0]));
+    if (precision == CV_PREC_BF16X8) {
+        lay->tc_slices = take(cv_tc_slices_bytes(net, lay->R));
+        lay->tc_exp = take(R * sizeof(int));
+        lay->tc_tab = take((size_t)3 * B * net->wmax * sizeof(float));
+    }
     lay->total = off;
     return CV_OK;
 }
@@ -62,7 +67,7 @@ static cv_status validate(const cv_net* net, const cv_cache* cache, const cv_bat
         return CV_EINVAL;
     }
     if (opt->sweeps < 0 || opt->alpha_mode < 0 || opt->alpha_mode > 2 ||
-        (opt->precision != CV_PREC_FP32 && opt->precision != CV_PREC_BF16X6)) {
+        (opt->precision != CV_PREC_FP32 && opt->precision != CV_PREC_BF16X8)) {
         cv_set_error("bad options");
         return CV_EINVAL;
     }
@@ -85,7 +90,7 @@ extern "C" cv_status cv_bound_batch_workspace(const cv_net* net, const cv_cache*
     if (s) return s;
     if (!bytes) { cv_set_error("null bytes"); return CV_EINVAL; }
     cv_ws_layout lay;
-    cv_ws_plan(net, cache, in->B, in->m, in->max_splits, in->max_rows, &lay);
+    cv_ws_plan(net, cache, in->B, in->m, in->max_splits, in->max_rows, opt->precision, &lay);
     *bytes = lay.total;
     return CV_OK;
 }
@@ -115,12 +120,12 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
         cv_set_error("required output pointer is null");
         return CV_EINVAL;
     }
-    if (opt->precision != CV_PREC_FP32) {
-        cv_set_error("this build implements precision CV_PREC_FP32 only");
+    if (opt->precision == CV_PREC_BF16X8 && !cv_tc_supported(cache)) {
+        cv_set_error("CV_PREC_BF16X8: the tensor-core back-substitution takes layers of at most 512 inputs");
         return CV_EUNSUPPORTED;
     }
     cv_ws_layout lay;
-    cv_ws_plan(net, cache, B, m, in->max_splits, in->max_rows, &lay);
+    cv_ws_plan(net, cache, B, m, in->max_splits, in->max_rows, opt->precision, &lay);
     if (!workspace || workspace_bytes < lay.total) {
         cv_set_error("workspace too small: need " + std::to_string(lay.total) + " bytes");
         return CV_EWORKSPACE;
@@ -152,7 +157,16 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
                                 out->infeasible, steps, &launches, st)))
         return s;
     if (tm) CV_CUDA(cudaEventRecord(tm->ev[3], st));
-    if (m > 0) {
+    if (m > 0 && opt->precision == CV_PREC_BF16X8) {
+        s = cv_backward_tc(net, cache, lay.R, m, in->C, in->t, out->l, out->u, out->mask, U, in->alpha,
+                           opt->alpha_mode, out->lo_clip, out->hi_clip, out->infeasible, out->lower, out->err_bound,
+                           out->final_A, out->final_c, (float*)(ws + lay.lam0), (float*)(ws + lay.lam1),
+                           (uint16_t*)(ws + lay.tc_slices), (int*)(ws + lay.tc_exp), (float*)(ws + lay.tc_tab),
+                           (double*)(ws + lay.part_bias),
+                           (double*)(ws + lay.part_pad), (double*)(ws + lay.part_f), (double*)(ws + lay.part_fmag),
+                           (double*)(ws + lay.acc_bias), (double*)(ws + lay.acc_pad), &launches, st);
+        if (s) return s;
+    } else if (m > 0) {
         s = cv_backward_t<float>(net, lay.R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
                             cache->root_state, cache->slot_of, out->l, out->u, out->mask, U, in->alpha,
                             opt->alpha_mode, cache->V, out->lo_clip, out->hi_clip, out->infeasible, out->lower,

@@ -242,14 +242,14 @@ __global__ void k_bwd_reduce(int R, int ncb, double gam, const double* part_bias
 __global__ void k_bwd_final(int R, int ncb, int rows_per_sub, const double* part_f,
                             const double* part_fmag, const double* acc_bias, const double* acc_pad,
                             const uint8_t* skip, float* lower, double* lower64, float* err, float* bias_out,
-                            double* bias_raw, double* pad_raw) {
+                            double* bias_raw, double* pad_raw, double fm_gamma) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     double f = 0.0, fm = 0.0;
     for (int c = 0; c < ncb; ++c) { f += part_f[(size_t)r * ncb + c]; fm += part_fmag[(size_t)r * ncb + c]; }
     // FP64 rounding of the sums above and of the bias accumulation: <= 2^-40 of the magnitudes
     const double b = acc_bias[r];
-    const double pad = acc_pad[r] * (1.0 + 1e-6) + ldexp(fm + fabs(b) + acc_pad[r], -40);
+    const double pad = acc_pad[r] * (1.0 + 1e-6) + fm_gamma * fm + ldexp(fm + fabs(b) + acc_pad[r], -40);
     const double v = f + b - pad;
     const bool sk = skip && skip[r / rows_per_sub];
     if (lower) lower[r] = sk ? INFINITY : __double2float_rd(v);
@@ -312,7 +312,7 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
         } else {
             k_bwd_final<<<(R + 255) / 256, 256, 0, st>>>(R, a.ncb, rows_per_sub, part_f, part_fmag,
                                                          acc_bias, acc_pad, skip, lower, lower64, err, bias_out,
-                                                         bias_raw, pad_raw);
+                                                         bias_raw, pad_raw, 0.0);
             CV_LAUNCH_CHECK("k_bwd_final");
         }
     }
@@ -339,4 +339,32 @@ int cv_bwd_ncb_max(const cv_net* net) {
     int w = 0;
     for (int i = 0; i < net->L; ++i) w = net->dims[i] > w ? net->dims[i] : w;
     return (w + BN - 1) / BN;
+}
+
+// Launchers of the spec-bound steps shared with the tensor-core back-substitution (cv_tc.cu):
+// the start from the spec rows, the per-layer reduction of the row partials, and the final
+// concretisation (fm_gamma: extra pad per unit of the concretisation's magnitude sum).
+cv_status cv_bwd_spec_init(int R, int nk, int m, const float* C, const float* t, const float* bk, const float* Vk,
+                           float* A, double* acc_bias, double* acc_pad, cudaStream_t st) {
+    dim3 blk(32, 8);
+    dim3 grd((R + 7) / 8);
+    k_bwd_init<float><<<grd, blk, 0, st>>>(R, nk, 1, m, nullptr, C, t, bk, Vk, A, acc_bias, acc_pad);
+    CV_LAUNCH_CHECK("k_bwd_init");
+    return CV_OK;
+}
+
+cv_status cv_bwd_reduce(int R, int ncb, const double* part_bias, const double* part_pad, double* acc_bias,
+                        double* acc_pad, cudaStream_t st) {
+    k_bwd_reduce<<<(R + 255) / 256, 256, 0, st>>>(R, ncb, Gam<float>::v, part_bias, part_pad, acc_bias, acc_pad);
+    CV_LAUNCH_CHECK("k_bwd_reduce");
+    return CV_OK;
+}
+
+cv_status cv_bwd_final(int R, int ncb, int rows_per_sub, const double* part_f, const double* part_fmag,
+                       const double* acc_bias, const double* acc_pad, const uint8_t* skip, float* lower, float* err,
+                       float* bias_out, double fm_gamma, cudaStream_t st) {
+    k_bwd_final<<<(R + 255) / 256, 256, 0, st>>>(R, ncb, rows_per_sub, part_f, part_fmag, acc_bias, acc_pad, skip,
+                                                 lower, nullptr, err, bias_out, nullptr, nullptr, fm_gamma);
+    CV_LAUNCH_CHECK("k_bwd_final");
+    return CV_OK;
 }

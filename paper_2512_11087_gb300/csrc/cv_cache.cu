@@ -135,6 +135,7 @@ void cache_free(cv_cache* c) {
     cudaFree(c->uc); cudaFree(c->PC); cudaFree(c->PCc); cudaFree(c->pscale); cudaFree(c->root_l);
     cudaFree(c->root_u); cudaFree(c->root_state); cudaFree(c->root_lo); cudaFree(c->root_hi);
     for (int i = 0; i <= CV_MAX_LAYERS; ++i) cudaFree(c->V[i]);
+    cv_tc_release(c);
     delete c;
 }
 
@@ -284,10 +285,11 @@ static cv_status finish_cache(cv_cache* c, cudaStream_t st) {
         k_padweights<<<(n->dims[i] + 7) / 8, blk, 0, st>>>(n->dims[i], n->dims[i - 1], n->W[i], n->b[i], zm, c->V[i]);
     }
     CV_LAUNCH_CHECK("cache tables");
+    cv_status s = cv_tc_prepare(c, xmag, zmag, st);
     CV_CUDA(cudaStreamSynchronize(st));
     cudaFree(xmag);
     cudaFree(zmag);
-    return CV_OK;
+    return s;
 }
 
 static cv_status new_cache(cv_net* net, cv_cache** out) {

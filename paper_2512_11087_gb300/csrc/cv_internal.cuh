@@ -1,6 +1,7 @@
 // Internal declarations of the Clip-and-Verify GB300 library (not part of the C-ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -28,6 +29,7 @@ cv_status cv_cuda_fail(cudaError_t e, const char* what);
 #define CV_DEV_SPLIT_RANGE 2
 #define CV_DEV_NONFINITE   4
 #define CV_DEV_TARGET      8
+#define CV_DEV_TIMEOUT     16
 
 // unit roundoff of FP32 round-to-nearest (with a small safety factor)
 #define CV_U32 (5.9604644775390625e-08 * 1.0001)
@@ -43,6 +45,17 @@ struct cv_net {
     float* b[CV_MAX_LAYERS + 1]; // device, b[i]: dims[i]
     int* status;                 // device status word
     int device;
+};
+
+// Split-BF16 copy of one layer's weights for the tensor-core back-substitution (cv_tc.cu).
+// W^(i) [K x N] is stored transposed (K-major) as three BF16 digit slices of the column-scaled
+// 24-bit fixed-point values, zero padded to Np x Kp (multiples of 64).
+struct cv_tc_w {
+    uint16_t* slices;   // [3][Np][Kp] BF16 bit patterns
+    int* fexp;          // [N] column exponents: |W_kq| <= 2^fexp[q]
+    double F1, F2;      // sum_q 2^fexp[q] zmag_q and sum_q (sum_k |W_kq|) zmag_q (pad constants)
+    int K, N, Kp, Np;
+    CUtensorMap tmap;   // 3-D map {Kp, Np, 3}, box {64, 64, 1}, 128-byte swizzle
 };
 
 struct cv_cache {
@@ -63,6 +76,7 @@ struct cv_cache {
     float* V[CV_MAX_LAYERS + 1]; // V[i] [dims[i]]: |W^(i)| zmag^(i-1) + |b^(i)| (pad weights)
     float* root_lo;    // [n0]
     float* root_hi;    // [n0]
+    cv_tc_w* tcw[CV_MAX_LAYERS + 1]; // tensor-core weights per layer (host objects), or null
 };
 
 struct cv_timer {
@@ -78,11 +92,26 @@ __host__ __device__ inline size_t cv_align256(size_t x) { return (x + 255) & ~(s
 // workspace carving: returns the offset of the next 256-aligned block
 struct cv_ws_layout {
     size_t rowflag, vmin, lam0, lam1, part_bias, part_pad, part_f, part_fmag, acc_bias, acc_pad, rowdesc, cc, total;
+    size_t tc_slices, tc_exp, tc_tab;  // split-BF16 back-substitution scratch (CV_PREC_BF16X8 only)
     int R, Rmax, ncb;  // rows of the spec backward, max constraint rows, column blocks
 };
 size_t cv_cc_workspace(int B, int Rmax, int n0);  // complete-clipping region (cv_complete.cu)
 cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
-                     int max_rows, cv_ws_layout* lay);
+                     int max_rows, int precision, cv_ws_layout* lay);
+
+// Tensor-core back-substitution (cv_tc.cu).  cv_tc_prepare builds the split weights of every
+// layer once per cache (called by the cache constructors; layers whose shape the path does not
+// take keep a null entry); cv_tc_release frees them.  cv_tc_slices_bytes: digit-slice scratch of R rows.
+cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaStream_t st);
+void cv_tc_release(cv_cache* c);
+bool cv_tc_supported(const cv_cache* c);
+size_t cv_tc_slices_bytes(const cv_net* net, int R);
+cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m, const float* C, const float* t,
+                         const float* l, const float* u, const int8_t* mask, int U, const float* alpha,
+                         int alpha_mode, const float* lo, const float* hi, const uint8_t* skip, float* lower,
+                         float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
+                         int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
+                         double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st);
 
 // kernels (launch wrappers); each returns CV_OK or a launch error
 cv_status cv_launch_rows(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
@@ -127,4 +156,11 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
                         T* const* keepP, cudaStream_t st);
 int cv_bwd_ncb_max(const cv_net* net);
+cv_status cv_bwd_spec_init(int R, int nk, int m, const float* C, const float* t, const float* bk, const float* Vk,
+                           float* A, double* acc_bias, double* acc_pad, cudaStream_t st);
+cv_status cv_bwd_reduce(int R, int ncb, const double* part_bias, const double* part_pad, double* acc_bias,
+                        double* acc_pad, cudaStream_t st);
+cv_status cv_bwd_final(int R, int ncb, int rows_per_sub, const double* part_f, const double* part_fmag,
+                       const double* acc_bias, const double* acc_pad, const uint8_t* skip, float* lower, float* err,
+                       float* bias_out, double fm_gamma, cudaStream_t st);
 

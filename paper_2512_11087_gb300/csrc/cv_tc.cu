@@ -1,0 +1,635 @@
+// Tensor-core back-substitution of the spec rows (a7 with precision CV_PREC_BF16X8): every
+// contraction P = Lam^(i) W^(i) of the CROWN recursion runs on tcgen05 tensor cores with TMA-fed
+// shared-memory tiles, at exactly known error.
+//
+// Split arithmetic.  A row r of Lam (and a column q of W) is scaled by a power of two 2^e_r
+// (2^f_q) not below its largest magnitude and rounded to a 24-bit fixed-point integer N, |N| <=
+// 2^23, with |x 2^-e - N 2^-23| <= 2^-24.  N is written in balanced base-256 digits,
+// N = X1 2^16 + X2 2^8 + X3 with X1 in [-128, 128] and X2, X3 in [-128, 127]; every digit is exact
+// in BF16.  The digit products X_i Y_j (|.| <= 2^14) are grouped by level s = i + j:
+//     P_rq = 2^(e_r + f_q - 46) sum_s L_s 2^(8 (6 - s)),  L_s = sum_k sum_{i+j=s} X_i(r,k) Y_j(k,q).
+// Levels 2..5 are kept (eight BF16 MMAs per K step: (1,1) (1,2) (2,1) (1,3) (2,2) (3,1) (2,3)
+// (3,2)); level 6 (X3 Y3 <= 2^14 per term) is dropped.  For K <= 256 every partial sum of every
+// level is an integer below 2^24 (level 4: 3 K 2^14 <= 1.5 2^23), so the FP32 accumulation in
+// tensor memory is exact in any order; longer K runs in chunks of 256 with an accumulator set
+// per chunk.  The error of P against the exact product of the FP32 operands is therefore
+//     |dP_rq| <= c 2^-24 (2^f_q S_r + 2^e_r T_q) + 2^(e_r + f_q) K 2^-31,
+//     S_r = sum_k |Lam_rk|,  T_q = sum_k |W_kq|,  c = 1 + 2^-6
+// (quantisation of both operands, the dropped level, and the FP32 sum of the four levels in the
+// epilogue, whose rounding is also covered by the gamma |Lam| V pad of the FP32 path).  Its
+// effect on the bound, sum_q |dP_rq| zmag_q, is charged to the row's pad by the splitting
+// kernel: 2^-24 c (S_r F1 + 2^e_r F2) + 2^e_r K 2^-31 F1, F1 = sum_q 2^f_q zmag_q,
+// F2 = sum_q T_q zmag_q (per layer, computed with the split weights).
+//
+// Tiles.  One CTA computes 128 rows x 64 columns of P over all of K: TMA loads the three digit
+// slices of the row tile and of the column tile (128-byte swizzle) into a two-stage ring; one
+// thread issues the tcgen05.mma instructions (M = 128, N = 64, K = 16) into four (or eight)
+// FP32 accumulators in tensor memory and commits each stage back to its producer; the four warps
+// then read their 32 rows of every accumulator with tcgen05.ld, form P in FP32 and run the
+// relaxation epilogue of the FP32 path (cv_backward.cu).  Every wait on an mbarrier is bounded;
+// a wait that runs out sets a status bit and the CTA skips the rest of its work.
+#include "cv_internal.cuh"
+
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+namespace {
+
+constexpr int TBM = 128, TBN = 64, TBK = 64;  // CTA tile and K step of the TMA boxes
+constexpr int KCH = 256;                       // K rows per exact accumulator set
+constexpr int KMAX = 512;                      // longest K the path takes (two sets)
+constexpr int NLEV = 4;                        // kept levels 2..5
+constexpr double PAD_C = 1.0 + 1.0 / 64.0;
+
+// balanced base-256 digits of |n| <= 2^23
+__device__ __forceinline__ void digits3(int n, int& x1, int& x2, int& x3) {
+    x3 = ((n + 128) & 255) - 128;
+    n = (n - x3) >> 8;
+    x2 = ((n + 128) & 255) - 128;
+    x1 = (n - x2) >> 8;
+}
+
+__device__ __forceinline__ uint16_t bf16_of_int(int v) {
+    // small integers (|v| <= 128) are exact in BF16: the top half of the FP32 pattern
+    return (uint16_t)(__float_as_uint((float)v) >> 16);
+}
+
+// exponent e with max_abs <= 2^e (0 for an all-zero vector)
+__device__ __forceinline__ int pow2_ceil_exp(float max_abs) {
+    if (!(max_abs > 0.f)) return 0;
+    int e;
+    frexpf(max_abs, &e);  // max_abs = m 2^e, m in [0.5, 1)
+    return e;
+}
+
+// Split the columns of W^(i) [K x N] into the digit slices of W^T [3][Np][Kp]; fexp, the column
+// sums T_q and the pad constants F1, F2 (accumulated in FP64 atomics).  One warp per column.
+__global__ void k_tc_wsplit(int K, int N, int Kp, int Np, const float* W, const float* zmag, uint16_t* S,
+                            int* fexp, double* F) {
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (q >= Np) return;
+    const size_t plane = (size_t)Np * Kp;
+    if (q >= N) {
+        for (int k = lane; k < Kp; k += 32) {
+            S[(size_t)q * Kp + k] = 0; S[plane + (size_t)q * Kp + k] = 0; S[2 * plane + (size_t)q * Kp + k] = 0;
+        }
+        return;
+    }
+    float mx = 0.f;
+    double tsum = 0.0;
+    for (int k = lane; k < K; k += 32) {
+        const float w = fabsf(W[(size_t)k * N + q]);
+        mx = fmaxf(mx, w);
+        tsum += (double)w;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        tsum += __shfl_xor_sync(0xffffffffu, tsum, off);
+    }
+    const int e = pow2_ceil_exp(mx);
+    for (int k = lane; k < Kp; k += 32) {
+        int x1 = 0, x2 = 0, x3 = 0;
+        if (k < K) digits3(__float2int_rn(ldexpf(W[(size_t)k * N + q], 23 - e)), x1, x2, x3);
+        S[(size_t)q * Kp + k] = bf16_of_int(x1);
+        S[plane + (size_t)q * Kp + k] = bf16_of_int(x2);
+        S[2 * plane + (size_t)q * Kp + k] = bf16_of_int(x3);
+    }
+    if (lane == 0) {
+        fexp[q] = e;
+        const double z = (double)zmag[q];
+        atomicAdd(&F[0], ldexp(1.0, e) * z);
+        atomicAdd(&F[1], tsum * z);
+    }
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+    });
+    return fn;
+}
+
+// 3-D map over digit slices [3][rows][Kp] (BF16), box {64, box_rows, 1}, 128-byte swizzle; rows
+// beyond `rows` read as zero.
+cv_status encode_slices(CUtensorMap* m, const void* base, int rows, int Kp, int box_rows) {
+    EncodeTiled enc = encoder();
+    if (!enc) { cv_set_error("cuTensorMapEncodeTiled is not available from the driver"); return CV_EUNSUPPORTED; }
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * (cuuint64_t)rows};
+    cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        cv_set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        return CV_ECUDA;
+    }
+    return CV_OK;
+}
+
+int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+void cv_tc_release(cv_cache* c) {
+    if (!c) return;
+    for (int i = 0; i <= CV_MAX_LAYERS; ++i) {
+        cv_tc_w* w = c->tcw[i];
+        if (!w) continue;
+        cudaFree(w->slices);
+        cudaFree(w->fexp);
+        delete w;
+        c->tcw[i] = nullptr;
+    }
+}
+
+bool cv_tc_supported(const cv_cache* c) {
+    for (int i = 1; i <= c->net->L; ++i)
+        if (!c->tcw[i]) return false;
+    return true;
+}
+
+cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaStream_t st) {
+    const cv_net* n = c->net;
+    for (int i = 1; i <= n->L; ++i) {
+        const int K = n->dims[i], N = n->dims[i - 1];
+        const int Kp = round_up(K, TBK), Np = round_up(N, TBN);
+        if (Kp > KMAX) continue;  // the path takes K <= 512 (two exact accumulator sets)
+        cv_tc_w* w = new cv_tc_w();
+        memset(w, 0, sizeof(*w));
+        c->tcw[i] = w;
+        w->K = K; w->N = N; w->Kp = Kp; w->Np = Np;
+        double* F = nullptr;
+        CV_CUDA(cudaMalloc(&w->slices, (size_t)3 * Np * Kp * sizeof(uint16_t)));
+        CV_CUDA(cudaMalloc(&w->fexp, (size_t)N * sizeof(int)));
+        CV_CUDA(cudaMalloc(&F, 2 * sizeof(double)));
+        CV_CUDA(cudaMemsetAsync(F, 0, 2 * sizeof(double), st));
+        const float* zm = (i == 1) ? xmag : zmag + n->hoff[i - 1];
+        k_tc_wsplit<<<(Np + 7) / 8, 256, 0, st>>>(K, N, Kp, Np, n->W[i], zm, w->slices, w->fexp, F);
+        CV_LAUNCH_CHECK("k_tc_wsplit");
+        double hF[2];
+        CV_CUDA(cudaMemcpyAsync(hF, F, sizeof(hF), cudaMemcpyDeviceToHost, st));
+        CV_CUDA(cudaStreamSynchronize(st));
+        cudaFree(F);
+        w->F1 = hF[0] * (1.0 + 1e-12);
+        w->F2 = hF[1] * (1.0 + 1e-12);
+        cv_status s = encode_slices(&w->tmap, w->slices, Np, Kp, TBN);
+        if (s) return s;
+    }
+    return CV_OK;
+}
+
+size_t cv_tc_slices_bytes(const cv_net* net, int R) {
+    int kp = 0;
+    for (int i = 1; i <= net->L; ++i) kp = std::max(kp, round_up(net->dims[i], TBK));
+    return (size_t)3 * R * kp * sizeof(uint16_t);
+}
+
+namespace {
+
+// Split rows of Lam [R x K] (row stride K) into digit slices [3][R][Kp]; the row exponent; the
+// contraction's error term added to the row's pad (see the file header).  One warp per row, eight
+// consecutive elements per lane (one 16-byte store per slice).
+__global__ void k_tc_rsplit(int R, int K, int Kp, const float* A, uint16_t* S, int* rexp, double* acc_pad,
+                            double F1, double F2) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= R) return;
+    const float* a = A + (size_t)r * K;
+    float mx = 0.f, ssum = 0.f;  // ssum: sum of |Lam_rk| rounded up
+    for (int k = lane; k < K; k += 32) {
+        const float v = fabsf(a[k]);
+        mx = fmaxf(mx, v);
+        ssum = __fadd_ru(ssum, v);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        ssum = __fadd_ru(ssum, __shfl_xor_sync(0xffffffffu, ssum, off));
+    }
+    const int e = pow2_ceil_exp(mx);
+    const size_t plane = (size_t)R * Kp;
+    uint16_t* s0 = S + (size_t)r * Kp;
+    for (int k0 = lane * 8; k0 < Kp; k0 += 256) {
+        unsigned w1[4], w2[4], w3[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            int d1[2], d2[2], d3[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int k = k0 + 2 * h + t;
+                d1[t] = d2[t] = d3[t] = 0;
+                if (k < K) digits3(__float2int_rn(ldexpf(a[k], 23 - e)), d1[t], d2[t], d3[t]);
+            }
+            w1[h] = (unsigned)bf16_of_int(d1[0]) | ((unsigned)bf16_of_int(d1[1]) << 16);
+            w2[h] = (unsigned)bf16_of_int(d2[0]) | ((unsigned)bf16_of_int(d2[1]) << 16);
+            w3[h] = (unsigned)bf16_of_int(d3[0]) | ((unsigned)bf16_of_int(d3[1]) << 16);
+        }
+        *(uint4*)(s0 + k0) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *(uint4*)(s0 + plane + k0) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        *(uint4*)(s0 + 2 * plane + k0) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+    }
+    if (lane == 0) {
+        rexp[r] = e;
+        const double pe = ldexp(1.0, e);
+        acc_pad[r] += (PAD_C * ldexp((double)ssum * F1 + pe * F2, -24) + pe * (double)K * ldexp(F1, -31)) *
+                      (1.0 + 1e-12);
+    }
+}
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned phase) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(su32(bar)), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sdesc(const void* p) {
+    uint64_t d = (uint64_t)((su32(p) >> 4) & 0x3fffu);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void tma3(void* dst, const CUtensorMap* m, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            su32(dst)),
+        "l"(m), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct TcArgs {
+    int R, K, N, i, Kp, nch;
+    int rows_per_sub, m, hoff, H;
+    const int* rexp; const int* fexp;
+    const float* root_l; const float* root_u; const int8_t* root_state;
+    const int* slot_of; const float* l; const float* u; const int8_t* mask; int U;
+    const float* alpha; int alpha_mode;
+    const float* bnext; const float* Vnext;
+    const float* T0; const float* T1; const float* T2;  // relaxation table of layer i-1 [B x N]
+    float* Aout;
+    const float* lo; const float* hi;
+    float* lam0;
+    double* part_bias; double* part_pad; double* part_f; double* part_fmag; int ncb;
+    int* status;
+};
+
+constexpr int STAGE_A = 3 * TBM * TBK * 2;  // bytes of the three A slices of one K step
+constexpr int STAGE_B = 3 * TBN * TBK * 2;
+constexpr int STAGE = STAGE_A + STAGE_B;
+constexpr int NSTAGE = 1;  // one stage: two CTAs share an SM and overlap each other's phases
+constexpr int TC_SMEM = NSTAGE * STAGE + 1024;
+
+__global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUtensorMap tA,
+                                                     const __grid_constant__ CUtensorMap tB, TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[2], empty[2], done;
+    __shared__ unsigned tmem_base;
+    __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5;
+    const int row0 = blockIdx.y * TBM, col0 = blockIdx.x * TBN;
+    const int KT = a.Kp / TBK;
+    const unsigned ncols = (unsigned)(a.nch * NLEV * TBN);  // 256 or 512
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < 2; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+
+    if (threadIdx.x == 0) {
+        // producer: TMA ring of NSTAGE stages
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % NSTAGE;
+            if (kt >= NSTAGE && !bar_wait(&empty[s], ((kt - NSTAGE) / NSTAGE) & 1)) { s_fail = 1; break; }
+            unsigned char* st = sm + s * STAGE;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])), "r"(STAGE)
+                         : "memory");
+            for (int z = 0; z < 3; ++z) {
+                tma3(st + z * (TBM * TBK * 2), &tA, kt * TBK, row0, z, &full[s]);
+                tma3(st + STAGE_A + z * (TBN * TBK * 2), &tB, kt * TBK, col0, z, &full[s]);
+            }
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer: eight digit products per 16-wide K step into the level accumulators
+        const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TBN >> 3) << 17) |
+                               ((unsigned)(TBM >> 4) << 24);
+        const int pi[8] = {0, 0, 1, 0, 1, 2, 1, 2};  // digit of A (slice)
+        const int pj[8] = {0, 1, 0, 2, 1, 0, 2, 1};  // digit of B
+        bool ok = true;
+        for (int kt = 0; kt < KT && ok; ++kt) {
+            const int s = kt % NSTAGE;
+            if (!bar_wait(&full[s], (kt / NSTAGE) & 1)) { s_fail = 1; ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char* st = sm + s * STAGE;
+            const int ch = (kt * TBK) / KCH;
+            const bool first_tile = (kt * TBK) % KCH == 0;
+            for (int kk = 0; kk < TBK / 16; ++kk) {
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const int lev = pi[p] + pj[p];  // level - 2
+                    const unsigned d = tmem + (unsigned)((ch * NLEV + lev) * TBN);
+                    const uint64_t da = sdesc(st + pi[p] * (TBM * TBK * 2)) + (uint64_t)(kk * 2);
+                    const uint64_t db = sdesc(st + STAGE_A + pj[p] * (TBN * TBK * 2)) + (uint64_t)(kk * 2);
+                    // the first product of each level in the first K step of a chunk starts the sum
+                    const bool first_of_level = (p == 0) || (p == 1) || (p == 3) || (p == 6);
+                    const unsigned acc = (first_tile && kk == 0 && first_of_level) ? 0u : 1u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                            d),
+                        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&empty[s]))
+                         : "memory");
+        }
+        if (ok)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&done))
+                         : "memory");
+    }
+    __syncthreads();
+    const bool fine = !s_fail && bar_wait(&done, 0);
+    if (!fine && threadIdx.x == 0) atomicOr(a.status, CV_DEV_TIMEOUT);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // Epilogue.  Stage what the tile's elements need in the (now idle) stage buffers: per column
+    // its exponent, b^(i-1) and V^(i-1); per (subdomain, column) the relaxation table of layer
+    // i-1 (i > 1) or the box (i = 1).  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its
+    // rows) and takes columns 32 (w / 4) .. + 31.
+    const int m = a.rows_per_sub;
+    const int sub0 = row0 / m;
+    const int sub1 = min(row0 + TBM - 1, a.R - 1) / m;
+    const int nsub = sub1 - sub0 + 1;
+    // staged when the tile's subdomains fit the stage buffer, else read from global memory
+    const bool staged = (size_t)nsub * TBN * 3 * sizeof(float) <= (size_t)NSTAGE * STAGE;
+    const int tstride = staged ? TBN : a.N;
+    const float* g_t0 = (a.i > 1) ? a.T0 : a.lo;
+    const float* g_t1 = (a.i > 1) ? a.T1 : a.hi;
+    const float* tb0 = staged ? (const float*)sm : g_t0 + (size_t)sub0 * a.N + col0;
+    const float* tb1 = staged ? (const float*)sm + (size_t)nsub * TBN : g_t1 + (size_t)sub0 * a.N + col0;
+    const float* tb2 = staged ? (const float*)sm + (size_t)2 * nsub * TBN
+                              : (a.i > 1 ? a.T2 + (size_t)sub0 * a.N + col0 : nullptr);
+    __shared__ int s_fexp[TBN];
+    __shared__ float s_bn[TBN], s_vn[TBN];
+    __shared__ double s_red[2][TBM];
+    if (fine) {
+        for (int c = threadIdx.x; c < TBN; c += blockDim.x) {
+            const int q = col0 + c;
+            const bool ok = q < a.N;
+            s_fexp[c] = ok ? a.fexp[q] : 0;
+            s_bn[c] = (ok && a.i > 1) ? a.bnext[q] : 0.f;
+            s_vn[c] = (ok && a.i > 1) ? a.Vnext[q] : 0.f;
+        }
+        if (staged) {
+            float* s_t = (float*)sm;
+            for (int x = threadIdx.x; x < nsub * TBN; x += blockDim.x) {
+                const int sb = sub0 + x / TBN, c = x % TBN, q = col0 + c;
+                float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+                if (q < a.N) {
+                    const size_t o = (size_t)sb * a.N + q;
+                    t0 = g_t0[o]; t1 = g_t1[o];
+                    if (a.i > 1) t2 = a.T2[o];
+                }
+                s_t[x] = t0; s_t[nsub * TBN + x] = t1; s_t[2 * nsub * TBN + x] = t2;
+            }
+        }
+    }
+    __syncthreads();
+    const int wq = warp & 3, half = warp >> 2;
+    const int tr = wq * 32 + (threadIdx.x & 31);  // row within the tile (tensor-memory lane)
+    const int r = row0 + tr;
+    const bool rok = fine && r < a.R;
+    const int sb = rok ? r / m - sub0 : 0;
+    const int er = rok ? a.rexp[r] : 0;
+    double pb = 0.0, pp = 0.0;
+    const unsigned lane_base = tmem + ((unsigned)(wq * 32) << 16);
+    const float* t0 = tb0 + (size_t)sb * tstride;
+    const float* t1 = tb1 + (size_t)sb * tstride;
+    const float* t2 = (a.i > 1) ? tb2 + (size_t)sb * tstride : nullptr;
+    for (int cc = 0; cc < 32 && fine; cc += 8) {
+        const int c0 = half * 32 + cc;
+        float acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+        for (int ch = 0; ch < a.nch; ++ch) {
+            float lv[NLEV][8];
+#pragma unroll
+            for (int v = 0; v < NLEV; ++v) tmem_ld8(lane_base + (unsigned)((ch * NLEV + v) * TBN + c0), lv[v]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // sum of the levels, L2 2^24 + L3 2^16 + L4 2^8 + L5 (FP32, three roundings)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                acc[j] += fmaf(lv[0][j], 16777216.f, fmaf(lv[1][j], 65536.f, fmaf(lv[2][j], 256.f, lv[3][j])));
+        }
+        if (!rok) continue;
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = c0 + j, q = col0 + c;
+            if (q >= a.N) continue;
+            const float p = ldexpf(acc[j], er + s_fexp[c] - 38);  // 2^(e + f - 46) times the 2^8 level unit
+            if (a.i > 1) {
+                // relaxation of neuron q by the sign of p (table of layer i-1; NaN: slope from alpha)
+                float d, e = 0.f;
+                if (p >= 0.f) {
+                    d = t0[c];
+                    if (d != d) d = a.alpha[((size_t)(sub0 + sb) * a.m + (r % a.m)) * a.H + a.hoff + q];
+                } else {
+                    d = t1[c];
+                    e = t2[c];
+                }
+                const float lam = p * d;
+                a.Aout[(size_t)r * a.N + q] = lam;
+                s1 = fmaf(p, e, s1);
+                s1 = fmaf(lam, s_bn[c], s1);
+                s2 = fmaf(fabsf(lam), s_vn[c], s2);
+            } else {
+                // FP32 terms in chains of four (charged 8 u of the magnitude sum in the final pad);
+                // the magnitude sum itself is rounded up
+                const float lo = t0[c], hi = t1[c];
+                s1 += fminf(p * lo, p * hi);
+                s2 = __fadd_ru(s2, __fmul_ru(fabsf(p), fmaxf(fabsf(lo), fabsf(hi))));
+                if (a.lam0) a.lam0[(size_t)r * a.N + q] = p;
+            }
+            if ((j & 3) == 3) { pb += (double)s1; pp += (double)s2; s1 = 0.f; s2 = 0.f; }
+        }
+        pb += (double)s1;
+        pp += (double)s2;
+    }
+    // the two column halves of a row meet in shared memory
+    if (half == 1) { s_red[0][tr] = pb; s_red[1][tr] = pp; }
+    __syncthreads();
+    if (half == 0 && rok) {
+        pb += s_red[0][tr];
+        pp += s_red[1][tr];
+        const size_t o = (size_t)r * a.ncb + blockIdx.x;
+        if (a.i > 1) { a.part_bias[o] = pb; a.part_pad[o] = pp; }
+        else { a.part_f[o] = pb; a.part_fmag[o] = pp; }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// Relaxation table of hidden layer i-1 for every subdomain: the slope for p >= 0 (1 / 0 for
+// stable neurons, the alpha rule otherwise, NaN when per-row slopes are given), and the slope
+// and intercept for p < 0 (u / (u - l), -s l for unstable neurons).
+__global__ void k_tc_relax(int B, int N, int hoff, const float* root_l, const float* root_u,
+                           const int8_t* root_state, const int* slot_of, const float* l, const float* u,
+                           const int8_t* mask, int U, int alpha_given, int alpha_mode, float* T0, float* T1,
+                           float* T2) {
+    const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (size_t)B * N) return;
+    const int sub = (int)(x / N), q = (int)(x % N);
+    const int g = hoff + q;
+    float lb, ub;
+    int st;
+    const int slot = (slot_of && l) ? slot_of[g] : -1;
+    if (slot >= 0) {
+        const size_t o = (size_t)sub * U + slot;
+        lb = l[o]; ub = u[o]; st = mask[o];
+    } else {
+        lb = root_l[g]; ub = root_u[g]; st = root_state[g];
+    }
+    float t0, t1, t2 = 0.f;
+    if (st > 0) { t0 = 1.f; t1 = 1.f; }
+    else if (st < 0) { t0 = 0.f; t1 = 0.f; }
+    else {
+        if (alpha_given) t0 = __int_as_float(0x7fc00000);
+        else t0 = (alpha_mode == CV_ALPHA_ONE) ? 1.f : (alpha_mode == CV_ALPHA_ZERO) ? 0.f : ((ub >= -lb) ? 1.f : 0.f);
+        const float s = ub / (ub - lb);
+        t1 = s;
+        t2 = -s * lb;
+    }
+    T0[x] = t0; T1[x] = t1; T2[x] = t2;
+}
+
+}  // namespace
+
+cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m, const float* C, const float* t,
+                         const float* l, const float* u, const int8_t* mask, int U, const float* alpha,
+                         int alpha_mode, const float* lo, const float* hi, const uint8_t* skip, float* lower,
+                         float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
+                         int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
+                         double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st) {
+    if (!cv_tc_supported(cache)) {
+        cv_set_error("tensor-core back-substitution: a layer is wider than 512 inputs");
+        return CV_EUNSUPPORTED;
+    }
+    if (R == 0) return CV_OK;
+    const int L = net->L;
+    cv_status s = cv_bwd_spec_init(R, net->dims[L], m, C, t, net->b[L], cache->V[L], lamA, acc_bias, acc_pad, st);
+    if (s) return s;
+    ++*launches;
+    CV_CUDA(cudaFuncSetAttribute(k_tc_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    float* cur = lamA;
+    float* nxt = lamB;
+    for (int i = L; i >= 1; --i) {
+        const cv_tc_w* w = cache->tcw[i];
+        const int nsub = R / (m > 0 ? m : 1);
+        const size_t tsz = (size_t)nsub * net->wmax;
+        if (i > 1) {
+            const size_t n = (size_t)nsub * w->N;
+            k_tc_relax<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                nsub, w->N, net->hoff[i - 1], cache->root_l, cache->root_u, cache->root_state, cache->slot_of, l, u,
+                mask, U, alpha != nullptr, alpha_mode, tab, tab + tsz, tab + 2 * tsz);
+            CV_LAUNCH_CHECK("k_tc_relax");
+            ++*launches;
+        }
+        k_tc_rsplit<<<(R + 7) / 8, 256, 0, st>>>(R, w->K, w->Kp, cur, slices, rexp, acc_pad, w->F1, w->F2);
+        CV_LAUNCH_CHECK("k_tc_rsplit");
+        CUtensorMap tA;
+        if ((s = encode_slices(&tA, slices, R, w->Kp, TBM))) return s;
+        TcArgs a;
+        memset(&a, 0, sizeof(a));
+        a.R = R; a.K = w->K; a.N = w->N; a.i = i; a.Kp = w->Kp; a.nch = (w->Kp + KCH - 1) / KCH;
+        a.rows_per_sub = m; a.m = m > 0 ? m : 1;
+        a.hoff = (i > 1) ? net->hoff[i - 1] : 0;
+        a.H = net->H;
+        a.rexp = rexp; a.fexp = w->fexp;
+        a.root_l = cache->root_l; a.root_u = cache->root_u; a.root_state = cache->root_state;
+        a.slot_of = cache->slot_of; a.l = l; a.u = u; a.mask = mask; a.U = U;
+        a.alpha = alpha; a.alpha_mode = alpha_mode;
+        a.bnext = (i > 1) ? net->b[i - 1] : nullptr;
+        a.Vnext = (i > 1) ? cache->V[i - 1] : nullptr;
+        a.T0 = tab; a.T1 = tab + tsz; a.T2 = tab + 2 * tsz;
+        a.Aout = nxt;
+        a.lo = lo; a.hi = hi; a.lam0 = lam0;
+        a.part_bias = part_bias; a.part_pad = part_pad; a.part_f = part_f; a.part_fmag = part_fmag;
+        a.ncb = (w->N + TBN - 1) / TBN;
+        a.status = net->status;
+        dim3 grd(a.ncb, (R + TBM - 1) / TBM);
+        k_tc_layer<<<grd, 256, TC_SMEM, st>>>(tA, w->tmap, a);
+        CV_LAUNCH_CHECK("k_tc_layer");
+        *launches += 2;
+        if (i > 1) {
+            if ((s = cv_bwd_reduce(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad, st))) return s;
+            ++*launches;
+            float* tmp = cur; cur = nxt; nxt = tmp;
+        } else {
+            // the concretisation's FP32 products and chains of four: 8 u of its magnitude sum
+            if ((s = cv_bwd_final(R, a.ncb, m, part_f, part_fmag, acc_bias, acc_pad, skip, lower, err, bias_out,
+                                  8.0 * CV_U32, st)))
+                return s;
+            ++*launches;
+        }
+    }
+    return CV_OK;
+}

@@ -156,12 +156,46 @@ def test_round_parity(name, kw):
     compare(case, g, o)
 
 
-def test_round_parity_alpha_given():
+@pytest.mark.parametrize("name,kw", [
+    ("mlp5x50_relaxed", dict(dims=[5] + [50] * 6 + [5], B=256, kmin=0, kmax=8, eps=0.05, centre="pm1",
+                             clip01=False, out_rows=1, sweeps=0)),
+    ("mlp24_complete", dict(dims=[24, 32, 32, 32, 6], B=48, kmin=1, kmax=4, eps=0.1, sweeps=10)),
+    ("mlp784_ragged", dict(dims=[784, 70, 70, 10], B=37, kmin=1, kmax=4, eps=0.02, sweeps=10)),
+    ("mlp784_targets", dict(dims=[784, 64, 64, 10], B=20, kmin=1, kmax=4, eps=0.02, sweeps=3, targets=7)),
+    ("mlp100_wide", dict(dims=[100, 300, 500, 7], B=11, kmin=1, kmax=3, eps=0.05, sweeps=3)),
+])
+def test_round_parity_tensor_core(name, kw):
+    """The split-BF16 tensor-core back-substitution (CV_PREC_BF16X8) against the same oracle, at
+    the same bar; K in (0, 512] covers one and two exact accumulator sets and ragged tiles."""
+    from paper_2512_11087_gb300 import capi
+    case = Case(**kw)
+    g = gpu_round(case, precision=capi.CV_PREC_BF16X8)
+    o = case.oracle()
+    compare(case, g, o)
+
+
+def test_tensor_core_refuses_wide_layers():
+    from paper_2512_11087_gb300 import capi, engine as E
+    case = Case([20, 600, 5], 4, 1, 2, 0.1, sweeps=0)
+    net = E.Net(case.layers)
+    c = case.cache
+    net.set_cache(f32(case.lo0), f32(case.hi0), f32(c["root_l"]), f32(c["root_u"]), c["ids"], f32(c["lA"]),
+                  f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
+    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, precision=capi.CV_PREC_BF16X8)
+    d = E.to_dev
+    with pytest.raises(RuntimeError, match="512"):
+        rnd.run(d(case.lo), d(case.hi), d(case.C), d(case.t), split_off=d(case.split_off),
+                split_ids=d(case.split_ids))
+    net.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_round_parity_alpha_given(precision):
     case = Case([30, 40, 40, 5], 16, 0, 3, 0.1, sweeps=0, seed=4)
     rng = np.random.default_rng(9)
     alpha = rng.uniform(0, 1, size=(case.B, case.m, case.net.H)).astype(np.float32)
     from paper_2512_11087_gb300 import engine as E
-    g = gpu_round(case, alpha=E.to_dev(alpha))
+    g = gpu_round(case, precision=precision, alpha=E.to_dev(alpha))
     o = case.oracle(alpha=alpha.astype(np.float64))
     compare(case, g, o)
 

@@ -41,7 +41,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16x8"])
+    p.add_argument("--precision", default="bf16x8", choices=["fp32", "bf16x8"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--subdomains", type=int, default=0,
                    help="smaller batch for profiler captures (default: the workload's own batch)")
@@ -260,6 +260,35 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
     e2e_value = world * B * args.steps / (e2e_ms / 1e3)
+
+    # the plain FP32 GPU path on the same inputs: its throughput and the agreement of the bounds
+    vs_fp32 = None
+    if prec != capi.CV_PREC_FP32:
+        r32 = E.Round(net, B, m, max_splits=kmax, relaxed=cfg["relaxed"], sweeps=cfg["sweeps"],
+                      precision=capi.CV_PREC_FP32)
+        for _ in range(2):
+            r32.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
+        t32 = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r32.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t32 += e0.elapsed_time(e1)
+        o32 = {k: v.clone() for k, v in r32.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi).items()}
+        o16 = rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
+        torch.cuda.synchronize()
+        feas = o32["infeasible"] == 0
+        l32, l16 = o32["lower"][feas].double(), o16["lower"][feas].double()
+        v32 = world * B * args.steps / (t32 / 1e3)
+        vs_fp32 = dict(value=v32, unit="subdomains/s", ms_per_step=t32 / args.steps, speedup=value / v32,
+                       mean_lower=float(l16.mean()), mean_lower_fp32=float(l32.mean()),
+                       mean_lower_rel_diff=float(abs(l16.mean() - l32.mean()) / l32.abs().mean()),
+                       max_abs_lower_diff=float((l16 - l32).abs().max()),
+                       verified_agree=float((o16["verified"] == o32["verified"]).double().mean()))
+        del r32
     status = capi.cv_device_status(net.handle)
 
     # roofline of the dominant kernel (complete clipping, ALU bound)
@@ -283,6 +312,8 @@ def main():
                                   alg_ops_per_launch=alg_ops, cc_row_steps=steps_cc),
                     e2e=dict(value=e2e_value, unit="subdomains/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches, device_status=status, clocks=clk)
+        if vs_fp32 is not None:
+            line["vs_fp32_path"] = vs_fp32
         if world == 1 and not args.no_cpu_baseline:
             n, cores = pick_sample(cfg, 3.0)
             rate, dt, cores = oracle_sample_rate(cfg, max(n * 4, 1), seed=21)

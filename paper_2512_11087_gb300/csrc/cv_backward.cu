@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs<T> a) {
 template <typename T>
 __global__ void k_bwd_init(int R, int nk, int mode, int m, const float* lam_init, const float* C,
                            const float* t, const float* bk, const float* Vk, T* A,
-                           double* acc_bias, double* acc_pad) {
+                           double* acc_bias, double* acc_pad, double gam) {
     const int r = blockIdx.x * blockDim.y + threadIdx.y;
     if (r >= R) return;
     double bs = 0.0, ps = 0.0;
@@ -224,7 +224,7 @@ __global__ void k_bwd_init(int R, int nk, int mode, int m, const float* lam_init
     if (threadIdx.x == 0) {
         double t0 = (mode == 1 && t) ? (double)t[r % m] : 0.0;
         acc_bias[r] = t0 + bs;
-        acc_pad[r] = Gam<T>::v * ps;
+        acc_pad[r] = gam * ps;
     }
 }
 
@@ -279,7 +279,7 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
         dim3 blk(32, 8);
         dim3 grd((R + 7) / 8);
         k_bwd_init<T><<<grd, blk, 0, st>>>(R, nk, init_mode, m, lam_init, C, t, net->b[k], V[k], lamA,
-                                            acc_bias, acc_pad);
+                                            acc_bias, acc_pad, Gam<T>::v);
         CV_LAUNCH_CHECK("k_bwd_init");
     }
     T* cur = lamA;
@@ -342,20 +342,21 @@ int cv_bwd_ncb_max(const cv_net* net) {
 }
 
 // Launchers of the spec-bound steps shared with the tensor-core back-substitution (cv_tc.cu):
-// the start from the spec rows, the per-layer reduction of the row partials, and the final
-// concretisation (fm_gamma: extra pad per unit of the concretisation's magnitude sum).
+// the start from the spec rows, the per-layer reduction of the row partials (gam: the pad per unit
+// of sum |Lam| V), and the final concretisation (fm_gamma: extra pad per unit of the
+// concretisation's magnitude sum).
 cv_status cv_bwd_spec_init(int R, int nk, int m, const float* C, const float* t, const float* bk, const float* Vk,
-                           float* A, double* acc_bias, double* acc_pad, cudaStream_t st) {
+                           float* A, double* acc_bias, double* acc_pad, double gam, cudaStream_t st) {
     dim3 blk(32, 8);
     dim3 grd((R + 7) / 8);
-    k_bwd_init<float><<<grd, blk, 0, st>>>(R, nk, 1, m, nullptr, C, t, bk, Vk, A, acc_bias, acc_pad);
+    k_bwd_init<float><<<grd, blk, 0, st>>>(R, nk, 1, m, nullptr, C, t, bk, Vk, A, acc_bias, acc_pad, gam);
     CV_LAUNCH_CHECK("k_bwd_init");
     return CV_OK;
 }
 
 cv_status cv_bwd_reduce(int R, int ncb, const double* part_bias, const double* part_pad, double* acc_bias,
-                        double* acc_pad, cudaStream_t st) {
-    k_bwd_reduce<<<(R + 255) / 256, 256, 0, st>>>(R, ncb, Gam<float>::v, part_bias, part_pad, acc_bias, acc_pad);
+                        double* acc_pad, double gam, cudaStream_t st) {
+    k_bwd_reduce<<<(R + 255) / 256, 256, 0, st>>>(R, ncb, gam, part_bias, part_pad, acc_bias, acc_pad);
     CV_LAUNCH_CHECK("k_bwd_reduce");
     return CV_OK;
 }

@@ -157,9 +157,9 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         T* const* keepP, cudaStream_t st);
 int cv_bwd_ncb_max(const cv_net* net);
 cv_status cv_bwd_spec_init(int R, int nk, int m, const float* C, const float* t, const float* bk, const float* Vk,
-                           float* A, double* acc_bias, double* acc_pad, cudaStream_t st);
+                           float* A, double* acc_bias, double* acc_pad, double gam, cudaStream_t st);
 cv_status cv_bwd_reduce(int R, int ncb, const double* part_bias, const double* part_pad, double* acc_bias,
-                        double* acc_pad, cudaStream_t st);
+                        double* acc_pad, double gam, cudaStream_t st);
 cv_status cv_bwd_final(int R, int ncb, int rows_per_sub, const double* part_f, const double* part_fmag,
                        const double* acc_bias, const double* acc_pad, const uint8_t* skip, float* lower, float* err,
                        float* bias_out, double fm_gamma, cudaStream_t st);

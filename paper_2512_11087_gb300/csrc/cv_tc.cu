@@ -15,8 +15,8 @@
 // per chunk.  The error of P against the exact product of the FP32 operands is therefore
 //     |dP_rq| <= c 2^-24 (2^f_q S_r + 2^e_r T_q) + 2^(e_r + f_q) K 2^-31,
 //     S_r = sum_k |Lam_rk|,  T_q = sum_k |W_kq|,  c = 1 + 2^-6
-// (quantisation of both operands, the dropped level, and the FP32 sum of the four levels in the
-// epilogue, whose rounding is also covered by the gamma |Lam| V pad of the FP32 path).  Its
+// (quantisation of both operands, the dropped level, and the part of the FP32 level sum that
+// exceeds 3 u sum_k |Lam_rk||W_kq|, which the 24 u gamma |Lam| V pad covers).  Its
 // effect on the bound, sum_q |dP_rq| zmag_q, is charged to the row's pad by the splitting
 // kernel: 2^-24 c (S_r F1 + 2^e_r F2) + 2^e_r K 2^-31 F1, F1 = sum_q 2^f_q zmag_q,
 // F2 = sum_q T_q zmag_q (per layer, computed with the split weights).
@@ -43,6 +43,10 @@ constexpr int KCH = 256;                       // K rows per exact accumulator s
 constexpr int KMAX = 512;                      // longest K the path takes (two sets)
 constexpr int NLEV = 4;                        // kept levels 2..5
 constexpr double PAD_C = 1.0 + 1.0 / 64.0;
+// Pad per unit of sum_k |Lam_k| V_k for each contraction (V = |W| zmag + |b|): the FP32 sum of
+// the levels (at most seven roundings with two accumulator sets) and the FP32 relaxation
+// epilogue (15 u, as in the CUDA-core path); the operand splitting is charged separately.
+constexpr double TC_GAMMA = 24.0 * CV_U32;
 
 // balanced base-256 digits of |n| <= 2^23
 __device__ __forceinline__ void digits3(int n, int& x1, int& x2, int& x3) {
@@ -575,7 +579,8 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
     }
     if (R == 0) return CV_OK;
     const int L = net->L;
-    cv_status s = cv_bwd_spec_init(R, net->dims[L], m, C, t, net->b[L], cache->V[L], lamA, acc_bias, acc_pad, st);
+    cv_status s =
+        cv_bwd_spec_init(R, net->dims[L], m, C, t, net->b[L], cache->V[L], lamA, acc_bias, acc_pad, TC_GAMMA, st);
     if (s) return s;
     ++*launches;
     CV_CUDA(cudaFuncSetAttribute(k_tc_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
@@ -620,7 +625,7 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         CV_LAUNCH_CHECK("k_tc_layer");
         *launches += 2;
         if (i > 1) {
-            if ((s = cv_bwd_reduce(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad, st))) return s;
+            if ((s = cv_bwd_reduce(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad, TC_GAMMA, st))) return s;
             ++*launches;
             float* tmp = cur; cur = nxt; nxt = tmp;
         } else {

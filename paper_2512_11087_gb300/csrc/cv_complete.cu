@@ -42,12 +42,12 @@
 
 namespace {
 
-constexpr int RMAX_CC = 8;  // rows per subdomain handled by complete clipping
+constexpr int RMAX_CC = 32;  // rows per subdomain handled by complete clipping
 constexpr int RTPL = 4;     // row counts up to this run in the main launch (two blocks per SM)
 // (target, side) tasks per work item: fewer for subdomains with more rows (longer tasks)
 __host__ __device__ __forceinline__ int tpi_of(int R) { return R <= 1 ? 256 : (R == 2 ? 64 : 16); }
 constexpr int NWARP = 16;   // warps per block at most
-constexpr int CAPC = 416;   // breakpoints a warp's compacted list holds
+constexpr int CAPC = 384;   // breakpoints a warp's compacted list holds
 constexpr int PF = 4;       // coefficients loaded ahead per lane in the element loops
 
 // Exact warp sum of non-negative per-lane 64-bit values whose total is below 2^62: three
@@ -226,51 +226,84 @@ __shared__ double cc_Sg[RMAX_CC];      // magnitude of g against the root box
 
 struct CCView {
     unsigned* keys;        // this warp's keys
-    long long* w64;
+    long long* w64;        // staged rows (main launch)
     float* gs;
     float* rg;
     unsigned short* cidx;  // this warp's list elements
+    float* bsm;            // this warp's multiplier slots (wide launch)
+    int* jsm;
 };
 
-__device__ __forceinline__ CCView cc_view(int n0, int Rs) {
+// Main launch: keys [nw][n0r] | w64 [RsS][n0] | g [RsS][n0] | 1/g [RsS][n0] | list [nw][CAPC].
+// Wide launch: keys [nw][n0r] | list [nw][CAPC] | multipliers [nw][RMAX_CC] | elements [nw][RMAX_CC].
+__device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
     const int n0r = (n0 + 31) & ~31;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
     CCView v;
     v.keys = (unsigned*)cc_smem + warp * n0r;
-    v.w64 = (long long*)((unsigned*)cc_smem + nw * n0r);
-    v.gs = (float*)(v.w64 + Rs * n0);
-    v.rg = v.gs + Rs * n0;
-    v.cidx = (unsigned short*)(v.rg + Rs * n0) + warp * CAPC;
+    if (!wide) {
+        v.w64 = (long long*)((unsigned*)cc_smem + nw * n0r);
+        v.gs = (float*)(v.w64 + RsS * n0);
+        v.rg = v.gs + RsS * n0;
+        v.cidx = (unsigned short*)(v.rg + RsS * n0) + warp * CAPC;
+        v.bsm = nullptr;
+        v.jsm = nullptr;
+    } else {
+        unsigned short* list0 = (unsigned short*)((unsigned*)cc_smem + nw * n0r);
+        v.cidx = list0 + warp * CAPC;
+        float* b0 = (float*)(list0 + nw * CAPC);
+        v.bsm = b0 + warp * RMAX_CC;
+        v.jsm = (int*)(b0 + nw * RMAX_CC) + warp * RMAX_CC;
+        v.w64 = nullptr;
+        v.gs = nullptr;
+        v.rg = nullptr;
+    }
     return v;
 }
 
 constexpr unsigned QINF = 0x7f800000u;  // bits of +inf; breakpoints q > 0 have bits in (0, QINF]
 
-// One (target, side) task of complete clipping with R active rows (R fixed at compile time, so the
-// multipliers live in registers).  Breakpoint keys are the raw bits of q_j = (-a'_j) * fl(1/g_kj):
-// for q > 0 (the search range) the unsigned order of the bits is the order of the values.
-template <int R>
-__device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side, int lane,
+// Rows of the task's subdomain: staged in shared memory (main launch) or read from the
+// workspace (subdomains with more rows than the main launch stages).
+struct CCRows {
+    const float* gs;
+    const float* rg;
+    const long long* w64;
+};
+
+// One (target, side) task of complete clipping with Rn active rows.  RC is a compile-time bound on
+// Rn: the main launch instantiates RC = Rn = 1..4 with the multipliers in registers; the wide
+// launch instantiates RC = 8, 16, 32 for any Rn <= RC with the multipliers in the warp's shared
+// slots bsm / jsm.  Breakpoint keys are the raw bits of q_j = (-a'_j) * fl(1/g_kj): for q > 0 (the
+// search range) the unsigned order of the bits is the order of the values.
+template <int RC, bool WIDE>
+__device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsigned* keys, unsigned short* cidx,
+                                        float* bsm, int* jsm, int Rn, int b, int c, int side, int lane,
                                         unsigned long long& my_steps) {
     const int n0 = a.n0;
-    const CCView sv = cc_view(n0, a.Rs);
-    unsigned* keys = sv.keys;
-    unsigned short* cidx = sv.cidx;
+    const int R = WIDE ? Rn : RC;
     const size_t o = (size_t)b * a.U + c;
     const float* ap = side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0;
     const float sa = side ? -1.f : 1.f;
     const float c0 = side ? -a.uc[c] : a.lc[c];
-    float beta[R];
-    int jprev[R];
+    float beta[WIDE ? 1 : RC];
+    int jprev[WIDE ? 1 : RC];
+    auto bget = [&](int p) -> float {
+        if constexpr (WIDE) return bsm[p]; else return beta[p];
+    };
 #pragma unroll
-    for (int p = 0; p < R; ++p) { beta[p] = 0.f; jprev[p] = -1; }
+    for (int p = 0; p < RC; ++p) {
+        if (WIDE && p >= R) break;
+        if constexpr (WIDE) { bsm[p] = 0.f; jsm[p] = -1; } else { beta[p] = 0.f; jprev[p] = -1; }
+    }
     // With one row, a' = a in every sweep, so one pass already repeats bit for bit.  More
     // generally a row step depends only on the other rows' multipliers: a row whose inputs have
     // not changed since its last step would repeat it exactly and is skipped (bit `k` of `dirty`
     // marks row k as having changed inputs), which leaves every multiplier as the full sweep
     // order gives it.
     const int nsweeps = (R == 1) ? 1 : a.sweeps;
-    unsigned dirty = (1u << R) - 1u;
+    const unsigned all_rows = (R >= 32) ? 0xffffffffu : ((1u << R) - 1u);
+    unsigned dirty = all_rows;
     for (int sw = 0; sw < nsweeps && dirty; ++sw) {
         bool changed = false;
 #pragma unroll 1
@@ -278,20 +311,25 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side,
             if (!((dirty >> k) & 1u)) continue;
             dirty &= ~(1u << k);
             ++my_steps;
-            const float* rk = sv.rg + k * n0;
-            const long long* wk = sv.w64 + k * n0;
+            const float* rk = rw.rg + k * n0;
+            const long long* wk = rw.w64 + k * n0;
             float bk = 0.f;
             int jp = -1;
+            if constexpr (WIDE) {
+                bk = bsm[k]; jp = jsm[k];
+            } else {
 #pragma unroll
-            for (int p = 0; p < R; ++p)
-                if (p == k) { bk = beta[p]; jp = jprev[p]; }
+                for (int p = 0; p < RC; ++p)
+                    if (p == k) { bk = beta[p]; jp = jprev[p]; }
+            }
             // q_j from a' = a + sum_{p != k} beta_p g_p (fma chain in increasing p)
             auto q_of = [&](float av, int j) -> float {
                 float apr = sa * av;
 #pragma unroll
-                for (int p = 0; p < R; ++p) {
-                    if (R > 1) {
-                        const float t = fmaf(beta[p], sv.gs[p * n0 + j], apr);
+                for (int p = 0; p < RC; ++p) {
+                    if (WIDE && p >= R) break;
+                    if (RC > 1) {
+                        const float t = fmaf(bget(p), rw.gs[p * n0 + j], apr);
                         apr = (p != k) ? t : apr;
                     }
                 }
@@ -479,12 +517,16 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side,
                 }
             }
             __syncwarp();  // the next step rewrites the key buffer
+            if constexpr (WIDE) {
+                bsm[k] = bn; jsm[k] = jn;  // every lane writes the same values
+            } else {
 #pragma unroll
-            for (int p = 0; p < R; ++p)
-                if (p == k) { beta[p] = bn; jprev[p] = jn; }
+                for (int p = 0; p < RC; ++p)
+                    if (p == k) { beta[p] = bn; jprev[p] = jn; }
+            }
             if (bn != bk) {
                 changed = true;
-                dirty |= ((1u << R) - 1u) & ~(1u << k);
+                dirty |= all_rows & ~(1u << k);
             }
         }
         if (!changed) break;
@@ -493,7 +535,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side,
     // box, which re-concretisation has already folded into l / u: nothing to update.
     bool any = false;
 #pragma unroll
-    for (int p = 0; p < R; ++p) any |= (beta[p] != 0.f);
+    for (int p = 0; p < RC; ++p) {
+        if (WIDE && p >= R) break;
+        any |= (bget(p) != 0.f);
+    }
     if (!any) return;
     // dual objective at beta, FP32 with its rounding bound
     const float* slo = a.lo + (size_t)b * n0;
@@ -517,7 +562,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side,
             const int jj = min(j0 + 32 * u, n0 - 1);
             float v = sa * av[u];
 #pragma unroll
-            for (int p = 0; p < R; ++p) v = fmaf(beta[p], sv.gs[p * n0 + jj], v);
+            for (int p = 0; p < RC; ++p) {
+                if (WIDE && p >= R) break;
+                v = fmaf(bget(p), rw.gs[p * n0 + jj], v);
+            }
             part += fminf(v * lv[u], v * hv[u]);  // 0 past n0 (lv = hv = 0)
         }
     }
@@ -526,9 +574,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side,
     float cst = c0;
     double scale = (double)psc + fabs((double)c0);
 #pragma unroll
-    for (int p = 0; p < R; ++p) {
-        cst = fmaf(beta[p], cc_hrow[p], cst);
-        scale += (double)beta[p] * (cc_Sg[p] + fabs((double)cc_hrow[p]));
+    for (int p = 0; p < RC; ++p) {
+        if (WIDE && p >= R) break;
+        cst = fmaf(bget(p), cc_hrow[p], cst);
+        scale += (double)bget(p) * (cc_Sg[p] + fabs((double)cc_hrow[p]));
     }
     const double gam = (double)(R + (n0 + 31) / 32 + 12) * CV_U32;
     const float pad = __double2float_ru(gam * scale * 1.0001);
@@ -540,14 +589,20 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side,
         for (int j = lane; j < n0; j += 32) {
             double v = (double)(sa * __ldg(ap + j));
 #pragma unroll
-            for (int p = 0; p < R; ++p) v += (double)beta[p] * (double)sv.gs[p * n0 + j];
+            for (int p = 0; p < RC; ++p) {
+                if (WIDE && p >= R) break;
+                v += (double)bget(p) * (double)rw.gs[p * n0 + j];
+            }
             d += fmin(v * (double)__ldg(slo + j), v * (double)__ldg(shi + j));
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
         d += (double)c0;
 #pragma unroll
-        for (int p = 0; p < R; ++p) d += (double)beta[p] * (double)cc_hrow[p];
+        for (int p = 0; p < RC; ++p) {
+            if (WIDE && p >= R) break;
+            d += (double)bget(p) * (double)cc_hrow[p];
+        }
         val = __double2float_rd(d - ldexp(scale, -40));
     }
     if (lane == 0) {
@@ -561,11 +616,9 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, int b, int c, int side,
 template <bool WIDE>
 __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a) {
     const int n0 = a.n0, Rs = a.Rs, B = a.B;
+    const int RsS = Rs < RTPL ? Rs : RTPL;  // rows staged by the main launch
     const int lane = threadIdx.x & 31;
-    const CCView sv = cc_view(n0, Rs);
-    long long* w64 = sv.w64;
-    float* gs = sv.gs;
-    float* rg = sv.rg;
+    const CCView sv = cc_view(n0, RsS, WIDE);
     __shared__ int s_item, s_pos, s_R, s_next;
     __shared__ unsigned long long nsteps;
     if (threadIdx.x == 0) nsteps = 0;
@@ -594,15 +647,17 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
         const int pos = s_pos;
         const int b = a.order[pos];
         if (b != cur_b) {
-            // stage the subdomain's rows
+            // stage the subdomain's row constants (and, in the main launch, its rows)
             if (threadIdx.x == 0) s_R = a.wR[b];
             __syncthreads();
             const int R = s_R;
-            const size_t base = (size_t)b * Rs * n0;
-            for (int i = threadIdx.x; i < R * n0; i += blockDim.x) {
-                w64[i] = a.ww[base + i];
-                gs[i] = a.wg[base + i];
-                rg[i] = a.wrg[base + i];
+            if (!WIDE) {
+                const size_t base = (size_t)b * Rs * n0;
+                for (int i = threadIdx.x; i < R * n0; i += blockDim.x) {
+                    sv.w64[i] = a.ww[base + i];
+                    sv.gs[i] = a.wg[base + i];
+                    sv.rg[i] = a.wrg[base + i];
+                }
             }
             if (threadIdx.x < R) {
                 cc_T64[threadIdx.x] = a.wT[(size_t)b * Rs + threadIdx.x];
@@ -613,6 +668,13 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
             cur_b = b;
         }
         const int R = s_R;
+        CCRows rw;
+        if (WIDE) {
+            const size_t base = (size_t)b * Rs * n0;
+            rw.gs = a.wg + base; rw.rg = a.wrg + base; rw.w64 = a.ww + base;
+        } else {
+            rw.gs = sv.gs; rw.rg = sv.rg; rw.w64 = sv.w64;
+        }
         const bool have_list = a.tgt_off != nullptr;
         const int t0 = have_list ? a.tgt_off[b] : 0;
         const int ntask = 2 * ntargets(a, b);
@@ -634,18 +696,15 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
             }
             if (a.mask[(size_t)b * a.U + c] != 0) continue;
             if (WIDE) {
-                switch (R) {
-                    case 5: cc_task<5>(a, b, c, side, lane, my_steps); break;
-                    case 6: cc_task<6>(a, b, c, side, lane, my_steps); break;
-                    case 7: cc_task<7>(a, b, c, side, lane, my_steps); break;
-                    default: cc_task<8>(a, b, c, side, lane, my_steps); break;
-                }
+                if (R <= 8) cc_task<8, true>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
+                else if (R <= 16) cc_task<16, true>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
+                else cc_task<32, true>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
             } else {
                 switch (R) {
-                    case 1: cc_task<1>(a, b, c, side, lane, my_steps); break;
-                    case 2: cc_task<2>(a, b, c, side, lane, my_steps); break;
-                    case 3: cc_task<3>(a, b, c, side, lane, my_steps); break;
-                    default: cc_task<4>(a, b, c, side, lane, my_steps); break;
+                    case 1: cc_task<1, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 1, b, c, side, lane, my_steps); break;
+                    case 2: cc_task<2, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 2, b, c, side, lane, my_steps); break;
+                    case 3: cc_task<3, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 3, b, c, side, lane, my_steps); break;
+                    default: cc_task<4, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 4, b, c, side, lane, my_steps); break;
                 }
             }
             __syncwarp();
@@ -680,8 +739,10 @@ __global__ void k_cc_post(CCArgs a) {
 template <bool WIDE>
 cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
     const size_t n0r = (a.n0 + 31) & ~31;
-    const size_t fixed = (size_t)a.Rs * a.n0 * (8 + 4 + 4);
-    const size_t per_warp = n0r * 4 + CAPC * 2;  // keys, compacted list elements
+    const size_t RsS = a.Rs < RTPL ? a.Rs : RTPL;
+    // main: staged rows + per warp keys and list; wide: per warp keys, list and multiplier slots
+    const size_t fixed = WIDE ? 0 : RsS * a.n0 * (8 + 4 + 4);
+    const size_t per_warp = n0r * 4 + CAPC * 2 + (WIDE ? (size_t)RMAX_CC * 8 : 0);
     const size_t limit = 220 * 1024;
     int nw = NWARP;
     while (nw > 1 && fixed + nw * per_warp > limit) --nw;
@@ -734,7 +795,7 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
                              int* launches, cudaStream_t st) {
     if (opt->sweeps <= 0 || lay->Rmax == 0 || cache->U == 0) return CV_OK;
     if (lay->Rmax > RMAX_CC) {
-        cv_set_error("complete clipping: more than 8 constraint rows per subdomain is not supported by this build");
+        cv_set_error("complete clipping: more than 32 constraint rows per subdomain are not supported");
         return CV_EUNSUPPORTED;
     }
     CCArgs a;

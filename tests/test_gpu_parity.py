@@ -148,6 +148,7 @@ def test_paper_toy_example_on_gpu():
     ("mlp784_targets", dict(dims=[784, 64, 64, 10], B=20, kmin=1, kmax=4, eps=0.02, sweeps=3, targets=7)),
     ("mlp100_no_splits", dict(dims=[100, 40, 40, 7], B=9, kmin=0, kmax=0, eps=0.05, sweeps=5)),
     ("mlp32_many_rows", dict(dims=[32, 40, 40, 6], B=40, kmin=0, kmax=2, eps=0.1, sweeps=6, cut_rows=(0, 6))),
+    ("mlp32_up_to_26_rows", dict(dims=[32, 40, 40, 6], B=24, kmin=0, kmax=2, eps=0.1, sweeps=4, cut_rows=(6, 24))),
 ])
 def test_round_parity(name, kw):
     case = Case(**kw)

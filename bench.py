@@ -150,6 +150,29 @@ def run_reference(args, cfg, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- sharding across ranks
+# Subdomains are independent: each rank bounds its own batch (its own split draws) and the only
+# cross-rank step is the max of the timed region, outside the data path.
+def shard_seed(rank):
+    """Seed of the split draws of a rank's batch."""
+    return 1 + rank
+
+
+def job_time_ms(local_ms, dist=None, device="cpu"):
+    """The job's time: the max over ranks of each rank's timed region."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, B, steps, total_ms):
+    """Whole-job throughput: the subdomains of all ranks over the job's time."""
+    return world * B * steps / (total_ms / 1e3)
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse_args()
@@ -181,7 +204,7 @@ def main():
     net = E.Net(layers)
     U = net.build_cache(lo0, hi0)
     ids = net.read_cache()["ids"]
-    so, si = WL.draw_splits(ids, B, kmin, kmax, seed=1 + rank)
+    so, si = WL.draw_splits(ids, B, kmin, kmax, seed=shard_seed(rank))
     lo, hi = WL.tile_box(lo0, hi0, B)
     C, t = WL.margin_spec(dims[-1])
     m = C.shape[0]
@@ -225,12 +248,8 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
-    total_ms = sum(times)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * B * args.steps / (total_ms / 1e3)
+    total_ms = job_time_ms(sum(times), dist, "cuda")
+    value = job_value(world, B, args.steps, total_ms)
 
     # end to end through the same C-ABI call with host buffers (pinned), copies inside the timed region
     hlo, hhi = torch.from_numpy(lo).pin_memory(), torch.from_numpy(hi).pin_memory()
@@ -255,11 +274,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = world * B * args.steps / (e2e_ms / 1e3)
+    e2e_ms = job_time_ms(e2e_ms, dist, "cuda")
+    e2e_value = job_value(world, B, args.steps, e2e_ms)
 
     # the plain FP32 GPU path on the same inputs: its throughput and the agreement of the bounds
     vs_fp32 = None
@@ -282,7 +298,8 @@ def main():
         torch.cuda.synchronize()
         feas = o32["infeasible"] == 0
         l32, l16 = o32["lower"][feas].double(), o16["lower"][feas].double()
-        v32 = world * B * args.steps / (t32 / 1e3)
+        t32 = job_time_ms(t32, dist, "cuda")
+        v32 = job_value(world, B, args.steps, t32)
         vs_fp32 = dict(value=v32, unit="subdomains/s", ms_per_step=t32 / args.steps, speedup=value / v32,
                        mean_lower=float(l16.mean()), mean_lower_fp32=float(l32.mean()),
                        mean_lower_rel_diff=float(abs(l16.mean() - l32.mean()) / l32.abs().mean()),

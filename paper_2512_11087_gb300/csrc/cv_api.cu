@@ -53,6 +53,9 @@ cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int
         lay->tc_slices = take(cv_tc_slices_bytes(net, lay->R));
         lay->tc_exp = take(R * sizeof(int));
         lay->tc_tab = take((size_t)3 * B * net->wmax * sizeof(float));
+        lay->tc_box = take(cv_tc_box_bytes(cache, B));
+        lay->tc_bexp = take((size_t)B * sizeof(int));
+        lay->tc_bsum = take((size_t)B * sizeof(float));
     }
     lay->total = off;
     return CV_OK;
@@ -151,7 +154,7 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
     if ((s = cv_launch_reconc(net, cache, in, opt, &lay, ws, out->lo_clip, out->hi_clip, out->l, out->u, out->mask,
                               out->infeasible, st)))
         return s;
-    launches += U > 0 ? 3 : 0;
+    launches += U > 0 ? (opt->precision == CV_PREC_BF16X8 ? 4 : 3) : 0;
     if (tm) CV_CUDA(cudaEventRecord(tm->ev[2], st));
     if ((s = cv_launch_complete(net, cache, in, opt, &lay, ws, out->lo_clip, out->hi_clip, out->l, out->u, out->mask,
                                 out->infeasible, steps, &launches, st)))

@@ -58,6 +58,15 @@ struct cv_tc_w {
     CUtensorMap tmap;   // 3-D map {Kp, Np, 3}, box {64, 64, 1}, 128-byte swizzle
 };
 
+// Split-BF16 copy of the re-concretisation operand PC [2U x 2n0] for the tensor cores (cv_tc.cu).
+struct cv_tc_pc {
+    uint16_t* slices;   // [3][Np][Kp] BF16 digits of the rows of PC (row-scaled), zero padded
+    int* fexp;          // [2U] row exponents
+    float* tsum;        // [2U] sum_k |PC_jk|, rounded up
+    int K, N, Kp, Np;
+    CUtensorMap tmap;   // 3-D map {Kp, Np, 3}, box {64, 64, 1}, 128-byte swizzle
+};
+
 struct cv_cache {
     const cv_net* net;
     int U, n0, H;
@@ -77,6 +86,7 @@ struct cv_cache {
     float* root_lo;    // [n0]
     float* root_hi;    // [n0]
     cv_tc_w* tcw[CV_MAX_LAYERS + 1]; // tensor-core weights per layer (host objects), or null
+    cv_tc_pc* tcpc;                  // tensor-core re-concretisation operand, or null
 };
 
 struct cv_timer {
@@ -93,6 +103,7 @@ __host__ __device__ inline size_t cv_align256(size_t x) { return (x + 255) & ~(s
 struct cv_ws_layout {
     size_t rowflag, vmin, lam0, lam1, part_bias, part_pad, part_f, part_fmag, acc_bias, acc_pad, rowdesc, cc, total;
     size_t tc_slices, tc_exp, tc_tab;  // split-BF16 back-substitution scratch (CV_PREC_BF16X8 only)
+    size_t tc_box, tc_bexp, tc_bsum;   // split-BF16 re-concretisation scratch (CV_PREC_BF16X8 only)
     int R, Rmax, ncb;  // rows of the spec backward, max constraint rows, column blocks
 };
 size_t cv_cc_workspace(int B, int Rmax, int n0);  // complete-clipping region (cv_complete.cu)
@@ -106,6 +117,10 @@ cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaS
 void cv_tc_release(cv_cache* c);
 bool cv_tc_supported(const cv_cache* c);
 size_t cv_tc_slices_bytes(const cv_net* net, int R);
+size_t cv_tc_box_bytes(const cv_cache* c, int B);
+cv_status cv_reconc_tc(const cv_cache* cache, int B, const float* lo, const float* hi, const float* rls,
+                       const float* rus, const float* l_in, const float* u_in, const uint8_t* infeasible, float* l,
+                       float* u, uint16_t* xslices, int* bexp, float* bsum, int* status, cudaStream_t st);
 cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m, const float* C, const float* t,
                          const float* l, const float* u, const int8_t* mask, int U, const float* alpha,
                          int alpha_mode, const float* lo, const float* hi, const uint8_t* skip, float* lower,

@@ -168,16 +168,22 @@ cv_status cv_launch_reconc(const cv_net* net, const cv_cache* cache, const cv_ba
                            const cv_options* opt, const cv_ws_layout* lay, char* ws,
                            const float* lo_clip, const float* hi_clip, float* l, float* u,
                            int8_t* mask, uint8_t* infeasible, cudaStream_t st) {
-    (void)net;
     const int U = cache->U, B = in->B;
     if (U == 0) return CV_OK;
     float* rls = (float*)(ws + lay->rowdesc);
     float* rus = rls + U;
     k_gather_root<<<(U + 255) / 256, 256, 0, st>>>(U, cache->ids, cache->root_l, cache->root_u, rls, rus);
-    dim3 grd((2 * U + BN - 1) / BN, (B + BM - 1) / BM);
-    k_reconc<<<grd, 256, 0, st>>>(B, U, cache->n0, lo_clip, hi_clip, cache->PC, cache->PCc, cache->pscale, rls,
-                                  rus, in->l_in, in->u_in, infeasible, l, u);
-    CV_LAUNCH_CHECK("k_reconc");
+    if (opt->precision == CV_PREC_BF16X8) {
+        cv_status s = cv_reconc_tc(cache, B, lo_clip, hi_clip, rls, rus, in->l_in, in->u_in, infeasible, l, u,
+                                   (uint16_t*)(ws + lay->tc_box), (int*)(ws + lay->tc_bexp),
+                                   (float*)(ws + lay->tc_bsum), net->status, st);
+        if (s) return s;
+    } else {
+        dim3 grd((2 * U + BN - 1) / BN, (B + BM - 1) / BM);
+        k_reconc<<<grd, 256, 0, st>>>(B, U, cache->n0, lo_clip, hi_clip, cache->PC, cache->PCc, cache->pscale, rls,
+                                      rus, in->l_in, in->u_in, infeasible, l, u);
+        CV_LAUNCH_CHECK("k_reconc");
+    }
     k_post_reconc<<<B, 256, 0, st>>>(*cache, *in, opt->enforce_splits, l, u, mask, infeasible);
     CV_LAUNCH_CHECK("k_post_reconc");
     return CV_OK;

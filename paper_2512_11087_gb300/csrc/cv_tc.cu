@@ -151,74 +151,36 @@ int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-void cv_tc_release(cv_cache* c) {
-    if (!c) return;
-    for (int i = 0; i <= CV_MAX_LAYERS; ++i) {
-        cv_tc_w* w = c->tcw[i];
-        if (!w) continue;
-        cudaFree(w->slices);
-        cudaFree(w->fexp);
-        delete w;
-        c->tcw[i] = nullptr;
-    }
-}
-
-bool cv_tc_supported(const cv_cache* c) {
-    for (int i = 1; i <= c->net->L; ++i)
-        if (!c->tcw[i]) return false;
-    return true;
-}
-
-cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaStream_t st) {
-    const cv_net* n = c->net;
-    for (int i = 1; i <= n->L; ++i) {
-        const int K = n->dims[i], N = n->dims[i - 1];
-        const int Kp = round_up(K, TBK), Np = round_up(N, TBN);
-        if (Kp > KMAX) continue;  // the path takes K <= 512 (two exact accumulator sets)
-        cv_tc_w* w = new cv_tc_w();
-        memset(w, 0, sizeof(*w));
-        c->tcw[i] = w;
-        w->K = K; w->N = N; w->Kp = Kp; w->Np = Np;
-        double* F = nullptr;
-        CV_CUDA(cudaMalloc(&w->slices, (size_t)3 * Np * Kp * sizeof(uint16_t)));
-        CV_CUDA(cudaMalloc(&w->fexp, (size_t)N * sizeof(int)));
-        CV_CUDA(cudaMalloc(&F, 2 * sizeof(double)));
-        CV_CUDA(cudaMemsetAsync(F, 0, 2 * sizeof(double), st));
-        const float* zm = (i == 1) ? xmag : zmag + n->hoff[i - 1];
-        k_tc_wsplit<<<(Np + 7) / 8, 256, 0, st>>>(K, N, Kp, Np, n->W[i], zm, w->slices, w->fexp, F);
-        CV_LAUNCH_CHECK("k_tc_wsplit");
-        double hF[2];
-        CV_CUDA(cudaMemcpyAsync(hF, F, sizeof(hF), cudaMemcpyDeviceToHost, st));
-        CV_CUDA(cudaStreamSynchronize(st));
-        cudaFree(F);
-        w->F1 = hF[0] * (1.0 + 1e-12);
-        w->F2 = hF[1] * (1.0 + 1e-12);
-        cv_status s = encode_slices(&w->tmap, w->slices, Np, Kp, TBN);
-        if (s) return s;
-    }
-    return CV_OK;
-}
-
-size_t cv_tc_slices_bytes(const cv_net* net, int R) {
-    int kp = 0;
-    for (int i = 1; i <= net->L; ++i) kp = std::max(kp, round_up(net->dims[i], TBK));
-    return (size_t)3 * R * kp * sizeof(uint16_t);
-}
 
 namespace {
 
-// Split rows of Lam [R x K] (row stride K) into digit slices [3][R][Kp]; the row exponent; the
-// contraction's error term added to the row's pad (see the file header).  One warp per row, eight
-// consecutive elements per lane (one 16-byte store per slice).
-__global__ void k_tc_rsplit(int R, int K, int Kp, const float* A, uint16_t* S, int* rexp, double* acc_pad,
-                            double F1, double F2) {
+// Row loaders of the splitting kernel: rows of a row-major matrix, or the box rows [lo_b | hi_b].
+struct RowLd {
+    const float* A;
+    int K;
+    __device__ float operator()(int r, int k) const { return A[(size_t)r * K + k]; }
+};
+struct BoxLd {
+    const float* lo;
+    const float* hi;
+    int n0;
+    __device__ float operator()(int r, int k) const {
+        return k < n0 ? lo[(size_t)r * n0 + k] : hi[(size_t)r * n0 + (k - n0)];
+    }
+};
+
+// Split R rows of length K into digit slices [3][R][Kp] and the row exponent; optionally the row's
+// absolute sum (rounded up) and the contraction's error term added to the row's pad (see the file
+// header).  One warp per row, eight consecutive elements per lane (one 16-byte store per slice).
+template <class Ld>
+__global__ void k_tc_split(int R, int plane_rows, int K, int Kp, Ld ld, uint16_t* S, int* rexp, float* rsum,
+                           double* acc_pad, double F1, double F2) {
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= R) return;
-    const float* a = A + (size_t)r * K;
-    float mx = 0.f, ssum = 0.f;  // ssum: sum of |Lam_rk| rounded up
+    float mx = 0.f, ssum = 0.f;  // ssum: sum of |row| rounded up
     for (int k = lane; k < K; k += 32) {
-        const float v = fabsf(a[k]);
+        const float v = fabsf(ld(r, k));
         mx = fmaxf(mx, v);
         ssum = __fadd_ru(ssum, v);
     }
@@ -228,7 +190,7 @@ __global__ void k_tc_rsplit(int R, int K, int Kp, const float* A, uint16_t* S, i
         ssum = __fadd_ru(ssum, __shfl_xor_sync(0xffffffffu, ssum, off));
     }
     const int e = pow2_ceil_exp(mx);
-    const size_t plane = (size_t)R * Kp;
+    const size_t plane = (size_t)plane_rows * Kp;  // slice stride (rows of the tensor map)
     uint16_t* s0 = S + (size_t)r * Kp;
     for (int k0 = lane * 8; k0 < Kp; k0 += 256) {
         unsigned w1[4], w2[4], w3[4];
@@ -239,7 +201,7 @@ __global__ void k_tc_rsplit(int R, int K, int Kp, const float* A, uint16_t* S, i
             for (int t = 0; t < 2; ++t) {
                 const int k = k0 + 2 * h + t;
                 d1[t] = d2[t] = d3[t] = 0;
-                if (k < K) digits3(__float2int_rn(ldexpf(a[k], 23 - e)), d1[t], d2[t], d3[t]);
+                if (k < K) digits3(__float2int_rn(ldexpf(ld(r, k), 23 - e)), d1[t], d2[t], d3[t]);
             }
             w1[h] = (unsigned)bf16_of_int(d1[0]) | ((unsigned)bf16_of_int(d1[1]) << 16);
             w2[h] = (unsigned)bf16_of_int(d2[0]) | ((unsigned)bf16_of_int(d2[1]) << 16);
@@ -251,9 +213,12 @@ __global__ void k_tc_rsplit(int R, int K, int Kp, const float* A, uint16_t* S, i
     }
     if (lane == 0) {
         rexp[r] = e;
-        const double pe = ldexp(1.0, e);
-        acc_pad[r] += (PAD_C * ldexp((double)ssum * F1 + pe * F2, -24) + pe * (double)K * ldexp(F1, -31)) *
-                      (1.0 + 1e-12);
+        if (rsum) rsum[r] = ssum;
+        if (acc_pad) {
+            const double pe = ldexp(1.0, e);
+            acc_pad[r] += (PAD_C * ldexp((double)ssum * F1 + pe * F2, -24) + pe * (double)K * ldexp(F1, -31)) *
+                          (1.0 + 1e-12);
+        }
     }
 }
 
@@ -598,8 +563,9 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
             CV_LAUNCH_CHECK("k_tc_relax");
             ++*launches;
         }
-        k_tc_rsplit<<<(R + 7) / 8, 256, 0, st>>>(R, w->K, w->Kp, cur, slices, rexp, acc_pad, w->F1, w->F2);
-        CV_LAUNCH_CHECK("k_tc_rsplit");
+        k_tc_split<RowLd><<<(R + 7) / 8, 256, 0, st>>>(R, R, w->K, w->Kp, RowLd{cur, w->K}, slices, rexp, nullptr,
+                                                        acc_pad, w->F1, w->F2);
+        CV_LAUNCH_CHECK("k_tc_split");
         CUtensorMap tA;
         if ((s = encode_slices(&tA, slices, R, w->Kp, TBM))) return s;
         TcArgs a;
@@ -637,4 +603,328 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         }
     }
     return CV_OK;
+}
+
+// ---------------------------------------------------------------- re-concretisation (a5)
+// out[b, j] = [lo_b | hi_b] . PC_j + PCc_j over K = 2 n0, on tensor cores.  Each chunk of 256 K
+// rows accumulates its four levels exactly in one of two tensor-memory sets; eight epilogue warps
+// drain a finished chunk into FP32 running sums (level sum: three roundings; sum over chunks: one
+// rounding per chunk) while the MMA warp fills the other set.  Pad: 12 u pscale_j (the FP32 sums,
+// the intercept, against |value| <= pscale_j over the root box) plus the splitting term of the
+// file header with S_b = sum |box row|, T_j = sum |PC_j|.  A padded value that straddles 0 is
+// recomputed in FP64 from the FP32 operands, as in the CUDA-core kernel.
+namespace {
+
+constexpr int RC_CHUNK_TILES = KCH / TBK;  // K tiles per exact chunk
+constexpr int RC_NSTAGE = 2;
+constexpr int RC_SMEM = RC_NSTAGE * STAGE + 1024;
+constexpr int RC_THREADS = 320;            // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
+constexpr double RC_GAMMA = 12.0 * CV_U32;
+
+struct RcArgs {
+    int B, U, N, n0, K, Kp;
+    const int* bexp; const float* bsum;   // box rows: exponent, sum |.| (rounded up)
+    const int* fexp; const float* tsum;   // PC rows
+    const float* PCc; const float* pscale;
+    const float* PC; const float* lo; const float* hi;
+    const float* rls; const float* rus; const float* l_in; const float* u_in; const uint8_t* infeasible;
+    float* l_out; float* u_out;
+    int* status;
+};
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(RC_THREADS, 1) k_tc_reconc(const __grid_constant__ CUtensorMap tX,
+                                                            const __grid_constant__ CUtensorMap tP, RcArgs a) {
+    extern __shared__ __align__(1024) unsigned char rc_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)rc_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[RC_NSTAGE], empty[RC_NSTAGE], tfull[2], tempty[2];
+    __shared__ unsigned tmem_base;
+    __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.y * TBM, col0 = blockIdx.x * TBN;
+    const int KT = a.Kp / TBK;
+    const int nch = (KT + RC_CHUNK_TILES - 1) / RC_CHUNK_TILES;
+    const unsigned ncols = 2u * NLEV * TBN;  // two accumulator sets
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < RC_NSTAGE; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])) : "memory");
+        }
+        for (int s = 0; s < 2; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&tfull[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(su32(&tempty[s])) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+
+    if (warp == 8) {
+        if (lane == 0) {
+            for (int kt = 0; kt < KT; ++kt) {
+                const int s = kt % RC_NSTAGE;
+                if (kt >= RC_NSTAGE && !bar_wait(&empty[s], ((kt - RC_NSTAGE) / RC_NSTAGE) & 1)) { s_fail = 1; break; }
+                unsigned char* st = sm + s * STAGE;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])),
+                             "r"(STAGE)
+                             : "memory");
+                for (int z = 0; z < 3; ++z) {
+                    tma3(st + z * (TBM * TBK * 2), &tX, kt * TBK, row0, z, &full[s]);
+                    tma3(st + STAGE_A + z * (TBN * TBK * 2), &tP, kt * TBK, col0, z, &full[s]);
+                }
+            }
+        }
+    } else if (warp == 9) {
+        if (lane == 0) {
+            const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TBN >> 3) << 17) |
+                                   ((unsigned)(TBM >> 4) << 24);
+            const int pi[8] = {0, 0, 1, 0, 1, 2, 1, 2};
+            const int pj[8] = {0, 1, 0, 2, 1, 0, 2, 1};
+            for (int kt = 0; kt < KT; ++kt) {
+                const int c = kt / RC_CHUNK_TILES, set = c & 1;
+                const bool chunk_start = (kt % RC_CHUNK_TILES) == 0;
+                const bool chunk_end = (kt % RC_CHUNK_TILES) == RC_CHUNK_TILES - 1 || kt == KT - 1;
+                if (chunk_start && c >= 2 && !bar_wait(&tempty[set], ((c - 2) >> 1) & 1)) { s_fail = 1; break; }
+                const int s = kt % RC_NSTAGE;
+                if (!bar_wait(&full[s], (kt / RC_NSTAGE) & 1)) { s_fail = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned char* st = sm + s * STAGE;
+                for (int kk = 0; kk < TBK / 16; ++kk) {
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) {
+                        const int lev = pi[p] + pj[p];
+                        const unsigned d = tmem + (unsigned)((set * NLEV + lev) * TBN);
+                        const uint64_t da = sdesc(st + pi[p] * (TBM * TBK * 2)) + (uint64_t)(kk * 2);
+                        const uint64_t db = sdesc(st + STAGE_A + pj[p] * (TBN * TBK * 2)) + (uint64_t)(kk * 2);
+                        const bool first_of_level = (p == 0) || (p == 1) || (p == 3) || (p == 6);
+                        const unsigned acc = (chunk_start && kk == 0 && first_of_level) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                d),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&empty[s]))
+                             : "memory");
+                if (chunk_end)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     su32(&tfull[set]))
+                                 : "memory");
+            }
+        }
+    } else {
+        // epilogue warps: drain every chunk into FP32 running sums
+        const int wq = warp & 3, half = warp >> 2;
+        const unsigned lane_base = tmem + ((unsigned)(wq * 32) << 16);
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nch; ++c) {
+            const int set = c & 1;
+            ok = __all_sync(0xffffffffu, bar_wait(&tfull[set], (c >> 1) & 1));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int cc = 0; cc < 32; cc += 8) {
+                float lv[NLEV][8];
+#pragma unroll
+                for (int v = 0; v < NLEV; ++v)
+                    tmem_ld8(lane_base + (unsigned)((set * NLEV + v) * TBN + half * 32 + cc), lv[v]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[cc + j] += fmaf(lv[0][j], 16777216.f, fmaf(lv[1][j], 65536.f, fmaf(lv[2][j], 256.f, lv[3][j])));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&tempty[set]);
+        }
+        if (!ok && lane == 0) atomicOr(a.status, CV_DEV_TIMEOUT);
+        const int b = row0 + wq * 32 + lane;
+        if (ok && b < a.B) {
+            const bool skip = a.infeasible[b] != 0;
+            const int eb = a.bexp[b];
+            const float sb = a.bsum[b];
+            const float c24 = 1.016f * 5.9604645e-08f;  // (1 + 2^-6) 2^-24, rounded up
+            unsigned straddle = 0u;                      // bit j: value straddles 0 after padding
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int jj = col0 + half * 32 + j;
+                if (jj >= a.N) continue;
+                const bool up = jj >= a.U;
+                const int slot = up ? jj - a.U : jj;
+                const size_t o = (size_t)b * a.U + slot;
+                const float inh = up ? (a.u_in ? a.u_in[o] : a.rus[slot]) : (a.l_in ? a.l_in[o] : a.rls[slot]);
+                float res = inh;
+                if (!skip) {
+                    const int fj = a.fexp[jj];
+                    const float val = ldexpf(acc[j], eb + fj - 38) + a.PCc[jj];
+                    // pad, every operation rounded up
+                    float pad = __fmul_ru((float)RC_GAMMA, a.pscale[jj]);
+                    pad = __fadd_ru(pad, __fmul_ru(c24, __fadd_ru(__fmul_ru(sb, ldexpf(1.f, fj)),
+                                                                  __fmul_ru(ldexpf(1.f, eb), a.tsum[jj]))));
+                    pad = __fadd_ru(pad, ldexpf((float)a.K, eb + fj - 31));
+                    const float lo_v = __fsub_rd(val, pad), hi_v = __fadd_ru(val, pad);
+                    if (lo_v < 0.f && hi_v >= 0.f) straddle |= 1u << j;
+                    res = up ? fminf(inh, hi_v) : fmaxf(inh, lo_v);
+                }
+                if (up) a.u_out[o] = res; else a.l_out[o] = res;
+            }
+            // rare: the stability decision is uncertain in FP32; recompute those bounds in FP64
+            while (straddle) {
+                const int j = __ffs(straddle) - 1;
+                straddle &= straddle - 1u;
+                const int jj = col0 + half * 32 + j;
+                const bool up = jj >= a.U;
+                const int slot = up ? jj - a.U : jj;
+                const size_t o = (size_t)b * a.U + slot;
+                const float inh = up ? (a.u_in ? a.u_in[o] : a.rus[slot]) : (a.l_in ? a.l_in[o] : a.rls[slot]);
+                double sacc = (double)a.PCc[jj], mag = fabs((double)a.PCc[jj]);
+                const float* pr = a.PC + (size_t)jj * a.K;
+                for (int k = 0; k < a.n0; ++k) {
+                    const double t1 = (double)pr[k] * (double)a.lo[(size_t)b * a.n0 + k];
+                    const double t2 = (double)pr[a.n0 + k] * (double)a.hi[(size_t)b * a.n0 + k];
+                    sacc += t1 + t2;
+                    mag += fabs(t1) + fabs(t2);
+                }
+                const double e64 = ldexp(mag, -40);
+                if (up) a.u_out[o] = fminf(inh, __double2float_ru(sacc + e64));
+                else a.l_out[o] = fmaxf(inh, __double2float_rd(sacc - e64));
+            }
+        }
+    }
+    if (threadIdx.x == 0 && s_fail) atomicOr(a.status, CV_DEV_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 9) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+}  // namespace
+
+size_t cv_tc_box_bytes(const cv_cache* c, int B) {
+    if (!c->tcpc) return 0;
+    return (size_t)3 * B * c->tcpc->Kp * sizeof(uint16_t);
+}
+
+cv_status cv_reconc_tc(const cv_cache* cache, int B, const float* lo, const float* hi, const float* rls,
+                       const float* rus, const float* l_in, const float* u_in, const uint8_t* infeasible, float* l,
+                       float* u, uint16_t* xslices, int* bexp, float* bsum, int* status, cudaStream_t st) {
+    const cv_tc_pc* pc = cache->tcpc;
+    if (!pc) { cv_set_error("tensor-core re-concretisation: no split operand"); return CV_EUNSUPPORTED; }
+    if (B == 0) return CV_OK;
+    const int n0 = cache->n0;
+    k_tc_split<BoxLd><<<(B + 7) / 8, 256, 0, st>>>(B, B, pc->K, pc->Kp, BoxLd{lo, hi, n0}, xslices, bexp, bsum,
+                                                    nullptr, 0.0, 0.0);
+    CV_LAUNCH_CHECK("k_tc_split");
+    CUtensorMap tX;
+    cv_status s = encode_slices(&tX, xslices, B, pc->Kp, TBM);
+    if (s) return s;
+    RcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.B = B; a.U = cache->U; a.N = pc->N; a.n0 = n0; a.K = pc->K; a.Kp = pc->Kp;
+    a.bexp = bexp; a.bsum = bsum; a.fexp = pc->fexp; a.tsum = pc->tsum;
+    a.PCc = cache->PCc; a.pscale = cache->pscale; a.PC = cache->PC; a.lo = lo; a.hi = hi;
+    a.rls = rls; a.rus = rus; a.l_in = l_in; a.u_in = u_in; a.infeasible = infeasible;
+    a.l_out = l; a.u_out = u; a.status = status;
+    CV_CUDA(cudaFuncSetAttribute(k_tc_reconc, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM));
+    dim3 grd(pc->Np / TBN, (B + TBM - 1) / TBM);
+    k_tc_reconc<<<grd, RC_THREADS, RC_SMEM, st>>>(tX, pc->tmap, a);
+    CV_LAUNCH_CHECK("k_tc_reconc");
+    return CV_OK;
+}
+
+void cv_tc_release(cv_cache* c) {
+    if (!c) return;
+    for (int i = 0; i <= CV_MAX_LAYERS; ++i) {
+        cv_tc_w* w = c->tcw[i];
+        if (!w) continue;
+        cudaFree(w->slices);
+        cudaFree(w->fexp);
+        delete w;
+        c->tcw[i] = nullptr;
+    }
+    if (c->tcpc) {
+        cudaFree(c->tcpc->slices);
+        cudaFree(c->tcpc->fexp);
+        cudaFree(c->tcpc->tsum);
+        delete c->tcpc;
+        c->tcpc = nullptr;
+    }
+}
+
+bool cv_tc_supported(const cv_cache* c) {
+    for (int i = 1; i <= c->net->L; ++i)
+        if (!c->tcw[i]) return false;
+    return true;
+}
+
+cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaStream_t st) {
+    const cv_net* n = c->net;
+    for (int i = 1; i <= n->L; ++i) {
+        const int K = n->dims[i], N = n->dims[i - 1];
+        const int Kp = round_up(K, TBK), Np = round_up(N, TBN);
+        if (Kp > KMAX) continue;  // the path takes K <= 512 (two exact accumulator sets)
+        cv_tc_w* w = new cv_tc_w();
+        memset(w, 0, sizeof(*w));
+        c->tcw[i] = w;
+        w->K = K; w->N = N; w->Kp = Kp; w->Np = Np;
+        double* F = nullptr;
+        CV_CUDA(cudaMalloc(&w->slices, (size_t)3 * Np * Kp * sizeof(uint16_t)));
+        CV_CUDA(cudaMalloc(&w->fexp, (size_t)N * sizeof(int)));
+        CV_CUDA(cudaMalloc(&F, 2 * sizeof(double)));
+        CV_CUDA(cudaMemsetAsync(F, 0, 2 * sizeof(double), st));
+        const float* zm = (i == 1) ? xmag : zmag + n->hoff[i - 1];
+        k_tc_wsplit<<<(Np + 7) / 8, 256, 0, st>>>(K, N, Kp, Np, n->W[i], zm, w->slices, w->fexp, F);
+        CV_LAUNCH_CHECK("k_tc_wsplit");
+        double hF[2];
+        CV_CUDA(cudaMemcpyAsync(hF, F, sizeof(hF), cudaMemcpyDeviceToHost, st));
+        CV_CUDA(cudaStreamSynchronize(st));
+        cudaFree(F);
+        w->F1 = hF[0] * (1.0 + 1e-12);
+        w->F2 = hF[1] * (1.0 + 1e-12);
+        cv_status s = encode_slices(&w->tmap, w->slices, Np, Kp, TBN);
+        if (s) return s;
+    }
+    if (c->U > 0) {
+        cv_tc_pc* pc = new cv_tc_pc();
+        memset(pc, 0, sizeof(*pc));
+        c->tcpc = pc;
+        pc->K = 2 * c->n0; pc->N = 2 * c->U;
+        pc->Kp = round_up(pc->K, TBK); pc->Np = round_up(pc->N, TBN);
+        CV_CUDA(cudaMalloc(&pc->slices, (size_t)3 * pc->Np * pc->Kp * sizeof(uint16_t)));
+        CV_CUDA(cudaMemsetAsync(pc->slices, 0, (size_t)3 * pc->Np * pc->Kp * sizeof(uint16_t), st));
+        CV_CUDA(cudaMalloc(&pc->fexp, (size_t)pc->N * sizeof(int)));
+        CV_CUDA(cudaMalloc(&pc->tsum, (size_t)pc->N * sizeof(float)));
+        // rows of PC, written into the first N of the Np slice rows (the rest stay zero)
+        k_tc_split<RowLd><<<(pc->N + 7) / 8, 256, 0, st>>>(pc->N, pc->Np, pc->K, pc->Kp, RowLd{c->PC, pc->K},
+                                                            pc->slices, pc->fexp, pc->tsum, nullptr, 0.0, 0.0);
+        CV_LAUNCH_CHECK("k_tc_split");
+        cv_status s = encode_slices(&pc->tmap, pc->slices, pc->Np, pc->Kp, TBN);
+        if (s) return s;
+    }
+    return CV_OK;
+}
+
+size_t cv_tc_slices_bytes(const cv_net* net, int R) {
+    int kp = 0;
+    for (int i = 1; i <= net->L; ++i) kp = std::max(kp, round_up(net->dims[i], TBK));
+    return (size_t)3 * R * kp * sizeof(uint16_t);
 }

@@ -257,16 +257,18 @@ def test_cache_build_parity():
         net.close()
 
 
-def test_graph_replay_matches_direct_call():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_matches_direct_call(precision):
     """A captured round (cv_graph_capture / cv_graph_launch) reads its buffers at replay time and
-    gives the same outputs as a direct cv_bound_batch call."""
+    gives the same outputs as a direct cv_bound_batch call (both precisions: the tensor-core path
+    encodes its TMA descriptors on the host during capture)."""
     from paper_2512_11087_gb300 import engine as E
     case = Case([24, 32, 32, 32, 6], 32, 1, 4, 0.1, sweeps=5, seed=2)
     net = E.Net(case.layers)
     c = case.cache
     net.set_cache(f32(case.lo0), f32(case.hi0), f32(c["root_l"]), f32(c["root_u"]), c["ids"], f32(c["lA"]),
                   f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
-    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, sweeps=case.sweeps)
+    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, sweeps=case.sweeps, precision=precision)
     d = E.to_dev
     lo, hi = d(case.lo), d(case.hi)
     args = (d(case.C), d(case.t))
@@ -299,14 +301,15 @@ def test_cnn_round_parity():
     compare(case, g, o)
 
 
-def test_bench_workload_full_size_sampled():
+@pytest.mark.parametrize("precision", [1, 0])
+def test_bench_workload_full_size_sampled(precision):
     """The benchmark's launch configuration: 784->256x6->10, 4096 subdomains with 1-4 splits,
-    relaxed + complete clipping with 10 sweeps.  The GPU bounds all subdomains; the oracle bounds a
-    sample (every subdomain with two or more active rows among the first 1024, plus others)."""
+    relaxed + complete clipping with 10 sweeps, split-precision tensor-core path (the bench's
+    default) and the plain FP32 path.  The GPU bounds all subdomains; the oracle bounds a sample."""
     from paper_2512_11087_gb300 import workloads as WL
     cfg = WL.CONFIGS["mlp784x256"]
     case = Case(cfg["dims"], cfg["B"], cfg["kmin"], cfg["kmax"], cfg["eps"], sweeps=cfg["sweeps"], seed=0)
-    g = gpu_round(case)
+    g = gpu_round(case, precision=precision)
     rng = np.random.default_rng(0)
     sample = np.unique(np.concatenate([rng.choice(case.B, 12, replace=False), [0, case.B - 1]]))
     sub = Case.__new__(Case)

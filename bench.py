@@ -27,9 +27,9 @@ CONFIG = "mlp784x256"
 ALG_OPS_BASE = 7  # per coordinate and row step of Algorithm 1, besides the argsort comparisons
 
 
-def workload_desc(cfg):
+def workload_desc(cfg, name=CONFIG):
     d = cfg["dims"]
-    return (f"{CONFIG}: ReLU MLP {d[0]}->{d[1]}x{len(d) - 2}->{d[-1]} He-normal seed 0; box eps={cfg['eps']} around "
+    return (f"{name}: ReLU MLP {d[0]}->{d[1]}x{len(d) - 2}->{d[-1]} He-normal seed 0; box eps={cfg['eps']} around "
             f"U[0,1]^{d[0]} clipped to [0,1]; B={cfg['B']} subdomains with {cfg['kmin']}-{cfg['kmax']} ReLU split "
             f"constraints each; 9 margin spec rows; relaxed clipping + complete clipping ({cfg['sweeps']} sweeps) "
             f"on every still-unstable cached neuron")
@@ -43,6 +43,8 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--precision", default="bf16x8", choices=["fp32", "bf16x8"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--config", default=CONFIG, choices=["mlp784x256", "mlp784x512x8"],
+                   help="workload (default: the metric's workload; mlp784x512x8 is the BaB stress shape)")
     p.add_argument("--subdomains", type=int, default=0,
                    help="smaller batch for profiler captures (default: the workload's own batch)")
     return p.parse_args()
@@ -143,7 +145,7 @@ def run_reference(args, cfg, rank, world):
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * total_dt / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
-                config=dict(workload=workload_desc(cfg), sample=f"{n} subdomains per step"),
+                config=dict(workload=workload_desc(cfg, args.config), sample=f"{n} subdomains per step"),
                 cpu_baseline=dict(value=value, unit="subdomains/s", cores=cores, kind="oracle",
                                   sample=f"{n} subdomains of the workload per step, FP64 C oracle, OpenMP"),
                 e2e=dict(value=value, unit="subdomains/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -177,7 +179,7 @@ def job_value(world, B, steps, total_ms):
 def main():
     args = parse_args()
     from paper_2512_11087_gb300 import workloads as WL
-    cfg = WL.CONFIGS[CONFIG]
+    cfg = WL.CONFIGS[args.config]
     if args.subdomains > 0:
         cfg = dict(cfg, B=args.subdomains)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -320,7 +322,7 @@ def main():
                     steps=args.steps, warmup=max(args.warmup, 3), ms_per_step=total_ms / args.steps,
                     higher_is_better=True, scaling="weak", vs_baseline=None,
                     dtype="f32" if args.precision == "fp32" else "bf16x8+f32", data="synthetic",
-                    config=dict(workload=workload_desc(cfg), precision=args.precision, cached_neurons=U,
+                    config=dict(workload=workload_desc(cfg, args.config), precision=args.precision, cached_neurons=U,
                                 l2="flushed (256 MiB write) before every timed step",
                                 phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
                                                   [round(x, 4) for x in ph_mean]))),

@@ -8,10 +8,12 @@
 // sum_{q_j <= q*} w_j reaches T_k = max_box(g_k.x + h_k) / 2 (the first non-positive
 // supergradient), clamped at 0.  This is the sorted-breakpoint rule of Algorithm 1 written as
 // a weighted quantile, so no sort is needed.  The quantile is found by shrinking a key bracket
-// (lo, hi] with F(lo) < T <= F(hi): each pass takes the min and max breakpoint key inside it
-// (done when they coincide) and splits it at the pivot interpolated from the weight still
-// needed (after eight passes, every other pass halves the range instead, which bounds the
-// count); the previous sweep's breakpoint is tried first (coordinate ascent mostly re-selects it).
+// (lo, hi] with F(lo) < T <= F(hi): the first pass over a large bracket takes F at two pivots
+// drawn from a 32-breakpoint sample around the target rank and keeps the slice between them;
+// each later pass takes the min and max breakpoint key inside the bracket (done when they
+// coincide) and splits it at the pivot interpolated from the weight still needed (after eight
+// passes, every other pass halves the range instead, which bounds the count); the previous
+// sweep's breakpoint is tried first (coordinate ascent mostly re-selects it).
 //
 // Decision arithmetic (reproduced by the oracle): a'_j = a_j + sum_{p != k} beta_p g_pj as an FP32
 // fma chain over increasing p, q_j = (-a'_j) * fl(1/g_kj); breakpoints with q > 0 are compared
@@ -48,6 +50,8 @@ constexpr int RTPL = 4;     // row counts up to this run in the main launch (two
 __host__ __device__ __forceinline__ int tpi_of(int R) { return R <= 1 ? 256 : (R == 2 ? 64 : 16); }
 constexpr int NWARP = 16;   // warps per block at most
 constexpr int CAPC = 384;   // breakpoints a warp's compacted list holds
+constexpr int SAMP_MIN = 64;     // brackets with more breakpoints start from sampled pivots
+constexpr float SAMP_D = 0.10f;  // rank margin of the sampled pivots around the target fraction
 constexpr int PF = 4;       // coefficients loaded ahead per lane in the element loops
 
 // Exact warp sum of non-negative per-lane 64-bit values whose total is below 2^62: three
@@ -438,6 +442,95 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 int m = n0;
                 unsigned ks = 0u;
                 const unsigned below = (1u << lane) - 1u;
+                if (cmin != cmax && ncnt > (unsigned)SAMP_MIN) {
+                    // First pivots from a sample: each lane takes its first breakpoint inside the bracket
+                    // among elements lane, lane+32, lane+64, lane+96.  With phi the fraction of the
+                    // bracket's weight still needed, p1 is the largest sample whose weighted rank is at
+                    // most phi - SAMP_D and p2 the smallest at least phi + SAMP_D.  One pass takes F at
+                    // both and moves the breakpoints between them to the front of the buffer (key and
+                    // element, at most CAPC); when the quantile lies there (most of the time) the later
+                    // passes read only that list, else the overwritten keys are recomputed.  The
+                    // pivots only steer the search: every decision still uses the exact sums.
+                    unsigned sk = 0u;
+                    float sw = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = lane + 32 * t;
+                        const int jj = j < n0 ? j : 0;
+                        const unsigned kk = keys[jj];
+                        const bool ok = sk == 0u && j < n0 && kk >= cmin && kk <= cmax;
+                        if (ok) { sk = kk; sw = (float)wk[jj]; }
+                    }
+                    // weight of the samples at or below each lane's own
+                    float cw = 0.f, tot = 0.f;
+#pragma unroll
+                    for (int s = 0; s < 32; ++s) {
+                        const unsigned k2 = __shfl_sync(0xffffffffu, sk, s);
+                        const float w2 = __shfl_sync(0xffffffffu, sw, s);
+                        tot += w2;
+                        cw += (k2 <= sk) ? w2 : 0.f;
+                    }
+                    const float phi = __fdividef((float)(T - Flo), (float)(Fhi - Flo));
+                    const bool has = sk != 0u;
+                    unsigned p1 = __reduce_max_sync(0xffffffffu, (has && cw <= (phi - SAMP_D) * tot) ? sk : 0u);
+                    unsigned p2 = __reduce_min_sync(0xffffffffu, (has && cw >= (phi + SAMP_D) * tot) ? sk : 0xffffffffu);
+                    if (p1 == 0u) p1 = cmin - 1u;
+                    if (p2 == 0xffffffffu) p2 = cmax;
+                    if (tot > 0.f && p1 < p2 && (p1 >= cmin || p2 < cmax)) {
+                        // F at both pivots; the breakpoints between them move to the front of the buffer
+                        // (at most CAPC of them)
+                        unsigned long long f1 = 0, f2 = 0;
+                        unsigned c1 = 0u, c2 = 0u;
+                        int wpos = 0;
+#pragma unroll 1
+                        for (int j0 = 0; j0 < n0; j0 += 32) {
+                            const int j = j0 + lane;
+                            const bool v = j < n0;
+                            const int jj = v ? j : 0;
+                            const unsigned kk = keys[jj];
+                            const unsigned long long w = (unsigned long long)wk[jj];
+                            const bool in = v && kk >= cmin && kk <= cmax;
+                            const bool L1 = in && kk <= p1;
+                            const bool L2 = in && kk <= p2;
+                            const bool M = L2 && !L1;
+                            const unsigned bal = __ballot_sync(0xffffffffu, M);
+                            const int q = wpos + __popc(bal & below);
+                            if (M && q < CAPC) {
+                                keys[q] = kk;
+                                cidx[q] = (unsigned short)j;
+                            }
+                            wpos += __popc(bal);
+                            f1 += L1 ? w : 0ull;
+                            f2 += L2 ? w : 0ull;
+                            c1 += L1 ? 1u : 0u;
+                            c2 += L2 ? 1u : 0u;
+                        }
+                        __syncwarp();
+                        const long long F1 = Flo + warp_sum64(f1);
+                        const long long F2 = Flo + warp_sum64(f2);
+                        const unsigned n1 = __reduce_add_sync(0xffffffffu, c1);
+                        const unsigned n2 = __reduce_add_sync(0xffffffffu, c2);
+                        bool keep = false;
+                        if (F1 >= T) {
+                            Fhi = F1; cmax = p1; ncnt = n1;
+                        } else if (F2 >= T) {
+                            Flo = F1; Fhi = F2; cmin = p1 + 1u; cmax = p2; ncnt = n2 - n1;
+                            keep = ncnt <= (unsigned)CAPC;
+                        } else {
+                            Flo = F2; cmin = p2 + 1u; ncnt -= n2;
+                        }
+                        if (keep) {
+                            listed = true;
+                            m = (int)ncnt;
+                        } else {
+                            // put back the keys the list overwrote
+                            const int wr = min(wpos, CAPC);
+                            for (int j = lane; j < wr; j += 32)
+                                keys[j] = __float_as_uint(q_of(__ldg(ap + j), j));
+                            __syncwarp();
+                        }
+                    }
+                }
 #pragma unroll 1
                 for (int it = 0; it < 96; ++it) {
                     if (cmin == cmax) { ks = cmin; break; }

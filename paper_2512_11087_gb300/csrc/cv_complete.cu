@@ -66,6 +66,13 @@ __device__ __forceinline__ long long warp_sum64(unsigned long long v) {
     return (long long)A + ((long long)B << 21) + ((long long)C << 42);
 }
 
+// n / d for 0 < n <= d < 2^63 to about 2^-23 relative, without a 64-bit integer conversion (those
+// run on the FP64 pipe): both are shifted until d fits in 24 bits and converted from 32 bits.
+__device__ __forceinline__ float ratio64(long long n, long long d) {
+    const int sh = max(0, 40 - __clzll(d));
+    return __fdividef((float)(unsigned)((unsigned long long)n >> sh), (float)(unsigned)((unsigned long long)d >> sh));
+}
+
 struct CCArgs {
     int B, U, n0, H, Rmax, Rs, sweeps;
     const int8_t* rowflag;
@@ -227,6 +234,7 @@ __shared__ long long cc_T64[RMAX_CC];  // thresholds (fixed point)
 __shared__ long long cc_W64[RMAX_CC];  // total weights (fixed point)
 __shared__ float cc_hrow[RMAX_CC];     // row constants h
 __shared__ double cc_Sg[RMAX_CC];      // magnitude of g against the root box
+__shared__ float cc_SgH[RMAX_CC];      // Sg + |h| rounded up
 
 struct CCView {
     unsigned* keys;        // this warp's keys
@@ -346,49 +354,115 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             const long long T = cc_T64[k];
             const long long W = cc_W64[k];
             // One pass over all n0 elements keeps the keys in the warp's buffer.  Without a previous
-            // breakpoint it takes F(0) = sum_{q <= 0} w and the extent and size of the search range;
-            // with one, F just below and at it.  F(+inf) is the row's total weight W.
-            // (Branch-free element loops: indices past n0 are clamped and contribute nothing.)
+            // breakpoint it takes F(0) = sum_{q <= 0} w (the paired pass: W minus the weight of q > 0,
+            // leaving the extent and size of the search range to the search); with one, F just below
+            // and at it.  F(+inf) is the row's total weight W.  (Branch-free element loops: indices
+            // past n0 are clamped and contribute nothing.)
             unsigned long long f0 = 0, flt = 0, fle = 0;
             unsigned mn = 0xffffffffu, mx = 0u, cnt = 0u;
-            if (warm) {
+            // extents (mn, mx, cnt) of the positive keys: the paired pass leaves them to the search
+            bool ext = true;
+            if (!WIDE && (n0 & 1) == 0) {
+                // Two adjacent elements per lane with packed FP32 arithmetic.  x = -a' is built as
+                // (-sa) a + sum_p (-beta_p) g_p with row k's own multiplier zeroed: negation is exact
+                // and commutes with round-to-nearest, so q = x * fl(1/g) has the bits of (-a') * fl(1/g)
+                // (up to the sign of a zero, and zero is never a breakpoint).
+                float nb[WIDE ? 1 : RC];
+#pragma unroll
+                for (int p = 0; p < (WIDE ? 1 : RC); ++p) nb[p] = (p == k) ? 0.f : -bget(p);
+                const float2 nsa2 = make_float2(-sa, -sa);
+                auto q2_of = [&](float2 av, int j) -> float2 {
+                    float2 x = __fmul2_rn(av, nsa2);
+#pragma unroll
+                    for (int p = 0; p < (WIDE ? 1 : RC); ++p)
+                        if (RC > 1) x = __ffma2_rn(make_float2(nb[p], nb[p]), *(const float2*)(rw.gs + p * n0 + j), x);
+                    return __fmul2_rn(x, *(const float2*)(rk + j));
+                };
+                const float2* ap2 = (const float2*)ap;
+                constexpr int P2 = 2;
+                if (warm) {
 #pragma unroll 1
-                for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
-                    float av[PF];
+                    for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
+                        float2 av[P2];
 #pragma unroll
-                    for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
+                        for (int u = 0; u < P2; ++u) av[u] = __ldg(ap2 + (min(j0 + 64 * u, n0 - 2) >> 1));
 #pragma unroll
-                    for (int u = 0; u < PF; ++u) {
-                        const int j = j0 + 32 * u;
-                        const bool v = j < n0;
-                        const int jj = v ? j : n0 - 1;
-                        const float q = q_of(av[u], jj);
-                        if (v) keys[j] = __float_as_uint(q);
-                        const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
-                        flt += (q < qp) ? w : 0ull;
-                        fle += (q <= qp) ? w : 0ull;
+                        for (int u = 0; u < P2; ++u) {
+                            const int j = j0 + 64 * u;
+                            const bool v = j < n0;
+                            const int jj = v ? j : n0 - 2;
+                            const float2 q = q2_of(av[u], jj);
+                            if (v) *(uint2*)(keys + j) = make_uint2(__float_as_uint(q.x), __float_as_uint(q.y));
+                            const longlong2 w = *(const longlong2*)(wk + jj);
+                            if (v) {
+                                if (q.x < qp) flt += (unsigned long long)w.x;
+                                if (q.y < qp) flt += (unsigned long long)w.y;
+                                if (q.x == qp) fle += (unsigned long long)w.x;
+                                if (q.y == qp) fle += (unsigned long long)w.y;
+                            }
+                        }
+                    }
+                    fle += flt;
+                } else {
+                    ext = false;
+#pragma unroll 1
+                    for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
+                        float2 av[P2];
+#pragma unroll
+                        for (int u = 0; u < P2; ++u) av[u] = __ldg(ap2 + (min(j0 + 64 * u, n0 - 2) >> 1));
+#pragma unroll
+                        for (int u = 0; u < P2; ++u) {
+                            const int j = j0 + 64 * u;
+                            const bool v = j < n0;
+                            const int jj = v ? j : n0 - 2;
+                            const float2 q = q2_of(av[u], jj);
+                            if (v) *(uint2*)(keys + j) = make_uint2(__float_as_uint(q.x), __float_as_uint(q.y));
+                            const longlong2 w = *(const longlong2*)(wk + jj);
+                            if (v && q.x > 0.f) f0 += (unsigned long long)w.x;  // weight of q > 0 here: F(0) = W - it
+                            if (v && q.y > 0.f) f0 += (unsigned long long)w.y;
+                        }
                     }
                 }
             } else {
+                if (warm) {
 #pragma unroll 1
-                for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
-                    float av[PF];
+                    for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
+                        float av[PF];
 #pragma unroll
-                    for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
+                        for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
 #pragma unroll
-                    for (int u = 0; u < PF; ++u) {
-                        const int j = j0 + 32 * u;
-                        const bool v = j < n0;
-                        const int jj = v ? j : n0 - 1;
-                        const float q = q_of(av[u], jj);
-                        const unsigned kk = __float_as_uint(q);
-                        if (v) keys[j] = kk;
-                        const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
-                        const bool pos = v && q > 0.f;
-                        f0 += (q <= 0.f) ? w : 0ull;
-                        mn = min(mn, pos ? kk : 0xffffffffu);
-                        mx = max(mx, pos ? kk : 0u);
-                        cnt += pos ? 1u : 0u;
+                        for (int u = 0; u < PF; ++u) {
+                            const int j = j0 + 32 * u;
+                            const bool v = j < n0;
+                            const int jj = v ? j : n0 - 1;
+                            const float q = q_of(av[u], jj);
+                            if (v) keys[j] = __float_as_uint(q);
+                            const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
+                            flt += (q < qp) ? w : 0ull;
+                            fle += (q <= qp) ? w : 0ull;
+                        }
+                    }
+                } else {
+#pragma unroll 1
+                    for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
+                        float av[PF];
+#pragma unroll
+                        for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
+#pragma unroll
+                        for (int u = 0; u < PF; ++u) {
+                            const int j = j0 + 32 * u;
+                            const bool v = j < n0;
+                            const int jj = v ? j : n0 - 1;
+                            const float q = q_of(av[u], jj);
+                            const unsigned kk = __float_as_uint(q);
+                            if (v) keys[j] = kk;
+                            const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
+                            const bool pos = v && q > 0.f;
+                            f0 += (q <= 0.f) ? w : 0ull;
+                            mn = min(mn, pos ? kk : 0xffffffffu);
+                            mx = max(mx, pos ? kk : 0u);
+                            cnt += pos ? 1u : 0u;
+                        }
                     }
                 }
             }
@@ -425,7 +499,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     search = !(F0 >= T || W < T);
                 }
             } else {
-                const long long F0 = warp_sum64(f0);
+                const long long F0 = ext ? warp_sum64(f0) : W - warp_sum64(f0);
                 Flo = F0;
                 search = !(F0 >= T || W < T);  // else beta = 0: slope at 0+ not positive, or no crossing
             }
@@ -433,6 +507,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 unsigned cmin = __reduce_min_sync(0xffffffffu, mn);
                 unsigned cmax = __reduce_max_sync(0xffffffffu, mx);
                 unsigned ncnt = __reduce_add_sync(0xffffffffu, cnt);
+                if (!ext) {
+                    // not taken yet: every positive key, at most n0 of them
+                    cmin = 1u; cmax = QINF; ncnt = (unsigned)n0;
+                }
                 // Shrink to a single key.  Each pass splits the bracket at a pivot interpolated from
                 // the weight still needed (after eight passes every other pass halves it) and takes F
                 // at the pivot and the extent and size of both halves.  Once the bracket holds at most
@@ -453,13 +531,14 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     // pivots only steer the search: every decision still uses the exact sums.
                     unsigned sk = 0u;
                     float sw = 0.f;
+                    const int shw = max(0, 40 - __clzll(Fhi - Flo));  // bracket weights fit 24 bits
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int j = lane + 32 * t;
                         const int jj = j < n0 ? j : 0;
                         const unsigned kk = keys[jj];
                         const bool ok = sk == 0u && j < n0 && kk >= cmin && kk <= cmax;
-                        if (ok) { sk = kk; sw = (float)wk[jj]; }
+                        if (ok) { sk = kk; sw = (float)(unsigned)((unsigned long long)wk[jj] >> shw); }
                     }
                     // weight of the samples at or below each lane's own
                     float cw = 0.f, tot = 0.f;
@@ -470,7 +549,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                         tot += w2;
                         cw += (k2 <= sk) ? w2 : 0.f;
                     }
-                    const float phi = __fdividef((float)(T - Flo), (float)(Fhi - Flo));
+                    const float phi = ratio64(T - Flo, Fhi - Flo);
                     const bool has = sk != 0u;
                     unsigned p1 = __reduce_max_sync(0xffffffffu, (has && cw <= (phi - SAMP_D) * tot) ? sk : 0u);
                     unsigned p2 = __reduce_min_sync(0xffffffffu, (has && cw >= (phi + SAMP_D) * tot) ? sk : 0xffffffffu);
@@ -479,8 +558,11 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     if (tot > 0.f && p1 < p2 && (p1 >= cmin || p2 < cmax)) {
                         // F at both pivots; the breakpoints between them move to the front of the buffer
                         // (at most CAPC of them)
-                        unsigned long long f1 = 0, f2 = 0;
-                        unsigned c1 = 0u, c2 = 0u;
+                        // offsets from cmin: d <= span inside the bracket (keys below it wrap past span),
+                        // d < e1 at or below p1, d < e2 at or below p2
+                        const unsigned span = cmax - cmin, e1 = p1 + 1u - cmin, e2 = p2 + 1u - cmin;
+                        unsigned long long f1 = 0, fM = 0;
+                        unsigned c1 = 0u, emn = 0xffffffffu, emx = 0u;
                         int wpos = 0;
 #pragma unroll 1
                         for (int j0 = 0; j0 < n0; j0 += 32) {
@@ -489,10 +571,9 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                             const int jj = v ? j : 0;
                             const unsigned kk = keys[jj];
                             const unsigned long long w = (unsigned long long)wk[jj];
-                            const bool in = v && kk >= cmin && kk <= cmax;
-                            const bool L1 = in && kk <= p1;
-                            const bool L2 = in && kk <= p2;
-                            const bool M = L2 && !L1;
+                            const unsigned d = v ? kk - cmin : 0xffffffffu;
+                            const bool L1 = d < e1;
+                            const bool M = !L1 && d < e2;
                             const unsigned bal = __ballot_sync(0xffffffffu, M);
                             const int q = wpos + __popc(bal & below);
                             if (M && q < CAPC) {
@@ -500,24 +581,26 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                                 cidx[q] = (unsigned short)j;
                             }
                             wpos += __popc(bal);
-                            f1 += L1 ? w : 0ull;
-                            f2 += L2 ? w : 0ull;
-                            c1 += L1 ? 1u : 0u;
-                            c2 += L2 ? 1u : 0u;
+                            if (L1) { f1 += w; ++c1; }
+                            if (M) fM += w;
+                            emn = min(emn, d);
+                            emx = max(emx, d <= span ? d : 0u);
                         }
                         __syncwarp();
                         const long long F1 = Flo + warp_sum64(f1);
-                        const long long F2 = Flo + warp_sum64(f2);
+                        const long long F2 = F1 + warp_sum64(fM);
                         const unsigned n1 = __reduce_add_sync(0xffffffffu, c1);
-                        const unsigned n2 = __reduce_add_sync(0xffffffffu, c2);
                         bool keep = false;
                         if (F1 >= T) {
                             Fhi = F1; cmax = p1; ncnt = n1;
+                            cmin += __reduce_min_sync(0xffffffffu, emn);
                         } else if (F2 >= T) {
-                            Flo = F1; Fhi = F2; cmin = p1 + 1u; cmax = p2; ncnt = n2 - n1;
+                            Flo = F1; Fhi = F2; cmin = p1 + 1u; cmax = p2; ncnt = (unsigned)wpos;
                             keep = ncnt <= (unsigned)CAPC;
                         } else {
-                            Flo = F2; cmin = p2 + 1u; ncnt -= n2;
+                            // at most the rest of the bracket
+                            Flo = F2; cmax = cmin + __reduce_max_sync(0xffffffffu, emx); cmin = p2 + 1u;
+                            ncnt -= n1 + (unsigned)wpos;
                         }
                         if (keep) {
                             listed = true;
@@ -540,14 +623,17 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     if (it >= 8 && (it & 1)) {
                         mid = lo + ((hi - lo) >> 1);
                     } else {
-                        const float fr = __fdividef((float)(T - Flo), (float)(Fhi - Flo));
+                        const float fr = ratio64(T - Flo, Fhi - Flo);
                         unsigned off = (unsigned)(fr * (float)(hi - lo));
                         off = min(max(off, 1u), hi - lo - 1u);
                         mid = lo + off;
                     }
                     const bool wr = listed || ncnt <= (unsigned)CAPC;
                     // F at the pivot; the largest key at or below it and the smallest above it (the
-                    // other extreme of either half is the bracket's own, cmin or cmax)
+                    // other extreme of either half is the bracket's own, cmin or cmax).  Offsets
+                    // d = key - cmin: inside the bracket d <= span (keys below it wrap past span), in
+                    // the lower half d <= dm; d - (dm + 1) is smallest for the upper half's least key.
+                    const unsigned span = cmax - cmin, dm = mid - cmin, dm1 = dm + 1u;
                     unsigned long long fm = 0;
                     unsigned mxL = 0u, mnR = 0xffffffffu, cl = 0u;
                     int wpos = 0;
@@ -558,7 +644,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                         const int jj = v ? j : 0;
                         const unsigned kk = keys[jj];
                         const int e = v ? (listed ? (int)cidx[jj] : jj) : 0;
-                        const bool in = v && kk > lo && kk <= hi;
+                        const unsigned d = v ? kk - cmin : 0xffffffffu;
+                        const bool in = d <= span;
                         if (wr) {
                             // in-place compaction: every write lands at or before the position read
                             const unsigned bal = __ballot_sync(0xffffffffu, in);
@@ -570,12 +657,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                             wpos += __popc(bal);
                         }
                         const unsigned long long w = (unsigned long long)wk[e];
-                        const bool L = in && kk <= mid;
-                        const bool Rt = in && kk > mid;
-                        fm += L ? w : 0ull;
-                        mxL = max(mxL, L ? kk : 0u);
-                        mnR = min(mnR, Rt ? kk : 0xffffffffu);
-                        cl += L ? 1u : 0u;
+                        const bool L = d <= dm;
+                        if (L) { fm += w; ++cl; }
+                        mxL = max(mxL, L ? d : 0u);
+                        mnR = min(mnR, d - dm1);
                     }
                     __syncwarp();
                     if (wr) { listed = true; m = wpos; }
@@ -583,11 +668,11 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     const unsigned nl = __reduce_add_sync(0xffffffffu, cl);
                     if (Fm >= T) {
                         hi = mid; Fhi = Fm;
-                        cmax = __reduce_max_sync(0xffffffffu, mxL);  // cmin stays
+                        cmax = cmin + __reduce_max_sync(0xffffffffu, mxL);  // cmin stays
                         ncnt = nl;
                     } else {
                         lo = mid; Flo = Fm;
-                        cmin = __reduce_min_sync(0xffffffffu, mnR);  // cmax stays
+                        cmin = cmin + dm1 + __reduce_min_sync(0xffffffffu, mnR);  // cmax stays
                         ncnt -= nl;
                     }
                 }
@@ -665,15 +750,16 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
     float cst = c0;
-    double scale = (double)psc + fabs((double)c0);
+    // rounding bound in FP32 with every operation rounded up (all terms are non-negative)
+    float scale = __fadd_ru(psc, fabsf(c0));
 #pragma unroll
     for (int p = 0; p < RC; ++p) {
         if (WIDE && p >= R) break;
         cst = fmaf(bget(p), cc_hrow[p], cst);
-        scale += (double)bget(p) * (cc_Sg[p] + fabs((double)cc_hrow[p]));
+        scale = __fmaf_ru(bget(p), cc_SgH[p], scale);
     }
-    const double gam = (double)(R + (n0 + 31) / 32 + 12) * CV_U32;
-    const float pad = __double2float_ru(gam * scale * 1.0001);
+    const float gam = __fmul_ru((float)(R + (n0 + 31) / 32 + 12), 5.9611e-08f);  // >= 2^-24 * 1.0001
+    const float pad = __fmul_ru(__fmul_ru(gam, scale), 1.0001f);
     float val = __fsub_rd(__fadd_rd(part, cst), pad);
     const float valhi = __fadd_ru(__fadd_ru(part, cst), pad);
     if (val < 0.f && valhi >= 0.f && cur < 0.f) {
@@ -696,7 +782,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             if (WIDE && p >= R) break;
             d += (double)bget(p) * (double)cc_hrow[p];
         }
-        val = __double2float_rd(d - ldexp(scale, -40));
+        val = __double2float_rd(d - ldexp((double)scale, -40));
     }
     if (lane == 0) {
         if (side == 0) { if (val > a.l[o]) a.l[o] = val; }
@@ -757,6 +843,7 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
                 cc_W64[threadIdx.x] = a.wW[(size_t)b * Rs + threadIdx.x];
                 cc_hrow[threadIdx.x] = a.wh[(size_t)b * Rs + threadIdx.x];
                 cc_Sg[threadIdx.x] = a.wSg[(size_t)b * Rs + threadIdx.x];
+                cc_SgH[threadIdx.x] = __double2float_ru(cc_Sg[threadIdx.x] + fabs((double)cc_hrow[threadIdx.x]));
             }
             cur_b = b;
         }

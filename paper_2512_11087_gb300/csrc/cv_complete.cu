@@ -379,7 +379,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     return __fmul2_rn(x, *(const float2*)(rk + j));
                 };
                 const float2* ap2 = (const float2*)ap;
-                constexpr int P2 = 2;
+                constexpr int P2 = 1;  // pairs per lane per iteration (deeper unrolling spills)
                 if (warm) {
 #pragma unroll 1
                     for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
@@ -724,27 +724,60 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
     const float psc = __ldg(a.pscale + (side ? a.U + c : c));
     const float cur = side == 0 ? a.l[o] : -a.u[o];
     float part = 0.f;
+    if (!WIDE && (n0 & 1) == 0) {
+        // two adjacent elements per lane, packed FP32: each lane sums at most ceil(n0/64) terms per
+        // component and one more to combine them, within the ceil(n0/32) the rounding bound allows
+        const float2* ap2 = (const float2*)ap;
+        const float2* slo2 = (const float2*)slo;
+        const float2* shi2 = (const float2*)shi;
+        const float2 sa2 = make_float2(sa, sa);
+        float2 part2 = make_float2(0.f, 0.f);
 #pragma unroll 1
-    for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
-        float av[PF], lv[PF], hv[PF];
+        for (int j0 = 2 * lane; j0 < n0; j0 += 64 * 2) {
+            float2 av[2], lv[2], hv[2];
 #pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const int jj = min(j0 + 32 * u, n0 - 1);
-            const bool in = j0 + 32 * u < n0;
-            av[u] = __ldg(ap + jj);
-            lv[u] = in ? __ldg(slo + jj) : 0.f;
-            hv[u] = in ? __ldg(shi + jj) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const int jj = min(j0 + 32 * u, n0 - 1);
-            float v = sa * av[u];
-#pragma unroll
-            for (int p = 0; p < RC; ++p) {
-                if (WIDE && p >= R) break;
-                v = fmaf(bget(p), rw.gs[p * n0 + jj], v);
+            for (int u = 0; u < 2; ++u) {
+                const int jj = min(j0 + 64 * u, n0 - 2);
+                const bool in = j0 + 64 * u < n0;
+                av[u] = __ldg(ap2 + (jj >> 1));
+                lv[u] = in ? __ldg(slo2 + (jj >> 1)) : make_float2(0.f, 0.f);
+                hv[u] = in ? __ldg(shi2 + (jj >> 1)) : make_float2(0.f, 0.f);
             }
-            part += fminf(v * lv[u], v * hv[u]);  // 0 past n0 (lv = hv = 0)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int jj = min(j0 + 64 * u, n0 - 2);
+                float2 v = __fmul2_rn(av[u], sa2);
+#pragma unroll
+                for (int p = 0; p < (WIDE ? 1 : RC); ++p)
+                    v = __ffma2_rn(make_float2(bget(p), bget(p)), *(const float2*)(rw.gs + p * n0 + jj), v);
+                const float2 t1 = __fmul2_rn(v, lv[u]), t2 = __fmul2_rn(v, hv[u]);
+                part2 = __fadd2_rn(part2, make_float2(fminf(t1.x, t2.x), fminf(t1.y, t2.y)));
+            }
+        }
+        part = part2.x + part2.y;
+    } else {
+#pragma unroll 1
+        for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
+            float av[PF], lv[PF], hv[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int jj = min(j0 + 32 * u, n0 - 1);
+                const bool in = j0 + 32 * u < n0;
+                av[u] = __ldg(ap + jj);
+                lv[u] = in ? __ldg(slo + jj) : 0.f;
+                hv[u] = in ? __ldg(shi + jj) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int jj = min(j0 + 32 * u, n0 - 1);
+                float v = sa * av[u];
+#pragma unroll
+                for (int p = 0; p < RC; ++p) {
+                    if (WIDE && p >= R) break;
+                    v = fmaf(bget(p), rw.gs[p * n0 + jj], v);
+                }
+                part += fminf(v * lv[u], v * hv[u]);  // 0 past n0 (lv = hv = 0)
+            }
         }
     }
 #pragma unroll

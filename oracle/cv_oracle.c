@@ -380,6 +380,35 @@ int orc_relaxed_clip_sequential(int n, int R, const double* G, const double* h,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Constraint importance heuristic (Appendix, details of heuristics): for the  */
+/* box centre xhat, the distance of row k's hyperplane g.x + h = 0 is          */
+/*   d_k = |g_k.xhat + h_k| / ||g_k||_2   (+inf for a zero row),               */
+/* and the rows are taken in ascending d (equal distances keep their order).   */
+/* perm receives the row indices in that order.                                */
+/* ------------------------------------------------------------------------- */
+void orc_row_order(int n, int R, const double* G, const double* h, const double* lo,
+                   const double* hi, int* perm) {
+    double* d = (double*)malloc(sizeof(double) * (R > 0 ? R : 1));
+    for (int k = 0; k < R; ++k) {
+        const double* g = G + (long)k * n;
+        double s = h[k], nn = 0.0;
+        for (int j = 0; j < n; ++j) {
+            s += g[j] * 0.5 * (lo[j] + hi[j]);
+            nn += g[j] * g[j];
+        }
+        d[k] = nn > 0.0 ? fabs(s) / sqrt(nn) : INFINITY;
+        perm[k] = k;
+    }
+    /* insertion sort: stable */
+    for (int a = 1; a < R; ++a) {
+        int p = perm[a], b = a - 1;
+        while (b >= 0 && d[perm[b]] > d[p]) { perm[b + 1] = perm[b]; --b; }
+        perm[b + 1] = p;
+    }
+    free(d);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Algorithm 1 (coordinate ascent over several constraints), repeated for     */
 /* `sweeps` passes.  Minimises a.x + c over the box subject to G x + h <= 0   */
 /* through the dual  max_{beta>=0} (a + beta^T G).xhat - |a + beta^T G|.eps   */
@@ -554,7 +583,8 @@ double orc_dual_value(int n, const double* a, double c, int R, const double* G,
 /* cached constraints of Section 3.4):                                        */
 /*  a2 rows from splits (cached planes) + extra rows                         */
 /*  a3 pre-check on the input box                                             */
-/*  a4 relaxed clipping (Algorithm 2), box rounded outward to FP32            */
+/*  a4 relaxed clipping (Algorithm 2, or Algorithm 3 for relaxed = 2 / 3),    */
+/*     box rounded outward to FP32                                            */
 /*  a5 re-concretisation of every cached plane over the clipped box,          */
 /*     intersected with the inherited bounds; split signs enforced (standard */
 /*     activation BaB) unless enforce_splits = 0 (the paper's relaxed-clipping */
@@ -642,13 +672,29 @@ static void one_subdomain(const cache_t* cc, int b,
         }
     }
 
-    /* a4: relaxed clipping (parallel) on the input box, rounded outward */
+    /* a4: relaxed clipping on the input box, rounded outward: relaxed = 1 the   */
+    /* parallel Algorithm 2; 2 the sequential Algorithm 3 over the active rows in */
+    /* their order; 3 Algorithm 3 with the rows in the constraint-importance      */
+    /* order (distances from the input box centre).  Complete clipping keeps the  */
+    /* active rows in their own order either way.                                 */
     double* clo = lo_c + (long)b * n0;
     double* chi = hi_c + (long)b * n0;
     for (int i = 0; i < n0; ++i) { clo[i] = lo[i]; chi[i] = hi[i]; }
-    if (relaxed && !infeas) {
+    if (relaxed == 1 && !infeas) {
         for (int k = 0; k < Ra; ++k)
             orc_relaxed_clip_row(n0, G + (long)k * n0, h[k], lo, hi, clo, chi);
+    } else if ((relaxed == 2 || relaxed == 3) && !infeas && Ra > 0) {
+        int* perm = (int*)malloc(sizeof(int) * Ra);
+        double* Gs = (double*)malloc(sizeof(double) * (size_t)Ra * n0);
+        double* hs = (double*)malloc(sizeof(double) * Ra);
+        if (relaxed == 3) orc_row_order(n0, Ra, G, h, lo, hi, perm);
+        else for (int k = 0; k < Ra; ++k) perm[k] = k;
+        for (int k = 0; k < Ra; ++k) {
+            memcpy(Gs + (long)k * n0, G + (long)perm[k] * n0, sizeof(double) * n0);
+            hs[k] = h[perm[k]];
+        }
+        if (orc_relaxed_clip_sequential(n0, Ra, Gs, hs, lo, hi, clo, chi)) infeas = 1;
+        free(perm); free(Gs); free(hs);
     }
     for (int i = 0; i < n0; ++i) {
         clo[i] = rdown32(clo[i]);

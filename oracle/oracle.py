@@ -46,6 +46,8 @@ def _load():
         _lib.orc_relaxed_clip_parallel.restype = I
         _lib.orc_relaxed_clip_sequential.argtypes = [I, I, P, P, P, P, P, P]
         _lib.orc_relaxed_clip_sequential.restype = I
+        _lib.orc_row_order.argtypes = [I, I, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
+        _lib.orc_row_order.restype = None
         _lib.orc_complete_clip.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
         _lib.orc_complete_clip.restype = D
         _lib.orc_complete_clip_f32.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
@@ -197,6 +199,17 @@ def relaxed_clip(G, h, lo, hi, sequential=False):
     fn = lib.orc_relaxed_clip_sequential if sequential else lib.orc_relaxed_clip_parallel
     inf = fn(lo.size, G.shape[0], _p(G), _p(h), _p(lo), _p(hi), _p(lo2), _p(hi2))
     return lo2, hi2, bool(inf)
+
+
+def row_order(G, h, lo, hi):
+    """Constraint importance heuristic (Appendix, details of heuristics): the row indices in
+    ascending distance |g.xhat + h| / ||g||_2 of their hyperplanes from the box centre (stable)."""
+    lib = _load()
+    G, h, lo, hi = _f64(np.atleast_2d(G)), _f64(np.atleast_1d(h)), _f64(lo), _f64(hi)
+    R = G.shape[0]
+    perm = np.zeros(max(R, 1), np.int32)
+    lib.orc_row_order(lo.size, R, _p(G), _p(h), _p(lo), _p(hi), perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return perm[:R]
 
 
 def complete_clip(a, c, G, h, lo, hi, sweeps):

@@ -3,8 +3,11 @@
 Pins: Lemma A.1 (box extremes at vertices), Theorem 1 (one-row complete clipping
 is the exact LP optimum; equals the fractional-knapsack greedy), Theorem 2
 (one-row relaxed clipping is component-wise tight), weak duality and monotone
-ascent for Algorithm 1 with several rows, the a-priori infeasibility test, and
-the order-dependency example of the Appendix (Algorithm 3 vs Algorithm 2)."""
+ascent for Algorithm 1 with several rows, the a-priori infeasibility test, the
+order-dependency example of the Appendix (Algorithm 3 vs Algorithm 2), the constraint
+importance order (hyperplane distances by least squares), and the batch round's relaxed
+modes (parallel, sequential, sequential in importance order) on a hand-derived example and
+against sampled feasible points."""
 import itertools
 
 import numpy as np
@@ -183,3 +186,104 @@ def test_fp32_decision_variant_multi_row():
         assert O.dual_value(a, c, G, h, lo, hi, b32.astype(np.float64)) == pytest.approx(v32, abs=1e-12 * sc)
         agree += abs(v32 - v64) <= 1e-6 * sc
     assert agree >= 55  # the FP64 and FP32-decision ascents end at the same point except near kinks
+
+
+def test_row_order_is_ascending_hyperplane_distance():
+    # Constraint importance heuristic (Appendix, details of heuristics): rows ascend in the
+    # distance of their hyperplane from the box centre.  The distance is measured here as the
+    # length of the least-norm correction that moves the centre onto the hyperplane
+    # (np.linalg.lstsq), not by the closed form the oracle uses.
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        n = int(rng.integers(2, 9))
+        R = int(rng.integers(1, 7))
+        lo, hi = rand_box(rng, n)
+        xh = (lo + hi) / 2
+        G = rng.normal(size=(R, n))
+        h = rng.normal(size=R) * 2.0
+        if R >= 3:
+            G[2], h[2] = G[0], h[0]          # an exact tie: stays after row 0
+        perm = O.row_order(G, h, lo, hi)
+        dist = []
+        for k in range(R):
+            y, *_ = np.linalg.lstsq(G[k][None, :], np.array([-h[k] - G[k] @ xh]), rcond=None)
+            dist.append(np.linalg.norm(y))
+        d = np.array(dist)[perm]
+        assert sorted(perm.tolist()) == list(range(R))
+        assert np.all(np.diff(d) >= -1e-12 * (1 + d[1:]))
+        if R >= 3:
+            assert perm.tolist().index(0) < perm.tolist().index(2)
+    # a zero row has no hyperplane: it goes last
+    G = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    perm = O.row_order(G, [1.0, -5.0, -0.5], [0.0, 0.0], [1.0, 1.0])
+    assert perm.tolist() == [2, 1, 0]
+
+
+def _two_input_round(relaxed):
+    # A 2-input ReLU net and two extra rows on the box [0,2] x [0,3]:
+    #   F1: x1 + x2 - 2 <= 0,   F2: -x2 + 1.4 <= 0.
+    # Theorem 2 by hand.  Parallel (Algorithm 2, both rows on the input box): F1 gives
+    # hi1 = 2 - lo2 = 2, hi2 = 2 - lo1 = 2; F2 gives lo2 = 1.4: box [0,2] x [1.4,2].
+    # Sequential in row order (F1 then F2): F1 -> [0,2] x [0,2], F2 -> [0,2] x [1.4,2].
+    # Sequential in the constraint-importance order: the centre (1, 1.5) lies at
+    # |1 + 1.5 - 2| / sqrt(2) = 0.354 from F1 and |-1.5 + 1.4| = 0.1 from F2, so F2 first:
+    # [0,2] x [1.4,3], then F1: hi1 = 2 - 1.4 = 0.6, hi2 = 2 - 0 = 2 -> [0,0.6] x [1.4,2].
+    from paper_2512_11087_gb300 import workloads as WL
+    net = O.Net(WL.he_mlp([2, 4, 1], seed=0))
+    lo, hi = np.array([0.0, 0.0]), np.array([2.0, 3.0])
+    cache = O.make_cache(O.root_crown(net, lo, hi))
+    G = np.array([[1.0, 1.0], [0.0, -1.0]])
+    h = np.array([-2.0, 1.4])
+    out = O.bound_batch(net, cache, lo[None], hi[None], row_off=np.array([0, 2], np.int32), G=G, h=h,
+                        C=np.ones((1, 1)), t=np.zeros(1), relaxed=relaxed, sweeps=0)
+    return out["lo_clip"][0], out["hi_clip"][0], out["infeasible"][0]
+
+
+@pytest.mark.parametrize("relaxed,want_lo,want_hi", [
+    (1, [0.0, 1.4], [2.0, 2.0]),
+    (2, [0.0, 1.4], [2.0, 2.0]),
+    (3, [0.0, 1.4], [0.6, 2.0]),
+])
+def test_round_relaxed_modes_on_hand_example(relaxed, want_lo, want_hi):
+    lo, hi, inf = _two_input_round(relaxed)
+    assert not inf
+    # the box is stored in FP32, rounded outward: within one FP32 step outside the exact value
+    for got, want, up in [(lo, want_lo, False), (hi, want_hi, True)]:
+        for g, w in zip(got, want):
+            step = float(np.spacing(np.float32(w)))
+            if up:
+                assert w <= g <= w + step
+            else:
+                assert w - step <= g <= w
+
+
+def test_round_sequential_modes_tighter_than_parallel_and_sound():
+    # Algorithm 3 clips each row against the box the earlier rows left, so its box lies
+    # inside Algorithm 2's; both contain every feasible point (sampled).
+    from paper_2512_11087_gb300 import workloads as WL
+    rng = np.random.default_rng(12)
+    net = O.Net(WL.he_mlp([4, 8, 8, 2], seed=3))
+    lo0, hi0 = np.full(4, -1.0), np.full(4, 1.0)
+    cache = O.make_cache(O.root_crown(net, lo0, hi0))
+    B = 12
+    lo, hi = np.tile(lo0, (B, 1)), np.tile(hi0, (B, 1))
+    row_off, G, h = WL.random_cut_rows(lo, hi, B, 1, 4, seed=5)
+    boxes = {}
+    for mode in (1, 2, 3):
+        o = O.bound_batch(net, cache, lo, hi, row_off=row_off, G=G, h=h, C=np.ones((1, 2)), t=np.zeros(1),
+                          relaxed=mode, sweeps=0)
+        boxes[mode] = (o["lo_clip"], o["hi_clip"], o["infeasible"])
+    X = rng.uniform(-1, 1, size=(20000, 4))
+    for b in range(B):
+        rows = slice(row_off[b], row_off[b + 1])
+        feas = np.all(X @ G[rows].T + h[rows] <= 0, axis=1)
+        for mode in (1, 2, 3):
+            l, u, inf = boxes[mode][0][b], boxes[mode][1][b], boxes[mode][2][b]
+            if inf:
+                assert not feas.any()
+                continue
+            assert np.all(X[feas] >= l - 1e-12) and np.all(X[feas] <= u + 1e-12)
+        if not boxes[1][2][b]:
+            for mode in (2, 3):
+                if not boxes[mode][2][b]:
+                    assert np.all(boxes[mode][0][b] >= boxes[1][0][b]) and np.all(boxes[mode][1][b] <= boxes[1][1][b])

@@ -31,8 +31,13 @@ def workload_desc(cfg, name=CONFIG):
     d = cfg["dims"]
     return (f"{name}: ReLU MLP {d[0]}->{d[1]}x{len(d) - 2}->{d[-1]} He-normal seed 0; box eps={cfg['eps']} around "
             f"U[0,1]^{d[0]} clipped to [0,1]; B={cfg['B']} subdomains with {cfg['kmin']}-{cfg['kmax']} ReLU split "
-            f"constraints each; 9 margin spec rows; relaxed clipping + complete clipping ({cfg['sweeps']} sweeps) "
-            f"on every still-unstable cached neuron")
+            f"constraints each; 9 margin spec rows; {RELAXED_DESC[cfg['relaxed']]} + complete clipping "
+            f"({cfg['sweeps']} sweeps) on every still-unstable cached neuron")
+
+
+RELAXED_DESC = {0: "no relaxed clipping", 1: "relaxed clipping",
+                2: "sequential relaxed clipping (Algorithm 3)",
+                3: "sequential relaxed clipping in the constraint-importance order"}
 
 
 def parse_args():
@@ -45,6 +50,9 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--config", default=CONFIG, choices=["mlp784x256", "mlp784x512x8"],
                    help="workload (default: the metric's workload; mlp784x512x8 is the BaB stress shape)")
+    p.add_argument("--relaxed", type=int, default=None, choices=[1, 2, 3],
+                   help="relaxed clipping: 1 parallel (Algorithm 2, the workload's), 2 sequential (Algorithm 3), "
+                        "3 sequential in the constraint-importance order")
     p.add_argument("--subdomains", type=int, default=0,
                    help="smaller batch for profiler captures (default: the workload's own batch)")
     return p.parse_args()
@@ -182,6 +190,8 @@ def main():
     cfg = WL.CONFIGS[args.config]
     if args.subdomains > 0:
         cfg = dict(cfg, B=args.subdomains)
+    if args.relaxed is not None:
+        cfg = dict(cfg, relaxed=args.relaxed)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -153,8 +153,27 @@ cv_status cv_timer_read(cv_timer* timer, float* ms, int* launches, long long* cc
 
 /* ---------------------------------------------------------------- one BaB round */
 
+/* Relaxed clipping of the input box (cv_options.relaxed), all with Theorem 2 per coordinate:
+ *  CV_RELAX_OFF                 none (the box is copied; the pre-check still runs)
+ *  CV_RELAX_PARALLEL            Algorithm 2: every active row against the input box
+ *  CV_RELAX_SEQUENTIAL          Algorithm 3 (Appendix, sequential clipping): the active rows one
+ *                               at a time, each against the box the earlier ones left, the
+ *                               pre-check repeated on that box (an infeasible row or an emptied
+ *                               box ends the subdomain, a redundant row is skipped); rows in their
+ *                               order (splits, then extra rows)
+ *  CV_RELAX_SEQUENTIAL_ORDERED  Algorithm 3 with the rows in the constraint-importance order of
+ *                               the Appendix's heuristics: ascending |g.xhat + h| / ||g||_2 on the
+ *                               input box, equal distances in row order
+ * Complete clipping uses the active rows in their own order whatever the mode.  The sequential
+ * modes keep the box in shared memory: 16 n_0 + 12 (max_splits + max_rows) bytes must stay
+ * within 220 KiB (else CV_EUNSUPPORTED).  Other values are refused (CV_EINVAL). */
+#define CV_RELAX_OFF 0
+#define CV_RELAX_PARALLEL 1
+#define CV_RELAX_SEQUENTIAL 2
+#define CV_RELAX_SEQUENTIAL_ORDERED 3
+
 typedef struct cv_options {
-    int relaxed;        /* 1: relaxed clipping of the input box (Theorem 2, Algorithm 2) */
+    int relaxed;        /* CV_RELAX_*: relaxed clipping of the input box (Theorem 2) */
     int sweeps;         /* complete clipping passes of Algorithm 1 (0: off) */
     int precision;      /* CV_PREC_* */
     int alpha_mode;     /* CV_ALPHA_*; ignored where batch.alpha is given */

@@ -20,6 +20,10 @@ CV_LAYER_DENSE = 0
 CV_LAYER_CONV2D = 1
 CV_PREC_FP32 = 0
 CV_PREC_BF16X8 = 1
+CV_RELAX_OFF = 0
+CV_RELAX_PARALLEL = 1
+CV_RELAX_SEQUENTIAL = 2
+CV_RELAX_SEQUENTIAL_ORDERED = 3
 CV_ALPHA_ADAPTIVE = 0
 CV_ALPHA_ONE = 1
 CV_ALPHA_ZERO = 2

@@ -69,7 +69,8 @@ static cv_status validate(const cv_net* net, const cv_cache* cache, const cv_bat
         cv_set_error("negative B, m, max_splits or max_rows");
         return CV_EINVAL;
     }
-    if (opt->sweeps < 0 || opt->alpha_mode < 0 || opt->alpha_mode > 2 ||
+    if (opt->relaxed < CV_RELAX_OFF || opt->relaxed > CV_RELAX_SEQUENTIAL_ORDERED || opt->sweeps < 0 ||
+        opt->alpha_mode < 0 || opt->alpha_mode > 2 ||
         (opt->precision != CV_PREC_FP32 && opt->precision != CV_PREC_BF16X8)) {
         cv_set_error("bad options");
         return CV_EINVAL;

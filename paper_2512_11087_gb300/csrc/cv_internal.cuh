@@ -12,6 +12,8 @@
 void cv_set_error(const std::string& msg);
 cv_status cv_cuda_fail(cudaError_t e, const char* what);
 
+#define CV_SEQ_SMEM_MAX (220 * 1024)  // dynamic shared memory of sequential relaxed clipping
+
 #define CV_CUDA(call)                                                   \
     do {                                                                \
         cudaError_t e_ = (call);                                        \

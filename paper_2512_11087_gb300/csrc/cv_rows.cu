@@ -11,9 +11,16 @@
 //     g_i > 0: hi_i <- min(hi_i, lo_i - v_min/g_i);  g_i < 0: lo_i <- max(lo_i, hi_i - v_min/g_i),
 //     evaluated in FP64 with v_min replaced by its certified lower bound and the result rounded
 //     outward to FP32.
+//     Sequential variant (Algorithm 3, Appendix "Sequential Clipping"): the active rows one at a
+//     time, each on the box the earlier rows left (kept in FP64 in shared memory), with the
+//     pre-check repeated on that box (stop when a row is infeasible or the box empties, skip a
+//     redundant row); optionally in the constraint-importance order of the Appendix's heuristics
+//     (ascending |g.xhat + h| / ||g||_2 on the input box, equal distances in row order).
 #include "cv_internal.cuh"
 
 #include <math.h>
+
+#include <string>
 
 namespace {
 
@@ -168,6 +175,134 @@ __global__ void k_relaxed(cv_cache cc, cv_batch_in in, int Rmax, int relaxed, co
     if (threadIdx.x == 0 && any_empty) infeasible[b] = 1;
 }
 
+// Warp then block sum of NV doubles per thread; every thread returns the same totals (warps added
+// in a fixed order).  `red` holds NV x (blockDim.x / 32) doubles; the caller separates uses with a
+// barrier.
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[q * nw + warp] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += red[q * nw + w];
+        v[q] = t;
+    }
+}
+
+// Algorithm 3: one block per subdomain, threads over coordinates; shared memory holds the
+// current box [2 x n0] in FP64, then the row order [Rmax] and distances [Rmax].
+__global__ void k_relaxed_seq(cv_cache cc, cv_batch_in in, int Rmax, int ordered, const int8_t* rowflag,
+                              float* lo_clip, float* hi_clip, uint8_t* infeasible, int* status) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    __shared__ double red[3 * 32];
+    __shared__ int s_empty, s_nact;
+    const int b = blockIdx.x;
+    const int n0 = cc.n0;
+    double* cl = (double*)rs_smem;
+    double* ch = cl + n0;
+    double* dist = ch + n0;
+    int* ord = (int*)(dist + Rmax);
+    const float* lo = in.lo + (size_t)b * n0;
+    const float* hi = in.hi + (size_t)b * n0;
+    const bool inf0 = infeasible[b] != 0;
+    if (threadIdx.x == 0) {
+        s_empty = 0;
+        int a = 0;
+        for (int k = 0; k < Rmax; ++k)
+            if (rowflag[(size_t)b * Rmax + k] == 0) ord[a++] = k;
+        s_nact = a;
+    }
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        cl[i] = (double)lo[i];
+        ch[i] = (double)hi[i];
+        if (!isfinite(cl[i]) || !isfinite(ch[i])) atomicOr(status, CV_DEV_NONFINITE);
+    }
+    __syncthreads();
+    const int nact = inf0 ? 0 : s_nact;
+    bool dummy = false;
+    if (ordered && nact > 1) {
+        // distances of the active rows' hyperplanes from the input box centre
+        for (int a = 0; a < nact; ++a) {
+            const RowRef r = row_ref(cc, in, b, ord[a], status, &dummy);
+            double v[2] = {0.0, 0.0};
+            for (int j = threadIdx.x; j < n0; j += blockDim.x) {
+                const double g = (double)(r.sign * r.g[j]);
+                v[0] += g * (0.5 * (cl[j] + ch[j]));
+                v[1] += g * g;
+            }
+            block_sums<2>(v, red);
+            if (threadIdx.x == 0) dist[a] = v[1] > 0.0 ? fabs(v[0] + (double)r.h) / sqrt(v[1]) : INFINITY;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {  // stable insertion sort of (distance, row)
+            for (int a = 1; a < nact; ++a) {
+                const double d = dist[a];
+                const int k = ord[a];
+                int c = a - 1;
+                while (c >= 0 && dist[c] > d) { dist[c + 1] = dist[c]; ord[c + 1] = ord[c]; --c; }
+                dist[c + 1] = d;
+                ord[c + 1] = k;
+            }
+        }
+        __syncthreads();
+    }
+    bool stop = false;
+    for (int a = 0; a < nact && !stop; ++a) {
+        const RowRef r = row_ref(cc, in, b, ord[a], status, &dummy);
+        // pre-check of the row on the current box (the certified minimum, as in k_rows)
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int j = threadIdx.x; j < n0; j += blockDim.x) {
+            const double g = (double)(r.sign * r.g[j]);
+            const double p = g * cl[j], q = g * ch[j];
+            v[0] += fmin(p, q);
+            v[1] += fmax(p, q);
+            v[2] += fmax(fabs(p), fabs(q));
+        }
+        block_sums<3>(v, red);
+        const double h = (double)r.h;
+        const double vmin = v[0] + h, vmax = v[1] + h;
+        const double vlo = vmin - ldexp(v[2] + fabs(h), -40);
+        if (vlo > 0.0) {  // infeasible on the current box: the subdomain is empty
+            stop = true;
+            if (threadIdx.x == 0) infeasible[b] = 1;
+        } else if (vmax > 0.0) {  // not redundant: Theorem 2 on the current box
+            for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+                const double g = (double)(r.sign * r.g[i]);
+                if (g == 0.0) continue;
+                const double t = -vlo / g;
+                if (g > 0.0) {
+                    double c = cl[i] + t;
+                    c += ldexp(fabs(cl[i]) + fabs(t), -50);
+                    if (c < ch[i]) ch[i] = c;
+                } else {
+                    double c = ch[i] + t;
+                    c -= ldexp(fabs(ch[i]) + fabs(t), -50);
+                    if (c > cl[i]) cl[i] = c;
+                }
+                if (cl[i] > ch[i]) s_empty = 1;
+            }
+        }
+        __syncthreads();
+        if (s_empty) stop = true;
+    }
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        const float fl = __double2float_rd(cl[i]), fh = __double2float_ru(ch[i]);
+        lo_clip[(size_t)b * n0 + i] = fl;
+        hi_clip[(size_t)b * n0 + i] = fh;
+        if (fl > fh) s_empty = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_empty) infeasible[b] = 1;
+}
+
 }  // namespace
 
 cv_status cv_launch_rows(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
@@ -185,7 +320,23 @@ cv_status cv_launch_relaxed(const cv_net* net, const cv_cache* cache, const cv_b
                             const cv_options* opt, const cv_ws_layout* lay, char* ws,
                             float* lo_clip, float* hi_clip, uint8_t* infeasible, cudaStream_t st) {
     (void)net;
-    k_relaxed<<<in->B, 256, 0, st>>>(*cache, *in, lay->Rmax, opt->relaxed && lay->Rmax > 0,
+    if ((opt->relaxed == CV_RELAX_SEQUENTIAL || opt->relaxed == CV_RELAX_SEQUENTIAL_ORDERED) && lay->Rmax > 0 &&
+        in->B > 0) {
+        const size_t smem = (size_t)cache->n0 * 16 + (size_t)lay->Rmax * 12;
+        if (smem > CV_SEQ_SMEM_MAX) {
+            cv_set_error("sequential relaxed clipping keeps the box in shared memory: 16 n0 + 12 (max_splits + "
+                         "max_rows) must stay within " + std::to_string((size_t)CV_SEQ_SMEM_MAX) + " bytes");
+            return CV_EUNSUPPORTED;
+        }
+        CV_CUDA(cudaFuncSetAttribute(k_relaxed_seq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_relaxed_seq<<<in->B, 256, smem, st>>>(*cache, *in, lay->Rmax,
+                                                opt->relaxed == CV_RELAX_SEQUENTIAL_ORDERED,
+                                                (const int8_t*)(ws + lay->rowflag), lo_clip, hi_clip, infeasible,
+                                                cache->net->status);
+        CV_LAUNCH_CHECK("k_relaxed_seq");
+        return CV_OK;
+    }
+    k_relaxed<<<in->B, 256, 0, st>>>(*cache, *in, lay->Rmax, opt->relaxed == CV_RELAX_PARALLEL && lay->Rmax > 0,
                                      (const int8_t*)(ws + lay->rowflag), (const double*)(ws + lay->vmin),
                                      lo_clip, hi_clip, infeasible, cache->net->status);
     CV_LAUNCH_CHECK("k_relaxed");

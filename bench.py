@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--relaxed", type=int, default=None, choices=[1, 2, 3],
                    help="relaxed clipping: 1 parallel (Algorithm 2, the workload's), 2 sequential (Algorithm 3), "
                         "3 sequential in the constraint-importance order")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep complete clipping's default work-item sizes instead of tuning them first")
     p.add_argument("--subdomains", type=int, default=0,
                    help="smaller batch for profiler captures (default: the workload's own batch)")
     return p.parse_args()
@@ -235,6 +237,13 @@ def main():
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    # complete clipping's work-item sizes, tuned on this batch before anything is timed
+    items_tuned = cfg["sweeps"] > 0 and not args.no_autotune
+    if items_tuned:
+        items, _ = rnd.autotune(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
+    else:
+        items = capi.cv_cc_items_get(net.cache)
+    torch.cuda.synchronize()
 
     clocks = Clocks(local)
     if rank == 0:
@@ -334,6 +343,7 @@ def main():
                     dtype="f32" if args.precision == "fp32" else "bf16x8+f32", data="synthetic",
                     config=dict(workload=workload_desc(cfg, args.config), precision=args.precision, cached_neurons=U,
                                 l2="flushed (256 MiB write) before every timed step",
+                                cc_items=dict(sizes=items, tuned=items_tuned),
                                 phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
                                                   [round(x, 4) for x in ph_mean]))),
                     roofline=dict(bound="alu", kernel="k_complete", achieved=achieved, peak=peak, unit="Gop/s",

@@ -258,6 +258,33 @@ cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* 
                          cv_batch_out* out, const cv_options* opt,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- scheduler tuning */
+
+/* Complete clipping runs as one persistent launch over uneven work: each subdomain's
+ * (target, side) tasks are cut into work items that thread blocks take from an atomic ticket
+ * (the paper's Algorithm 1 per task; the split into items is this library's scheduling, with
+ * no counterpart in the paper).  items[c] is the number of tasks per item for subdomains with
+ * c + 1 active rows (c = 2: three or more).  The item size changes no result, only the time.
+ * A cache starts with CV_CC_ITEMS_1/2/3.  cv_cc_items_set: each value in [1, 4096] (else
+ * CV_EINVAL); it affects later rounds and graph captures that use the cache. */
+#define CV_CC_ITEMS_1 256
+#define CV_CC_ITEMS_2 64
+#define CV_CC_ITEMS_3 16
+cv_status cv_cc_items_set(cv_cache* cache, const int items[3]);
+cv_status cv_cc_items_get(const cv_cache* cache, int items[3]);
+
+/* Autotuner of the item sizes for a batch: runs cv_bound_batch on (in, out, opt, workspace)
+ * repeatedly on `stream` and times its complete-clipping phase with CUDA events: one row class
+ * at a time, the candidates 128/256/512 (one row), 32/64/128 (two), 8/16/32/64 (three or more),
+ * each round twice, the faster time counting; the fastest sizes stay in the cache.
+ * best (may be NULL) receives them, best_ms (may be NULL) their phase time in milliseconds.
+ * Host-synchronous (it reads the events), so it cannot be captured in a CUDA graph; `out`
+ * holds the last round's results.  opt->sweeps must be > 0 (else CV_EINVAL: nothing to tune);
+ * opt->timer is ignored. */
+cv_status cv_autotune_cc(cv_net* net, cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                         const cv_options* opt, void* workspace, size_t workspace_bytes, void* stream,
+                         int best[3], float* best_ms);
+
 /* ---------------------------------------------------------------- CUDA graph of a round */
 
 /* A captured, instantiated CUDA graph of one cv_bound_batch call.  Replays run the same round

@@ -103,6 +103,9 @@ def load():
         "cv_alpha_grad": ([P, P, P, P, P, P, ctypes.c_size_t, P], I),
         "cv_alpha_adam": ([P, P, P, P, ctypes.c_longlong, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, P], I),
+        "cv_cc_items_set": ([P, P], I),
+        "cv_cc_items_get": ([P, P], I),
+        "cv_autotune_cc": ([P, P, P, P, P, P, ctypes.c_size_t, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -117,7 +120,8 @@ def exported_symbols():
                         "cv_cache_build", "cv_cache_create", "cv_cache_size", "cv_cache_read", "cv_cache_destroy",
                         "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
                         "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
-                        "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy")]
+                        "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy",
+                        "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc")]
 
 
 def _check(st):
@@ -282,6 +286,31 @@ def cv_timer_read(t):
     steps = ctypes.c_longlong()
     _check(load().cv_timer_read(t, ctypes.cast(ms, P), ctypes.byref(n), ctypes.byref(steps)))
     return list(ms), n.value, steps.value
+
+
+CC_ITEMS_DEFAULT = (256, 64, 16)
+
+
+def cv_cc_items_set(cache, items):
+    arr = (ctypes.c_int * 3)(*[int(v) for v in items])
+    _check(load().cv_cc_items_set(cache, ctypes.cast(arr, P)))
+
+
+def cv_cc_items_get(cache):
+    arr = (ctypes.c_int * 3)()
+    _check(load().cv_cc_items_get(cache, ctypes.cast(arr, P)))
+    return list(arr)
+
+
+def cv_autotune_cc(net, cache, bi, bo, opt, workspace, workspace_bytes, stream=None):
+    """Times complete clipping of this batch over the item-size grid; keeps the fastest sizes in
+    the cache and returns (sizes, their phase time in ms)."""
+    best = (ctypes.c_int * 3)()
+    ms = ctypes.c_float()
+    _check(load().cv_autotune_cc(net, cache, ctypes.byref(bi), ctypes.byref(bo), ctypes.byref(opt),
+                                 ptr(workspace), int(workspace_bytes), stream_ptr(stream), ctypes.cast(best, P),
+                                 ctypes.byref(ms)))
+    return list(best), ms.value
 
 
 def cv_relaxed_clip_static(net, cache, bi, lo_clip, hi_clip, infeasible, relaxed=1, stream=None):

@@ -271,3 +271,75 @@ extern "C" void cv_graph_destroy(cv_graph* graph) {
     cudaGraphDestroy(graph->graph);
     delete graph;
 }
+
+// ---------------------------------------------------------------- scheduler tuning
+
+extern "C" cv_status cv_cc_items_set(cv_cache* cache, const int items[3]) {
+    if (!cache || !items) { cv_set_error("cv_cc_items_set: null argument"); return CV_EINVAL; }
+    for (int c = 0; c < 3; ++c)
+        if (items[c] < 1 || items[c] > 4096) {
+            cv_set_error("cv_cc_items_set: tasks per item must lie in [1, 4096]");
+            return CV_EINVAL;
+        }
+    for (int c = 0; c < 3; ++c) cache->cc_items[c] = items[c];
+    return CV_OK;
+}
+
+extern "C" cv_status cv_cc_items_get(const cv_cache* cache, int items[3]) {
+    if (!cache || !items) { cv_set_error("cv_cc_items_get: null argument"); return CV_EINVAL; }
+    for (int c = 0; c < 3; ++c) items[c] = cache->cc_items[c];
+    return CV_OK;
+}
+
+extern "C" cv_status cv_autotune_cc(cv_net* net, cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                                    const cv_options* opt, void* workspace, size_t workspace_bytes, void* stream,
+                                    int best[3], float* best_ms) {
+    if (!net || !cache || !in || !out || !opt) { cv_set_error("cv_autotune_cc: null argument"); return CV_EINVAL; }
+    if (opt->sweeps <= 0) { cv_set_error("cv_autotune_cc: sweeps = 0, no complete clipping to tune"); return CV_EINVAL; }
+    static const int cand[3][4] = {{128, 256, 512, 0}, {32, 64, 128, 0}, {8, 16, 32, 64}};
+    cv_timer* timer = nullptr;
+    cv_status s = cv_timer_create(&timer);
+    if (s) return s;
+    cv_options o = *opt;
+    o.timer = timer;
+    int cur[3], keep[3], orig[3];
+    for (int c = 0; c < 3; ++c) cur[c] = keep[c] = orig[c] = cache->cc_items[c];
+    float best_t = 0.f;
+    bool have = false;
+    // time one setting: the faster of two rounds
+    auto time_it = [&](const int it[3], float* t) -> cv_status {
+        for (int c = 0; c < 3; ++c) cache->cc_items[c] = it[c];
+        float tb = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cv_status e = cv_bound_batch(net, cache, in, out, &o, workspace, workspace_bytes, stream);
+            if (e) return e;
+            float ms[CV_N_PHASES];
+            if ((e = cv_timer_read(timer, ms, nullptr, nullptr))) return e;
+            if (rep == 0 || ms[2] < tb) tb = ms[2];
+        }
+        *t = tb;
+        return CV_OK;
+    };
+    float t0 = 0.f;
+    s = time_it(cur, &t0);  // the first rounds also warm the caches and the code
+    if (!s) s = time_it(cur, &t0);
+    if (!s) { best_t = t0; have = true; }
+    for (int c = 0; c < 3 && !s; ++c) {
+        for (int i = 0; i < 4 && !s; ++i) {
+            const int v = cand[c][i];
+            if (v == 0 || v == cur[c]) continue;
+            int trial[3] = {cur[0], cur[1], cur[2]};
+            trial[c] = v;
+            float t = 0.f;
+            s = time_it(trial, &t);
+            if (!s && t < best_t) { best_t = t; for (int q = 0; q < 3; ++q) keep[q] = trial[q]; }
+        }
+        for (int q = 0; q < 3; ++q) cur[q] = keep[q];
+    }
+    cv_timer_destroy(timer);
+    for (int c = 0; c < 3; ++c) cache->cc_items[c] = s ? orig[c] : keep[c];  // unchanged on an error
+    if (s) return s;
+    if (best) for (int c = 0; c < 3; ++c) best[c] = keep[c];
+    if (best_ms) *best_ms = have ? best_t : 0.f;
+    return CV_OK;
+}

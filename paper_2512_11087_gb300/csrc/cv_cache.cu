@@ -296,6 +296,9 @@ static cv_status new_cache(cv_net* net, cv_cache** out) {
     cv_cache* c = new cv_cache();
     memset(c, 0, sizeof(*c));
     c->net = net;
+    c->cc_items[0] = CV_CC_ITEMS_1;
+    c->cc_items[1] = CV_CC_ITEMS_2;
+    c->cc_items[2] = CV_CC_ITEMS_3;
     c->n0 = net->dims[0];
     c->H = net->H;
     *out = c;

@@ -29,14 +29,15 @@
 //
 // GB300 mapping (persistent scheduling of uneven work): k_cc_prep writes each subdomain's active
 // rows (g, 1/g, fixed-point weights, threshold, total weight) to the workspace once; a
-// single-block scan turns the per-subdomain task counts into work items (256 (target, side)
-// tasks for one row, 64 for two, 16 for more: longer tasks, smaller items), subdomains with more
-// rows first; a persistent k_complete grid (two blocks of 16 warps per SM) takes items from an
-// atomic ticket, stages the item's rows in shared memory, and its warps take the item's tasks one
-// at a time from a shared counter.  The task body is compiled for each row count (multipliers in
-// registers); subdomains with more than four rows run in a separate launch of one block per SM
-// (more registers).  Each warp keeps its breakpoint keys in its own shared buffer and loads the
-// target's coefficients four per lane ahead, so the element loops stay short and rolled.
+// single-block scan turns the per-subdomain task counts into work items (by default 256 (target,
+// side) tasks for one row, 64 for two, 16 for more: longer tasks, smaller items; the cache holds
+// the sizes, which cv_cc_items_set and the autotuner change), subdomains with more rows first; a
+// persistent k_complete grid (two blocks of 16 warps per SM) takes items from an atomic ticket,
+// stages the item's rows in shared memory, and its warps take the item's tasks one at a time from
+// a shared counter.  The task body is compiled for each row count (multipliers in registers);
+// subdomains with more than four rows run in a separate launch of one block per SM (more
+// registers).  Each warp keeps its breakpoint keys in its own shared buffer; for even n0 the main
+// launch's element loops take two adjacent coefficients per lane with packed FP32 arithmetic.
 #include "cv_internal.cuh"
 
 #include <climits>
@@ -47,7 +48,6 @@ namespace {
 constexpr int RMAX_CC = 32;  // rows per subdomain handled by complete clipping
 constexpr int RTPL = 4;     // row counts up to this run in the main launch (two blocks per SM)
 // (target, side) tasks per work item: fewer for subdomains with more rows (longer tasks)
-__host__ __device__ __forceinline__ int tpi_of(int R) { return R <= 1 ? 256 : (R == 2 ? 64 : 16); }
 constexpr int NWARP = 16;   // warps per block at most
 constexpr int CAPC = 384;   // breakpoints a warp's compacted list holds
 constexpr int SAMP_MIN = 64;     // brackets with more breakpoints start from sampled pivots
@@ -75,6 +75,7 @@ __device__ __forceinline__ float ratio64(long long n, long long d) {
 
 struct CCArgs {
     int B, U, n0, H, Rmax, Rs, sweeps;
+    int tpi[3];  // tasks per work item for subdomains with 1, 2 and more active rows
     const int8_t* rowflag;
     const float* lA; const float* lc; const float* uA; const float* uc;
     const int* slot_of; const float* pscale;
@@ -98,6 +99,8 @@ struct CCArgs {
     unsigned* ticket;                        // [2] item tickets: wide items, the rest
 };
 
+__device__ __forceinline__ int tpi_of(const CCArgs& a, int R) { return a.tpi[R <= 1 ? 0 : (R == 2 ? 1 : 2)]; }
+
 __device__ __forceinline__ int ntargets(const CCArgs& a, int b) {
     return a.tgt_off ? a.tgt_off[b + 1] - a.tgt_off[b] : a.U;
 }
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
                 if (a.rowflag[(size_t)b * a.Rmax + k] == 0) rowsel[r++] = k;
         R = r;
         a.wR[b] = r;
-        a.wcnt[b] = r > 0 ? (2 * ntargets(a, b) + tpi_of(r) - 1) / tpi_of(r) : 0;
+        a.wcnt[b] = r > 0 ? (2 * ntargets(a, b) + tpi_of(a, r) - 1) / tpi_of(a, r) : 0;
     }
     __syncthreads();
     const int ns = a.split_off ? a.split_off[b + 1] - a.split_off[b] : 0;
@@ -891,8 +894,8 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
         const bool have_list = a.tgt_off != nullptr;
         const int t0 = have_list ? a.tgt_off[b] : 0;
         const int ntask = 2 * ntargets(a, b);
-        const int first = (item - a.ioff[pos]) * tpi_of(R);
-        const int last = min(first + tpi_of(R), ntask);
+        const int first = (item - a.ioff[pos]) * tpi_of(a, R);
+        const int last = min(first + tpi_of(a, R), ntask);
         if (threadIdx.x == 0) s_next = first;
         __syncthreads();
         // the warps take the item's tasks one at a time from its counter
@@ -1014,6 +1017,7 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     CCArgs a;
     a.B = in->B; a.U = cache->U; a.n0 = cache->n0; a.H = cache->H; a.Rmax = lay->Rmax; a.sweeps = opt->sweeps;
     a.Rs = lay->Rmax < RMAX_CC ? lay->Rmax : RMAX_CC;
+    for (int i = 0; i < 3; ++i) a.tpi[i] = cache->cc_items[i];
     a.rowflag = (const int8_t*)(ws + lay->rowflag);
     a.lA = cache->lA; a.lc = cache->lc; a.uA = cache->uA; a.uc = cache->uc;
     a.slot_of = cache->slot_of; a.pscale = cache->pscale;

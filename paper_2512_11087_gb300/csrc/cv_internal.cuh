@@ -89,6 +89,7 @@ struct cv_cache {
     float* root_hi;    // [n0]
     cv_tc_w* tcw[CV_MAX_LAYERS + 1]; // tensor-core weights per layer (host objects), or null
     cv_tc_pc* tcpc;                  // tensor-core re-concretisation operand, or null
+    int cc_items[3];   // complete clipping: tasks per work item for 1, 2 and more active rows
 };
 
 struct cv_timer {

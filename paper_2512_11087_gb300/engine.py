@@ -105,6 +105,14 @@ class Round:
                             stream)
         return self.out
 
+    def autotune(self, lo, hi, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, row_off=None, G=None,
+                 h=None, alpha=None, tgt_off=None, tgt_ids=None, stream=None):
+        """Tunes complete clipping's work-item sizes on this batch (cv_autotune_cc); the sizes stay in
+        the network's cache.  Returns (sizes, their complete-clipping time in ms)."""
+        bi = self._bi(lo, hi, C, t, l_in, u_in, split_off, split_ids, row_off, G, h, alpha, tgt_off, tgt_ids)
+        return capi.cv_autotune_cc(self.net.handle, self.net.cache, bi, self.bo, self.opt, self.ws, self.ws_bytes,
+                                   stream)
+
     def capture(self, lo, hi, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, row_off=None, G=None,
                 h=None, alpha=None, tgt_off=None, tgt_ids=None):
         """CUDA graph of a round on these (device) buffers; replay with replay().  The tensors passed

@@ -32,7 +32,7 @@
 // single-block scan turns the per-subdomain task counts into work items (by default 256 (target,
 // side) tasks for one row, 64 for two, 16 for more: longer tasks, smaller items; the cache holds
 // the sizes, which cv_cc_items_set and the autotuner change), subdomains with more rows first; a
-// persistent k_complete grid (two blocks of 16 warps per SM) takes items from an atomic ticket,
+// persistent k_complete grid (two blocks of 14 warps per SM) takes items from an atomic ticket,
 // stages the item's rows in shared memory, and its warps take the item's tasks one at a time from
 // a shared counter.  The task body is compiled for each row count (multipliers in registers);
 // subdomains with more than four rows run in a separate launch of one block per SM (more
@@ -48,7 +48,7 @@ namespace {
 constexpr int RMAX_CC = 32;  // rows per subdomain handled by complete clipping
 constexpr int RTPL = 4;     // row counts up to this run in the main launch (two blocks per SM)
 // (target, side) tasks per work item: fewer for subdomains with more rows (longer tasks)
-constexpr int NWARP = 16;   // warps per block at most
+constexpr int NWARP = 14;   // warps per block at most (two blocks per SM leave 72 registers a thread)
 constexpr int CAPC = 384;   // breakpoints a warp's compacted list holds
 constexpr int SAMP_MIN = 64;     // brackets with more breakpoints start from sampled pivots
 constexpr float SAMP_D = 0.10f;  // rank margin of the sampled pivots around the target fraction
@@ -384,11 +384,12 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 const float2* ap2 = (const float2*)ap;
                 constexpr int P2 = 1;  // pairs per lane per iteration (deeper unrolling spills)
                 if (warm) {
+                    float2 avn = __ldg(ap2 + (min(2 * lane, n0 - 2) >> 1));
 #pragma unroll 1
                     for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
                         float2 av[P2];
-#pragma unroll
-                        for (int u = 0; u < P2; ++u) av[u] = __ldg(ap2 + (min(j0 + 64 * u, n0 - 2) >> 1));
+                        av[0] = avn;  // loaded one iteration ahead (L2 latency)
+                        avn = __ldg(ap2 + (min(j0 + 64, n0 - 2) >> 1));
 #pragma unroll
                         for (int u = 0; u < P2; ++u) {
                             const int j = j0 + 64 * u;
@@ -408,11 +409,12 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     fle += flt;
                 } else {
                     ext = false;
+                    float2 avn = __ldg(ap2 + (min(2 * lane, n0 - 2) >> 1));
 #pragma unroll 1
                     for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
                         float2 av[P2];
-#pragma unroll
-                        for (int u = 0; u < P2; ++u) av[u] = __ldg(ap2 + (min(j0 + 64 * u, n0 - 2) >> 1));
+                        av[0] = avn;  // loaded one iteration ahead (L2 latency)
+                        avn = __ldg(ap2 + (min(j0 + 64, n0 - 2) >> 1));
 #pragma unroll
                         for (int u = 0; u < P2; ++u) {
                             const int j = j0 + 64 * u;

@@ -112,8 +112,11 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_sample_rate(cfg, n_sub, seed=1):
-    """Time the FP64 oracle on n_sub subdomains of the workload with all host threads."""
+def oracle_sample_rate(cfg, n_sub, offset=0):
+    """Time the FP64 oracle on n_sub subdomains of the workload with all host threads.  The sample is
+    evenly spaced over the batch the GPU arm bounds (rank 0's split draws of all B subdomains),
+    starting at `offset`, so that it has the batch's mix of row counts (a subdomain whose rows the
+    pre-check drops costs almost nothing, one with four active rows the most)."""
     import numpy as np
     from oracle import oracle as O
     from paper_2512_11087_gb300 import workloads as WL
@@ -121,7 +124,14 @@ def oracle_sample_rate(cfg, n_sub, seed=1):
     net = O.Net(layers)
     lo0, hi0 = WL.box(cfg["dims"][0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
     cache = O.make_cache(O.root_crown(net, lo0, hi0))
-    so, si = WL.draw_splits(cache["ids"], n_sub, cfg["kmin"], cfg["kmax"], seed=seed)
+    B = cfg["B"]
+    off_all, ids_all = WL.draw_splits(cache["ids"], B, cfg["kmin"], cfg["kmax"], seed=shard_seed(0))
+    pick = (offset + (np.arange(n_sub) * B) // max(n_sub, 1)) % B
+    counts = off_all[pick + 1] - off_all[pick]
+    so = np.zeros(n_sub + 1, np.int32)
+    so[1:] = np.cumsum(counts)
+    si = np.concatenate([ids_all[off_all[b]:off_all[b + 1]] for b in pick]).astype(np.int32) if n_sub else \
+        np.zeros(0, np.int32)
     lo, hi = WL.tile_box(lo0, hi0, n_sub)
     C, t = WL.margin_spec(cfg["dims"][-1])
     cores = os.cpu_count() or 1
@@ -133,21 +143,22 @@ def oracle_sample_rate(cfg, n_sub, seed=1):
 
 
 def pick_sample(cfg, budget_s):
-    """Subdomain count whose oracle run takes about budget_s seconds on all host threads."""
-    rate, dt, cores = oracle_sample_rate(cfg, max(1, os.cpu_count() or 1), seed=7)
-    n = int(max(1, min(cfg["B"], rate * budget_s)))
+    """Subdomain count (at least 16) whose oracle run takes about budget_s seconds on all host threads."""
+    rate, dt, cores = oracle_sample_rate(cfg, 16, offset=5)
+    n = int(max(16, min(cfg["B"], rate * budget_s)))
     return n, cores
 
 
 def run_reference(args, cfg, rank, world):
     if rank != 0:
         return
-    n, cores = pick_sample(cfg, 6.0)
-    for _ in range(args.warmup):
-        oracle_sample_rate(cfg, n, seed=11)
+    # about 6 s of oracle work per step, less for long runs: the whole run stays within a few minutes
+    n, cores = pick_sample(cfg, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
+    for w in range(args.warmup):
+        oracle_sample_rate(cfg, n, offset=11 + w)
     total_dt, total_n = 0.0, 0
     for k in range(args.steps):
-        rate, dt, cores = oracle_sample_rate(cfg, n, seed=100 + k)
+        rate, dt, cores = oracle_sample_rate(cfg, n, offset=k)
         total_dt += dt
         total_n += n
     value = total_n / total_dt
@@ -155,9 +166,11 @@ def run_reference(args, cfg, rank, world):
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * total_dt / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
-                config=dict(workload=workload_desc(cfg, args.config), sample=f"{n} subdomains per step"),
+                config=dict(workload=workload_desc(cfg, args.config),
+                            sample=f"{n} subdomains per step, evenly spaced over the batch"),
                 cpu_baseline=dict(value=value, unit="subdomains/s", cores=cores, kind="oracle",
-                                  sample=f"{n} subdomains of the workload per step, FP64 C oracle, OpenMP"),
+                                  sample=f"{n} subdomains of the workload's batch per step (evenly spaced), "
+                                         f"FP64 C oracle, OpenMP"),
                 e2e=dict(value=value, unit="subdomains/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -354,11 +367,11 @@ def main():
         if vs_fp32 is not None:
             line["vs_fp32_path"] = vs_fp32
         if world == 1 and not args.no_cpu_baseline:
-            n, cores = pick_sample(cfg, 3.0)
-            rate, dt, cores = oracle_sample_rate(cfg, max(n * 4, 1), seed=21)
+            n, cores = pick_sample(cfg, 12.0)
+            rate, dt, cores = oracle_sample_rate(cfg, n, offset=3)
             line["cpu_baseline"] = dict(value=rate, unit="subdomains/s", cores=cores, kind="oracle",
-                                        sample=f"{max(n * 4, 1)} subdomains of the same workload, FP64 C oracle "
-                                               f"({dt:.1f} s on {cores} threads)")
+                                        sample=f"{n} subdomains of the benchmark batch (evenly spaced), FP64 C "
+                                               f"oracle ({dt:.1f} s on {cores} threads)")
         print(json.dumps(line), flush=True)
     capi.cv_timer_destroy(timer)
     net.close()

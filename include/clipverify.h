@@ -266,7 +266,8 @@ cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* 
  * no counterpart in the paper).  items[c] is the number of tasks per item for subdomains with
  * c + 1 active rows (c = 2: three or more).  The item size changes no result, only the time.
  * A cache starts with CV_CC_ITEMS_1/2/3.  cv_cc_items_set: each value in [1, 4096] (else
- * CV_EINVAL); it affects later rounds and graph captures that use the cache. */
+ * CV_EINVAL); it affects rounds run and graphs captured after the call (a graph captured before
+ * keeps the sizes it was captured with). */
 #define CV_CC_ITEMS_1 256
 #define CV_CC_ITEMS_2 64
 #define CV_CC_ITEMS_3 16

@@ -409,6 +409,71 @@ void orc_row_order(int n, int R, const double* G, const double* h, const double*
 }
 
 /* ------------------------------------------------------------------------- */
+/* Input BaB split step (Algorithm 4: Domain_Filter, then Batch_Split with the */
+/* parent's hyperplanes shared by both children; Section 3.3, final-layer     */
+/* bounds as constraints).  Parents verified or infeasible are dropped.  For  */
+/* each kept parent b, in order, with U = { r : lower_r <= 0 } its unproven  */
+/* spec rows:                                                                 */
+/*   axis = argmax_i (hi_i - lo_i) * sum_{r in U} |A_r,i|  (FP32, r ascending; */
+/*          the first maximum; the widest axis when every score is 0)         */
+/*   mid  = fl(fl(lo + hi) * 0.5)  on that axis (FP32)                       */
+/*   children [lo, mid] and [mid, hi] on the axis, the parent's box elsewhere */
+/*   |U| = 1: each child gets the row  A_r.x + c_r <= 0  (the only part of    */
+/*            the parent where f_r may still be <= 0); otherwise no row.     */
+/* The arithmetic is FP32 on purpose: the GPU takes the same decisions in the */
+/* same precision.  Returns the number of children (2K).                      */
+/* ------------------------------------------------------------------------- */
+int orc_input_split(int B, int n0, int m, const float* lo, const float* hi, const float* A, const float* c,
+                    const float* lower, const unsigned char* verified, const unsigned char* infeasible,
+                    float* lo_out, float* hi_out, int* row_off, float* G, float* h, int* parent) {
+    int K = 0, nr = 0;
+    row_off[0] = 0;
+    for (int b = 0; b < B; ++b) {
+        if (verified[b] || infeasible[b]) continue;
+        const float* l = lo + (long)b * n0;
+        const float* u = hi + (long)b * n0;
+        int nun = 0, r1 = -1;
+        for (int r = 0; r < m; ++r)
+            if (!(lower[(long)b * m + r] > 0.0f)) { ++nun; r1 = r; }
+        int ax = 0;
+        float best = -1.0f;
+        for (int i = 0; i < n0; ++i) {
+            float w = u[i] - l[i];
+            float sc = 0.0f;
+            for (int r = 0; r < m; ++r)
+                if (!(lower[(long)b * m + r] > 0.0f)) sc += fabsf(A[((long)b * m + r) * n0 + i]);
+            float score = w * sc;
+            if (score > best) { best = score; ax = i; }
+        }
+        if (!(best > 0.0f)) {
+            best = -1.0f;
+            for (int i = 0; i < n0; ++i) {
+                float w = u[i] - l[i];
+                if (w > best) { best = w; ax = i; }
+            }
+        }
+        float sum = l[ax] + u[ax];
+        float mid = sum * 0.5f;
+        for (int k = 0; k < 2; ++k) {
+            int ch = 2 * K + k;
+            float* lo2 = lo_out + (long)ch * n0;
+            float* hi2 = hi_out + (long)ch * n0;
+            for (int i = 0; i < n0; ++i) { lo2[i] = l[i]; hi2[i] = u[i]; }
+            if (k == 0) hi2[ax] = mid; else lo2[ax] = mid;
+            if (nun == 1) {
+                for (int i = 0; i < n0; ++i) G[(long)nr * n0 + i] = A[((long)b * m + r1) * n0 + i];
+                h[nr] = c[(long)b * m + r1];
+                ++nr;
+            }
+            row_off[ch + 1] = nr;
+            parent[ch] = b;
+        }
+        ++K;
+    }
+    return 2 * K;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Algorithm 1 (coordinate ascent over several constraints), repeated for     */
 /* `sweeps` passes.  Minimises a.x + c over the box subject to G x + h <= 0   */
 /* through the dual  max_{beta>=0} (a + beta^T G).xhat - |a + beta^T G|.eps   */

@@ -48,6 +48,8 @@ def _load():
         _lib.orc_relaxed_clip_sequential.restype = I
         _lib.orc_row_order.argtypes = [I, I, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
         _lib.orc_row_order.restype = None
+        _lib.orc_input_split.argtypes = [I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        _lib.orc_input_split.restype = I
         _lib.orc_complete_clip.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
         _lib.orc_complete_clip.restype = D
         _lib.orc_complete_clip_f32.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
@@ -210,6 +212,30 @@ def row_order(G, h, lo, hi):
     perm = np.zeros(max(R, 1), np.int32)
     lib.orc_row_order(lo.size, R, _p(G), _p(h), _p(lo), _p(hi), perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     return perm[:R]
+
+
+def input_split(lo, hi, final_A, final_c, lower, verified, infeasible):
+    """Input-BaB split step (Algorithm 4: Domain_Filter, Batch_Split sharing the parents' planes).
+    lo, hi [B x n0]; final_A [B x m x n0]; final_c, lower [B x m]; verified, infeasible [B].
+    Returns dict(lo, hi [2K x n0], row_off [2K+1], G [rows x n0], h [rows], parent [2K])."""
+    lib = _load()
+    f32 = lambda x: np.ascontiguousarray(np.asarray(x, np.float32))
+    u8 = lambda x: np.ascontiguousarray(np.asarray(x, np.uint8))
+    lo, hi, A, c, lower = f32(lo), f32(hi), f32(final_A), f32(final_c), f32(lower)
+    B, n0 = lo.shape
+    m = lower.shape[1] if lower.ndim == 2 else 1
+    ver, inf = u8(verified), u8(infeasible)
+    lo2 = np.zeros((2 * max(B, 1), n0), np.float32)
+    hi2 = np.zeros_like(lo2)
+    ro = np.zeros(2 * B + 1, np.int32)
+    G = np.zeros((2 * max(B, 1), n0), np.float32)
+    h = np.zeros(2 * max(B, 1), np.float32)
+    par = np.zeros(2 * max(B, 1), np.int32)
+    pf = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    n = lib.orc_input_split(B, n0, m, pf(lo), pf(hi), pf(A), pf(c), pf(lower), pf(ver), pf(inf), pf(lo2), pf(hi2),
+                            pf(ro), pf(G), pf(h), pf(par))
+    nr = int(ro[n])
+    return dict(lo=lo2[:n], hi=hi2[:n], row_off=ro[:n + 1], G=G[:nr], h=h[:nr], parent=par[:n])
 
 
 def complete_clip(a, c, G, h, lo, hi, sweeps):

@@ -347,6 +347,39 @@ cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_alpha_in* i
 cv_status cv_alpha_adam(float* alpha, float* m1, float* m2, const float* grad, long long n, int t,
                         float lr, float beta1, float beta2, float eps, void* stream);
 
+/* ---------------------------------------------------------------- input branch and bound */
+
+/* One split step of input BaB with Clip-and-Verify (Algorithm 4: Domain_Filter, Batch_Split with
+ * the parents' hyperplanes shared by both children; Section 3.3, using final-layer bounds for
+ * clipping).  For B bounded parents (the outputs of a cv_bound_batch call with final_A/final_c):
+ *  - a parent that is verified or infeasible is dropped; the K kept parents, in their order,
+ *    give children 2k (lower half) and 2k + 1 (upper half);
+ *  - the split axis maximises (hi_i - lo_i) * sum_r |final_A_r,i| over the spec rows r that are
+ *    not yet proven (lower_r <= 0), the extent of those planes along axis i (FP32, rows summed in
+ *    increasing r); when every score is 0 the widest axis; the lowest index on ties;
+ *  - the split point is fl(fl(lo_i + hi_i) * 0.5) (FP32), the children [lo_i, mid] and [mid, hi_i];
+ *  - when exactly one spec row r is not yet proven, both children get its plane as the
+ *    constraint row final_A_r . x + final_c_r <= 0: points where the plane is positive already
+ *    satisfy f_r > 0 and every other row is proven on the whole parent.  With several rows
+ *    unproven the points still to verify form a union of such half-spaces, not an intersection,
+ *    so no row is passed (a joint row would be unsound).
+ * Pass the children's boxes and rows to cv_bound_batch (extra rows: row_off, G, h; relaxed
+ * clipping then clips each child with its inherited plane, as Algorithm 4 orders it).
+ * Inputs (device): lo, hi [B x n_0] the parents' (clipped) boxes; final_A [B x m x n_0],
+ *   final_c [B x m], lower [B x m]; verified, infeasible [B] (0/1).
+ * Outputs (device, caller-allocated for the worst case K = B): lo_out, hi_out [2B x n_0];
+ *   row_off [2B + 1] (CSR over the children, 0 or 1 row each); G [2B x n_0], h [2B];
+ *   parent [2B] (index of each child's parent); n_children [1] (2K).  Entries past the
+ *   2K children (and row_off past 2K) are left unwritten.
+ * workspace: cv_input_split_workspace() bytes of device memory.  B = 0 writes n_children = 0 and
+ * row_off[0] = 0.  Errors: CV_EINVAL for a null pointer (B > 0) or n_0, m < 1. */
+cv_status cv_input_split_workspace(int B, size_t* bytes);
+cv_status cv_input_split(int B, int n0, int m, const float* lo, const float* hi, const float* final_A,
+                         const float* final_c, const float* lower, const uint8_t* verified,
+                         const uint8_t* infeasible, float* lo_out, float* hi_out, int* row_off, float* G,
+                         float* h, int* parent, int* n_children, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Size of the library's fixed device scratch array used by cv_relaxed_clip_static. */

@@ -106,6 +106,8 @@ def load():
         "cv_cc_items_set": ([P, P], I),
         "cv_cc_items_get": ([P, P], I),
         "cv_autotune_cc": ([P, P, P, P, P, P, ctypes.c_size_t, P, P, P], I),
+        "cv_input_split_workspace": ([I, P], I),
+        "cv_input_split": ([I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -121,7 +123,8 @@ def exported_symbols():
                         "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
                         "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
                         "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy",
-                        "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc")]
+                        "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc", "cv_input_split_workspace",
+                        "cv_input_split")]
 
 
 def _check(st):
@@ -286,6 +289,21 @@ def cv_timer_read(t):
     steps = ctypes.c_longlong()
     _check(load().cv_timer_read(t, ctypes.cast(ms, P), ctypes.byref(n), ctypes.byref(steps)))
     return list(ms), n.value, steps.value
+
+
+def cv_input_split_workspace(B):
+    n = ctypes.c_size_t()
+    _check(load().cv_input_split_workspace(int(B), ctypes.byref(n)))
+    return n.value
+
+
+def cv_input_split(B, n0, m, lo, hi, final_A, final_c, lower, verified, infeasible, lo_out, hi_out, row_off, G, h,
+                   parent, n_children, workspace, workspace_bytes, stream=None):
+    """Input-BaB split step (Algorithm 4); all arrays are device tensors (see the header)."""
+    _check(load().cv_input_split(int(B), int(n0), int(m), ptr(lo), ptr(hi), ptr(final_A), ptr(final_c), ptr(lower),
+                                 ptr(verified), ptr(infeasible), ptr(lo_out), ptr(hi_out), ptr(row_off), ptr(G),
+                                 ptr(h), ptr(parent), ptr(n_children), ptr(workspace), int(workspace_bytes),
+                                 stream_ptr(stream)))
 
 
 CC_ITEMS_DEFAULT = (256, 64, 16)

@@ -182,3 +182,25 @@ def optimize_alpha(state: AlphaState, alpha, steps=20, lr=0.1, decay=0.98):
     lower, _ = state.bound_and_grad(alpha)
     history.append(lower)
     return alpha, history
+
+
+def input_split(lo, hi, final_A, final_c, lower, verified, infeasible, stream=None):
+    """Input-BaB split step on device tensors (cv_input_split): returns dict(lo, hi [2K x n0],
+    row_off [2K + 1], G [rows x n0], h [rows], parent [2K]) as device tensors."""
+    B, n0 = lo.shape
+    m = lower.shape[1]
+    dev = lo.device
+    f32 = dict(dtype=torch.float32, device=dev)
+    lo2, hi2 = torch.empty(2 * max(B, 1), n0, **f32), torch.empty(2 * max(B, 1), n0, **f32)
+    ro = torch.zeros(2 * B + 1, dtype=torch.int32, device=dev)
+    G, h = torch.empty(2 * max(B, 1), n0, **f32), torch.empty(2 * max(B, 1), **f32)
+    par = torch.empty(2 * max(B, 1), dtype=torch.int32, device=dev)
+    nch = torch.zeros(1, dtype=torch.int32, device=dev)
+    wsb = capi.cv_input_split_workspace(B)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+    capi.cv_input_split(B, n0, m, lo, hi, final_A, final_c, lower, verified, infeasible, lo2, hi2, ro, G, h, par,
+                        nch, ws, wsb, stream)
+    n = int(nch.item())
+    nr = int(ro[n].item()) if n else 0
+    return dict(lo=lo2[:n], hi=hi2[:n], row_off=ro[:n + 1], G=G[:nr], h=h[:nr], parent=par[:n])
+

@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--relaxed", type=int, default=None, choices=[1, 2, 3],
                    help="relaxed clipping: 1 parallel (Algorithm 2, the workload's), 2 sequential (Algorithm 3), "
                         "3 sequential in the constraint-importance order")
+    p.add_argument("--input-bab", action="store_true",
+                   help="time the input-BaB split step (cv_input_split) on the workload's bounded batch instead")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep complete clipping's default work-item sizes instead of tuning them first")
     p.add_argument("--subdomains", type=int, default=0,
@@ -203,6 +205,88 @@ def job_value(world, B, steps, total_ms):
     return world * B * steps / (total_ms / 1e3)
 
 
+# ---------------------------------------------------------------- input-BaB split step
+def run_input_split(args, cfg):
+    """Times cv_input_split (Algorithm 4's Domain_Filter + Batch_Split) on the outputs of one round of
+    the workload (final planes included), the L2 flushed before every step; roofline against the
+    measured HBM copy bandwidth with the bytes the step must move for this batch."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
+    torch.cuda.set_device(0)
+    dims, B, kmin, kmax = cfg["dims"], cfg["B"], cfg["kmin"], cfg["kmax"]
+    layers = WL.he_mlp(dims, seed=0)
+    lo0, hi0 = WL.box(dims[0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    net.build_cache(lo0, hi0)
+    so, si = WL.draw_splits(net.read_cache()["ids"], B, kmin, kmax, seed=shard_seed(0))
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    C, t = WL.margin_spec(dims[-1])
+    m, n0 = C.shape[0], dims[0]
+    rnd = E.Round(net, B, m, max_splits=kmax, relaxed=cfg["relaxed"], sweeps=cfg["sweeps"],
+                  precision=capi.CV_PREC_BF16X8, want_final=True)
+    d = E.to_dev
+    out = rnd.run(d(lo), d(hi), d(C), d(t), split_off=d(so), split_ids=d(si))
+    torch.cuda.synchronize()
+    f32 = dict(dtype=torch.float32, device="cuda")
+    lo2, hi2 = torch.empty(2 * B, n0, **f32), torch.empty(2 * B, n0, **f32)
+    ro = torch.zeros(2 * B + 1, dtype=torch.int32, device="cuda")
+    G, h = torch.empty(2 * B, n0, **f32), torch.empty(2 * B, **f32)
+    par = torch.empty(2 * B, dtype=torch.int32, device="cuda")
+    nch = torch.zeros(1, dtype=torch.int32, device="cuda")
+    wsb = capi.cv_input_split_workspace(B)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, **f32)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        capi.cv_input_split(B, n0, m, out["lo_clip"], out["hi_clip"], out["final_A"], out["final_c"], out["lower"],
+                            out["verified"], out["infeasible"], lo2, hi2, ro, G, h, par, nch, ws, wsb, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    # bytes the step must move: every parent's flags and spec lower bounds; per kept parent its box,
+    # the planes of its unproven rows (the axis scores), two child boxes, and two inherited rows
+    # when exactly one row is unproven; offsets and parent indices
+    ver = out["verified"].cpu().numpy().astype(bool)
+    inf = out["infeasible"].cpu().numpy().astype(bool)
+    unp = (~(out["lower"].cpu().numpy() > 0)).sum(axis=1)
+    kept = ~ver & ~inf
+    K = int(kept.sum())
+    byts = B * (2 + 4 * m) + int(np.sum(4 * n0 * unp[kept])) + K * (8 * n0 + 2 * 8 * n0 + 2 * 8) \
+        + int(np.sum(kept & (unp == 1))) * 2 * (4 * n0 + 4)
+    achieved = byts / (ms * 1e-3) / 1e9
+    peak, peak_src = 6800.0, "fallback"
+    try:
+        peak, peak_src = float(json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                            "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    line = dict(metric="parent subdomains split per second (input BaB)", value=B / (ms * 1e-3), unit="subdomains/s",
+                n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=workload_desc(cfg, args.config) + "; one round with final planes, then the split",
+                            kept_parents=K, children=2 * K, parents_with_one_unproven_row=int(np.sum(kept & (unp == 1))),
+                            l2="flushed (256 MiB write) before every timed step"),
+                roofline=dict(bound="hbm", kernel="cv_input_split (k_split_mark, k_split_scan, k_split_write)",
+                              achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=None,
+                              alg_bytes_per_step=byts, peak_source=peak_src),
+                gpu_launches=3 * args.steps)
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse_args()
@@ -217,6 +301,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)
+        return
+    if args.input_bab:
+        run_input_split(args, cfg)
         return
 
     import numpy as np

@@ -31,47 +31,74 @@ __device__ __forceinline__ bool better(float s, int i, float bs, int bi) {
     return s > bs || (s == bs && i < bi);
 }
 
-// one block per parent: keep flag, single unproven row, split axis
+// one block per parent: keep flag, single unproven row, split axis.  The unproven rows are listed
+// in shared memory (dynamic, m ints) first; each thread then scores four consecutive axes with one
+// 16-byte load per row when n0 is a multiple of 4 and the planes are 16-byte aligned (independent loads; the sum of every axis still
+// runs over the rows in increasing order), else one axis at a time.
 __global__ void k_split_mark(int B, int n0, int m, const float* lo, const float* hi, const float* A,
                              const float* lower, const uint8_t* verified, const uint8_t* infeasible, SplitWs w) {
+    extern __shared__ int s_rows[];
     const int b = blockIdx.x;
     __shared__ float rs[32];
     __shared__ int ri[32];
-    __shared__ int s_nun, s_r1;
+    __shared__ int s_nun;
     const bool keep = !verified[b] && !infeasible[b];
-    if (threadIdx.x == 0) {
-        int nun = 0, r1 = -1;
-        for (int r = 0; r < m; ++r)
-            if (!(lower[(size_t)b * m + r] > 0.f)) { ++nun; r1 = r; }
-        s_nun = nun;
-        s_r1 = r1;
-    }
-    __syncthreads();
     if (!keep) {
         if (threadIdx.x == 0) { w.keep[b] = 0; w.axis[b] = 0; w.row1[b] = -1; }
         return;
     }
+    const float* lb = lower + (size_t)b * m;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) s_rows[r] = !(lb[r] > 0.f);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nun = 0;
+        for (int r = 0; r < m; ++r)
+            if (s_rows[r]) s_rows[nun++] = r;  // in place: nun <= r
+        s_nun = nun;
+    }
+    __syncthreads();
+    const int nun = s_nun;
     const float* l = lo + (size_t)b * n0;
     const float* u = hi + (size_t)b * n0;
     const float* Ab = A + (size_t)b * m * n0;
-    const float* lb = lower + (size_t)b * m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool vec = (n0 & 3) == 0 && ((uintptr_t)A & 15) == 0;  // 16-byte aligned rows
     for (int pass = 0; pass < 2; ++pass) {
         // pass 0: plane extents; pass 1 (only when no extent is positive): widths
         float bs = -1.f;
         int bi = 0x7fffffff;
-        for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-            const float wd = __fsub_rn(u[i], l[i]);
-            float sc;
-            if (pass == 0) {
-                float acc = 0.f;
-                for (int r = 0; r < m; ++r)
-                    if (!(lb[r] > 0.f)) acc = __fadd_rn(acc, fabsf(Ab[(size_t)r * n0 + i]));
-                sc = __fmul_rn(wd, acc);
-            } else {
-                sc = wd;
+        if (vec) {
+            for (int i4 = threadIdx.x; 4 * i4 < n0; i4 += blockDim.x) {
+                const int i = 4 * i4;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                if (pass == 0) {
+#pragma unroll 4
+                    for (int q = 0; q < nun; ++q) {
+                        const float4 v = __ldg((const float4*)(Ab + (size_t)s_rows[q] * n0 + i));
+                        acc[0] = __fadd_rn(acc[0], fabsf(v.x));
+                        acc[1] = __fadd_rn(acc[1], fabsf(v.y));
+                        acc[2] = __fadd_rn(acc[2], fabsf(v.z));
+                        acc[3] = __fadd_rn(acc[3], fabsf(v.w));
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float wd = __fsub_rn(u[i + e], l[i + e]);
+                    const float sc = (pass == 0) ? __fmul_rn(wd, acc[e]) : wd;
+                    if (sc > bs) { bs = sc; bi = i + e; }  // increasing axis: the first maximum
+                }
             }
-            if (sc > bs) { bs = sc; bi = i; }  // increasing i: the first maximum of this thread
+        } else {
+            for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+                const float wd = __fsub_rn(u[i], l[i]);
+                float sc = wd;
+                if (pass == 0) {
+                    float acc = 0.f;
+                    for (int q = 0; q < nun; ++q) acc = __fadd_rn(acc, fabsf(Ab[(size_t)s_rows[q] * n0 + i]));
+                    sc = __fmul_rn(wd, acc);
+                }
+                if (sc > bs) { bs = sc; bi = i; }
+            }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -87,13 +114,13 @@ __global__ void k_split_mark(int B, int n0, int m, const float* lo, const float*
             if (better(rs[q], ri[q], fs, fi)) { fs = rs[q]; fi = ri[q]; }
         __syncthreads();
         if (pass == 0 && fs > 0.f) {
-            if (threadIdx.x == 0) { w.keep[b] = 1; w.axis[b] = fi; w.row1[b] = (s_nun == 1) ? s_r1 : -1; }
+            if (threadIdx.x == 0) { w.keep[b] = 1; w.axis[b] = fi; w.row1[b] = (nun == 1) ? s_rows[0] : -1; }
             return;
         }
         if (pass == 1 && threadIdx.x == 0) {
             w.keep[b] = 1;
             w.axis[b] = (fi == 0x7fffffff) ? 0 : fi;
-            w.row1[b] = (s_nun == 1) ? s_r1 : -1;
+            w.row1[b] = (nun == 1) ? s_rows[0] : -1;
         }
     }
 }
@@ -210,7 +237,12 @@ extern "C" cv_status cv_input_split(int B, int n0, int m, const float* lo, const
     w.row1 = (int*)p; p += step;
     w.cpos = (int*)p; p += step;
     w.rpos = (int*)p;
-    k_split_mark<<<B, 256, 0, st>>>(B, n0, m, lo, hi, final_A, lower, verified, infeasible, w);
+    const size_t mark_smem = (size_t)m * sizeof(int);
+    if (mark_smem > 48 * 1024) {
+        cv_set_error("cv_input_split: more than 12288 spec rows");
+        return CV_EINVAL;
+    }
+    k_split_mark<<<B, 256, mark_smem, st>>>(B, n0, m, lo, hi, final_A, lower, verified, infeasible, w);
     CV_LAUNCH_CHECK("k_split_mark");
     k_split_scan<<<1, 1024, 0, st>>>(B, w, row_off, n_children);
     CV_LAUNCH_CHECK("k_split_scan");

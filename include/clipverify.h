@@ -258,6 +258,24 @@ cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* 
                          cv_batch_out* out, const cv_options* opt,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- complete clipping of the spec */
+
+/* Complete clipping (Theorem 1, Algorithm 1, opt->sweeps passes) applied to the final linear bound
+ * of every spec row that a round left unproven: for subdomain b and spec row r with lower <= 0,
+ * maximises over beta >= 0 the dual of  min final_A_r . x + final_c_r  over the clipped box under the
+ * subdomain's active rows (splits and extra rows, as the round's pre-check keeps them), and raises
+ * lower[b, r] to the dual value when it is larger.  Any beta >= 0 gives a valid bound: the value is
+ * evaluated in FP32 with its rounding pad (FP64 when the padded value straddles 0), as for the
+ * cached neurons.  verified is recomputed from the new bounds.
+ * Call after cv_bound_batch with the same `in` and with out->final_A / final_c requested; reads
+ * out->lo_clip, hi_clip, infeasible, final_A, final_c; updates out->lower and out->verified.  The
+ * breakpoint decisions are those of the cached-neuron step (FP32 keys, exact fixed-point weights).
+ * opt->sweeps must be > 0 (else CV_EINVAL); the other options are not used.  workspace:
+ * cv_spec_clip_workspace() bytes, 256-byte aligned. */
+cv_status cv_spec_clip_workspace(const cv_net* net, const cv_cache* cache, const cv_batch_in* in, size_t* bytes);
+cv_status cv_spec_clip(cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                       const cv_options* opt, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- scheduler tuning */
 
 /* Complete clipping runs as one persistent launch over uneven work: each subdomain's

@@ -106,6 +106,8 @@ def load():
         "cv_cc_items_set": ([P, P], I),
         "cv_cc_items_get": ([P, P], I),
         "cv_autotune_cc": ([P, P, P, P, P, P, ctypes.c_size_t, P, P, P], I),
+        "cv_spec_clip_workspace": ([P, P, P, P], I),
+        "cv_spec_clip": ([P, P, P, P, P, P, ctypes.c_size_t, P], I),
         "cv_input_split_workspace": ([I, P], I),
         "cv_input_split": ([I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P], I),
     }
@@ -124,7 +126,7 @@ def exported_symbols():
                         "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
                         "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy",
                         "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc", "cv_input_split_workspace",
-                        "cv_input_split")]
+                        "cv_input_split", "cv_spec_clip_workspace", "cv_spec_clip")]
 
 
 def _check(st):
@@ -289,6 +291,18 @@ def cv_timer_read(t):
     steps = ctypes.c_longlong()
     _check(load().cv_timer_read(t, ctypes.cast(ms, P), ctypes.byref(n), ctypes.byref(steps)))
     return list(ms), n.value, steps.value
+
+
+def cv_spec_clip_workspace(net, cache, bi):
+    n = ctypes.c_size_t()
+    _check(load().cv_spec_clip_workspace(net, cache, ctypes.byref(bi), ctypes.byref(n)))
+    return n.value
+
+
+def cv_spec_clip(net, cache, bi, bo, opt, workspace, workspace_bytes, stream=None):
+    """Complete clipping of the spec rows' final planes after a round (see the header)."""
+    _check(load().cv_spec_clip(net, cache, ctypes.byref(bi), ctypes.byref(bo), ctypes.byref(opt), ptr(workspace),
+                               int(workspace_bytes), stream_ptr(stream)))
 
 
 def cv_input_split_workspace(B):

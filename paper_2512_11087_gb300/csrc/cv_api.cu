@@ -343,3 +343,73 @@ extern "C" cv_status cv_autotune_cc(cv_net* net, cv_cache* cache, const cv_batch
     if (best_ms) *best_ms = have ? best_t : 0.f;
     return CV_OK;
 }
+
+// ---------------------------------------------------------------- complete clipping of the spec planes
+
+namespace {
+// layout of cv_spec_clip's workspace: row status and minima, the complete-clipping region, scales
+struct SpecWs { size_t rowflag, vmin, cc, sscale, total; };
+SpecWs spec_ws(const cv_cache* cache, const cv_batch_in* in) {
+    SpecWs w;
+    const size_t Rm = (size_t)in->B * (size_t)(in->max_splits + in->max_rows);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = cv_align256(off + (bytes ? bytes : 1)); return o; };
+    w.rowflag = take(Rm);
+    w.vmin = take(Rm * sizeof(double));
+    w.cc = take(cv_cc_workspace(in->B, in->max_splits + in->max_rows, cache->n0));
+    w.sscale = take((size_t)in->B * in->m * sizeof(float));
+    w.total = off;
+    return w;
+}
+}  // namespace
+
+extern "C" cv_status cv_spec_clip_workspace(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
+                                            size_t* bytes) {
+    cv_options o;
+    cv_options_default(&o);
+    cv_status s = validate(net, cache, in, &o, false);
+    if (s) return s;
+    if (!bytes) { cv_set_error("null bytes"); return CV_EINVAL; }
+    *bytes = spec_ws(cache, in).total;
+    return CV_OK;
+}
+
+extern "C" cv_status cv_spec_clip(cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                                  const cv_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
+    cv_status s = validate(net, cache, in, opt);
+    if (s) return s;
+    if (!out) { cv_set_error("null output"); return CV_EINVAL; }
+    if (opt->sweeps <= 0) { cv_set_error("cv_spec_clip: sweeps = 0, nothing to do"); return CV_EINVAL; }
+    const int B = in->B, m = in->m;
+    if (B == 0 || m == 0) return CV_OK;
+    if (!out->lo_clip || !out->hi_clip || !out->infeasible || !out->verified || !out->lower || !out->final_A ||
+        !out->final_c) {
+        cv_set_error("cv_spec_clip: needs lo_clip, hi_clip, infeasible, verified, lower, final_A and final_c");
+        return CV_EINVAL;
+    }
+    const SpecWs w = spec_ws(cache, in);
+    if (!workspace || workspace_bytes < w.total) {
+        cv_set_error("workspace too small: need " + std::to_string(w.total) + " bytes");
+        return CV_EWORKSPACE;
+    }
+    if (((uintptr_t)workspace & 255) != 0) { cv_set_error("workspace must be 256-byte aligned"); return CV_EINVAL; }
+    char* ws = (char*)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    cv_ws_layout lay;
+    memset(&lay, 0, sizeof(lay));
+    lay.Rmax = in->max_splits + in->max_rows;
+    lay.R = B * m;
+    lay.rowflag = w.rowflag;
+    lay.vmin = w.vmin;
+    lay.cc = w.cc;
+    lay.total = w.total;
+    int launches = 0;
+    // the active rows, as the round's pre-check found them on the input box (infeasible flags the
+    // round already set are set again; none is cleared)
+    if ((s = cv_launch_rows(net, cache, in, &lay, ws, out->infeasible, st))) return s;
+    if ((s = cv_launch_spec_clip(net, cache, in, out, opt, &lay, ws, (float*)(ws + w.sscale), &launches, st)))
+        return s;
+    k_verified<<<(B + 255) / 256, 256, 0, st>>>(B, m, out->lower, out->infeasible, out->verified);
+    CV_LAUNCH_CHECK("k_verified");
+    return CV_OK;
+}

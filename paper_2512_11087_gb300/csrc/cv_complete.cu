@@ -41,6 +41,7 @@
 #include "cv_internal.cuh"
 
 #include <climits>
+#include <cstring>
 #include <math.h>
 
 namespace {
@@ -76,6 +77,12 @@ __device__ __forceinline__ float ratio64(long long n, long long d) {
 struct CCArgs {
     int B, U, n0, H, Rmax, Rs, sweeps;
     int tpi[3];  // tasks per work item for subdomains with 1, 2 and more active rows
+    // spec-plane mode (cv_spec_clip): the targets are the m spec rows' final planes of each subdomain
+    int spec, m;
+    const float* sA;      // [B x m x n0] final planes
+    const float* sc;      // [B x m] their intercepts
+    const float* sscale;  // [B x m] magnitude scale of each plane (error pad)
+    float* slower;        // [B x m] spec lower bounds, raised in place
     const int8_t* rowflag;
     const float* lA; const float* lc; const float* uA; const float* uc;
     const int* slot_of; const float* pscale;
@@ -105,6 +112,9 @@ __device__ __forceinline__ int ntargets(const CCArgs& a, int b) {
     return a.tgt_off ? a.tgt_off[b + 1] - a.tgt_off[b] : a.U;
 }
 
+// tasks of a subdomain: both sides of every target, or one per spec row in spec-plane mode
+__device__ __forceinline__ int ntasks(const CCArgs& a, int b) { return a.spec ? a.m : 2 * ntargets(a, b); }
+
 // Per subdomain: the first Rs active rows, their data in the workspace, and the item count.
 __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
     const int b = blockIdx.x;
@@ -118,7 +128,7 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
                 if (a.rowflag[(size_t)b * a.Rmax + k] == 0) rowsel[r++] = k;
         R = r;
         a.wR[b] = r;
-        a.wcnt[b] = r > 0 ? (2 * ntargets(a, b) + tpi_of(a, r) - 1) / tpi_of(a, r) : 0;
+        a.wcnt[b] = r > 0 ? (ntasks(a, b) + tpi_of(a, r) - 1) / tpi_of(a, r) : 0;
     }
     __syncthreads();
     const int ns = a.split_off ? a.split_off[b + 1] - a.split_off[b] : 0;
@@ -291,16 +301,18 @@ struct CCRows {
 // launch instantiates RC = 8, 16, 32 for any Rn <= RC with the multipliers in the warp's shared
 // slots bsm / jsm.  Breakpoint keys are the raw bits of q_j = (-a'_j) * fl(1/g_kj): for q > 0 (the
 // search range) the unsigned order of the bits is the order of the values.
-template <int RC, bool WIDE>
+template <int RC, bool WIDE, bool SPEC>
 __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsigned* keys, unsigned short* cidx,
                                         float* bsm, int* jsm, int Rn, int b, int c, int side, int lane,
                                         unsigned long long& my_steps) {
     const int n0 = a.n0;
     const int R = WIDE ? Rn : RC;
-    const size_t o = (size_t)b * a.U + c;
-    const float* ap = side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0;
-    const float sa = side ? -1.f : 1.f;
-    const float c0 = side ? -a.uc[c] : a.lc[c];
+    // the target plane a.x + c0 (lower side; the upper side is the negated upper plane), or in
+    // spec-plane mode spec row c's final plane
+    const size_t o = SPEC ? (size_t)b * a.m + c : (size_t)b * a.U + c;
+    const float* ap = SPEC ? a.sA + o * n0 : (side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0);
+    const float sa = (!SPEC && side) ? -1.f : 1.f;
+    const float c0 = SPEC ? a.sc[o] : (side ? -a.uc[c] : a.lc[c]);
     float beta[WIDE ? 1 : RC];
     int jprev[WIDE ? 1 : RC];
     auto bget = [&](int p) -> float {
@@ -726,8 +738,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
     // dual objective at beta, FP32 with its rounding bound
     const float* slo = a.lo + (size_t)b * n0;
     const float* shi = a.hi + (size_t)b * n0;
-    const float psc = __ldg(a.pscale + (side ? a.U + c : c));
-    const float cur = side == 0 ? a.l[o] : -a.u[o];
+    const float psc = SPEC ? a.sscale[o] : __ldg(a.pscale + (side ? a.U + c : c));
+    const float cur = SPEC ? a.slower[o] : (side == 0 ? a.l[o] : -a.u[o]);
     float part = 0.f;
     if (!WIDE && (n0 & 1) == 0) {
         // two adjacent elements per lane, packed FP32: each lane sums at most ceil(n0/64) terms per
@@ -823,14 +835,15 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
         val = __double2float_rd(d - ldexp((double)scale, -40));
     }
     if (lane == 0) {
-        if (side == 0) { if (val > a.l[o]) a.l[o] = val; }
+        if (SPEC) { if (val > a.slower[o]) a.slower[o] = val; }
+        else if (side == 0) { if (val > a.l[o]) a.l[o] = val; }
         else { const float ub = -val; if (ub < a.u[o]) a.u[o] = ub; }
     }
 }
 
 // WIDE: the items of subdomains with more than RTPL rows (one block per SM, more registers);
 // otherwise the rest.
-template <bool WIDE>
+template <bool WIDE, bool SPEC>
 __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a) {
     const int n0 = a.n0, Rs = a.Rs, B = a.B;
     const int RsS = Rs < RTPL ? Rs : RTPL;  // rows staged by the main launch
@@ -895,7 +908,7 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
         }
         const bool have_list = a.tgt_off != nullptr;
         const int t0 = have_list ? a.tgt_off[b] : 0;
-        const int ntask = 2 * ntargets(a, b);
+        const int ntask = SPEC ? a.m : 2 * ntargets(a, b);
         const int first = (item - a.ioff[pos]) * tpi_of(a, R);
         const int last = min(first + tpi_of(a, R), ntask);
         if (threadIdx.x == 0) s_next = first;
@@ -906,23 +919,31 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
             if (lane == 0) t = atomicAdd(&s_next, 1);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= last) break;
-            const int ti = t >> 1, side = t & 1;
-            const int c = have_list ? a.tgt_ids[t0 + ti] : ti;
-            if (c < 0 || c >= a.U) {
-                if (lane == 0) atomicOr(a.status, CV_DEV_TARGET);
-                continue;
+            int c, side;
+            if (SPEC) {
+                c = t;
+                side = 0;
+                if (a.slower[(size_t)b * a.m + c] > 0.f) continue;  // proven already
+            } else {
+                const int ti = t >> 1;
+                side = t & 1;
+                c = have_list ? a.tgt_ids[t0 + ti] : ti;
+                if (c < 0 || c >= a.U) {
+                    if (lane == 0) atomicOr(a.status, CV_DEV_TARGET);
+                    continue;
+                }
+                if (a.mask[(size_t)b * a.U + c] != 0) continue;
             }
-            if (a.mask[(size_t)b * a.U + c] != 0) continue;
             if (WIDE) {
-                if (R <= 8) cc_task<8, true>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
-                else if (R <= 16) cc_task<16, true>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
-                else cc_task<32, true>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
+                if (R <= 8) cc_task<8, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
+                else if (R <= 16) cc_task<16, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
+                else cc_task<32, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
             } else {
                 switch (R) {
-                    case 1: cc_task<1, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 1, b, c, side, lane, my_steps); break;
-                    case 2: cc_task<2, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 2, b, c, side, lane, my_steps); break;
-                    case 3: cc_task<3, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 3, b, c, side, lane, my_steps); break;
-                    default: cc_task<4, false>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 4, b, c, side, lane, my_steps); break;
+                    case 1: cc_task<1, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 1, b, c, side, lane, my_steps); break;
+                    case 2: cc_task<2, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 2, b, c, side, lane, my_steps); break;
+                    case 3: cc_task<3, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 3, b, c, side, lane, my_steps); break;
+                    default: cc_task<4, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 4, b, c, side, lane, my_steps); break;
                 }
             }
             __syncwarp();
@@ -954,7 +975,7 @@ __global__ void k_cc_post(CCArgs a) {
     if (threadIdx.x == 0 && bad) a.infeasible[b] = 1;
 }
 
-template <bool WIDE>
+template <bool WIDE, bool SPEC>
 cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
     const size_t n0r = (a.n0 + 31) & ~31;
     const size_t RsS = a.Rs < RTPL ? a.Rs : RTPL;
@@ -969,24 +990,45 @@ cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
         cv_set_error("complete clipping: input dimension too large for the shared-memory row cache");
         return CV_EUNSUPPORTED;
     }
-    CV_CUDA(cudaFuncSetAttribute(k_complete<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CV_CUDA(cudaFuncSetAttribute(k_complete<WIDE, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per = 0;
     CV_CUDA(cudaGetDevice(&dev));
     CV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_complete<WIDE>, nw * 32, smem));
+    CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_complete<WIDE, SPEC>, nw * 32, smem));
     if (per < 1) per = 1;
-    k_complete<WIDE><<<sms * per, nw * 32, smem, st>>>(a);
+    k_complete<WIDE, SPEC><<<sms * per, nw * 32, smem, st>>>(a);
     CV_LAUNCH_CHECK("k_complete");
     ++*launches;
     return CV_OK;
 }
 
+template <bool SPEC>
 cv_status launch_cc(const CCArgs& a, int* launches, cudaStream_t st) {
     if (a.Rs > RTPL) {
-        cv_status s = launch_cc_one<true>(a, launches, st);
+        cv_status s = launch_cc_one<true, SPEC>(a, launches, st);
         if (s) return s;
     }
-    return launch_cc_one<false>(a, launches, st);
+    return launch_cc_one<false, SPEC>(a, launches, st);
+}
+
+// spec-plane mode: magnitude scale of every final plane against its subdomain's clipped box,
+// sum_j |A_j| max(|lo_j|, |hi_j|) + |c| rounded up (the error pad of the dual value)
+__global__ void k_spec_scale(int m, int n0, const float* A, const float* c, const float* lo, const float* hi,
+                             float* sscale) {
+    const size_t o = blockIdx.x;  // b * m + r
+    const size_t b = o / (size_t)m;
+    double mag = 0.0;
+    for (int j = threadIdx.x; j < n0; j += blockDim.x)
+        mag += (double)fabsf(A[o * n0 + j]) * (double)fmaxf(fabsf(lo[b * n0 + j]), fabsf(hi[b * n0 + j]));
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        sscale[o] = __double2float_ru((t + fabs((double)c[o])) * (1.0 + 1e-12));
+    }
 }
 
 }  // namespace
@@ -1020,6 +1062,7 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     a.B = in->B; a.U = cache->U; a.n0 = cache->n0; a.H = cache->H; a.Rmax = lay->Rmax; a.sweeps = opt->sweeps;
     a.Rs = lay->Rmax < RMAX_CC ? lay->Rmax : RMAX_CC;
     for (int i = 0; i < 3; ++i) a.tpi[i] = cache->cc_items[i];
+    a.spec = 0; a.m = 0; a.sA = nullptr; a.sc = nullptr; a.sscale = nullptr; a.slower = nullptr;
     a.rowflag = (const int8_t*)(ws + lay->rowflag);
     a.lA = cache->lA; a.lc = cache->lc; a.uA = cache->uA; a.uc = cache->uc;
     a.slot_of = cache->slot_of; a.pscale = cache->pscale;
@@ -1053,9 +1096,62 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     k_cc_scan<<<1, 1024, 0, st>>>(a);
     CV_LAUNCH_CHECK("k_cc_scan");
     *launches += 3;  // prep, scan, post
-    cv_status s = launch_cc(a, launches, st);
+    cv_status s = launch_cc<false>(a, launches, st);
     if (s) return s;
     k_cc_post<<<in->B, 256, 0, st>>>(a);
     CV_LAUNCH_CHECK("k_cc_post");
     return CV_OK;
+}
+
+cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                              const cv_options* opt, const cv_ws_layout* lay, char* ws, float* sscale,
+                              int* launches, cudaStream_t st) {
+    (void)net;
+    if (opt->sweeps <= 0 || lay->Rmax == 0 || in->B == 0 || in->m == 0) return CV_OK;
+    if (lay->Rmax > RMAX_CC) {
+        cv_set_error("spec clipping: more than 32 constraint rows per subdomain are not supported");
+        return CV_EUNSUPPORTED;
+    }
+    CCArgs a;
+    memset(&a, 0, sizeof(a));
+    a.B = in->B; a.U = cache->U; a.n0 = cache->n0; a.H = cache->H; a.Rmax = lay->Rmax; a.sweeps = opt->sweeps;
+    a.Rs = lay->Rmax < RMAX_CC ? lay->Rmax : RMAX_CC;
+    for (int i = 0; i < 3; ++i) a.tpi[i] = cache->cc_items[i];
+    a.rowflag = (const int8_t*)(ws + lay->rowflag);
+    a.lA = cache->lA; a.lc = cache->lc; a.uA = cache->uA; a.uc = cache->uc;
+    a.slot_of = cache->slot_of; a.pscale = cache->pscale;
+    a.root_lo = cache->root_lo; a.root_hi = cache->root_hi;
+    a.split_off = in->split_off; a.split_ids = in->split_ids;
+    a.row_off = in->row_off; a.G = in->G; a.h = in->h;
+    a.tgt_off = nullptr; a.tgt_ids = nullptr;
+    a.lo = out->lo_clip; a.hi = out->hi_clip;
+    a.infeasible = out->infeasible; a.status = cache->net->status;
+    a.spec = 1; a.m = in->m;
+    a.sA = out->final_A; a.sc = out->final_c; a.sscale = sscale; a.slower = out->lower;
+    const size_t B = in->B, Rs = a.Rs, n0 = cache->n0;
+    char* p = ws + lay->cc;
+    a.wg = (float*)p; p += cv_align256(B * Rs * n0 * 4);
+    a.wrg = (float*)p; p += cv_align256(B * Rs * n0 * 4);
+    a.ww = (long long*)p; p += cv_align256(B * Rs * n0 * 8);
+    a.wT = (long long*)p; p += cv_align256(B * Rs * 8);
+    a.wW = (long long*)p; p += cv_align256(B * Rs * 8);
+    a.wSg = (double*)p; p += cv_align256(B * Rs * 8);
+    a.wh = (float*)p; p += cv_align256(B * Rs * 4);
+    a.wR = (int*)p; p += cv_align256(B * 4);
+    a.wcnt = (int*)p; p += cv_align256(B * 4);
+    a.order = (int*)p; p += cv_align256(B * 4);
+    a.ioff = (int*)p; p += cv_align256((B + 1) * 4);
+    a.nplaced = (int*)p;
+    a.wide = a.nplaced + 1;
+    p += 256;
+    a.ticket = (unsigned*)p;
+    k_spec_scale<<<(unsigned)(B * in->m), 256, 0, st>>>(in->m, (int)n0, out->final_A, out->final_c, out->lo_clip,
+                                                       out->hi_clip, sscale);
+    CV_LAUNCH_CHECK("k_spec_scale");
+    k_cc_prep<<<in->B, 256, 0, st>>>(a);
+    CV_LAUNCH_CHECK("k_cc_prep");
+    k_cc_scan<<<1, 1024, 0, st>>>(a);
+    CV_LAUNCH_CHECK("k_cc_scan");
+    *launches += 3;
+    return launch_cc<true>(a, launches, st);
 }

@@ -110,6 +110,10 @@ struct cv_ws_layout {
     int R, Rmax, ncb;  // rows of the spec backward, max constraint rows, column blocks
 };
 size_t cv_cc_workspace(int B, int Rmax, int n0);  // complete-clipping region (cv_complete.cu)
+// complete clipping of the spec rows' final planes (cv_complete.cu); sscale: [B x m] floats of scratch
+cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
+                              const cv_options* opt, const cv_ws_layout* lay, char* ws, float* sscale,
+                              int* launches, cudaStream_t st);
 cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
                      int max_rows, int precision, cv_ws_layout* lay);
 

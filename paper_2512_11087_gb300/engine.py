@@ -105,6 +105,17 @@ class Round:
                             stream)
         return self.out
 
+    def spec_clip(self, lo, hi, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, row_off=None, G=None,
+                  h=None, alpha=None, tgt_off=None, tgt_ids=None, stream=None):
+        """After run() on the same inputs (with want_final): complete clipping of the spec rows' final
+        planes (cv_spec_clip); raises out["lower"] and updates out["verified"] in place."""
+        bi = self._bi(lo, hi, C, t, l_in, u_in, split_off, split_ids, row_off, G, h, alpha, tgt_off, tgt_ids)
+        n = capi.cv_spec_clip_workspace(self.net.handle, self.net.cache, bi)
+        if getattr(self, "_sws", None) is None or self._sws.numel() < max(n, 256):
+            self._sws = torch.empty(max(n, 256), dtype=torch.uint8, device=self.ws.device)
+        capi.cv_spec_clip(self.net.handle, self.net.cache, bi, self.bo, self.opt, self._sws, n, stream)
+        return self.out
+
     def autotune(self, lo, hi, C, t, l_in=None, u_in=None, split_off=None, split_ids=None, row_off=None, G=None,
                  h=None, alpha=None, tgt_off=None, tgt_ids=None, stream=None):
         """Tunes complete clipping's work-item sizes on this batch (cv_autotune_cc); the sizes stay in

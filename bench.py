@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--relaxed", type=int, default=None, choices=[1, 2, 3],
                    help="relaxed clipping: 1 parallel (Algorithm 2, the workload's), 2 sequential (Algorithm 3), "
                         "3 sequential in the constraint-importance order")
+    p.add_argument("--spec-clip", action="store_true",
+                   help="time complete clipping of the spec rows' final planes (cv_spec_clip) after a round")
     p.add_argument("--input-bab", action="store_true",
                    help="time the input-BaB split step (cv_input_split) on the workload's bounded batch instead")
     p.add_argument("--no-autotune", action="store_true",
@@ -287,6 +289,59 @@ def run_input_split(args, cfg):
     net.close()
 
 
+# ---------------------------------------------------------------- complete clipping of the spec planes
+def run_spec_clip(args, cfg):
+    """Times cv_spec_clip (Algorithm 1 on the final plane of every unproven spec row) after a round of
+    the workload: each step re-runs the round untimed (fresh bounds), flushes the L2, then times the
+    spec clipping alone with CUDA events; reports the verified subdomains before and after."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
+    torch.cuda.set_device(0)
+    dims, B, kmin, kmax = cfg["dims"], cfg["B"], cfg["kmin"], cfg["kmax"]
+    layers = WL.he_mlp(dims, seed=0)
+    lo0, hi0 = WL.box(dims[0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    net.build_cache(lo0, hi0)
+    so, si = WL.draw_splits(net.read_cache()["ids"], B, kmin, kmax, seed=shard_seed(0))
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    C, t = WL.margin_spec(dims[-1])
+    m = C.shape[0]
+    rnd = E.Round(net, B, m, max_splits=kmax, relaxed=cfg["relaxed"], sweeps=cfg["sweeps"],
+                  precision=capi.CV_PREC_BF16X8, want_final=True)
+    d = E.to_dev
+    args_ = (d(lo), d(hi), d(C), d(t))
+    kw = dict(split_off=d(so), split_ids=d(si))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    times, before, after, raised = [], 0, 0, 0
+    for k in range(max(args.warmup, 3) + args.steps):
+        out = rnd.run(*args_, **kw)
+        torch.cuda.synchronize()
+        l0 = out["lower"].clone()
+        v0 = int(out["verified"].sum().item())
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rnd.spec_clip(*args_, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= max(args.warmup, 3):
+            times.append(e0.elapsed_time(e1))
+        before, after = v0, int(out["verified"].sum().item())
+        raised = int((out["lower"] > l0).sum().item())
+    ms = sum(times) / len(times)
+    line = dict(metric="subdomains spec-clipped per second", value=B / (ms * 1e-3), unit="subdomains/s", n_gpus=1,
+                steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=workload_desc(cfg, args.config) + "; then complete clipping of the final "
+                            "planes of the unproven spec rows (same sweeps)",
+                            spec_rows=B * m, spec_rows_raised=raised, verified_before=before, verified_after=after,
+                            l2="flushed (256 MiB write) before every timed step"))
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse_args()
@@ -304,6 +359,9 @@ def main():
         return
     if args.input_bab:
         run_input_split(args, cfg)
+        return
+    if args.spec_clip:
+        run_spec_clip(args, cfg)
         return
 
     import numpy as np

@@ -474,6 +474,93 @@ int orc_input_split(int B, int n0, int m, const float* lo, const float* hi, cons
 }
 
 /* ------------------------------------------------------------------------- */
+/* BaBSR intercept score of a cached neuron (Appendix, neuron selection       */
+/* heuristic): for an unstable neuron (mask 0, l < 0 < u)                     */
+/*   score = max(0,-l) max(0,u) / (u - l) * w,  w = max(0, -weight) or 1      */
+/* (the intercept of the upper ReLU line times the weight of the neuron in    */
+/* the bound); -1 for any other neuron.  FP32, in this order, so that the GPU */
+/* takes the same decisions.                                                  */
+/* ------------------------------------------------------------------------- */
+static float babsr_score(float l, float u, signed char mask, const float* weight, long o) {
+    if (mask != 0 || !(l < 0.0f) || !(u > 0.0f)) return -1.0f;
+    float p = fmaxf(0.0f, -l) * fmaxf(0.0f, u);
+    float s = p / (u - l);
+    if (weight) s = s * fmaxf(0.0f, -weight[o]);
+    return s;
+}
+
+/* Activation BaB split step (Algorithm 5: Domain_Filter, Batch_Split on one  */
+/* ReLU).  Verified or infeasible parents are dropped; a kept parent branches */
+/* on its highest-scoring unstable cached neuron (the first slot among equal  */
+/* scores); child 2k gets the split z <= 0 (code -(id+1)), child 2k+1 z >= 0  */
+/* (+(id+1)), after the parent's own codes; both inherit the parent's box and */
+/* cached bounds.  A kept parent with no unstable cached neuron gets no       */
+/* children and stuck[b] = 1.  Returns the number of children.                */
+int orc_activation_split(int B, int U, int n0, const int* ids, const int* split_off, const int* split_ids,
+                         const float* lo, const float* hi, const float* l, const float* u,
+                         const signed char* mask, const float* weight, const unsigned char* verified,
+                         const unsigned char* infeasible, int* split_off_out, int* split_ids_out,
+                         float* lo_out, float* hi_out, float* l_out, float* u_out, int* parent, int* branched,
+                         unsigned char* stuck) {
+    int n = 0, ns = 0;
+    split_off_out[0] = 0;
+    for (int b = 0; b < B; ++b) {
+        stuck[b] = 0;
+        if (verified[b] || infeasible[b]) continue;
+        int best = -1;
+        float bs = -1.0f;
+        for (int c = 0; c < U; ++c) {
+            long o = (long)b * U + c;
+            float sc = babsr_score(l[o], u[o], mask[o], weight, o);
+            if (sc > bs) { bs = sc; best = c; }  /* unstable scores are >= 0 > -1: the first maximum */
+        }
+        if (best < 0) { stuck[b] = 1; continue; }
+        int k0 = split_off ? split_off[b] : 0, k1 = split_off ? split_off[b + 1] : 0;
+        for (int side = 0; side < 2; ++side) {
+            for (int q = k0; q < k1; ++q) split_ids_out[ns++] = split_ids[q];
+            split_ids_out[ns++] = side ? ids[best] + 1 : -(ids[best] + 1);
+            split_off_out[n + 1] = ns;
+            memcpy(lo_out + (long)n * n0, lo + (long)b * n0, sizeof(float) * n0);
+            memcpy(hi_out + (long)n * n0, hi + (long)b * n0, sizeof(float) * n0);
+            memcpy(l_out + (long)n * U, l + (long)b * U, sizeof(float) * U);
+            memcpy(u_out + (long)n * U, u + (long)b * U, sizeof(float) * U);
+            parent[n] = b;
+            branched[n] = best;
+            ++n;
+        }
+    }
+    return n;
+}
+
+/* Top-k targets for complete clipping (Algorithms 4/5 Top-K_Heuristic with  */
+/* the BaBSR score): per subdomain and hidden layer, the k unstable cached     */
+/* neurons of highest score (a neuron outranks another with a higher score,   */
+/* or an equal one and a lower slot), listed in slot order as a CSR of slots. */
+/* layer_of[c]: the hidden layer of slot c.  Returns the number of entries.   */
+int orc_select_targets(int B, int U, const int* layer_of, const float* l, const float* u, const signed char* mask,
+                       const float* weight, int k, int* tgt_off, int* tgt_ids) {
+    int n = 0;
+    tgt_off[0] = 0;
+    for (int b = 0; b < B; ++b) {
+        for (int c = 0; c < U; ++c) {
+            long o = (long)b * U + c;
+            float sc = babsr_score(l[o], u[o], mask[o], weight, o);
+            if (sc < 0.0f) continue;
+            int rank = 0;
+            for (int c2 = 0; c2 < U; ++c2) {
+                if (layer_of[c2] != layer_of[c] || c2 == c) continue;
+                long o2 = (long)b * U + c2;
+                float s2 = babsr_score(l[o2], u[o2], mask[o2], weight, o2);
+                if (s2 > sc || (s2 == sc && c2 < c)) ++rank;
+            }
+            if (rank < k) tgt_ids[n++] = c;
+        }
+        tgt_off[b + 1] = n;
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Algorithm 1 (coordinate ascent over several constraints), repeated for     */
 /* `sweeps` passes.  Minimises a.x + c over the box subject to G x + h <= 0   */
 /* through the dual  max_{beta>=0} (a + beta^T G).xhat - |a + beta^T G|.eps   */

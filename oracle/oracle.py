@@ -50,6 +50,10 @@ def _load():
         _lib.orc_row_order.restype = None
         _lib.orc_input_split.argtypes = [I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_input_split.restype = I
+        _lib.orc_activation_split.argtypes = [I, I, I] + [P] * 20
+        _lib.orc_activation_split.restype = I
+        _lib.orc_select_targets.argtypes = [I, I, P, P, P, P, P, I, P, P]
+        _lib.orc_select_targets.restype = I
         _lib.orc_complete_clip.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
         _lib.orc_complete_clip.restype = D
         _lib.orc_complete_clip_f32.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
@@ -236,6 +240,60 @@ def input_split(lo, hi, final_A, final_c, lower, verified, infeasible):
                             pf(ro), pf(G), pf(h), pf(par))
     nr = int(ro[n])
     return dict(lo=lo2[:n], hi=hi2[:n], row_off=ro[:n + 1], G=G[:nr], h=h[:nr], parent=par[:n])
+
+
+def _pf(x):
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def activation_split(ids, split_off, split_ids, lo, hi, l, u, mask, weight, verified, infeasible):
+    """Activation-BaB split step (Algorithm 5: Domain_Filter, Batch_Split on the highest BaBSR score).
+    Returns dict(split_off, split_ids, lo, hi, l, u, parent, branched [children], stuck [B])."""
+    lib = _load()
+    f32 = lambda x: np.ascontiguousarray(np.asarray(x, np.float32))
+    i32 = lambda x: np.ascontiguousarray(np.asarray(x, np.int32))
+    lo, hi, l, u = f32(lo), f32(hi), f32(l), f32(u)
+    B, n0 = lo.shape
+    U = l.shape[1]
+    mask = np.ascontiguousarray(np.asarray(mask, np.int8))
+    ver, inf = (np.ascontiguousarray(np.asarray(x, np.uint8)) for x in (verified, infeasible))
+    so = i32(split_off) if split_off is not None else np.zeros(B + 1, np.int32)
+    si = i32(split_ids) if split_ids is not None and len(split_ids) else np.zeros(1, np.int32)
+    w = f32(weight) if weight is not None else None
+    cap = 2 * max(B, 1)
+    so2 = np.zeros(2 * B + 1, np.int32)
+    si2 = np.zeros(2 * (int(so[-1]) + B) + 1, np.int32)
+    lo2, hi2 = np.zeros((cap, n0), np.float32), np.zeros((cap, n0), np.float32)
+    l2, u2 = np.zeros((cap, U), np.float32), np.zeros((cap, U), np.float32)
+    par, br = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+    stuck = np.zeros(max(B, 1), np.uint8)
+    n = lib.orc_activation_split(B, U, n0, _pf(i32(ids)), _pf(so), _pf(si), _pf(lo), _pf(hi), _pf(l), _pf(u),
+                                 _pf(mask), _pf(w) if w is not None else None, _pf(ver), _pf(inf), _pf(so2),
+                                 _pf(si2), _pf(lo2), _pf(hi2), _pf(l2), _pf(u2), _pf(par), _pf(br), _pf(stuck))
+    return dict(split_off=so2[:n + 1], split_ids=si2[:so2[n]], lo=lo2[:n], hi=hi2[:n], l=l2[:n], u=u2[:n],
+                parent=par[:n], branched=br[:n], stuck=stuck[:B])
+
+
+def layer_of_slots(net, ids):
+    """Hidden layer (1-based) of every cache slot, from the global ids (hidden layer i holds ids
+    hoff_i .. hoff_i + n_i - 1)."""
+    hoff = np.cumsum([0] + list(net.dims[1:-1]))
+    return (np.searchsorted(hoff, np.asarray(ids), side="right")).astype(np.int32)
+
+
+def select_targets(layer_of, l, u, mask, weight, k):
+    """Top-k BaBSR targets per subdomain and hidden layer, in slot order (CSR)."""
+    lib = _load()
+    l = np.ascontiguousarray(np.asarray(l, np.float32))
+    u = np.ascontiguousarray(np.asarray(u, np.float32))
+    mask = np.ascontiguousarray(np.asarray(mask, np.int8))
+    B, U = l.shape
+    w = np.ascontiguousarray(np.asarray(weight, np.float32)) if weight is not None else None
+    off = np.zeros(B + 1, np.int32)
+    ids = np.zeros(max(B * U, 1), np.int32)
+    n = lib.orc_select_targets(B, U, _pf(np.ascontiguousarray(layer_of, dtype=np.int32)), _pf(l), _pf(u), _pf(mask),
+                               _pf(w) if w is not None else None, int(k), _pf(off), _pf(ids))
+    return off, ids[:n]
 
 
 def complete_clip(a, c, G, h, lo, hi, sweeps):

@@ -398,6 +398,47 @@ cv_status cv_input_split(int B, int n0, int m, const float* lo, const float* hi,
                          float* h, int* parent, int* n_children, void* workspace, size_t workspace_bytes,
                          void* stream);
 
+/* ---------------------------------------------------------------- activation branch and bound */
+
+/* BaBSR intercept score of a cached neuron c of a subdomain (Appendix, neuron selection heuristic):
+ * -1 unless the neuron is unstable (mask 0, l < 0 < u); else
+ *   max(0, -l) * max(0, u) / (u - l) * w,  w = max(0, -weight[c]) (w = 1 when weight is NULL)
+ * in FP32, in this order: the intercept of the neuron's upper ReLU line times its weight in the
+ * bound (for instance the mean over the spec rows of its coefficient in the final linear bound).
+ *
+ * One activation-BaB split step (Algorithm 5: Domain_Filter, Batch_Split).  For B bounded parents:
+ * a verified or infeasible parent is dropped; a kept parent branches on its highest-scoring cached
+ * neuron (the lowest slot among equal scores) and gives children 2k (split z <= 0, code -(id+1))
+ * and 2k + 1 (z >= 0, code +(id+1)), each with the parent's split codes first, the parent's
+ * (clipped) box and its cached bounds (to pass as l_in / u_in).  A kept parent without any
+ * unstable cached neuron gets no children and stuck = 1.
+ * Inputs (device): split_off [B + 1] / split_ids (may be NULL: no splits); lo, hi [B x n_0];
+ *   l, u [B x U], mask [B x U]; weight [B x U] or NULL; verified, infeasible [B].
+ * Outputs (device, caller-allocated for the worst case): split_off_out [2B + 1]; split_ids_out
+ *   [2 (split_off[B] + B)]; lo_out, hi_out [2B x n_0]; l_out, u_out [2B x U]; parent, branched
+ *   [2B] (parent index, branching slot); stuck [B]; n_children [1].
+ * workspace: cv_activation_split_workspace() bytes.  Errors: CV_EINVAL for a null pointer (B > 0)
+ * or a cache without unstable neurons. */
+cv_status cv_activation_split_workspace(int B, size_t* bytes);
+cv_status cv_activation_split(const cv_net* net, const cv_cache* cache, int B, const int* split_off,
+                              const int* split_ids, const float* lo, const float* hi, const float* l,
+                              const float* u, const int8_t* mask, const float* weight, const uint8_t* verified,
+                              const uint8_t* infeasible, int* split_off_out, int* split_ids_out, float* lo_out,
+                              float* hi_out, float* l_out, float* u_out, int* parent, int* branched,
+                              uint8_t* stuck, int* n_children, void* workspace, size_t workspace_bytes,
+                              void* stream);
+
+/* Top-k targets for complete clipping (Algorithms 4 and 5, Top-K_Heuristic, with the score
+ * above): per subdomain and hidden layer, the k unstable cached neurons of highest score (a higher
+ * score first, then the lower slot), listed per subdomain in slot order as a CSR of cache slots to
+ * pass as tgt_off / tgt_ids.  Inputs (device): l, u, mask [B x U]; weight [B x U] or NULL.  Outputs
+ * (device): tgt_off [B + 1]; tgt_ids [B x U] at most.  k >= 0.  workspace:
+ * cv_select_targets_workspace() bytes.  CV_EUNSUPPORTED above 17066 cached neurons. */
+cv_status cv_select_targets_workspace(int B, int U, size_t* bytes);
+cv_status cv_select_targets(const cv_net* net, const cv_cache* cache, int B, const float* l, const float* u,
+                            const int8_t* mask, const float* weight, int k, int* tgt_off, int* tgt_ids,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Size of the library's fixed device scratch array used by cv_relaxed_clip_static. */

@@ -108,6 +108,10 @@ def load():
         "cv_autotune_cc": ([P, P, P, P, P, P, ctypes.c_size_t, P, P, P], I),
         "cv_spec_clip_workspace": ([P, P, P, P], I),
         "cv_spec_clip": ([P, P, P, P, P, P, ctypes.c_size_t, P], I),
+        "cv_activation_split_workspace": ([I, P], I),
+        "cv_activation_split": ([P, P, I] + [P] * 21 + [ctypes.c_size_t, P], I),
+        "cv_select_targets_workspace": ([I, I, P], I),
+        "cv_select_targets": ([P, P, I, P, P, P, P, I, P, P, P, ctypes.c_size_t, P], I),
         "cv_input_split_workspace": ([I, P], I),
         "cv_input_split": ([I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P], I),
     }
@@ -126,7 +130,9 @@ def exported_symbols():
                         "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
                         "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy",
                         "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc", "cv_input_split_workspace",
-                        "cv_input_split", "cv_spec_clip_workspace", "cv_spec_clip")]
+                        "cv_input_split", "cv_spec_clip_workspace", "cv_spec_clip",
+                        "cv_activation_split_workspace", "cv_activation_split", "cv_select_targets_workspace",
+                        "cv_select_targets")]
 
 
 def _check(st):
@@ -303,6 +309,37 @@ def cv_spec_clip(net, cache, bi, bo, opt, workspace, workspace_bytes, stream=Non
     """Complete clipping of the spec rows' final planes after a round (see the header)."""
     _check(load().cv_spec_clip(net, cache, ctypes.byref(bi), ctypes.byref(bo), ctypes.byref(opt), ptr(workspace),
                                int(workspace_bytes), stream_ptr(stream)))
+
+
+def cv_activation_split_workspace(B):
+    n = ctypes.c_size_t()
+    _check(load().cv_activation_split_workspace(int(B), ctypes.byref(n)))
+    return n.value
+
+
+def cv_activation_split(net, cache, B, split_off, split_ids, lo, hi, l, u, mask, weight, verified, infeasible,
+                        split_off_out, split_ids_out, lo_out, hi_out, l_out, u_out, parent, branched, stuck,
+                        n_children, workspace, workspace_bytes, stream=None):
+    """Activation-BaB split step (Algorithm 5, BaBSR branching); device tensors (see the header)."""
+    _check(load().cv_activation_split(net, cache, int(B), ptr(split_off), ptr(split_ids), ptr(lo), ptr(hi), ptr(l),
+                                      ptr(u), ptr(mask), ptr(weight), ptr(verified), ptr(infeasible),
+                                      ptr(split_off_out), ptr(split_ids_out), ptr(lo_out), ptr(hi_out), ptr(l_out),
+                                      ptr(u_out), ptr(parent), ptr(branched), ptr(stuck), ptr(n_children),
+                                      ptr(workspace), int(workspace_bytes), stream_ptr(stream)))
+
+
+def cv_select_targets_workspace(B, U):
+    n = ctypes.c_size_t()
+    _check(load().cv_select_targets_workspace(int(B), int(U), ctypes.byref(n)))
+    return n.value
+
+
+def cv_select_targets(net, cache, B, l, u, mask, weight, k, tgt_off, tgt_ids, workspace, workspace_bytes,
+                      stream=None):
+    """Top-k BaBSR targets per subdomain and hidden layer (CSR of cache slots)."""
+    _check(load().cv_select_targets(net, cache, int(B), ptr(l), ptr(u), ptr(mask), ptr(weight), int(k),
+                                    ptr(tgt_off), ptr(tgt_ids), ptr(workspace), int(workspace_bytes),
+                                    stream_ptr(stream)))
 
 
 def cv_input_split_workspace(B):

@@ -215,3 +215,44 @@ def input_split(lo, hi, final_A, final_c, lower, verified, infeasible, stream=No
     nr = int(ro[n].item()) if n else 0
     return dict(lo=lo2[:n], hi=hi2[:n], row_off=ro[:n + 1], G=G[:nr], h=h[:nr], parent=par[:n])
 
+
+def activation_split(net: Net, split_off, split_ids, lo, hi, l, u, mask, verified, infeasible, weight=None,
+                     stream=None):
+    """Activation-BaB split step on device tensors (cv_activation_split): dict(split_off, split_ids, lo, hi,
+    l, u, parent, branched [children], stuck [B]) as device tensors."""
+    B, n0 = lo.shape
+    U = l.shape[1]
+    dev = lo.device
+    nsp = int(split_off[-1].item()) if split_off is not None and B else 0
+    f32 = dict(dtype=torch.float32, device=dev)
+    i32 = dict(dtype=torch.int32, device=dev)
+    cap = 2 * max(B, 1)
+    so2 = torch.zeros(2 * B + 1, **i32)
+    si2 = torch.zeros(2 * (nsp + B) + 1, **i32)
+    lo2, hi2 = torch.empty(cap, n0, **f32), torch.empty(cap, n0, **f32)
+    l2, u2 = torch.empty(cap, U, **f32), torch.empty(cap, U, **f32)
+    par, br = torch.empty(cap, **i32), torch.empty(cap, **i32)
+    stuck = torch.zeros(max(B, 1), dtype=torch.uint8, device=dev)
+    nch = torch.zeros(1, **i32)
+    wsb = capi.cv_activation_split_workspace(B)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+    capi.cv_activation_split(net.handle, net.cache, B, split_off, split_ids, lo, hi, l, u, mask, weight, verified,
+                             infeasible, so2, si2, lo2, hi2, l2, u2, par, br, stuck, nch, ws, wsb, stream)
+    n = int(nch.item())
+    ns = int(so2[n].item()) if n else 0
+    return dict(split_off=so2[:n + 1], split_ids=si2[:ns], lo=lo2[:n], hi=hi2[:n], l=l2[:n], u=u2[:n],
+                parent=par[:n], branched=br[:n], stuck=stuck[:B])
+
+
+def select_targets(net: Net, l, u, mask, k, weight=None, stream=None):
+    """Top-k BaBSR targets per subdomain and hidden layer (cv_select_targets): (tgt_off, tgt_ids)."""
+    B, U = l.shape
+    dev = l.device
+    off = torch.zeros(B + 1, dtype=torch.int32, device=dev)
+    ids = torch.empty(max(B * U, 1), dtype=torch.int32, device=dev)
+    wsb = capi.cv_select_targets_workspace(B, U)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+    capi.cv_select_targets(net.handle, net.cache, B, l, u, mask, weight, k, off, ids, ws, wsb, stream)
+    n = int(off[-1].item())
+    return off, ids[:n]
+

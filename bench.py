@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--relaxed", type=int, default=None, choices=[1, 2, 3],
                    help="relaxed clipping: 1 parallel (Algorithm 2, the workload's), 2 sequential (Algorithm 3), "
                         "3 sequential in the constraint-importance order")
+    p.add_argument("--activation-bab", action="store_true",
+                   help="time the activation-BaB split (cv_activation_split) and top-20 targets (cv_select_targets)")
     p.add_argument("--spec-clip", action="store_true",
                    help="time complete clipping of the spec rows' final planes (cv_spec_clip) after a round")
     p.add_argument("--input-bab", action="store_true",
@@ -342,6 +344,100 @@ def run_spec_clip(args, cfg):
     net.close()
 
 
+# ---------------------------------------------------------------- activation-BaB steps
+def run_activation_bab(args, cfg):
+    """Times the activation-BaB split step and the top-20 target selection on the outputs of one
+    round of the workload (L2 flushed before every timed call); HBM roofline of the split with the
+    bytes it must move for this batch."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
+    torch.cuda.set_device(0)
+    dims, B, kmin, kmax = cfg["dims"], cfg["B"], cfg["kmin"], cfg["kmax"]
+    layers = WL.he_mlp(dims, seed=0)
+    lo0, hi0 = WL.box(dims[0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    U = net.build_cache(lo0, hi0)
+    so, si = WL.draw_splits(net.read_cache()["ids"], B, kmin, kmax, seed=shard_seed(0))
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    C, t = WL.margin_spec(dims[-1])
+    m, n0 = C.shape[0], dims[0]
+    rnd = E.Round(net, B, m, max_splits=kmax, relaxed=cfg["relaxed"], sweeps=cfg["sweeps"],
+                  precision=capi.CV_PREC_BF16X8)
+    d = E.to_dev
+    dso, dsi = d(so), d(si)
+    out = rnd.run(d(lo), d(hi), d(C), d(t), split_off=dso, split_ids=dsi)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        ts = []
+        for k in range(max(args.warmup, 3) + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= max(args.warmup, 3):
+                ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts), res
+
+    # outputs allocated once: the timed calls are the library's alone
+    f32 = dict(dtype=torch.float32, device="cuda")
+    i32 = dict(dtype=torch.int32, device="cuda")
+    so2, si2 = torch.zeros(2 * B + 1, **i32), torch.zeros(2 * (len(si) + B) + 1, **i32)
+    lo2, hi2 = torch.empty(2 * B, n0, **f32), torch.empty(2 * B, n0, **f32)
+    l2, u2 = torch.empty(2 * B, U, **f32), torch.empty(2 * B, U, **f32)
+    par, br = torch.empty(2 * B, **i32), torch.empty(2 * B, **i32)
+    stuck = torch.zeros(B, dtype=torch.uint8, device="cuda")
+    nch = torch.zeros(1, **i32)
+    wsa = capi.cv_activation_split_workspace(B)
+    wa = torch.empty(max(wsa, 256), dtype=torch.uint8, device="cuda")
+    toff, tids = torch.zeros(B + 1, **i32), torch.empty(B * U, **i32)
+    wst = capi.cv_select_targets_workspace(B, U)
+    wt = torch.empty(max(wst, 256), dtype=torch.uint8, device="cuda")
+    split = lambda: capi.cv_activation_split(net.handle, net.cache, B, dso, dsi, out["lo_clip"], out["hi_clip"],
+                                             out["l"], out["u"], out["mask"], None, out["verified"],
+                                             out["infeasible"], so2, si2, lo2, hi2, l2, u2, par, br, stuck, nch, wa,
+                                             wsa, stream)
+    topk = lambda: capi.cv_select_targets(net.handle, net.cache, B, out["l"], out["u"], out["mask"], None, 20, toff,
+                                          tids, wt, wst, stream)
+    ms_split, _ = timed(split)
+    ms_topk, _ = timed(topk)
+    K = int(nch.item()) // 2
+    kept = np.zeros(B, bool)
+    kept[par[:2 * K].cpu().numpy()] = True
+    nsp = np.diff(so)
+    # bytes the split must move: every parent's flags; per kept parent its bounds and mask (the
+    # scores), box and split codes (read once), and two children's boxes, bounds, split codes and
+    # offsets, parent and branching slot
+    kp = int(kept.sum())
+    byts = B * 2 + kp * (9 * U + 8 * n0) + int(np.sum(nsp[kept])) * 4 \
+        + 2 * kp * (8 * n0 + 8 * U + 12) + 2 * int(np.sum(nsp[kept] + 1)) * 4
+    peak = 6800.0
+    try:
+        peak = float(json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                 "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    ach = byts / (ms_split * 1e-3) / 1e9
+    line = dict(metric="parent subdomains branched per second (activation BaB)", value=B / (ms_split * 1e-3),
+                unit="subdomains/s", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=ms_split,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=workload_desc(cfg, args.config) + "; one round, then the split and the "
+                            "top-20 targets per hidden layer", cached_neurons=U, kept_parents=K,
+                            topk_ms=ms_topk, topk_targets=int(toff[-1].item()),
+                            l2="flushed (256 MiB write) before every timed call"),
+                roofline=dict(bound="hbm", kernel="cv_activation_split (k_act_mark, k_scan2, k_act_write)",
+                              achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=None,
+                              alg_bytes_per_step=byts),
+                gpu_launches=3 * args.steps)
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse_args()
@@ -362,6 +458,9 @@ def main():
         return
     if args.spec_clip:
         run_spec_clip(args, cfg)
+        return
+    if args.activation_bab:
+        run_activation_bab(args, cfg)
         return
 
     import numpy as np

@@ -1012,22 +1012,23 @@ cv_status launch_cc(const CCArgs& a, int* launches, cudaStream_t st) {
 }
 
 // spec-plane mode: magnitude scale of every final plane against its subdomain's clipped box,
-// sum_j |A_j| max(|lo_j|, |hi_j|) + |c| rounded up (the error pad of the dual value)
+// sum_j |A_j| max(|lo_j|, |hi_j|) + |c|, an upper bound (FP32, every operation rounded up: the
+// terms are non-negative) for the error pad of the dual value
 __global__ void k_spec_scale(int m, int n0, const float* A, const float* c, const float* lo, const float* hi,
                              float* sscale) {
     const size_t o = blockIdx.x;  // b * m + r
     const size_t b = o / (size_t)m;
-    double mag = 0.0;
+    float mag = 0.f;
     for (int j = threadIdx.x; j < n0; j += blockDim.x)
-        mag += (double)fabsf(A[o * n0 + j]) * (double)fmaxf(fabsf(lo[b * n0 + j]), fabsf(hi[b * n0 + j]));
-    __shared__ double red[32];
-    for (int off = 16; off > 0; off >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, off);
+        mag = __fmaf_ru(fabsf(A[o * n0 + j]), fmaxf(fabsf(lo[b * n0 + j]), fabsf(hi[b * n0 + j])), mag);
+    __shared__ float red[32];
+    for (int off = 16; off > 0; off >>= 1) mag = __fadd_ru(mag, __shfl_xor_sync(0xffffffffu, mag, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        sscale[o] = __double2float_ru((t + fabs((double)c[o])) * (1.0 + 1e-12));
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = __fadd_ru(t, red[w]);
+        sscale[o] = __fadd_ru(t, fabsf(c[o]));
     }
 }
 

@@ -11,7 +11,8 @@
 // lists, boxes and cached bounds).  cv_select_targets (three launches): k_topk_mark (block per
 // subdomain: scores in shared memory, the unstable slots compacted in slot order so that every
 // layer's are contiguous, each ranked among its layer's), a one-block scan, k_topk_write (ordered
-// compaction into the CSR).  All of it streams the per-subdomain arrays once: HBM-bound.
+// compaction into the CSR).  The ranking gives each unstable slot a warp, whose lanes compare it
+// with 32 slots of its layer at a time.  The split streams the per-subdomain arrays once: HBM-bound.
 #include "cv_internal.cuh"
 
 #include <string>
@@ -191,18 +192,28 @@ __global__ void k_topk_mark(int U, int k, NetLayers nl, const int* ids, const fl
         __syncthreads();
     }
     const int n = s_n;
-    // rank of every unstable slot among its layer's (contiguous in the list: slots follow layers)
-    int mine = 0;
+    // first and last list position of every layer (the list follows the slots, so the layers)
+    __shared__ int s_first[CV_MAX_LAYERS + 1], s_last[CV_MAX_LAYERS + 1];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int li = lay[i];
+        if (i == 0 || lay[i - 1] != li) s_first[li] = i;
+        if (i == n - 1 || lay[i + 1] != li) s_last[li] = i;
+    }
+    __syncthreads();
+    // a warp per unstable slot: its lanes count the slots of the same layer that outrank it, 32 at a
+    // time, until k are found
+    int mine = 0;
+    for (int i = warp; i < n; i += nw) {
         const int c = lst[i], li = lay[i];
         const float s = sc[c];
-        int a = i, z = i;
-        while (a > 0 && lay[a - 1] == li) --a;
-        while (z + 1 < n && lay[z + 1] == li) ++z;
+        const int a = s_first[li], z = s_last[li];
         int rank = 0;
-        for (int j = a; j <= z && rank < k; ++j)
-            if (j != i && outranks(sc[lst[j]], lst[j], s, c)) ++rank;
-        if (rank < k) { sel[(size_t)b * U + c] = 1; ++mine; }
+        for (int j0 = a; j0 <= z && rank < k; j0 += 32) {
+            const int j = j0 + lane;
+            const bool o = j <= z && j != i && outranks(sc[lst[j]], lst[j], s, c);
+            rank += __popc(__ballot_sync(0xffffffffu, o));
+        }
+        if (rank < k && lane == 0) { sel[(size_t)b * U + c] = 1; ++mine; }
     }
     atomicAdd(&s_cnt, mine);
     __syncthreads();

@@ -16,7 +16,7 @@
  * Weights are passed concatenated: W^(i) is dims[i] x dims[i-1] row-major.
  * Hidden neurons get a global id: hoff[i] + j for neuron j of hidden layer i.
  *
- * Conventions fixed where the paper leaves room (each is a reading listed in the design doc):
+ * Conventions fixed where the paper leaves room (readings of the paper, not its words):
  *  - every linear constraint is a row  g.x + h <= 0  (Theorem 2 and Algorithm 2's update);
  *  - an activation split  z_j >= 0  gives the row  -Abar_j.x - cbar_j <= 0,  a split
  *    z_j <= 0  gives  Aund_j.x + cund_j <= 0  (Section 3.4, "validate" implication);

@@ -44,7 +44,7 @@ typedef int cv_status;
 #define CV_ECUDA        4  /* CUDA runtime error (message in cv_last_error) */
 #define CV_ETIMEOUT     5  /* a bounded device wait ran out */
 #define CV_ENOMEM       6  /* device allocation failed */
-#define CV_EUNSUPPORTED 7  /* feature not available in this build / for this net */
+#define CV_EUNSUPPORTED 7  /* feature not supported by the library, or not for this net / these sizes */
 #define CV_EWORKSPACE   8  /* caller workspace too small */
 #define CV_EDEVICE      9  /* a kernel reported a bad input (see cv_device_status) */
 

@@ -616,7 +616,7 @@ def main():
         if vs_fp32 is not None:
             line["vs_fp32_path"] = vs_fp32
         if world == 1 and not args.no_cpu_baseline:
-            n, cores = pick_sample(cfg, 12.0)
+            n, cores = pick_sample(cfg, 20.0)  # the pick overestimates the cost: about 10-15 s
             rate, dt, cores = oracle_sample_rate(cfg, n, offset=3)
             line["cpu_baseline"] = dict(value=rate, unit="subdomains/s", cores=cores, kind="oracle",
                                         sample=f"{n} subdomains of the benchmark batch (evenly spaced), FP64 C "

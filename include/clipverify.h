@@ -150,6 +150,13 @@ void      cv_timer_destroy(cv_timer* timer);
  * time in milliseconds, launches (may be NULL) its kernel launch count, cc_steps (may be NULL)
  * the row steps of Algorithm 1 it executed. */
 cv_status cv_timer_read(cv_timer* timer, float* ms, int* launches, long long* cc_steps);
+/* Decision counters of the last timed call's complete clipping (Algorithm 1 with two or more rows):
+ * stats[0] row steps whose FP32 breakpoint decision was certified (re-decided on float-float
+ * breakpoints, see cv_bound_batch), stats[1] of them with more than one candidate breakpoint,
+ * stats[2] with a widened window, stats[3] left with the FP32 decision because it could not be
+ * settled (still a valid multiplier), stats[4] of those with more than 64 candidates.
+ * Synchronous. */
+cv_status cv_timer_read_cc(cv_timer* timer, long long stats[5]);
 
 /* ---------------------------------------------------------------- one BaB round */
 
@@ -252,6 +259,14 @@ cv_status cv_bound_batch_workspace(const cv_net* net, const cv_cache* cache,
 
 /* One round: constraint rows from splits and extra rows, pre-check, relaxed clipping,
  * re-concretisation, complete clipping, back-substitution of the spec, verified flags.
+ * Complete clipping (Theorem 1, Algorithm 1, opt->sweeps passes over the active rows) takes the
+ * decisions of the paper's sorted-breakpoint rule: the breakpoints are located in FP32, and with
+ * two or more rows every decision whose neighbouring breakpoints lie within their a-priori FP32
+ * error is re-decided on breakpoints recomputed in float-float arithmetic, with the multipliers
+ * kept as float-float sums; only breakpoints equal to within about 2^-44 of their magnitude can be
+ * ordered differently from exact arithmetic.  The bound is the dual objective at the leading
+ * FP32 parts of the multipliers, padded by its rounding bound (any multipliers >= 0 give a valid
+ * bound).
  * workspace: device memory of at least cv_bound_batch_workspace() bytes, 256-byte
  * aligned, used only during the call's kernels (stream-ordered). */
 cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* in,
@@ -269,8 +284,9 @@ cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* 
  * cached neurons.  verified is recomputed from the new bounds.
  * Call after cv_bound_batch with the same `in` and with out->final_A / final_c requested; reads
  * out->lo_clip, hi_clip, infeasible, final_A, final_c; updates out->lower and out->verified.  The
- * breakpoint decisions are those of the cached-neuron step (FP32 keys, exact fixed-point weights).
- * opt->sweeps must be > 0 (else CV_EINVAL); the other options are not used.  workspace:
+ * breakpoint decisions are those of the cached-neuron step (see cv_bound_batch).
+ * opt->sweeps must be > 0 (else CV_EINVAL); opt->timer (optional) records the call as its
+ * complete-clipping phase and its decision counters; the other options are not used.  workspace:
  * cv_spec_clip_workspace() bytes, 256-byte aligned. */
 cv_status cv_spec_clip_workspace(const cv_net* net, const cv_cache* cache, const cv_batch_in* in, size_t* bytes);
 cv_status cv_spec_clip(cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,

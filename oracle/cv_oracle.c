@@ -640,81 +640,6 @@ double orc_complete_clip(int n, const double* a, double c, int R, const double* 
     return val;
 }
 
-/* Algorithm 1 with the breakpoint positions taken in FP32, the precision in   */
-/* which the CUDA kernel takes that decision (the paper fixes none).  The     */
-/* decision arithmetic is fixed as follows, every operation IEEE-754 binary32 */
-/* round-to-nearest:  a'_j = a_j + sum_{p != k} beta_p G_pj  as the fma chain  */
-/* over p in increasing order starting from a_j (the multiplier sum of the    */
-/* text of Section 3.2, formed afresh for every row step);                    */
-/* q_j = (-a'_j) * (1/G_kj).  Weights, the threshold and the cumulative sums  */
-/* stay FP64, and the returned dual value D(beta) (Eq. 4) is evaluated in     */
-/* FP64 at the FP32 multipliers.  Inputs a and G are FP32 values.  Near a     */
-/* kink where two breakpoints coalesce, the order of nearly equal q's is      */
-/* decided by this arithmetic; both sides then follow the same ascent.        */
-typedef struct { float q; double w; int j; } bpf_t;
-static int bpf_cmp(const void* A, const void* B) {
-    const bpf_t* x = (const bpf_t*)A; const bpf_t* y = (const bpf_t*)B;
-    if (x->q < y->q) return -1;
-    if (x->q > y->q) return 1;
-    return (x->j < y->j) ? -1 : (x->j > y->j);
-}
-
-double orc_complete_clip_f32(int n, const float* a, double c, int R, const float* G,
-                             const double* h, const double* lo, const double* hi,
-                             int sweeps, float* beta, double* scale) {
-    float* apr = (float*)malloc(sizeof(float) * (n > 0 ? n : 1));
-    bpf_t* bp = (bpf_t*)malloc(sizeof(bpf_t) * (n > 0 ? n : 1));
-    for (int k = 0; k < R; ++k) beta[k] = 0.0f;
-    for (int sw = 0; sw < sweeps; ++sw) {
-        for (int k = 0; k < R; ++k) {
-            const float* gk = G + (long)k * n;
-            int nb = 0;
-            double s0 = h[k];
-            for (int j = 0; j < n; ++j) {
-                float v = a[j];
-                for (int p = 0; p < R; ++p)
-                    if (p != k) v = fmaf(beta[p], G[(long)p * n + j], v);
-                apr[j] = v;
-                double gd = (double)gk[j];
-                s0 += fmax(gd * lo[j], gd * hi[j]);
-                if (gk[j] != 0.0f) {
-                    float r = 1.0f / gk[j];
-                    float na = -apr[j];
-                    bp[nb].q = na * r;
-                    bp[nb].w = fabs(gd) * (0.5 * (hi[j] - lo[j]));
-                    bp[nb].j = j;
-                    ++nb;
-                }
-            }
-            qsort(bp, nb, sizeof(bpf_t), bpf_cmp);
-            float bn = 0.0f;
-            if (s0 > 0.0) {
-                double s = s0;
-                for (int i = 0; i < nb; ++i) {
-                    s -= 2.0 * bp[i].w;
-                    if (s <= 0.0) { bn = bp[i].q; break; }
-                }
-            }
-            if (!(bn > 0.0f)) bn = 0.0f;
-            beta[k] = bn;
-        }
-    }
-    double val = c, sc = fabs(c);
-    for (int k = 0; k < R; ++k) { val += (double)beta[k] * h[k]; sc += (double)beta[k] * fabs(h[k]); }
-    for (int j = 0; j < n; ++j) {
-        double v = a[j], va = fabs((double)a[j]);
-        for (int p = 0; p < R; ++p) {
-            v += (double)beta[p] * (double)G[(long)p * n + j];
-            va += (double)beta[p] * fabs((double)G[(long)p * n + j]);
-        }
-        val += fmin(v * lo[j], v * hi[j]);
-        sc += va * fmax(fabs(lo[j]), fabs(hi[j]));
-    }
-    if (scale) *scale = sc;
-    free(apr); free(bp);
-    return val;
-}
-
 /* The dual objective D(beta) of Eq. 4 at a given beta (any beta >= 0 gives a */
 /* valid lower bound: weak duality).                                          */
 double orc_dual_value(int n, const double* a, double c, int R, const double* G,
@@ -741,9 +666,8 @@ double orc_dual_value(int n, const double* a, double c, int R, const double* G,
 /*     intersected with the inherited bounds; split signs enforced (standard */
 /*     activation BaB) unless enforce_splits = 0 (the paper's relaxed-clipping */
 /*     walk-through keeps the split neuron's clipped bounds as they are)      */
-/*  a6 complete clipping (Algorithm 1, `sweeps` passes) of every still-       */
-/*     unstable target, both sides, breakpoint positions in FP32              */
-/*     (orc_complete_clip_f32; the cached planes are FP32 values)             */
+/*  a6 complete clipping (Algorithm 1, `sweeps` passes, orc_complete_clip)  */
+/*     of every still-unstable target, both sides                             */
 /*  a7 CROWN back-substitution of the spec rows C with the subdomain's bounds */
 /*  a8 concretisation over the clipped box; verified iff all f_r > 0         */
 /* Infeasible subdomains stop at the step that finds them; they report        */
@@ -888,25 +812,23 @@ static void one_subdomain(const cache_t* cc, int b,
 
     /* a6: complete clipping of the still-unstable targets */
     if (!infeas && sweeps > 0 && Ra > 0) {
-        float* beta = (float*)malloc(sizeof(float) * Ra);
-        float* Gf = (float*)malloc(sizeof(float) * (size_t)Ra * n0);
-        float* af = (float*)malloc(sizeof(float) * n0);
-        for (long q = 0; q < (long)Ra * n0; ++q) Gf[q] = (float)G[q];
+        double* beta = (double*)malloc(sizeof(double) * Ra);
+        double* an = (double*)malloc(sizeof(double) * n0);
         int nt = tgt_off ? tgt_off[b + 1] - tgt_off[b] : U;
         for (int ti = 0; ti < nt; ++ti) {
             int c = tgt_off ? tgt_ids[tgt_off[b] + ti] : ti;
             if (c < 0 || c >= U || mk[c] != 0) continue;
             double sc;
-            for (int q = 0; q < n0; ++q) af[q] = (float)cc->lA[(long)c * n0 + q];
-            double L1 = orc_complete_clip_f32(n0, af, cc->lc[c], Ra, Gf, h, clo, chi, sweeps, beta, &sc);
+            /* lower side: min of the lower plane; upper side: -min of the negated upper plane */
+            double L1 = orc_complete_clip(n0, cc->lA + (long)c * n0, cc->lc[c], Ra, G, h, clo, chi, sweeps, beta, &sc);
             if (L1 > lb[c]) lb[c] = L1;
             if (sc > ls[c]) ls[c] = sc;
-            for (int q = 0; q < n0; ++q) af[q] = -(float)cc->uA[(long)c * n0 + q];
-            double L2 = orc_complete_clip_f32(n0, af, -cc->uc[c], Ra, Gf, h, clo, chi, sweeps, beta, &sc);
+            for (int q = 0; q < n0; ++q) an[q] = -cc->uA[(long)c * n0 + q];
+            double L2 = orc_complete_clip(n0, an, -cc->uc[c], Ra, G, h, clo, chi, sweeps, beta, &sc);
             if (-L2 < ub[c]) ub[c] = -L2;
             if (sc > us[c]) us[c] = sc;
         }
-        free(beta); free(Gf); free(af);
+        free(beta); free(an);
         for (int c = 0; c < U; ++c) {
             if (mk[c] == 0) mk[c] = stab_state(lb[c], ub[c]);
             if (lb[c] > ub[c]) infeas = 1;

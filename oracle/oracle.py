@@ -56,8 +56,6 @@ def _load():
         _lib.orc_select_targets.restype = I
         _lib.orc_complete_clip.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
         _lib.orc_complete_clip.restype = D
-        _lib.orc_complete_clip_f32.argtypes = [I, P, D, I, P, P, P, P, I, P, P]
-        _lib.orc_complete_clip_f32.restype = D
         _lib.orc_dual_value.argtypes = [I, P, D, I, P, P, P, P, P]
         _lib.orc_dual_value.restype = D
         _lib.orc_bound_batch.argtypes = ([I, P, P, P] + [I, P, P, P, P, P] + [P, P, P] +
@@ -305,21 +303,6 @@ def complete_clip(a, c, G, h, lo, hi, sweeps):
     sc = ctypes.c_double()
     v = lib.orc_complete_clip(a.size, _p(a), float(c), R, _p(G), _p(h), _p(lo), _p(hi), int(sweeps),
                               _p(beta), ctypes.byref(sc))
-    return v, beta[:R], sc.value
-
-
-def complete_clip_f32(a, c, G, h, lo, hi, sweeps):
-    """Algorithm 1 with FP32 breakpoint decisions (the batch oracle's a6): (value, beta, scale).
-    a and G are rounded to FP32 first."""
-    lib = _load()
-    a = np.ascontiguousarray(np.asarray(a, np.float32))
-    G = np.ascontiguousarray(np.atleast_2d(np.asarray(G, np.float32)))
-    h, lo, hi = _f64(np.atleast_1d(h)), _f64(lo), _f64(hi)
-    R = G.shape[0] if G.size else 0
-    beta = np.zeros(max(R, 1), np.float32)
-    sc = ctypes.c_double()
-    v = lib.orc_complete_clip_f32(a.size, _p(a), float(c), R, _p(G), _p(h), _p(lo), _p(hi), int(sweeps),
-                                  _p(beta), ctypes.byref(sc))
     return v, beta[:R], sc.value
 
 

@@ -95,6 +95,7 @@ def load():
         "cv_timer_create": ([ctypes.POINTER(P)], I),
         "cv_timer_destroy": ([P], None),
         "cv_timer_read": ([P, P, P, P], I),
+        "cv_timer_read_cc": ([P, P], I),
         "cv_relaxed_clip_static": ([P, P, P, P, P, P, I, P], I),
         "cv_graph_capture": ([P, P, P, P, P, P, ctypes.c_size_t, ctypes.POINTER(P)], I),
         "cv_graph_launch": ([P, P], I),
@@ -127,7 +128,7 @@ def exported_symbols():
     return [n for n in ("cv_last_error", "cv_net_create", "cv_net_destroy", "cv_net_dims", "cv_device_status",
                         "cv_cache_build", "cv_cache_create", "cv_cache_size", "cv_cache_read", "cv_cache_destroy",
                         "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
-                        "cv_timer_destroy", "cv_timer_read", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
+                        "cv_timer_destroy", "cv_timer_read", "cv_timer_read_cc", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
                         "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy",
                         "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc", "cv_input_split_workspace",
                         "cv_input_split", "cv_spec_clip_workspace", "cv_spec_clip",
@@ -297,6 +298,14 @@ def cv_timer_read(t):
     steps = ctypes.c_longlong()
     _check(load().cv_timer_read(t, ctypes.cast(ms, P), ctypes.byref(n), ctypes.byref(steps)))
     return list(ms), n.value, steps.value
+
+
+def cv_timer_read_cc(t):
+    """Complete clipping's decision counters of the last timed call: (certified row steps, with several
+    candidates, with a widened window, left with the FP32 decision, of those over the candidate limit)."""
+    st = (ctypes.c_longlong * 5)()
+    _check(load().cv_timer_read_cc(t, ctypes.cast(st, P)))
+    return tuple(int(v) for v in st)
 
 
 def cv_spec_clip_workspace(net, cache, bi):

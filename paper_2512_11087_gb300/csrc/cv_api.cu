@@ -141,7 +141,7 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
     int launches = 0;
     unsigned long long* steps = nullptr;
     if (tm) {
-        CV_CUDA(cudaMemsetAsync(tm->d_steps, 0, sizeof(unsigned long long), st));
+        CV_CUDA(cudaMemsetAsync(tm->d_steps, 0, CV_TIMER_COUNTERS * sizeof(unsigned long long), st));
         CV_CUDA(cudaEventRecord(tm->ev[0], st));
         steps = tm->d_steps;
     }
@@ -198,8 +198,8 @@ extern "C" cv_status cv_timer_create(cv_timer** out) {
     cv_timer* t = new cv_timer();
     memset(t, 0, sizeof(*t));
     for (int i = 0; i <= CV_N_PHASES; ++i) CV_CUDA(cudaEventCreate(&t->ev[i]));
-    CV_CUDA(cudaMalloc(&t->d_steps, sizeof(unsigned long long)));
-    CV_CUDA(cudaMemset(t->d_steps, 0, sizeof(unsigned long long)));
+    CV_CUDA(cudaMalloc(&t->d_steps, CV_TIMER_COUNTERS * sizeof(unsigned long long)));
+    CV_CUDA(cudaMemset(t->d_steps, 0, CV_TIMER_COUNTERS * sizeof(unsigned long long)));
     *out = t;
     return CV_OK;
 }
@@ -223,6 +223,16 @@ extern "C" cv_status cv_timer_read(cv_timer* t, float* ms, int* launches, long l
         CV_CUDA(cudaMemcpy(&v, t->d_steps, sizeof(v), cudaMemcpyDeviceToHost));
         *cc_steps = (long long)v;
     }
+    return CV_OK;
+}
+
+extern "C" cv_status cv_timer_read_cc(cv_timer* t, long long stats[5]) {
+    if (!t || !stats) { cv_set_error("cv_timer_read_cc: null"); return CV_EINVAL; }
+    if (!t->used) { cv_set_error("cv_timer_read_cc: no timed call yet"); return CV_EINVAL; }
+    unsigned long long v[CV_TIMER_COUNTERS];
+    CV_CUDA(cudaEventSynchronize(t->ev[CV_N_PHASES]));
+    CV_CUDA(cudaMemcpy(v, t->d_steps, sizeof(v), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 5; ++i) stats[i] = (long long)v[1 + i];
     return CV_OK;
 }
 
@@ -357,7 +367,7 @@ SpecWs spec_ws(const cv_cache* cache, const cv_batch_in* in) {
     w.rowflag = take(Rm);
     w.vmin = take(Rm * sizeof(double));
     w.cc = take(cv_cc_workspace(in->B, in->max_splits + in->max_rows, cache->n0));
-    w.sscale = take((size_t)in->B * in->m * sizeof(float));
+    w.sscale = take((size_t)2 * in->B * in->m * sizeof(float));  // plane scales, then plane maxima
     w.total = off;
     return w;
 }
@@ -404,12 +414,24 @@ extern "C" cv_status cv_spec_clip(cv_net* net, const cv_cache* cache, const cv_b
     lay.cc = w.cc;
     lay.total = w.total;
     int launches = 0;
+    cv_timer* tm = opt->timer;
+    if (tm) {
+        CV_CUDA(cudaMemsetAsync(tm->d_steps, 0, CV_TIMER_COUNTERS * sizeof(unsigned long long), st));
+        for (int i = 0; i <= CV_N_PHASES; ++i) CV_CUDA(cudaEventRecord(tm->ev[i], st));
+    }
     // the active rows, as the round's pre-check found them on the input box (infeasible flags the
     // round already set are set again; none is cleared)
     if ((s = cv_launch_rows(net, cache, in, &lay, ws, out->infeasible, st))) return s;
-    if ((s = cv_launch_spec_clip(net, cache, in, out, opt, &lay, ws, (float*)(ws + w.sscale), &launches, st)))
+    if ((s = cv_launch_spec_clip(net, cache, in, out, opt, &lay, ws, (float*)(ws + w.sscale),
+                                 tm ? tm->d_steps : nullptr, &launches, st)))
         return s;
     k_verified<<<(B + 255) / 256, 256, 0, st>>>(B, m, out->lower, out->infeasible, out->verified);
     CV_LAUNCH_CHECK("k_verified");
+    if (tm) {
+        // the whole call counts as the complete-clipping phase
+        for (int i = 3; i <= CV_N_PHASES; ++i) CV_CUDA(cudaEventRecord(tm->ev[i], st));
+        tm->launches = launches + 2;
+        tm->used = true;
+    }
     return CV_OK;
 }

@@ -84,15 +84,17 @@ __global__ void k_root_bounds(int nk, int n0, const double* lower64, const doubl
 
 // concretisation operand rows and magnitude scales
 __global__ void k_build_pc(int U, int n0, const float* lA, const float* lc, const float* uA, const float* uc,
-                           const float* xmag, float* PC, float* PCc, float* pscale) {
+                           const float* xmag, float* PC, float* PCc, float* pscale, float* amax) {
     const int c = blockIdx.x;  // 0..2U-1
     if (c >= 2 * U) return;
     const bool up = c >= U;
     const int s = up ? c - U : c;
     const float* A = up ? uA : lA;
     double mag = 0.0;
+    float vmax = 0.f;
     for (int q = threadIdx.x; q < n0; q += blockDim.x) {
         const float v = A[(size_t)s * n0 + q];
+        vmax = fmaxf(vmax, fabsf(v));
         const float pos = fmaxf(v, 0.f), neg = fminf(v, 0.f);
         // lower: [A+ | A-] against [lo | hi];  upper: [A- | A+]
         PC[(size_t)c * 2 * n0 + q] = up ? neg : pos;
@@ -100,12 +102,18 @@ __global__ void k_build_pc(int U, int n0, const float* lA, const float* lc, cons
         mag += (double)fabsf(v) * (double)xmag[q];
     }
     __shared__ double red[32];
-    for (int off = 16; off > 0; off >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
+    __shared__ float redm[32];
+    for (int off = 16; off > 0; off >>= 1) {
+        mag += __shfl_xor_sync(0xffffffffu, mag, off);
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = mag; redm[threadIdx.x >> 5] = vmax; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += red[w]; m = fmaxf(m, redm[w]); }
+        amax[c] = m;
         const float cc = up ? uc[s] : lc[s];
         PCc[c] = cc;
         pscale[c] = __double2float_ru((t + fabs((double)cc)) * (1.0 + 1e-12));
@@ -132,7 +140,7 @@ cv_status dalloc(T** p, size_t n) {
 void cache_free(cv_cache* c) {
     if (!c) return;
     cudaFree(c->ids); cudaFree(c->slot_of); cudaFree(c->lA); cudaFree(c->lc); cudaFree(c->uA);
-    cudaFree(c->uc); cudaFree(c->PC); cudaFree(c->PCc); cudaFree(c->pscale); cudaFree(c->root_l);
+    cudaFree(c->uc); cudaFree(c->PC); cudaFree(c->PCc); cudaFree(c->pscale); cudaFree(c->amax); cudaFree(c->root_l);
     cudaFree(c->root_u); cudaFree(c->root_state); cudaFree(c->root_lo); cudaFree(c->root_hi);
     for (int i = 0; i <= CV_MAX_LAYERS; ++i) cudaFree(c->V[i]);
     cv_tc_release(c);
@@ -265,7 +273,7 @@ static cv_status finish_cache(cv_cache* c, cudaStream_t st) {
     const cv_net* n = c->net;
     const int H = n->H, U = c->U, n0 = c->n0;
     if (dalloc(&c->slot_of, H) || dalloc(&c->PC, (size_t)2 * U * 2 * n0) || dalloc(&c->PCc, 2 * U) ||
-        dalloc(&c->pscale, 2 * U))
+        dalloc(&c->pscale, 2 * U) || dalloc(&c->amax, 2 * U))
         return CV_ENOMEM;
     k_slot_of<<<(H + 255) / 256, 256, 0, st>>>(H, U, c->ids, c->slot_of);
     if (U > 0) k_slot_set<<<(U + 255) / 256, 256, 0, st>>>(U, c->ids, c->slot_of);
@@ -273,7 +281,7 @@ static cv_status finish_cache(cv_cache* c, cudaStream_t st) {
     if (dalloc(&xmag, n0)) return CV_ENOMEM;
     k_absmax<<<(n0 + 255) / 256, 256, 0, st>>>(n0, c->root_lo, c->root_hi, xmag);
     if (U > 0)
-        k_build_pc<<<2 * U, 256, 0, st>>>(U, n0, c->lA, c->lc, c->uA, c->uc, xmag, c->PC, c->PCc, c->pscale);
+        k_build_pc<<<2 * U, 256, 0, st>>>(U, n0, c->lA, c->lc, c->uA, c->uc, xmag, c->PC, c->PCc, c->pscale, c->amax);
     // V^(i) = |W^(i)| zmag^(i-1) + |b^(i)|; zmag^(0) = xmag, zmag^(i) = max(|l|,|u|) of layer i
     float* zmag = nullptr;
     if (dalloc(&zmag, H > 0 ? H : 1)) { cudaFree(xmag); return CV_ENOMEM; }

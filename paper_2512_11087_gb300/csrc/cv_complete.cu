@@ -15,17 +15,24 @@
 // passes, every other pass halves the range instead, which bounds the count); the previous
 // sweep's breakpoint is tried first (coordinate ascent mostly re-selects it).
 //
-// Decision arithmetic (reproduced by the oracle): a'_j = a_j + sum_{p != k} beta_p g_pj as an FP32
-// fma chain over increasing p, q_j = (-a'_j) * fl(1/g_kj); breakpoints with q > 0 are compared
-// through the raw bits of q (for positive floats the unsigned order of the bits is the order of
-// the values).  Weights are exact 64-bit fixed-point integers (w scaled by 2^s_k, s_k chosen so
-// the row's total stays below 2^62), so every cumulative sum is exact and order independent and
-// the quantile decision matches an FP64 evaluation; warp sums use three 21-bit redux.sync limbs.
-// A sweep that changes no multiplier ends the ascent (the next would repeat it bit for bit); with
-// a single row a' = a, so one pass suffices.  The bound is the dual objective at the final beta,
-// evaluated in FP32 and padded by its rounding bound (any beta >= 0 gives a valid bound), or in
-// FP64 when the padded value straddles 0 so that the stability decision is exact.  With every
-// multiplier 0 it equals the re-concretised bound already stored, and is skipped.
+// Decision arithmetic: a'_j = a_j + sum_{p != k} beta_p g_pj as an FP32 fma chain over increasing p
+// from the leading FP32 parts of the multipliers, q_j = (-a'_j) * fl(1/g_kj); breakpoints with q > 0
+// are compared through the raw bits of q (for positive floats the unsigned order of the bits is the
+// order of the values).  Weights are exact 64-bit fixed-point integers (w scaled by 2^s_k, s_k chosen
+// so the row's total stays below 2^62), so every cumulative sum is exact and order independent;
+// warp sums use three 21-bit redux.sync limbs.  With one row a' = a exactly and one pass is the whole
+// ascent; the selected breakpoint is then within a few FP32 ulps of the exact one.  With two or more
+// rows the FP32 decision of every row step is certified against the a-priori error of the keys: the
+// elements whose breakpoints could be ordered differently in exact arithmetic are re-decided on
+// float-float breakpoints, and the multipliers are kept as float-float sums (beta_hi + beta_lo), so
+// the ascent follows the paper's FP64 sorted-breakpoint rule (only breakpoints equal to within about
+// 2^-44 of their magnitude can be ordered differently).  A row step whose inputs (the other rows'
+// multipliers) did not change since its last step is skipped, and a sweep that changes no multiplier
+// ends the ascent: both would repeat the previous result exactly.  The bound is the dual objective at
+// the leading parts of the final multipliers, evaluated in FP32 and padded by its rounding bound
+// (any beta >= 0 gives a valid bound), or in FP64 when the padded value straddles 0 so that the
+// stability decision is exact.  With every multiplier 0 it equals the re-concretised bound already
+// stored, and is skipped.
 //
 // GB300 mapping (persistent scheduling of uneven work): k_cc_prep writes each subdomain's active
 // rows (g, 1/g, fixed-point weights, threshold, total weight) to the workspace once; a
@@ -49,7 +56,10 @@ namespace {
 constexpr int RMAX_CC = 32;  // rows per subdomain handled by complete clipping
 constexpr int RTPL = 4;     // row counts up to this run in the main launch (two blocks per SM)
 // (target, side) tasks per work item: fewer for subdomains with more rows (longer tasks)
-constexpr int NWARP = 14;   // warps per block at most (two blocks per SM leave 72 registers a thread)
+#ifndef CV_CC_NWARP
+#define CV_CC_NWARP 14
+#endif
+constexpr int NWARP = CV_CC_NWARP;  // warps per block at most (two blocks per SM of 14 leave 72 registers a thread)
 constexpr int CAPC = 384;   // breakpoints a warp's compacted list holds
 constexpr int SAMP_MIN = 64;     // brackets with more breakpoints start from sampled pivots
 constexpr float SAMP_D = 0.10f;  // rank margin of the sampled pivots around the target fraction
@@ -92,11 +102,17 @@ struct CCArgs {
     const int* tgt_off; const int* tgt_ids;
     const float* lo; const float* hi;
     float* l; float* u; int8_t* mask; uint8_t* infeasible; int* status;
-    unsigned long long* steps;  // optional counter of executed row steps
+    unsigned long long* steps;  // optional counters: [0] executed row steps, [1] certified row steps,
+                                // [2] of them with several candidates, [3] with a widened window,
+                                // [4] left with the FP32 decision, [5] of them over the candidate limit
+    const float* amax;    // [2U] max |A| of the cached lower / upper planes (error bounds of the keys)
+    const float* samax;   // [B x m] max |A| of the final planes (spec-plane mode)
     // workspace
     float* wg; float* wrg; long long* ww;   // [B][Rs][n0]
     long long* wT; long long* wW;           // [B][Rs] threshold, total weight (fixed point)
     double* wSg; float* wh;                  // [B][Rs]
+    float* wGm;                              // [B][Rs] max |g| of every active row
+    float* wRm;                              // [B][Rs] max |fl(1/g)| of every active row
     int* wR;                                 // [B] active rows used
     int* wcnt;                               // [B] work items
     int* order;                              // [B] positions -> subdomains, more rows first
@@ -149,10 +165,14 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
         }
         const size_t base = ((size_t)b * Rs + r) * n0;
         double smax = 0.0, wsum = 0.0, sgm = 0.0;
+        float gmx = 0.f, rmx = 0.f;
         for (int j = lane; j < n0; j += 32) {
             const float g = sg * gp[j];
+            gmx = fmaxf(gmx, fabsf(g));
             a.wg[base + j] = g;
-            a.wrg[base + j] = (g != 0.f) ? 1.f / g : 0.f;
+            const float rg = (g != 0.f) ? 1.f / g : 0.f;
+            rmx = fmaxf(rmx, fabsf(rg));
+            a.wrg[base + j] = rg;
             const double gd = (double)g, l0 = (double)lo[j], h0 = (double)hi[j];
             smax += fmax(gd * l0, gd * h0);
             wsum += fabs(gd) * (0.5 * (h0 - l0));
@@ -163,6 +183,8 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
             smax += __shfl_xor_sync(0xffffffffu, smax, off);
             wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
             sgm += __shfl_xor_sync(0xffffffffu, sgm, off);
+            gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, off));
+            rmx = fmaxf(rmx, __shfl_xor_sync(0xffffffffu, rmx, off));
         }
         // fixed-point weights: scale so that the row total stays below 2^62
         const int sh = (wsum > 0.0) ? 61 - ilogb(wsum) : 0;
@@ -180,6 +202,8 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
             a.wT[(size_t)b * Rs + r] = (T <= 0.0) ? LLONG_MIN : __double2ll_ru(ldexp(T, sh));
             a.wh[(size_t)b * Rs + r] = hh;
             a.wSg[(size_t)b * Rs + r] = sgm;
+            a.wGm[(size_t)b * Rs + r] = gmx;
+            a.wRm[(size_t)b * Rs + r] = rmx;
         }
     }
 }
@@ -248,6 +272,8 @@ __shared__ long long cc_W64[RMAX_CC];  // total weights (fixed point)
 __shared__ float cc_hrow[RMAX_CC];     // row constants h
 __shared__ double cc_Sg[RMAX_CC];      // magnitude of g against the root box
 __shared__ float cc_SgH[RMAX_CC];      // Sg + |h| rounded up
+__shared__ float cc_Gm[RMAX_CC];       // max |g| of every row
+__shared__ float cc_Rm[RMAX_CC];       // max |fl(1/g)| of every row
 
 struct CCView {
     unsigned* keys;        // this warp's keys
@@ -255,12 +281,15 @@ struct CCView {
     float* gs;
     float* rg;
     unsigned short* cidx;  // this warp's list elements
-    float* bsm;            // this warp's multiplier slots (wide launch)
+    float* bsm;            // this warp's multiplier slots (wide launch): leading parts
+    float* blsm;           // trailing parts
     int* jsm;
 };
 
-// Main launch: keys [nw][n0r] | w64 [RsS][n0] | g [RsS][n0] | 1/g [RsS][n0] | list [nw][CAPC].
-// Wide launch: keys [nw][n0r] | list [nw][CAPC] | multipliers [nw][RMAX_CC] | elements [nw][RMAX_CC].
+// Main launch: keys [nw][n0r] | w64 [RsS][n0] | g [RsS][n0] | 1/g [RsS][n0] | list [nw][CAPC] |
+// multipliers' trailing parts and a copy of their leading parts [nw][2 RMAX_CC].
+// Wide launch: keys [nw][n0r] | list [nw][CAPC] | multipliers [nw][RMAX_CC] | elements [nw][RMAX_CC] |
+// multipliers' trailing parts [nw][RMAX_CC].
 __device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
     const int n0r = (n0 + 31) & ~31;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -272,6 +301,7 @@ __device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
         v.rg = v.gs + RsS * n0;
         v.cidx = (unsigned short*)(v.rg + RsS * n0) + warp * CAPC;
         v.bsm = nullptr;
+        v.blsm = (float*)((unsigned short*)(v.rg + RsS * n0) + nw * CAPC) + warp * 2 * RMAX_CC;
         v.jsm = nullptr;
     } else {
         unsigned short* list0 = (unsigned short*)((unsigned*)cc_smem + nw * n0r);
@@ -279,6 +309,7 @@ __device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
         float* b0 = (float*)(list0 + nw * CAPC);
         v.bsm = b0 + warp * RMAX_CC;
         v.jsm = (int*)(b0 + nw * RMAX_CC) + warp * RMAX_CC;
+        v.blsm = (float*)((int*)(b0 + nw * RMAX_CC) + nw * RMAX_CC) + warp * RMAX_CC;
         v.w64 = nullptr;
         v.gs = nullptr;
         v.rg = nullptr;
@@ -296,6 +327,349 @@ struct CCRows {
     const long long* w64;
 };
 
+// Outcome of a certified row step (see cc_certify): the multiplier as beta_hi + beta_lo, its element,
+// and counters (certified, several candidates, widened window, FP32 decision kept, of which over the
+// candidate limit).
+struct CertState {
+    float bn, bln;
+    int jn;
+    unsigned cs[5];
+};
+
+// Certified decision of one row step of Algorithm 1 with R >= 2 rows (row k).  The FP32 search decided
+// the crossing q* (element jn; dec = 1) or beta = 0 from F(0) >= T (dec = 0) on keys
+// q_j = fl(-a'_j * fl(1/g_kj)), a' formed by an FP32 fma chain from the leading parts bh of the
+// multipliers.  Each key lies within
+//   E_j = 2u'|q_j| + (n + 1) u' S_j |fl(1/g_kj)|,  S_j = |a_j| + sum_{p != k} |bh_p g_pj|,  u' = 2^-24 * 1.001,
+// of the exact breakpoint -(a_j + sum_{p != k} beta_p g_pj) / g_kj with the full multipliers bh + bl:
+// n = the number of nonzero multipliers p != k (one fma rounding each), one more u' S_j for all the
+// dropped trailing parts, two roundings in the product (with every other multiplier 0, a' = a exactly).
+// The window [L, H] = [q* - E*, q* + E*] (the point 0 for dec = 0) is where the exact crossing can lie.
+// A screening pass over the keys (S_j bounded by max|a| + sum_p |bh_p| max|g_p|, 1% margin) marks the
+// elements whose interval might meet the window; each is then tested with its own S_j.  Candidates
+// (interval meets the window) have their breakpoints recomputed in float-float arithmetic (error a few
+// 2^-48 of S_j |1/g_kj|, inside the 0.1% margin of u'); exact zeros (S_j = 0) form one group at 0.  The
+// elements surely below the window weigh F(< q*) (F(<= 0)) minus the candidates the FP32 keys put there.
+// Walking the candidates in exact order (equal values by element) after that weight, the first to reach
+// the threshold T is the exact crossing provided its breakpoint lies in the window: every element
+// outside the window is then ordered against it.  Otherwise the window grows to it and a full pass
+// repeats the selection (at most twice).  A crossing at or below 0 with 0 in the window is beta = 0.
+// Left unsettled (more than CAPC candidates or the window still moving), the FP32 decision stands: still
+// a valid multiplier.  The result is the decision of the sorted-breakpoint rule on exact breakpoints
+// except between breakpoints equal to within about 2^-44 of their magnitude.
+// Memory: keys (the warp's key buffer, every element's key), cidx (the warp's list buffer, free here),
+// gs / rk / wk the staged rows, bh / bl the multipliers' leading and trailing parts (shared slots).
+// Once more than 64 candidates' breakpoints are written over the key buffer, keys are recomputed from
+// the target plane.
+__device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const float* gs, const float* rk,
+                                        const long long* wk, unsigned* keys, unsigned short* cidx, const float* ap,
+                                        float sa, const float* bh, const float* bl, float amx, long long T,
+                                        long long Fdec, int dec, CertState* st) {
+    const float cu1 = 5.9665e-08f;  // >= 2^-24 * 1.001
+    const float tu = 1.1933e-07f;   // >= 2 * 2^-24 * 1.001
+    float smx = amx;
+    int nnz = 0;
+    for (int p = 0; p < R; ++p) {
+        if (p == k) continue;
+        const float b = bh[p];
+        smx = __fmaf_ru(fabsf(b), cc_Gm[p], smx);
+        nnz += b != 0.f;
+    }
+    const float Ru = nnz ? __fmul_ru((float)(nnz + 1), cu1) : 0.f;
+    const float c1 = __fmul_ru(Ru, smx);
+    const int jn0 = st->jn;
+    const float qs = dec == 1 ? st->bn : 0.f;
+    const float Es = dec == 1 ? __fmaf_ru(c1, fabsf(rk[jn0]), __fmul_ru(tu, qs)) : 0.f;
+    float Lw = __fsub_rd(qs, Es), Hw = __fadd_ru(qs, Es);
+    st->cs[0] = 1u; st->cs[1] = 0u; st->cs[2] = 0u; st->cs[3] = 0u; st->cs[4] = 0u;
+    // the FP32 key of element j exactly as the key pass forms it
+    auto key_calc = [&](int j) -> float {
+        float x = sa * __ldg(ap + j);
+        for (int p = 0; p < R; ++p)
+            if (p != k) x = fmaf(bh[p], gs[p * n0 + j], x);
+        return (-x) * rk[j];
+    };
+    bool keys_ok = true;  // the key buffer holds every element's key
+    // the element's own interval against the window: 1 below, 2 candidate, 3 exact zero inside, 0 else
+    auto classify = [&](int j, float q, float av) -> int {
+        const float r = rk[j];
+        if (r == 0.f) return 0;  // g_kj = 0: no breakpoint (weight 0)
+        float S = fabsf(av);
+        for (int p = 0; p < R; ++p)
+            if (p != k) S = __fmaf_ru(fabsf(bh[p]), fabsf(gs[p * n0 + j]), S);
+        if (S == 0.f) return 0.f < Lw ? 1 : (0.f <= Hw ? 3 : 0);
+        const float E = __fmaf_ru(__fmul_ru(Ru, S), fabsf(r), __fmul_ru(tu, fabsf(q)));
+        if (__fadd_ru(q, E) < Lw) return 1;
+        return __fsub_rd(q, E) <= Hw ? 2 : 0;
+    };
+    // breakpoint of element j in float-float: -(sh + sl) / g_kj with sh + sl = a'_j.  The quotient is
+    // refined once: qh from fl(1/g), the remainder qh g + sh by fma, the correction from it.
+    auto ff_key = [&](int j, float av, float& kh, float& kl) {
+        float sh = sa * av, sl = 0.f;
+        for (int p = 0; p < R; ++p) {
+            if (p == k) continue;
+            const float b1 = bh[p], b2 = bl[p], g = gs[p * n0 + j];
+            const float pr = __fmul_rn(b1, g);
+            float pe = __fmaf_rn(b1, g, -pr);  // exact error of the product
+            pe = __fmaf_rn(b2, g, pe);
+            const float t = __fadd_rn(sh, pr);
+            const float bb = __fsub_rn(t, sh);
+            const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(pr, bb));
+            sh = t;
+            sl = __fadd_rn(sl, __fadd_rn(er, pe));
+        }
+        const float t = __fadd_rn(sh, sl);
+        sl = __fsub_rn(sl, __fsub_rn(t, sh));
+        sh = t;
+        const float gk = gs[k * n0 + j], r = rk[j];
+        const float qh = __fmul_rn(-sh, r);
+        const float rem = __fmaf_rn(qh, gk, sh);  // qh g + sh
+        const float ql = __fmul_rn(-__fadd_rn(rem, sl), r);
+        kh = __fadd_rn(qh, ql);
+        kl = __fsub_rn(ql, __fsub_rn(kh, qh));
+    };
+    // the crossing element's coefficient, loaded early (it is almost always the one candidate)
+    const float a_jn = dec == 1 ? __ldg(ap + jn0) : 0.f;
+    // screening bound (1% above the first test)
+    const float sc1 = c1 * 1.01f, stu = tu * 1.01f, sEs = Es * 1.01f;
+    const unsigned below_lanes = (1u << lane) - 1u;
+    bool ok = false;
+    float rh = 0.f, rl = 0.f;
+    int rj = -1;
+#pragma unroll 1
+    for (int it = 0; it < 3 && !ok; ++it) {
+        // 1. Classify the elements against the window.  it = 0: a screen over the keys marks the
+        // elements to test (bits of a per-lane mask, 32 iterations at a time); each is tested with its
+        // own bound, and the weight surely below is F(< q*) minus the candidates and zeros counted there.
+        // Later passes (a widened window) test every element and sum the surely-below weight directly.
+        // Candidates stay in registers, two per lane; a lane with more sends the pass to `spill`, which
+        // repeats it listing every candidate in cidx.
+        unsigned long long fb = 0ull, fz = 0ull;
+        int c0 = -1, c1e = -1, nc = 0;
+        float a0 = 0.f, a1 = 0.f;
+        bool spill = false;
+        int nloc = 0;
+        // the element's class with the bookkeeping of this pass
+        auto take = [&](int jj, float q, float av) -> int {
+            const int cls = classify(jj, q, av);
+            if (it == 0) {
+                const bool counted = dec == 1 ? q < qs : q <= 0.f;
+                if ((cls == 2 || cls == 3) && counted) fb += (unsigned long long)wk[jj];
+            } else if (cls == 1) {
+                fb += (unsigned long long)wk[jj];
+            }
+            if (cls == 3) fz += (unsigned long long)wk[jj];
+            if (cls == 2) {
+                if (nloc == 0) { c0 = jj; a0 = av; }
+                else if (nloc == 1) { c1e = jj; a1 = av; }
+                ++nloc;
+            }
+            return cls;
+        };
+        if (it == 0) {
+            // With E_j <= c1 max|1/g_k| + tu |q_j|, an element can meet the window only if
+            // |q_j - q*| <= X = (c1 max|1/g_k| + tu |q*| + E*) / (1 - tu): a range of key bits when it
+            // lies in one sign (one subtraction and one comparison per key), |q| <= X around 0 for
+            // dec = 0; otherwise the float test of the screen bound.
+            const float X = __fmul_ru(__fadd_ru(__fmaf_ru(c1, cc_Rm[k], __fmul_ru(tu, fabsf(qs))), Es), 1.0000002f);
+            int mode = 2;  // 0: positive range [klo, klo + span]; 1: |q| <= X; 2: float test
+            unsigned klo = 0u, span = 0u;
+            if (dec == 0) {
+                mode = 1;
+                span = __float_as_uint(X);
+            } else {
+                const float lo_ = __fsub_rd(qs, X);
+                if (lo_ > 0.f && X < INFINITY) {
+                    mode = 0;
+                    klo = __float_as_uint(lo_);
+                    span = __float_as_uint(__fadd_ru(qs, X)) - klo;
+                }
+            }
+            const bool vec = ((n0 & 3) == 0) && (((size_t)keys & 15u) == 0u);
+#pragma unroll 1
+            for (int cb = 0; cb < n0; cb += 1024) {
+                unsigned msk = 0u;  // bit i: element cb + 4 (32 (i / 4) + lane) + i % 4 (vec) or cb + 32 i + lane
+                if (vec && mode != 2) {
+#pragma unroll 2
+                    for (int i = 0; i < 8; ++i) {
+                        const int j = cb + 4 * (32 * i + lane);
+                        const bool v = j < n0;
+                        const uint4 kk = *(const uint4*)(keys + (v ? j : 0));
+                        const unsigned t[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const bool in = v && (mode == 0 ? (t[e] - klo) <= span : (t[e] & 0x7fffffffu) <= span);
+                            msk |= (unsigned)in << (4 * i + e);
+                        }
+                    }
+                } else {
+#pragma unroll 8
+                    for (int i = 0; i < 32; ++i) {
+                        const int j = cb + 32 * i + lane;
+                        const int jj = j < n0 ? j : n0 - 1;
+                        const unsigned kb = keys[jj];
+                        const float q = __uint_as_float(kb);
+                        bool scr;
+                        if (mode == 0) scr = (kb - klo) <= span;
+                        else if (mode == 1) scr = (kb & 0x7fffffffu) <= span;
+                        else scr = fabsf(q - qs) <= fmaf(sc1, fabsf(rk[jj]), fmaf(stu, fabsf(q), sEs));
+                        msk |= (unsigned)(j < n0 && scr) << i;
+                    }
+                }
+                while (msk) {
+                    const int i = __ffs(msk) - 1;
+                    msk &= msk - 1u;
+                    const int j = (vec && mode != 2) ? cb + 4 * (32 * (i >> 2) + lane) + (i & 3) : cb + 32 * i + lane;
+                    take(j, __uint_as_float(keys[j]), j == jn0 ? a_jn : __ldg(ap + j));
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int j0 = 0; j0 < n0; j0 += 32) {
+                const int j = j0 + lane;
+                if (j < n0) take(j, keys_ok ? __uint_as_float(keys[j]) : key_calc(j), __ldg(ap + j));
+            }
+        }
+        nc = __reduce_add_sync(0xffffffffu, (unsigned)nloc);
+        spill = __any_sync(0xffffffffu, nloc > 2);
+        if (spill) {
+            // every candidate listed in cidx (a slow pass, for rows with many near-ties)
+            fb = 0ull; fz = 0ull; c0 = -1; c1e = -1; nloc = 0;
+            int ncl = 0;
+#pragma unroll 1
+            for (int j0 = 0; j0 < n0; j0 += 32) {
+                const int j = j0 + lane;
+                const bool v = j < n0;
+                const int jj = v ? j : n0 - 1;
+                const float q = keys_ok ? __uint_as_float(keys[jj]) : key_calc(jj);
+                bool look = v;
+                if (it == 0) look = v && fabsf(q - qs) <= fmaf(sc1, fabsf(rk[jj]), fmaf(stu, fabsf(q), sEs));
+                const int cls = look ? take(jj, q, __ldg(ap + jj)) : 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, cls == 2);
+                const int pos = ncl + __popc(bal & below_lanes);
+                if (cls == 2 && pos < CAPC) cidx[pos] = (unsigned short)jj;
+                ncl += __popc(bal);
+            }
+            nc = ncl;
+        }
+        __syncwarp();
+        long long Fz = 0, Fb = 0;
+        if (__any_sync(0xffffffffu, fz != 0ull)) Fz = warp_sum64(fz);
+        if (__any_sync(0xffffffffu, fb != 0ull)) Fb = warp_sum64(fb);
+        if (it == 0) Fb = Fdec - Fb;
+        if (nc > 1) st->cs[1] = 1u;
+        if (spill && (nc > CAPC || (nc > 64 && 2 * nc > ((n0 + 31) & ~31)))) { st->cs[4] = 1u; break; }
+        // 2. the candidates' breakpoints: per lane two in registers (slots 0, 1); in spill mode the first
+        // 64 listed go to registers (lane t % 32, slot t / 32) and the rest over the key buffer
+        // (keys[2t], keys[2t + 1]), after which keys are recomputed
+        float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
+        int cj0 = c0, cj1 = c1e;
+        if (spill) {
+            cj0 = lane < nc ? (int)cidx[lane] : -1;
+            cj1 = lane + 32 < nc ? (int)cidx[lane + 32] : -1;
+            a0 = cj0 >= 0 ? __ldg(ap + cj0) : 0.f;
+            a1 = cj1 >= 0 ? __ldg(ap + cj1) : 0.f;
+        }
+        if (cj0 >= 0) ff_key(cj0, a0, ch0, cl0);
+        if (cj1 >= 0) ff_key(cj1, a1, ch1, cl1);
+        if (spill && nc > 64) {
+            __syncwarp();
+            for (int t = lane + 64; t < nc; t += 32) {
+                float h2, l2;
+                const int j = cidx[t];
+                ff_key(j, __ldg(ap + j), h2, l2);
+                keys[2 * t] = __float_as_uint(h2);
+                keys[2 * t + 1] = __float_as_uint(l2);
+            }
+            keys_ok = false;
+            __syncwarp();
+        }
+        // 3. walk the candidates in exact order after Fb; the exact zeros form one group at 0
+        long long F = Fb;
+        bool found = false;
+        if (F >= T) {
+            found = true;  // the crossing lies below the window
+            rh = -INFINITY; rl = 0.f; rj = -1;
+        } else if (nc == 1 && Fz == 0) {
+            // one candidate: no ordering to do
+            const unsigned bal = __ballot_sync(0xffffffffu, cj0 >= 0);
+            const int src = __ffs(bal) - 1;
+            const float kh = __shfl_sync(0xffffffffu, ch0, src), kl = __shfl_sync(0xffffffffu, cl0, src);
+            const int kj = __shfl_sync(0xffffffffu, cj0, src);
+            F += wk[kj];
+            if (F >= T) { found = true; rh = kh; rl = kl; rj = kj; }
+        } else if (nc > 0 || Fz != 0) {
+            unsigned taken = 0u;  // bit u: this lane's slot u (u >= 2: listed candidate lane + 32 u)
+            bool tz = (Fz == 0);
+#pragma unroll 1
+            for (int s2 = 0; s2 <= nc && !found; ++s2) {
+                float kh = INFINITY, kl = 0.f;
+                int kj = INT_MAX, ku = -1;
+                auto better = [&](float h2, float l2, int j2) {
+                    return h2 < kh || (h2 == kh && (l2 < kl || (l2 == kl && j2 < kj)));
+                };
+                if (cj0 >= 0 && !(taken & 1u) && better(ch0, cl0, cj0)) { kh = ch0; kl = cl0; kj = cj0; ku = 0; }
+                if (cj1 >= 0 && !(taken & 2u) && better(ch1, cl1, cj1)) { kh = ch1; kl = cl1; kj = cj1; ku = 1; }
+                if (spill)
+                    for (int u = 2, t = lane + 64; t < nc; ++u, t += 32) {
+                        if ((taken >> u) & 1u) continue;
+                        const float h2 = __uint_as_float(keys[2 * t]), l2 = __uint_as_float(keys[2 * t + 1]);
+                        const int j2 = cidx[t];
+                        if (better(h2, l2, j2)) { kh = h2; kl = l2; kj = j2; ku = u; }
+                    }
+                if (!tz && lane == 0 && better(0.f, 0.f, -1)) { kh = 0.f; kl = 0.f; kj = -1; ku = 31; }
+                // element and lane in one word (elements < 65536)
+                int tag = ((kj == INT_MAX ? 0xffff : (kj & 0xffff)) << 5) | lane;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float h2 = __shfl_xor_sync(0xffffffffu, kh, off);
+                    const float l2 = __shfl_xor_sync(0xffffffffu, kl, off);
+                    const int t2 = __shfl_xor_sync(0xffffffffu, tag, off);
+                    if (h2 < kh || (h2 == kh && (l2 < kl || (l2 == kl && t2 < tag)))) { kh = h2; kl = l2; tag = t2; }
+                }
+                if (kh == INFINITY) break;  // none left
+                const int src = tag & 31;
+                kj = (tag >> 5) == 0xffff ? -1 : (tag >> 5);
+                const int slot = __shfl_sync(0xffffffffu, ku, src);
+                if (lane == src) {
+                    if (slot == 31) tz = true;
+                    else taken |= 1u << slot;
+                }
+                F += (slot == 31) ? Fz : wk[kj];
+                if (F >= T) { found = true; rh = kh; rl = kl; rj = kj; }
+            }
+        }
+        if (!found) {
+            // the crossing lies above the window
+            st->cs[2] = 1u;
+            Hw = INFINITY;
+            continue;
+        }
+        // settled when the crossing's breakpoint lies in the window, or at or below 0 with 0 inside it
+        const bool le0 = rh < 0.f || (rh == 0.f && rl <= 0.f);
+        const bool inside = (rh > Lw || (rh == Lw && rl >= 0.f)) && (rh < Hw || (rh == Hw && rl <= 0.f));
+        if (inside || (le0 && Lw <= 0.f && 0.f <= Hw)) {
+            ok = true;
+            break;
+        }
+        st->cs[2] = 1u;
+        if (rh == -INFINITY) Lw = -INFINITY;
+        else {
+            Lw = fminf(Lw, nextafterf(rh, -INFINITY));  // |trailing part| <= half an ulp of the leading one
+            Hw = fmaxf(Hw, nextafterf(rh, INFINITY));
+        }
+    }
+    if (!ok) {
+        st->cs[3] = 1u;  // the FP32 decision stands
+        return;
+    }
+    if (rh < 0.f || (rh == 0.f && rl <= 0.f)) {
+        st->bn = 0.f; st->bln = 0.f; st->jn = -1;
+    } else {
+        st->bn = rh; st->bln = rl; st->jn = rj;
+    }
+}
+
 // One (target, side) task of complete clipping with Rn active rows.  RC is a compile-time bound on
 // Rn: the main launch instantiates RC = Rn = 1..4 with the multipliers in registers; the wide
 // launch instantiates RC = 8, 16, 32 for any Rn <= RC with the multipliers in the warp's shared
@@ -303,8 +677,10 @@ struct CCRows {
 // search range) the unsigned order of the bits is the order of the values.
 template <int RC, bool WIDE, bool SPEC>
 __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsigned* keys, unsigned short* cidx,
-                                        float* bsm, int* jsm, int Rn, int b, int c, int side, int lane,
-                                        unsigned long long& my_steps) {
+                                        float* bsm, float* blsm, int* jsm, int Rn, int b, int c, int side, int lane,
+                                        unsigned long long& my_steps, unsigned (&my_cs)[5]) {
+    // with two or more rows the FP32 decisions are certified (see cc_certify below)
+    constexpr bool CERT = WIDE || RC >= 2;
     const int n0 = a.n0;
     const int R = WIDE ? Rn : RC;
     // the target plane a.x + c0 (lower side; the upper side is the negated upper plane), or in
@@ -313,15 +689,19 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
     const float* ap = SPEC ? a.sA + o * n0 : (side ? a.uA + (size_t)c * n0 : a.lA + (size_t)c * n0);
     const float sa = (!SPEC && side) ? -1.f : 1.f;
     const float c0 = SPEC ? a.sc[o] : (side ? -a.uc[c] : a.lc[c]);
-    float beta[WIDE ? 1 : RC];
+    // multipliers as unevaluated sums beta_hi + beta_lo of two floats (the trailing part stays 0
+    // with one row); keys and the dual value use the leading parts
+    float beta[WIDE ? 1 : RC] = {};
     int jprev[WIDE ? 1 : RC];
     auto bget = [&](int p) -> float {
         if constexpr (WIDE) return bsm[p]; else return beta[p];
     };
+    // trailing parts in the warp's shared slots (read only by the certification)
 #pragma unroll
     for (int p = 0; p < RC; ++p) {
         if (WIDE && p >= R) break;
         if constexpr (WIDE) { bsm[p] = 0.f; jsm[p] = -1; } else { beta[p] = 0.f; jprev[p] = -1; }
+        if (CERT) blsm[p] = 0.f;
     }
     // With one row, a' = a in every sweep, so one pass already repeats bit for bit.  More
     // generally a row step depends only on the other rows' multipliers: a row whose inputs have
@@ -340,7 +720,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             ++my_steps;
             const float* rk = rw.rg + k * n0;
             const long long* wk = rw.w64 + k * n0;
-            float bk = 0.f;
+            float bk = 0.f, blk = 0.f;
             int jp = -1;
             if constexpr (WIDE) {
                 bk = bsm[k]; jp = jsm[k];
@@ -349,6 +729,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 for (int p = 0; p < RC; ++p)
                     if (p == k) { bk = beta[p]; jp = jprev[p]; }
             }
+            if (CERT) blk = blsm[k];
             // q_j from a' = a + sum_{p != k} beta_p g_p (fma chain in increasing p)
             auto q_of = [&](float av, int j) -> float {
                 float apr = sa * av;
@@ -486,6 +867,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             __syncwarp();
             float bn = 0.f;
             int jn = -1;
+            bool zdec = false;  // F(0) >= T: the FP32 decision is beta = 0
+            long long Fdec = 0; // F(< q*) of the FP32 decision q* (F(<= 0) when it is beta = 0)
             // bracket (lo, hi] of key bits with F(lo) < T <= F(hi); mn, mx, cnt: extent and size of the
             // breakpoints inside it
             unsigned lo = 0u, hi = QINF;
@@ -496,6 +879,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 if (Flt < T && T <= Fle) {
                     bn = qp;  // the same breakpoint as last time
                     jn = jp;
+                    Fdec = Flt;
                 } else {
                     // missed: F(0) and the extent of the side of qp that holds the answer
                     const unsigned kp = __float_as_uint(qp);
@@ -514,11 +898,15 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     const long long F0 = warp_sum64(f0);
                     if (lo == 0u) Flo = F0;
                     search = !(F0 >= T || W < T);
+                    zdec = F0 >= T;
+                    Fdec = F0;
                 }
             } else {
                 const long long F0 = ext ? warp_sum64(f0) : W - warp_sum64(f0);
                 Flo = F0;
                 search = !(F0 >= T || W < T);  // else beta = 0: slope at 0+ not positive, or no crossing
+                zdec = F0 >= T;
+                Fdec = F0;
             }
             if (search) {
                 unsigned cmin = __reduce_min_sync(0xffffffffu, mn);
@@ -593,10 +981,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                             const bool M = !L1 && d < e2;
                             const unsigned bal = __ballot_sync(0xffffffffu, M);
                             const int q = wpos + __popc(bal & below);
-                            if (M && q < CAPC) {
-                                keys[q] = kk;
-                                cidx[q] = (unsigned short)j;
-                            }
+                            if (M && q < CAPC) cidx[q] = (unsigned short)j;
                             wpos += __popc(bal);
                             if (L1) { f1 += w; ++c1; }
                             if (M) fM += w;
@@ -622,12 +1007,6 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                         if (keep) {
                             listed = true;
                             m = (int)ncnt;
-                        } else {
-                            // put back the keys the list overwrote
-                            const int wr = min(wpos, CAPC);
-                            for (int j = lane; j < wr; j += 32)
-                                keys[j] = __float_as_uint(q_of(__ldg(ap + j), j));
-                            __syncwarp();
                         }
                     }
                 }
@@ -659,18 +1038,15 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                         const int j = j0 + lane;
                         const bool v = j < m;
                         const int jj = v ? j : 0;
-                        const unsigned kk = keys[jj];
                         const int e = v ? (listed ? (int)cidx[jj] : jj) : 0;
+                        const unsigned kk = keys[e];
                         const unsigned d = v ? kk - cmin : 0xffffffffu;
                         const bool in = d <= span;
                         if (wr) {
                             // in-place compaction: every write lands at or before the position read
                             const unsigned bal = __ballot_sync(0xffffffffu, in);
                             const int q = wpos + __popc(bal & below);
-                            if (in) {
-                                keys[q] = kk;
-                                cidx[q] = (unsigned short)e;
-                            }
+                            if (in) cidx[q] = (unsigned short)e;
                             wpos += __popc(bal);
                         }
                         const unsigned long long w = (unsigned long long)wk[e];
@@ -694,12 +1070,13 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     }
                 }
                 bn = (ks != 0u) ? __uint_as_float(ks) : 0.f;
+                Fdec = Flo;  // F(< ks): the bracket's lower end is ks - 1
                 // the element holding the selected breakpoint (lowest index among ties)
                 if (ks != 0u) {
                     if (listed) {
                         int jm = INT_MAX;
                         for (int j = lane; j < m; j += 32)
-                            if (keys[j] == ks) jm = min(jm, (int)cidx[j]);
+                            if (keys[cidx[j]] == ks) jm = min(jm, (int)cidx[j]);
                         jm = __reduce_min_sync(0xffffffffu, jm);
                         jn = (jm == INT_MAX) ? -1 : jm;
                     } else {
@@ -711,6 +1088,29 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     }
                 }
             }
+            float bln = 0.f;
+            if constexpr (CERT) {
+                const int dec = (jn >= 0 && bn > 0.f) ? 1 : (zdec ? 0 : 2);
+                if (dec != 2) {
+                    CertState cst;
+                    cst.bn = bn; cst.bln = 0.f; cst.jn = jn;
+                    const float amx = SPEC ? a.samax[o] : __ldg(a.amax + (side ? a.U + c : c));
+                    if constexpr (WIDE) {
+                        cc_certify(n0, R, k, lane, rw.gs, rk, wk, keys, cidx, ap, sa, bsm, blsm, amx, T, Fdec, dec,
+                                   &cst);
+                    } else {
+                        // the leading parts in the warp's shared slots after the trailing ones
+#pragma unroll
+                        for (int p = 0; p < RC; ++p) blsm[RMAX_CC + p] = beta[p];
+                        __syncwarp();
+                        cc_certify(n0, R, k, lane, rw.gs, rk, wk, keys, cidx, ap, sa, blsm + RMAX_CC, blsm, amx, T,
+                                   Fdec, dec, &cst);
+                    }
+                    bn = cst.bn; bln = cst.bln; jn = cst.jn;
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) my_cs[i] += cst.cs[i];
+                }
+            }
             __syncwarp();  // the next step rewrites the key buffer
             if constexpr (WIDE) {
                 bsm[k] = bn; jsm[k] = jn;  // every lane writes the same values
@@ -719,7 +1119,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 for (int p = 0; p < RC; ++p)
                     if (p == k) { beta[p] = bn; jprev[p] = jn; }
             }
-            if (bn != bk) {
+            if (CERT) blsm[k] = bln;
+            if (bn != bk || bln != blk) {
                 changed = true;
                 dirty |= all_rows & ~(1u << k);
             }
@@ -800,7 +1201,16 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
     float cst = c0;
-    // rounding bound in FP32 with every operation rounded up (all terms are non-negative)
+    // Rounding bound gam * scale, scale = sum_j S_j max(|lo_j|, |hi_j|) + |c0| + sum_p beta_p |h_p| with
+    // S_j = |a_j| + sum_p beta_p |g_pj| (bounded through the root box: psc and Sg + |h| per row, in FP32
+    // with every operation rounded up).  Operation count, in units of u = 2^-24 times scale:
+    //  - v_j = a_j + sum_p beta_p g_pj: R fma roundings; the product with lo or hi: 1;
+    //  - the sums: the packed path adds ceil(n0/64) terms per component, 1 to combine them and 5 shuffle
+    //    levels; the scalar path ceil(n0/32) terms and 5 levels; cst = c0 + sum_p beta_p h_p: R fmas,
+    //    disjoint terms of the same scale;
+    //  - the dropped trailing parts of the multipliers change D by at most u * scale: 1.
+    // So R + ceil(n0/32) + 7 suffices on both paths; gam takes R + ceil(n0/32) + 12 (second-order terms
+    // are inside the factors 1.0001).  The final sum and the pad are rounded outward.
     float scale = __fadd_ru(psc, fabsf(c0));
 #pragma unroll
     for (int p = 0; p < RC; ++p) {
@@ -832,7 +1242,18 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             if (WIDE && p >= R) break;
             d += (double)bget(p) * (double)cc_hrow[p];
         }
-        val = __double2float_rd(d - ldexp((double)scale, -40));
+        // D at the leading parts differs from D at the full multipliers (the ascent's point) by at most
+        // sum_p |beta_lo,p| (sum_j |g_pj| max(|lo_j|, |hi_j|) + |h_p|); charged so that the bound never
+        // exceeds the value at the full multipliers (in the FP32 path the 12 u of slack in gam covers it)
+        float tpad = 0.f;
+        if (CERT) {
+#pragma unroll
+            for (int p = 0; p < RC; ++p) {
+                if (WIDE && p >= R) break;
+                tpad = __fmaf_ru(fabsf(blsm[p]), cc_SgH[p], tpad);
+            }
+        }
+        val = __double2float_rd(d - ldexp((double)scale, -40) - (double)tpad);
     }
     if (lane == 0) {
         if (SPEC) { if (val > a.slower[o]) a.slower[o] = val; }
@@ -850,9 +1271,10 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
     const int lane = threadIdx.x & 31;
     const CCView sv = cc_view(n0, RsS, WIDE);
     __shared__ int s_item, s_pos, s_R, s_next;
-    __shared__ unsigned long long nsteps;
-    if (threadIdx.x == 0) nsteps = 0;
+    __shared__ unsigned long long nsteps, ncs[5];
+    if (threadIdx.x == 0) { nsteps = 0; ncs[0] = ncs[1] = ncs[2] = ncs[3] = ncs[4] = 0; }
     unsigned long long my_steps = 0;
+    unsigned my_cs[5] = {0u, 0u, 0u, 0u, 0u};
     const int ibeg = WIDE ? 0 : *a.wide;
     const int total = WIDE ? *a.wide : a.ioff[B];
     const int np = *a.nplaced;
@@ -895,6 +1317,8 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
                 cc_hrow[threadIdx.x] = a.wh[(size_t)b * Rs + threadIdx.x];
                 cc_Sg[threadIdx.x] = a.wSg[(size_t)b * Rs + threadIdx.x];
                 cc_SgH[threadIdx.x] = __double2float_ru(cc_Sg[threadIdx.x] + fabs((double)cc_hrow[threadIdx.x]));
+                cc_Gm[threadIdx.x] = a.wGm[(size_t)b * Rs + threadIdx.x];
+                cc_Rm[threadIdx.x] = a.wRm[(size_t)b * Rs + threadIdx.x];
             }
             cur_b = b;
         }
@@ -935,23 +1359,31 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
                 if (a.mask[(size_t)b * a.U + c] != 0) continue;
             }
             if (WIDE) {
-                if (R <= 8) cc_task<8, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
-                else if (R <= 16) cc_task<16, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
-                else cc_task<32, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.jsm, R, b, c, side, lane, my_steps);
+                if (R <= 8) cc_task<8, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, R, b, c, side, lane, my_steps, my_cs);
+                else if (R <= 16) cc_task<16, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, R, b, c, side, lane, my_steps, my_cs);
+                else cc_task<32, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, R, b, c, side, lane, my_steps, my_cs);
             } else {
                 switch (R) {
-                    case 1: cc_task<1, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 1, b, c, side, lane, my_steps); break;
-                    case 2: cc_task<2, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 2, b, c, side, lane, my_steps); break;
-                    case 3: cc_task<3, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 3, b, c, side, lane, my_steps); break;
-                    default: cc_task<4, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, nullptr, 4, b, c, side, lane, my_steps); break;
+                    case 1: cc_task<1, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 1, b, c, side, lane, my_steps, my_cs); break;
+                    case 2: cc_task<2, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 2, b, c, side, lane, my_steps, my_cs); break;
+                    case 3: cc_task<3, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 3, b, c, side, lane, my_steps, my_cs); break;
+                    default: cc_task<4, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 4, b, c, side, lane, my_steps, my_cs); break;
                 }
             }
             __syncwarp();
         }
     }
-    if (a.steps && lane == 0 && my_steps) atomicAdd(&nsteps, my_steps);
+    if (a.steps && lane == 0) {
+        if (my_steps) atomicAdd(&nsteps, my_steps);
+        for (int i = 0; i < 5; ++i)
+            if (my_cs[i]) atomicAdd(&ncs[i], (unsigned long long)my_cs[i]);
+    }
     __syncthreads();
-    if (a.steps && threadIdx.x == 0 && nsteps) atomicAdd(a.steps, nsteps);
+    if (a.steps && threadIdx.x == 0) {
+        if (nsteps) atomicAdd(a.steps, nsteps);
+        for (int i = 0; i < 5; ++i)
+            if (ncs[i]) atomicAdd(a.steps + 1 + i, ncs[i]);
+    }
 }
 
 // stability of the targets after clipping; l > u means the subdomain is empty
@@ -981,7 +1413,7 @@ cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
     const size_t RsS = a.Rs < RTPL ? a.Rs : RTPL;
     // main: staged rows + per warp keys and list; wide: per warp keys, list and multiplier slots
     const size_t fixed = WIDE ? 0 : RsS * a.n0 * (8 + 4 + 4);
-    const size_t per_warp = n0r * 4 + CAPC * 2 + (WIDE ? (size_t)RMAX_CC * 8 : 0);
+    const size_t per_warp = n0r * 4 + CAPC * 2 + (WIDE ? (size_t)RMAX_CC * 12 : (size_t)RMAX_CC * 8);
     const size_t limit = 220 * 1024;
     int nw = NWARP;
     while (nw > 1 && fixed + nw * per_warp > limit) --nw;
@@ -1015,20 +1447,27 @@ cv_status launch_cc(const CCArgs& a, int* launches, cudaStream_t st) {
 // sum_j |A_j| max(|lo_j|, |hi_j|) + |c|, an upper bound (FP32, every operation rounded up: the
 // terms are non-negative) for the error pad of the dual value
 __global__ void k_spec_scale(int m, int n0, const float* A, const float* c, const float* lo, const float* hi,
-                             float* sscale) {
+                             float* sscale, float* samax) {
     const size_t o = blockIdx.x;  // b * m + r
     const size_t b = o / (size_t)m;
-    float mag = 0.f;
-    for (int j = threadIdx.x; j < n0; j += blockDim.x)
-        mag = __fmaf_ru(fabsf(A[o * n0 + j]), fmaxf(fabsf(lo[b * n0 + j]), fabsf(hi[b * n0 + j])), mag);
-    __shared__ float red[32];
-    for (int off = 16; off > 0; off >>= 1) mag = __fadd_ru(mag, __shfl_xor_sync(0xffffffffu, mag, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
+    float mag = 0.f, amx = 0.f;
+    for (int j = threadIdx.x; j < n0; j += blockDim.x) {
+        const float av = fabsf(A[o * n0 + j]);
+        mag = __fmaf_ru(av, fmaxf(fabsf(lo[b * n0 + j]), fabsf(hi[b * n0 + j])), mag);
+        amx = fmaxf(amx, av);
+    }
+    __shared__ float red[32], redm[32];
+    for (int off = 16; off > 0; off >>= 1) {
+        mag = __fadd_ru(mag, __shfl_xor_sync(0xffffffffu, mag, off));
+        amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, off));
+    }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = mag; redm[threadIdx.x >> 5] = amx; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = __fadd_ru(t, red[w]);
+        float t = 0.f, mm = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t = __fadd_ru(t, red[w]); mm = fmaxf(mm, redm[w]); }
         sscale[o] = __fadd_ru(t, fabsf(c[o]));
+        samax[o] = mm;
     }
 }
 
@@ -1042,7 +1481,7 @@ size_t cv_cc_workspace(int B, int Rmax, int n0) {
     s += cv_align256(b * Rs * n0 * 4) * 2;  // wg, wrg
     s += cv_align256(b * Rs * n0 * 8);      // ww
     s += cv_align256(b * Rs * 8) * 3;       // wT, wW, wSg
-    s += cv_align256(b * Rs * 4);           // wh
+    s += cv_align256(b * Rs * 4) * 3;       // wh, wGm, wRm
     s += cv_align256(b * 4) * 3;            // wR, wcnt, order
     s += cv_align256((b + 1) * 4);          // ioff
     s += 256 * 2;                           // nplaced, ticket
@@ -1074,6 +1513,7 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     a.lo = lo_clip; a.hi = hi_clip;
     a.l = l; a.u = u; a.mask = mask; a.infeasible = infeasible; a.status = net->status;
     a.steps = step_counter;
+    a.amax = cache->amax; a.samax = nullptr;
     // workspace carve (the layout of cv_cc_workspace)
     const size_t B = in->B, Rs = a.Rs, n0 = cache->n0;
     char* p = ws + lay->cc;
@@ -1084,6 +1524,8 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     a.wW = (long long*)p; p += cv_align256(B * Rs * 8);
     a.wSg = (double*)p; p += cv_align256(B * Rs * 8);
     a.wh = (float*)p; p += cv_align256(B * Rs * 4);
+    a.wGm = (float*)p; p += cv_align256(B * Rs * 4);
+    a.wRm = (float*)p; p += cv_align256(B * Rs * 4);
     a.wR = (int*)p; p += cv_align256(B * 4);
     a.wcnt = (int*)p; p += cv_align256(B * 4);
     a.order = (int*)p; p += cv_align256(B * 4);
@@ -1106,7 +1548,7 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
 
 cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
                               const cv_options* opt, const cv_ws_layout* lay, char* ws, float* sscale,
-                              int* launches, cudaStream_t st) {
+                              unsigned long long* step_counter, int* launches, cudaStream_t st) {
     (void)net;
     if (opt->sweeps <= 0 || lay->Rmax == 0 || in->B == 0 || in->m == 0) return CV_OK;
     if (lay->Rmax > RMAX_CC) {
@@ -1129,6 +1571,9 @@ cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv
     a.infeasible = out->infeasible; a.status = cache->net->status;
     a.spec = 1; a.m = in->m;
     a.sA = out->final_A; a.sc = out->final_c; a.sscale = sscale; a.slower = out->lower;
+    a.amax = cache->amax;
+    a.samax = sscale + (size_t)in->B * in->m;  // the scratch holds the scales, then the maxima
+    a.steps = step_counter;
     const size_t B = in->B, Rs = a.Rs, n0 = cache->n0;
     char* p = ws + lay->cc;
     a.wg = (float*)p; p += cv_align256(B * Rs * n0 * 4);
@@ -1138,6 +1583,8 @@ cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv
     a.wW = (long long*)p; p += cv_align256(B * Rs * 8);
     a.wSg = (double*)p; p += cv_align256(B * Rs * 8);
     a.wh = (float*)p; p += cv_align256(B * Rs * 4);
+    a.wGm = (float*)p; p += cv_align256(B * Rs * 4);
+    a.wRm = (float*)p; p += cv_align256(B * Rs * 4);
     a.wR = (int*)p; p += cv_align256(B * 4);
     a.wcnt = (int*)p; p += cv_align256(B * 4);
     a.order = (int*)p; p += cv_align256(B * 4);
@@ -1147,7 +1594,7 @@ cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv
     p += 256;
     a.ticket = (unsigned*)p;
     k_spec_scale<<<(unsigned)(B * in->m), 256, 0, st>>>(in->m, (int)n0, out->final_A, out->final_c, out->lo_clip,
-                                                       out->hi_clip, sscale);
+                                                       out->hi_clip, sscale, sscale + B * in->m);
     CV_LAUNCH_CHECK("k_spec_scale");
     k_cc_prep<<<in->B, 256, 0, st>>>(a);
     CV_LAUNCH_CHECK("k_cc_prep");

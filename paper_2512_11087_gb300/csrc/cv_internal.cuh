@@ -81,6 +81,7 @@ struct cv_cache {
     float* PC;         // [2U x 2n0]: row c < U: [A̲⁺_c | A̲⁻_c]; row U+c: [Ā⁻_c | Ā⁺_c]
     float* PCc;        // [2U]: lc, uc
     float* pscale;     // [2U]: |A|.xmag_root + |c| of the lower / upper plane
+    float* amax;       // [2U]: max_q |A_q| of the lower / upper plane (complete clipping's error bounds)
     float* root_l;     // [H]
     float* root_u;     // [H]
     int8_t* root_state;// [H] +1 / -1 / 0
@@ -92,9 +93,10 @@ struct cv_cache {
     int cc_items[3];   // complete clipping: tasks per work item for 1, 2 and more active rows
 };
 
+#define CV_TIMER_COUNTERS 6
 struct cv_timer {
     cudaEvent_t ev[CV_N_PHASES + 1];
-    unsigned long long* d_steps;  // device counter of complete-clipping row steps
+    unsigned long long* d_steps;  // device counters: complete-clipping row steps, then cv_timer_read_cc's five
     int launches;
     bool used;
 };
@@ -110,10 +112,11 @@ struct cv_ws_layout {
     int R, Rmax, ncb;  // rows of the spec backward, max constraint rows, column blocks
 };
 size_t cv_cc_workspace(int B, int Rmax, int n0);  // complete-clipping region (cv_complete.cu)
-// complete clipping of the spec rows' final planes (cv_complete.cu); sscale: [B x m] floats of scratch
+// complete clipping of the spec rows' final planes (cv_complete.cu); sscale: [2 x B x m] floats of scratch;
+// step_counter: optional device counters as in cv_launch_complete (six)
 cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
                               const cv_options* opt, const cv_ws_layout* lay, char* ws, float* sscale,
-                              int* launches, cudaStream_t st);
+                              unsigned long long* step_counter, int* launches, cudaStream_t st);
 cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
                      int max_rows, int precision, cv_ws_layout* lay);
 

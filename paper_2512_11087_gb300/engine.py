@@ -91,6 +91,28 @@ class Round:
         self.ws_bytes = capi.cv_bound_batch_workspace(net.handle, net.cache, probe, self.opt)
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
         self.bo = capi.make_batch_out(**self.out)
+        self.timer = None
+
+    def __del__(self):
+        if getattr(self, "timer", None) is not None:
+            try:
+                capi.cv_timer_destroy(self.timer)
+            except Exception:
+                pass
+            self.timer = None
+
+    def enable_timer(self):
+        """Record phase times and complete clipping's counters on every later call (cv_timer)."""
+        if self.timer is None:
+            self.timer = capi.cv_timer_create()
+            self.opt.timer = self.timer
+        return self
+
+    def cc_stats(self):
+        """(row steps, certified row steps, with several candidates, widened, left with the FP32 decision,
+        of those over the candidate limit) of the last call run with the timer."""
+        _, _, steps = capi.cv_timer_read(self.timer)
+        return (steps,) + capi.cv_timer_read_cc(self.timer)
 
     def _bi(self, lo, hi, C, t, l_in, u_in, split_off, split_ids, row_off, G, h, alpha, tgt_off, tgt_ids):
         return capi.make_batch_in(self.B, lo, hi, self.m, C, t, l_in=l_in, u_in=u_in, split_off=split_off,

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
 SOUND = 1e-12
+LAST_CC_STATS = []  # decision counters of the last gpu_round (complete clipping)
 
 
 def gpu_round(case: Case, precision=0, **kw):
@@ -30,12 +31,18 @@ def gpu_round(case: Case, precision=0, **kw):
                   f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
     rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, max_rows=case.max_rows, relaxed=case.relaxed,
                   sweeps=case.sweeps, precision=precision, alpha_mode=case.alpha_mode, enforce_splits=case.enforce)
+    rnd.enable_timer()
     d = E.to_dev
     out = rnd.run(d(case.lo), d(case.hi), d(case.C), d(case.t), split_off=d(case.split_off),
                   split_ids=d(case.split_ids), row_off=d(case.row_off), G=d(case.G), h=d(case.h),
                   tgt_off=d(case.tgt_off), tgt_ids=d(case.tgt_ids), **kw)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
+    # complete clipping's decisions with two or more rows: every one certified
+    st = rnd.cc_stats()
+    LAST_CC_STATS[:] = st
+    print("cc row steps, certified, several candidates, widened, uncertified, over the limit:", st)
+    assert st[4] == 0, st
     from paper_2512_11087_gb300 import capi
     assert capi.cv_device_status(net.handle) == 0
     net.close()
@@ -311,7 +318,7 @@ def test_bench_workload_full_size_sampled(precision):
     case = Case(cfg["dims"], cfg["B"], cfg["kmin"], cfg["kmax"], cfg["eps"], sweeps=cfg["sweeps"], seed=0)
     g = gpu_round(case, precision=precision)
     rng = np.random.default_rng(0)
-    sample = np.unique(np.concatenate([rng.choice(case.B, 12, replace=False), [0, case.B - 1]]))
+    sample = np.unique(np.concatenate([rng.choice(case.B, 254, replace=False), [0, case.B - 1]]))
     sub = Case.__new__(Case)
     sub.__dict__.update(case.__dict__)
     sub.B = sample.size

@@ -1,11 +1,11 @@
 """Complete clipping of the spec rows' final planes (cv_spec_clip) through the C-ABI.
 
-Parity: after a GPU round with final planes out, every unproven spec row of every subdomain is
-recomputed by the oracle's Algorithm 1 (FP32 breakpoint decisions, complete_clip_f32) on the same
-FP32 plane, clipped box and active rows; the GPU bound must lie within 1e-5 of the oracle's scale
-and never above it (beyond the oracle's own rounding), rows already proven stay bit for bit, and
-verified follows the new bounds.  Soundness: on a small network the new bounds hold at sampled
-feasible points."""
+Parity: the oracle runs its own round with final planes (FP64 CROWN, its clipped box) and applies
+its FP64 Algorithm 1 (complete_clip) to every spec row it leaves unproven, over that plane, box and
+the subdomain's active rows; the GPU's round followed by cv_spec_clip must lie within 1e-5 of the
+oracle's scale and never above it (beyond the oracle's own rounding).  Rows the GPU had already
+proven stay bit for bit, and verified follows the new bounds.  No oracle input comes from the GPU.
+Soundness: on a small network the new bounds hold at sampled feasible points."""
 import numpy as np
 import pytest
 
@@ -74,7 +74,9 @@ def test_spec_clip_parity(kw):
     from oracle import oracle as O
     case = Case(**kw)
     g0, g1 = _run(case)
+    o = case.oracle(want_final=True)
     raised = 0
+    assert np.array_equal(g0["infeasible"], o["infeasible"])
     for b in range(case.B):
         if g0["infeasible"][b]:
             assert np.array_equal(g1["lower"][b].view(np.uint32), g0["lower"][b].view(np.uint32))
@@ -85,10 +87,11 @@ def test_spec_clip_parity(kw):
             if l0 > 0 or h.size == 0:
                 assert np.float32(l1).view(np.uint32) == np.float32(l0).view(np.uint32)
                 continue
-            v, _, sc = O.complete_clip_f32(g0["final_A"][b, r], float(g0["final_c"][b, r]), G, h,
-                                           g0["lo_clip"][b].astype(np.float64), g0["hi_clip"][b].astype(np.float64),
-                                           case.sweeps)
-            want = max(l0, v)
+            # the oracle's own plane and box
+            v, _, sc = O.complete_clip(o["final_A"][b, r], float(o["final_c"][b, r]), G, h, o["lo_clip"][b],
+                                       o["hi_clip"][b], case.sweeps)
+            want = max(float(o["lower"][b, r]), v)
+            sc = max(sc, float(o["lower_scale"][b, r]))
             assert l1 >= l0
             assert l1 <= want + SOUND * sc, (b, r, l1, want)
             assert abs(l1 - want) <= TOL * sc, (b, r, l1, want, sc)

@@ -151,43 +151,6 @@ def test_order_dependency_example():
     assert np.all(p_lo <= b_lo) and np.all(p_hi >= b_hi)
 
 
-def test_fp32_decision_variant_matches_theorem_1():
-    # Algorithm 1 with FP32 breakpoint decisions: one row still gives the LP optimum up to
-    # the FP32 rounding of beta, and the dual value is never above the LP optimum
-    rng = np.random.default_rng(7)
-    for _ in range(200):
-        n = int(rng.integers(1, 6))
-        lo, hi = rand_box(rng, n)
-        lo, hi = lo.astype(np.float32).astype(np.float64), hi.astype(np.float32).astype(np.float64)
-        g, h = cutting_row(rng, lo, hi)
-        g = g.astype(np.float32).astype(np.float64)
-        a, c = rng.normal(size=n).astype(np.float32).astype(np.float64), rng.normal()
-        lp = lp_vertex(a, c, [g], [h], lo, hi)
-        v, beta, sc = O.complete_clip_f32(a, c, [g], [h], lo, hi, sweeps=2)
-        assert v <= lp + 1e-12 * sc
-        assert v == pytest.approx(lp, abs=1e-6 * sc)
-
-
-def test_fp32_decision_variant_multi_row():
-    rng = np.random.default_rng(8)
-    agree = 0
-    for _ in range(60):
-        n, R = int(rng.integers(2, 5)), int(rng.integers(2, 4))
-        lo, hi = rand_box(rng, n)
-        lo, hi = lo.astype(np.float32).astype(np.float64), hi.astype(np.float32).astype(np.float64)
-        x0 = lo + (hi - lo) * rng.uniform(0.3, 0.7, n)
-        G = rng.normal(size=(R, n)).astype(np.float32).astype(np.float64)
-        h = -(G @ x0) - rng.uniform(0.0, 0.3, R) * (np.abs(G) @ ((hi - lo) / 2))
-        a, c = rng.normal(size=n).astype(np.float32).astype(np.float64), rng.normal()
-        lp = lp_vertex(a, c, G, h, lo, hi)
-        v32, b32, sc = O.complete_clip_f32(a, c, G, h, lo, hi, sweeps=5)
-        v64, b64, _ = O.complete_clip(a, c, G, h, lo, hi, sweeps=5)
-        assert np.all(b32 >= 0) and v32 <= lp + 1e-12 * sc                    # weak duality
-        assert O.dual_value(a, c, G, h, lo, hi, b32.astype(np.float64)) == pytest.approx(v32, abs=1e-12 * sc)
-        agree += abs(v32 - v64) <= 1e-6 * sc
-    assert agree >= 55  # the FP64 and FP32-decision ascents end at the same point except near kinks
-
-
 def test_row_order_is_ascending_hyperplane_distance():
     # Constraint importance heuristic (Appendix, details of heuristics): rows ascend in the
     # distance of their hyperplane from the box centre.  The distance is measured here as the

@@ -56,7 +56,7 @@ def test_clipped_spec_plane_is_sound_and_not_looser():
             a64 = out["final_A"][b, r]
             a32 = a64.astype(np.float32).astype(np.float64)
             c32 = out["final_c"][b, r] - np.abs(a64 - a32) @ np.maximum(np.abs(lb), np.abs(ub))
-            v, beta, _ = O.complete_clip_f32(a32, c32, G, h, lb, ub, 10)
+            v, beta, _ = O.complete_clip(a32, c32, G, h, lb, ub, 10)
             plain = O.dual_value(a32, c32, G, h, lb, ub, np.zeros(len(h)))
             assert v >= plain - 1e-9 * (1 + abs(plain))
             if feas.any():

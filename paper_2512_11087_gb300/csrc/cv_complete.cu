@@ -60,7 +60,7 @@ constexpr int RTPL = 4;     // row counts up to this run in the main launch (two
 #define CV_CC_NWARP 14
 #endif
 constexpr int NWARP = CV_CC_NWARP;  // warps per block at most (two blocks per SM of 14 leave 72 registers a thread)
-constexpr int CAPC = 384;   // breakpoints a warp's compacted list holds
+constexpr int CAPC = 256;   // breakpoints a warp's compacted list holds
 constexpr int SAMP_MIN = 64;     // brackets with more breakpoints start from sampled pivots
 constexpr float SAMP_D = 0.10f;  // rank margin of the sampled pivots around the target fraction
 constexpr int PF = 4;       // coefficients loaded ahead per lane in the element loops
@@ -276,6 +276,8 @@ __shared__ float cc_Gm[RMAX_CC];       // max |g| of every row
 __shared__ float cc_Rm[RMAX_CC];       // max |fl(1/g)| of every row
 
 struct CCView {
+    float* blo;            // the staged subdomain's clipped box [n0] (lower ends)
+    float* bhi;            // (upper ends)
     unsigned* keys;        // this warp's keys
     long long* w64;        // staged rows (main launch)
     float* gs;
@@ -287,9 +289,9 @@ struct CCView {
 };
 
 // Main launch: keys [nw][n0r] | w64 [RsS][n0] | g [RsS][n0] | 1/g [RsS][n0] | list [nw][CAPC] |
-// multipliers' trailing parts and a copy of their leading parts [nw][2 RMAX_CC].
+// multipliers' trailing parts and a copy of their leading parts [nw][2 RMAX_CC] | box [2][n0].
 // Wide launch: keys [nw][n0r] | list [nw][CAPC] | multipliers [nw][RMAX_CC] | elements [nw][RMAX_CC] |
-// multipliers' trailing parts [nw][RMAX_CC].
+// multipliers' trailing parts [nw][RMAX_CC] | box [2][n0].
 __device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
     const int n0r = (n0 + 31) & ~31;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -303,6 +305,7 @@ __device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
         v.bsm = nullptr;
         v.blsm = (float*)((unsigned short*)(v.rg + RsS * n0) + nw * CAPC) + warp * 2 * RMAX_CC;
         v.jsm = nullptr;
+        v.blo = (float*)((unsigned short*)(v.rg + RsS * n0) + nw * CAPC) + nw * 2 * RMAX_CC;
     } else {
         unsigned short* list0 = (unsigned short*)((unsigned*)cc_smem + nw * n0r);
         v.cidx = list0 + warp * CAPC;
@@ -310,14 +313,36 @@ __device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
         v.bsm = b0 + warp * RMAX_CC;
         v.jsm = (int*)(b0 + nw * RMAX_CC) + warp * RMAX_CC;
         v.blsm = (float*)((int*)(b0 + nw * RMAX_CC) + nw * RMAX_CC) + warp * RMAX_CC;
+        v.blo = (float*)((int*)(b0 + nw * RMAX_CC) + nw * RMAX_CC) + nw * RMAX_CC;
         v.w64 = nullptr;
         v.gs = nullptr;
         v.rg = nullptr;
     }
+    v.bhi = v.blo + n0;
     return v;
 }
 
 constexpr unsigned QINF = 0x7f800000u;  // bits of +inf; breakpoints q > 0 have bits in (0, QINF]
+
+// Copies n floats from global src into the warp's shared buffer dst with cp.async, every copy in
+// flight at once, and waits for them (16-byte pieces when src is 16-byte aligned and n % 4 == 0;
+// dst is 16-byte aligned).  One L2 round trip per plane instead of one per element loop iteration.
+__device__ __forceinline__ void cc_plane_to_smem(unsigned* dst, const float* src, int n, int lane) {
+    const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+    const size_t gsrc = __cvta_generic_to_global(src);
+    if ((n & 3) == 0 && (gsrc & 15u) == 0) {
+        for (int c = lane; c < (n >> 2); c += 32)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16u * c), "l"(gsrc + 16u * c)
+                         : "memory");
+    } else {
+        for (int c = lane; c < n; c += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sdst + 4u * c), "l"(gsrc + 4u * c)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+}
 
 // Rows of the task's subdomain: staged in shared memory (main launch) or read from the
 // workspace (subdomains with more rows than the main launch stages).
@@ -554,11 +579,68 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
         }
         __syncwarp();
         long long Fz = 0, Fb = 0;
+        bool found = false;
         if (__any_sync(0xffffffffu, fz != 0ull)) Fz = warp_sum64(fz);
         if (__any_sync(0xffffffffu, fb != 0ull)) Fb = warp_sum64(fb);
         if (it == 0) Fb = Fdec - Fb;
         if (nc > 1) st->cs[1] = 1u;
-        if (spill && (nc > CAPC || (nc > 64 && 2 * nc > ((n0 + 31) & ~31)))) { st->cs[4] = 1u; break; }
+        if (spill && (nc > CAPC || (nc > 64 && 2 * nc > ((n0 + 31) & ~31)))) {
+            // Too many candidates to list: the crossing is found by bisection on the exact order
+            // (breakpoint's leading part, trailing part, element) without storing them, each step a pass
+            // that sums the weight of the candidates at or below a point (slow; rows with many near-ties).
+            st->cs[4] = 1u;
+            const bool it0 = it == 0;
+            auto ordf = [](float f) -> unsigned {
+                const unsigned u = __float_as_uint(f);
+                return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+            };
+            auto unord = [](unsigned o) -> float { return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o); };
+            // weight of the elements at or below (X1, X2, X3) in the exact order, plus Fb
+            auto count_le = [&](unsigned X1, unsigned X2, int X3) -> long long {
+                unsigned long long f = 0ull;
+                for (int j0 = 0; j0 < n0; j0 += 32) {
+                    const int j = j0 + lane;
+                    if (j >= n0) continue;
+                    const float q = keys_ok ? __uint_as_float(keys[j]) : key_calc(j);
+                    if (it0 && !(fabsf(q - qs) <= fmaf(sc1, fabsf(rk[j]), fmaf(stu, fabsf(q), sEs)))) continue;
+                    const float av = __ldg(ap + j);
+                    if (classify(j, q, av) != 2) continue;
+                    float kh, kl;
+                    ff_key(j, av, kh, kl);
+                    const unsigned o1 = ordf(kh), o2 = ordf(kl);
+                    if (o1 < X1 || (o1 == X1 && (o2 < X2 || (o2 == X2 && j <= X3)))) f += (unsigned long long)wk[j];
+                }
+                long long F2 = Fb + warp_sum64(f);
+                // the exact zeros: the point (0, 0, -1)
+                const unsigned z = ordf(0.f);
+                if (z < X1 || (z == X1 && (z < X2 || (z == X2 && -1 <= X3)))) F2 += Fz;
+                return F2;
+            };
+            if (Fb >= T) {
+                found = true;
+                rh = -INFINITY; rl = 0.f; rj = -1;
+            } else {
+                // invariants F(<= low end) < T <= F(<= high end); ordinal 0 lies below every key
+                unsigned l1 = 0u, h1 = 0xffffffffu;
+                while (h1 - l1 > 1u) {
+                    const unsigned m1 = l1 + ((h1 - l1) >> 1);
+                    if (count_le(m1, 0xffffffffu, INT_MAX) >= T) h1 = m1; else l1 = m1;
+                }
+                unsigned l2 = 0u, h2 = 0xffffffffu;
+                while (h2 - l2 > 1u) {
+                    const unsigned m2 = l2 + ((h2 - l2) >> 1);
+                    if (count_le(h1, m2, INT_MAX) >= T) h2 = m2; else l2 = m2;
+                }
+                int l3 = -2, h3 = n0;
+                while (h3 - l3 > 1) {
+                    const int m3 = l3 + ((h3 - l3) >> 1);
+                    if (count_le(h1, h2, m3) >= T) h3 = m3; else l3 = m3;
+                }
+                found = true;
+                rh = unord(h1); rl = unord(h2); rj = h3;
+            }
+        }
+        if (!found) {
         // 2. the candidates' breakpoints: per lane two in registers (slots 0, 1); in spill mode the first
         // 64 listed go to registers (lane t % 32, slot t / 32) and the rest over the key buffer
         // (keys[2t], keys[2t + 1]), after which keys are recomputed
@@ -586,7 +668,6 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
         }
         // 3. walk the candidates in exact order after Fb; the exact zeros form one group at 0
         long long F = Fb;
-        bool found = false;
         if (F >= T) {
             found = true;  // the crossing lies below the window
             rh = -INFINITY; rl = 0.f; rj = -1;
@@ -639,6 +720,7 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
                 if (F >= T) { found = true; rh = kh; rl = kl; rj = kj; }
             }
         }
+        }
         if (!found) {
             // the crossing lies above the window
             st->cs[2] = 1u;
@@ -677,8 +759,9 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
 // search range) the unsigned order of the bits is the order of the values.
 template <int RC, bool WIDE, bool SPEC>
 __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsigned* keys, unsigned short* cidx,
-                                        float* bsm, float* blsm, int* jsm, int Rn, int b, int c, int side, int lane,
-                                        unsigned long long& my_steps, unsigned (&my_cs)[5]) {
+                                        float* bsm, float* blsm, int* jsm, const float* blo, const float* bhi, int Rn,
+                                        int b, int c, int side, int lane, unsigned long long& my_steps,
+                                        unsigned (&my_cs)[5]) {
     // with two or more rows the FP32 decisions are certified (see cc_certify below)
     constexpr bool CERT = WIDE || RC >= 2;
     const int n0 = a.n0;
@@ -743,9 +826,12 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 }
                 return (-apr) * rk[j];
             };
+            // the target plane into the warp's key buffer; the key pass overwrites it with the keys
+            cc_plane_to_smem(keys, ap, n0, lane);
             // previous breakpoint of this row (same value for every lane)
             float qp = 0.f;
-            if (jp >= 0) qp = q_of(__ldg(ap + jp), jp);
+            if (jp >= 0) qp = q_of(__uint_as_float(keys[jp]), jp);
+            __syncwarp();
             const bool warm = qp > 0.f;
             const long long T = cc_T64[k];
             const long long W = cc_W64[k];
@@ -774,15 +860,13 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                         if (RC > 1) x = __ffma2_rn(make_float2(nb[p], nb[p]), *(const float2*)(rw.gs + p * n0 + j), x);
                     return __fmul2_rn(x, *(const float2*)(rk + j));
                 };
-                const float2* ap2 = (const float2*)ap;
-                constexpr int P2 = 1;  // pairs per lane per iteration (deeper unrolling spills)
+                const float2* ap2 = (const float2*)keys;  // the plane, overwritten pair by pair
+                constexpr int P2 = 1;  // pairs per lane per iteration
                 if (warm) {
-                    float2 avn = __ldg(ap2 + (min(2 * lane, n0 - 2) >> 1));
-#pragma unroll 1
+#pragma unroll 2
                     for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
                         float2 av[P2];
-                        av[0] = avn;  // loaded one iteration ahead (L2 latency)
-                        avn = __ldg(ap2 + (min(j0 + 64, n0 - 2) >> 1));
+                        av[0] = ap2[min(j0, n0 - 2) >> 1];
 #pragma unroll
                         for (int u = 0; u < P2; ++u) {
                             const int j = j0 + 64 * u;
@@ -802,12 +886,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     fle += flt;
                 } else {
                     ext = false;
-                    float2 avn = __ldg(ap2 + (min(2 * lane, n0 - 2) >> 1));
-#pragma unroll 1
+#pragma unroll 2
                     for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
                         float2 av[P2];
-                        av[0] = avn;  // loaded one iteration ahead (L2 latency)
-                        avn = __ldg(ap2 + (min(j0 + 64, n0 - 2) >> 1));
+                        av[0] = ap2[min(j0, n0 - 2) >> 1];
 #pragma unroll
                         for (int u = 0; u < P2; ++u) {
                             const int j = j0 + 64 * u;
@@ -827,7 +909,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
                         float av[PF];
 #pragma unroll
-                        for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
+                        for (int u = 0; u < PF; ++u) av[u] = __uint_as_float(keys[min(j0 + 32 * u, n0 - 1)]);
 #pragma unroll
                         for (int u = 0; u < PF; ++u) {
                             const int j = j0 + 32 * u;
@@ -845,7 +927,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
                         float av[PF];
 #pragma unroll
-                        for (int u = 0; u < PF; ++u) av[u] = __ldg(ap + min(j0 + 32 * u, n0 - 1));
+                        for (int u = 0; u < PF; ++u) av[u] = __uint_as_float(keys[min(j0 + 32 * u, n0 - 1)]);
 #pragma unroll
                         for (int u = 0; u < PF; ++u) {
                             const int j = j0 + 32 * u;
@@ -1136,16 +1218,20 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
         any |= (bget(p) != 0.f);
     }
     if (!any) return;
-    // dual objective at beta, FP32 with its rounding bound
-    const float* slo = a.lo + (size_t)b * n0;
-    const float* shi = a.hi + (size_t)b * n0;
+    // dual objective at beta, FP32 with its rounding bound: the plane again in the key buffer (the keys
+    // are no longer needed), the box as staged for the work item
+    __syncwarp();
+    cc_plane_to_smem(keys, ap, n0, lane);
+    const float* apl = (const float*)keys;
+    const float* slo = blo;
+    const float* shi = bhi;
     const float psc = SPEC ? a.sscale[o] : __ldg(a.pscale + (side ? a.U + c : c));
     const float cur = SPEC ? a.slower[o] : (side == 0 ? a.l[o] : -a.u[o]);
     float part = 0.f;
     if (!WIDE && (n0 & 1) == 0) {
         // two adjacent elements per lane, packed FP32: each lane sums at most ceil(n0/64) terms per
         // component and one more to combine them, within the ceil(n0/32) the rounding bound allows
-        const float2* ap2 = (const float2*)ap;
+        const float2* ap2 = (const float2*)apl;
         const float2* slo2 = (const float2*)slo;
         const float2* shi2 = (const float2*)shi;
         const float2 sa2 = make_float2(sa, sa);
@@ -1157,9 +1243,9 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             for (int u = 0; u < 2; ++u) {
                 const int jj = min(j0 + 64 * u, n0 - 2);
                 const bool in = j0 + 64 * u < n0;
-                av[u] = __ldg(ap2 + (jj >> 1));
-                lv[u] = in ? __ldg(slo2 + (jj >> 1)) : make_float2(0.f, 0.f);
-                hv[u] = in ? __ldg(shi2 + (jj >> 1)) : make_float2(0.f, 0.f);
+                av[u] = ap2[jj >> 1];
+                lv[u] = in ? slo2[jj >> 1] : make_float2(0.f, 0.f);
+                hv[u] = in ? shi2[jj >> 1] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -1181,9 +1267,9 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             for (int u = 0; u < PF; ++u) {
                 const int jj = min(j0 + 32 * u, n0 - 1);
                 const bool in = j0 + 32 * u < n0;
-                av[u] = __ldg(ap + jj);
-                lv[u] = in ? __ldg(slo + jj) : 0.f;
-                hv[u] = in ? __ldg(shi + jj) : 0.f;
+                av[u] = apl[jj];
+                lv[u] = in ? slo[jj] : 0.f;
+                hv[u] = in ? shi[jj] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < PF; ++u) {
@@ -1226,13 +1312,13 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
         // the stability decision is uncertain in FP32: evaluate D(beta) in FP64
         double d = 0.0;
         for (int j = lane; j < n0; j += 32) {
-            double v = (double)(sa * __ldg(ap + j));
+            double v = (double)(sa * apl[j]);
 #pragma unroll
             for (int p = 0; p < RC; ++p) {
                 if (WIDE && p >= R) break;
                 v += (double)bget(p) * (double)rw.gs[p * n0 + j];
             }
-            d += fmin(v * (double)__ldg(slo + j), v * (double)__ldg(shi + j));
+            d += fmin(v * (double)slo[j], v * (double)shi[j]);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
@@ -1311,6 +1397,10 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
                     sv.rg[i] = a.wrg[base + i];
                 }
             }
+            for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+                sv.blo[i] = a.lo[(size_t)b * n0 + i];
+                sv.bhi[i] = a.hi[(size_t)b * n0 + i];
+            }
             if (threadIdx.x < R) {
                 cc_T64[threadIdx.x] = a.wT[(size_t)b * Rs + threadIdx.x];
                 cc_W64[threadIdx.x] = a.wW[(size_t)b * Rs + threadIdx.x];
@@ -1359,15 +1449,15 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
                 if (a.mask[(size_t)b * a.U + c] != 0) continue;
             }
             if (WIDE) {
-                if (R <= 8) cc_task<8, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, R, b, c, side, lane, my_steps, my_cs);
-                else if (R <= 16) cc_task<16, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, R, b, c, side, lane, my_steps, my_cs);
-                else cc_task<32, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, R, b, c, side, lane, my_steps, my_cs);
+                if (R <= 8) cc_task<8, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, sv.blo, sv.bhi, R, b, c, side, lane, my_steps, my_cs);
+                else if (R <= 16) cc_task<16, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, sv.blo, sv.bhi, R, b, c, side, lane, my_steps, my_cs);
+                else cc_task<32, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, sv.blo, sv.bhi, R, b, c, side, lane, my_steps, my_cs);
             } else {
                 switch (R) {
-                    case 1: cc_task<1, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 1, b, c, side, lane, my_steps, my_cs); break;
-                    case 2: cc_task<2, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 2, b, c, side, lane, my_steps, my_cs); break;
-                    case 3: cc_task<3, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 3, b, c, side, lane, my_steps, my_cs); break;
-                    default: cc_task<4, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, 4, b, c, side, lane, my_steps, my_cs); break;
+                    case 1: cc_task<1, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 1, b, c, side, lane, my_steps, my_cs); break;
+                    case 2: cc_task<2, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 2, b, c, side, lane, my_steps, my_cs); break;
+                    case 3: cc_task<3, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 3, b, c, side, lane, my_steps, my_cs); break;
+                    default: cc_task<4, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 4, b, c, side, lane, my_steps, my_cs); break;
                 }
             }
             __syncwarp();
@@ -1412,7 +1502,7 @@ cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
     const size_t n0r = (a.n0 + 31) & ~31;
     const size_t RsS = a.Rs < RTPL ? a.Rs : RTPL;
     // main: staged rows + per warp keys and list; wide: per warp keys, list and multiplier slots
-    const size_t fixed = WIDE ? 0 : RsS * a.n0 * (8 + 4 + 4);
+    const size_t fixed = (WIDE ? 0 : RsS * a.n0 * (8 + 4 + 4)) + (size_t)a.n0 * 8;  // rows, box
     const size_t per_warp = n0r * 4 + CAPC * 2 + (WIDE ? (size_t)RMAX_CC * 12 : (size_t)RMAX_CC * 8);
     const size_t limit = 220 * 1024;
     int nw = NWARP;

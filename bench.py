@@ -24,7 +24,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CONFIG = "mlp784x256"
-ALG_OPS_BASE = 7  # per coordinate and row step of Algorithm 1, besides the argsort comparisons
+# lane operations per coordinate and row step of Algorithm 1 (a' and the breakpoint 3, the weight 1,
+# the slope update 3, the crossing test and bookkeeping 3): the count of the benchmark table
+CC_OPS_PER_COORD = 10
 
 
 def workload_desc(cfg, name=CONFIG):
@@ -48,8 +50,13 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--precision", default="bf16x8", choices=["fp32", "bf16x8"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--config", default=CONFIG, choices=["mlp784x256", "mlp784x512x8"],
-                   help="workload (default: the metric's workload; mlp784x512x8 is the BaB stress shape)")
+    p.add_argument("--config", default=CONFIG,
+                   choices=["mlp784x256", "mlp5x50", "cnn3x32", "mlp784x1024", "mlp784x512x8"],
+                   help="workload (default: the metric's workload, with the others nested in its line)")
+    p.add_argument("--full-stress", action="store_true",
+                   help="with --config mlp784x512x8: its own line at the full 65,536 subdomains")
+    p.add_argument("--no-other-configs", action="store_true",
+                   help="only the metric's workload (no nested lines for the other configurations)")
     p.add_argument("--relaxed", type=int, default=None, choices=[1, 2, 3],
                    help="relaxed clipping: 1 parallel (Algorithm 2, the workload's), 2 sequential (Algorithm 3), "
                         "3 sequential in the constraint-importance order")
@@ -123,7 +130,18 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_sample_rate(cfg, n_sub, offset=0):
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample_rate(cfg, n_sub, offset=0, threads=None):
     """Time the FP64 oracle on n_sub subdomains of the workload with all host threads.  The sample is
     evenly spaced over the batch the GPU arm bounds (rank 0's split draws of all B subdomains),
     starting at `offset`, so that it has the batch's mix of row counts (a subdomain whose rows the
@@ -145,7 +163,7 @@ def oracle_sample_rate(cfg, n_sub, offset=0):
         np.zeros(0, np.int32)
     lo, hi = WL.tile_box(lo0, hi0, n_sub)
     C, t = WL.margin_spec(cfg["dims"][-1])
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     O.bound_batch(net, cache, lo, hi, split_off=so, split_ids=si, C=C, t=t, relaxed=cfg["relaxed"],
                   sweeps=cfg["sweeps"], nthreads=cores)
@@ -439,9 +457,386 @@ def run_activation_bab(args, cfg):
 
 
 # ---------------------------------------------------------------- GPU arm
+# ---------------------------------------------------------------- the other workload configurations
+# One entry per further configuration of the benchmark table: its own metric, timing (CUDA events,
+# at least 3 warm-up steps, the L2 flushed before every timed step), the roofline of its dominant
+# phase and the oracle on a bounded sample.  The default run nests them in the headline's JSON line.
+
+def _timed(fn, steps, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts
+
+
+def _layers_of(cfg):
+    from paper_2512_11087_gb300 import workloads as WL
+    if "convs" in cfg:
+        return WL.he_cnn(cfg["in_shape"], cfg["convs"], cfg["fcs"], seed=0)
+    return WL.he_mlp(cfg["dims"], seed=0)
+
+
+def _macs(dims):
+    """Multiply-adds of one spec row's back-substitution through the (dense) layers."""
+    return sum(dims[i] * dims[i - 1] for i in range(1, len(dims)))
+
+
+def _oracle_rate(cfg, layers, lo0, hi0, n_sub, mk_batch, budget_s=5.0, spec_rows=None):
+    """Subdomains per second of the FP64 oracle on at most n_sub subdomains of the configuration's
+    batch (whole subdomains; the root cache is built first and not timed)."""
+    import numpy as np
+    from oracle import oracle as O
+    net = O.Net(layers)
+    cache = O.make_cache(O.root_crown(net, lo0, hi0))
+    cores = os.cpu_count() or 1
+    n = max(1, n_sub)
+    kw = mk_batch(cache, n)
+    t0 = time.perf_counter()
+    O.bound_batch(net, cache, kw.pop("lo"), kw.pop("hi"), nthreads=cores, **kw)
+    dt = time.perf_counter() - t0
+    return dict(value=n / dt, unit="subdomains/s", cores=cores, kind="oracle",
+                sample=f"{n} subdomains of the configuration's batch, FP64 C oracle ({dt:.1f} s on {cores} threads)")
+
+
+def bench_mlp5x50(steps, warmup, flush, stream, peaks, cpu=True):
+    """Configuration 1: 5->50x6->5, B = 256, 0-8 splits, one output-plane row per subdomain, relaxed
+    clipping, one spec row; launch-bound, timed as replays of a captured graph (microseconds per round)."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import engine as E, workloads as WL
+    cfg = WL.CONFIGS["mlp5x50"]
+    layers = _layers_of(cfg)
+    lo0, hi0 = WL.box(cfg["dims"][0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    net.build_cache(lo0, hi0)
+    ids = net.read_cache()["ids"]
+    B = cfg["B"]
+    C, t = WL.margin_spec(cfg["dims"][-1])
+    C, t = C[:1], t[:1]
+    d = E.to_dev
+    # the spec row's root plane (a GPU round on the root box), shifted to cut every box
+    r0 = E.Round(net, 1, 1, want_final=True)
+    o0 = r0.run(d(lo0[None]), d(hi0[None]), d(C), d(t))
+    a = o0["final_A"][0, 0].cpu().numpy()
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    ro, G, h = WL.shifted_plane_rows(a, 0.0, lo, hi, B, seed=2)
+    so, si = WL.draw_splits(ids, B, cfg["kmin"], cfg["kmax"], seed=1)
+    rnd = E.Round(net, B, 1, max_splits=cfg["kmax"], max_rows=1, relaxed=1, sweeps=0)
+    rnd.capture(d(lo), d(hi), d(C), d(t), split_off=d(so), split_ids=d(si), row_off=d(ro), G=d(G), h=d(h))
+    ts = _timed(lambda: rnd.replay(stream), steps, warmup, flush, stream)
+    ms = statistics.mean(ts)
+    out = dict(config="mlp5x50: ReLU MLP 5->50x6->5, box width 0.1 around U[-1,1]^5, B=256, 0-8 splits, one "
+                      "output-plane row per subdomain, relaxed clipping, spec row e0-e1; graph replays",
+               metric="microseconds per round", value=1e3 * ms, unit="us", higher_is_better=False,
+               subdomains_per_s=B / (ms / 1e3), steps=steps, warmup=warmup,
+               roofline=dict(bound="launch", note="a few microseconds of work per kernel: launch latency, not a "
+                                                   "throughput roofline"))
+    if cpu:
+        def mk(cache, n):
+            so2, si2 = WL.draw_splits(cache["ids"], n, cfg["kmin"], cfg["kmax"], seed=1)
+            l2, h2 = WL.tile_box(lo0, hi0, n)
+            return dict(lo=l2, hi=h2, split_off=so2, split_ids=si2, row_off=ro[:n + 1], G=G[:n], h=h[:n], C=C, t=t,
+                        relaxed=1, sweeps=0)
+        out["cpu_baseline"] = _oracle_rate(cfg, layers, lo0, hi0, B, mk)
+    capi_destroy_graph(rnd)
+    net.close()
+    return out
+
+
+def capi_destroy_graph(rnd):
+    from paper_2512_11087_gb300 import capi
+    if getattr(rnd, "graph", None) is not None:
+        capi.cv_graph_destroy(rnd.graph)
+        rnd.graph = None
+
+
+def _phase_roofline(phases, steps_cc, n0, dims, Bm, peaks, prec):
+    """Roofline of the dominant phase of a round: complete clipping against the measured FP32 issue
+    peak (about 10 lane operations per coordinate and row step), or the spec back-substitution
+    (2 x rows x sum_i n_i n_(i-1) flops) against the FP32 FMA peak (CUDA cores) or the BF16 tensor
+    peak divided by the 8 digit products of the split-precision path."""
+    names = ["rows+relaxed", "reconcretize", "complete_clip", "backsubst"]
+    k = max(range(4), key=lambda i: phases[i])
+    if k == 2:
+        ach = steps_cc * n0 * CC_OPS_PER_COORD / (phases[2] / 1e3) / 1e9
+        pk = peaks["fma_lane_gops"]
+        return dict(bound="alu", kernel="k_complete", phase=names[k], achieved=ach, peak=pk, unit="Gop/s",
+                    frac=ach / pk, traffic=None, peak_source="measured (cv_fp32_fma_peak, lane FMAs/s)")
+    if k == 3:
+        fl = 2.0 * Bm * _macs(dims) / (phases[3] / 1e3) / 1e12
+        if prec == 1:
+            pk = peaks["bf16_tflops"] / 8.0
+            src = "MEASURED_PEAKS bf16 burst / 8 digit products"
+            return dict(bound="tensor", kernel="k_tc_layer", phase=names[k], achieved=fl, peak=pk, unit="TFLOP/s",
+                        frac=fl / pk, traffic=None, peak_source=src)
+        pk = 2.0 * peaks["fma_lane_gops"] / 1e3
+        return dict(bound="alu", kernel="k_bwd_layer<float>", phase=names[k], achieved=fl, peak=pk,
+                    unit="TFLOP/s", frac=fl / pk, traffic=None, peak_source="measured FP32 FMA peak x 2 flops")
+    return dict(bound="hbm", phase=names[k], note="rows / re-concretisation dominate", achieved=None, peak=None)
+
+
+def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
+    """Configuration 3: the CIFAR-style CNN on 3x32x32, B = 2048, 1-16 splits, complete clipping (10
+    sweeps) on the top-20 BaBSR targets per hidden layer chosen from a first round's bounds; the timed
+    round is one replay of its captured graph.  Conv layers are dense (Toeplitz) inside the library,
+    whose tensor-core back-substitution takes at most 512 inputs per layer: this one runs the FP32 path."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
+    cfg = WL.CONFIGS["cnn3x32"]
+    layers = _layers_of(cfg)
+    n0 = int(np.prod(cfg["in_shape"]))
+    lo0, hi0 = WL.box(n0, cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    U = net.build_cache(lo0, hi0)
+    ids = net.read_cache()["ids"]
+    B = cfg["B"]
+    C, t = WL.margin_spec(layers[-1]["out_shape"][0])
+    m = C.shape[0]
+    so, si = WL.draw_splits(ids, B, cfg["kmin"], cfg["kmax"], seed=1)
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    d = E.to_dev
+    dlo, dhi, dC, dt_, dso, dsi = d(lo), d(hi), d(C), d(t), d(so), d(si)
+    r0 = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=0)
+    o0 = r0.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
+    toff, tids = E.select_targets(net, o0["l"], o0["u"], o0["mask"], cfg["topk"])
+    torch.cuda.synchronize()
+    ntg = int(toff[-1].item())
+    del r0
+    rnd = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=cfg["sweeps"])
+    rnd.enable_timer()
+    rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, tgt_off=toff, tgt_ids=tids)
+    ph, _, steps_cc = capi.cv_timer_read(rnd.timer)
+    rnd.opt.timer = None
+    rnd.capture(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, tgt_off=toff, tgt_ids=tids)
+    ts = _timed(lambda: rnd.replay(stream), steps, warmup, flush, stream)
+    ms = statistics.mean(ts)
+    dims = [n0] + [int(np.prod(l["out_shape"])) for l in layers]
+    out = dict(config=f"cnn3x32: ReLU CNN 3x32x32 -> conv16 4x4 s2 p1 -> conv32 4x4 s2 p1 -> conv32 3x3 s1 p1 -> "
+                      f"FC100 -> FC10, eps=2/255 around U[0,1] clipped to [0,1]; B={B}, 1-16 splits (uneven), "
+                      f"9 margin rows, relaxed + complete clipping (10 sweeps) on the top-20 targets per hidden "
+                      f"layer ({ntg} in all); FP32 path; one captured-graph replay per round",
+               metric="subdomains bounded+clipped per second", value=B / (ms / 1e3), unit="subdomains/s",
+               higher_is_better=True, ms_per_step=ms, steps=steps, warmup=warmup, cached_neurons=U,
+               phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
+                                 [round(x, 3) for x in ph])),
+               roofline=_phase_roofline(ph, steps_cc, n0, dims, B * m, peaks, 0))
+    if cpu:
+        from oracle import oracle as O
+        onet = O.Net(layers)
+
+        def mk(cache, n):
+            # the oracle's own top-20 targets, from its own round without complete clipping (not timed)
+            so2, si2 = WL.draw_splits(cache["ids"], n, cfg["kmin"], cfg["kmax"], seed=1)
+            l2, h2 = WL.tile_box(lo0, hi0, n)
+            o = O.bound_batch(onet, cache, l2, h2, split_off=so2, split_ids=si2, C=C, t=t, relaxed=1, sweeps=0,
+                              nthreads=os.cpu_count() or 1)
+            mask = np.where(o["l"] >= 0, 1, np.where(o["u"] <= 0, -1, 0)).astype(np.int8)
+            to, ti = O.select_targets(O.layer_of_slots(onet, cache["ids"]), o["l"], o["u"], mask, None, cfg["topk"])
+            return dict(lo=l2, hi=h2, split_off=so2, split_ids=si2, C=C, t=t, relaxed=1, sweeps=cfg["sweeps"],
+                        tgt_off=to, tgt_ids=ti)
+        out["cpu_baseline"] = _oracle_rate(cfg, layers, lo0, hi0, 4, mk)
+    capi_destroy_graph(rnd)
+    net.close()
+    return out
+
+
+def bench_alpha(steps, warmup, flush, stream, peaks, cpu=True, adam_steps=20):
+    """Configuration 4: slope optimisation on 784->1024x4->10, B = 1024, 0-12 splits: one step is 20
+    Adam iterations (cv_alpha_grad: forward keeping the layer products, reverse sweep of the adjoint;
+    cv_alpha_adam) on the bounds, box and masks of a round.  Layers of 1024 inputs exceed the
+    tensor-core back-substitution's 512, so the contractions run on CUDA cores (FP32)."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
+    cfg = WL.CONFIGS["mlp784x1024"]
+    dims = cfg["dims"]
+    layers = _layers_of(cfg)
+    lo0, hi0 = WL.box(dims[0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    U = net.build_cache(lo0, hi0)
+    ids = net.read_cache()["ids"]
+    B = cfg["B"]
+    C, t = WL.margin_spec(dims[-1])
+    m = C.shape[0]
+    so, si = WL.draw_splits(ids, B, cfg["kmin"], cfg["kmax"], seed=1)
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    d = E.to_dev
+    rnd = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=0)
+    o = rnd.run(d(lo), d(hi), d(C), d(t), split_off=d(so), split_ids=d(si))
+    st = E.AlphaState(net, o["lo_clip"], o["hi_clip"], o["l"], o["u"], o["mask"], d(C), d(t))
+    H = net.H
+    alpha = torch.ones(B, m, H, dtype=torch.float32, device="cuda")
+    m1, m2 = torch.zeros_like(alpha), torch.zeros_like(alpha)
+    lower = torch.empty(B, m, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(alpha)
+    a0 = alpha.clone()
+    ai = capi.make_alpha_in(B, m, st.lo, st.hi, st.l, st.u, st.mask, st.C, st.t, alpha, None)
+
+    def step():
+        alpha.copy_(a0)
+        m1.zero_()
+        m2.zero_()
+        for it in range(1, adam_steps + 1):
+            capi.cv_alpha_grad(net.handle, net.cache, ai, lower, grad, st.ws, st.ws_bytes, stream)
+            capi.cv_alpha_adam(alpha, m1, m2, grad, it, 0.1 * 0.98 ** (it - 1), stream=stream)
+
+    capi.cv_alpha_grad(net.handle, net.cache, ai, lower, grad, st.ws, st.ws_bytes, stream)
+    f0 = float(lower[torch.isfinite(lower)].double().mean())
+    ts = _timed(step, steps, warmup, flush, stream)
+    capi.cv_alpha_grad(net.handle, net.cache, ai, lower, grad, st.ws, st.ws_bytes, stream)
+    f1 = float(lower[torch.isfinite(lower)].double().mean())
+    ms = statistics.mean(ts)
+    # forward and reverse sweep: two contractions of B m rows through the layers per iteration
+    fl = adam_steps * 2 * 2.0 * B * m * _macs(dims) / (ms / 1e3) / 1e12
+    pk = 2.0 * peaks["fma_lane_gops"] / 1e3
+    out = dict(config="mlp784x1024: ReLU MLP 784->1024x4->10, eps=0.02 around U[0,1]^784 clipped to [0,1]; B=1024, "
+                      "0-12 splits; per (subdomain, spec row, neuron) slopes, 20 Adam steps (lr 0.1, x0.98 per step) "
+                      "through the hand-written adjoint; FP32 CUDA-core contractions",
+               metric="subdomains optimised per second (20 Adam steps each)", value=B / (ms / 1e3),
+               unit="subdomains/s", higher_is_better=True, ms_per_step=ms, steps=steps, warmup=warmup,
+               cached_neurons=U, mean_bound_before=f0, mean_bound_after=f1,
+               roofline=dict(bound="alu", kernel="cv_alpha_grad (forward + reverse contractions)", achieved=fl,
+                             peak=pk, unit="TFLOP/s", frac=fl / pk, traffic=None,
+                             peak_source="measured FP32 FMA peak x 2 flops"))
+    if cpu:
+        from oracle import oracle as O
+        onet = O.Net(layers)
+        cache = O.make_cache(O.root_crown(onet, lo0, hi0))
+        n = 1
+        so2, si2 = WL.draw_splits(cache["ids"], n, cfg["kmin"], cfg["kmax"], seed=1)
+        l2, h2 = WL.tile_box(lo0, hi0, n)
+        orr = O.bound_batch(onet, cache, l2, h2, split_off=so2, split_ids=si2, C=C, t=t, relaxed=1, sweeps=0)
+        hl, hu = cache["root_l"].copy(), cache["root_u"].copy()
+        hl[cache["ids"]], hu[cache["ids"]] = orr["l"][0], orr["u"][0]
+        hs = np.where(hl >= 0, 1, np.where(hu <= 0, -1, 0)).astype(np.int8)
+        al = np.ones((m, onet.H))
+        mm1, mm2 = np.zeros_like(al), np.zeros_like(al)
+        t0 = time.perf_counter()
+        for it in range(1, adam_steps + 1):
+            _, g = O.alpha_grad(onet, hl, hu, hs, orr["lo_clip"][0], orr["hi_clip"][0], C, t, al)
+            O.adam_step(al, mm1, mm2, g, it, 0.1 * 0.98 ** (it - 1))
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = dict(value=n / dt, unit="subdomains/s", cores=1, kind="oracle",
+                                   sample=f"{n} subdomain, 20 oracle gradient + Adam steps in FP64 ({dt:.1f} s, one "
+                                          f"thread)")
+    net.close()
+    return out
+
+
+def bench_stress(steps, warmup, flush, stream, peaks, cpu=True, B=None):
+    """Configuration 5: the BaB stress shape 784->512x8->10 at its full 65,536 subdomains with 0-24
+    splits, relaxed + complete clipping (10 sweeps), split-precision (tensor-core) back-substitution;
+    the work-item sizes stay at their defaults (tuning would rerun the round many times)."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
+    cfg = WL.CONFIGS["mlp784x512x8"]
+    dims = cfg["dims"]
+    B = B or cfg["B"]
+    layers = _layers_of(cfg)
+    lo0, hi0 = WL.box(dims[0], cfg["eps"], seed=0, centre=cfg["centre"], clip01=cfg["clip01"])
+    net = E.Net(layers)
+    U = net.build_cache(lo0, hi0)
+    ids = net.read_cache()["ids"]
+    C, t = WL.margin_spec(dims[-1])
+    m = C.shape[0]
+    so, si = WL.draw_splits(ids, B, cfg["kmin"], cfg["kmax"], seed=1)
+    lo, hi = WL.tile_box(lo0, hi0, B)
+    d = E.to_dev
+    dlo, dhi, dC, dt_, dso, dsi = d(lo), d(hi), d(C), d(t), d(so), d(si)
+    rnd = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=cfg["sweeps"], precision=capi.CV_PREC_BF16X8)
+    rnd.enable_timer()
+    phases = []
+
+    def step():
+        rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, stream=stream)
+
+    ts = _timed(step, steps, warmup, flush, stream)
+    ph, _, steps_cc = capi.cv_timer_read(rnd.timer)
+    cs = rnd.cc_stats()
+    ms = statistics.mean(ts)
+    out = dict(config=f"mlp784x512x8: ReLU MLP 784->512x8->10, eps=0.02 around U[0,1]^784 clipped to [0,1]; B={B} "
+                      f"subdomains with 0-24 splits; 9 margin rows; relaxed + complete clipping (10 sweeps) on every "
+                      f"still-unstable cached neuron; split-BF16 tensor-core back-substitution; default item sizes",
+               metric="subdomains bounded+clipped per second", value=B / (ms / 1e3), unit="subdomains/s",
+               higher_is_better=True, ms_per_step=ms, steps=steps, warmup=warmup, cached_neurons=U,
+               phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
+                                 [round(x, 2) for x in ph])),
+               cc_row_steps=steps_cc, cc_certified=cs[1],
+               roofline=_phase_roofline(ph, steps_cc, dims[0], dims, B * m, peaks, 1))
+    if cpu:
+        def mk(cache, n):
+            off_all, ids_all = WL.draw_splits(cache["ids"], cfg["B"], cfg["kmin"], cfg["kmax"], seed=1)
+            pick = (np.arange(n) * cfg["B"]) // n
+            counts = off_all[pick + 1] - off_all[pick]
+            so2 = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+            si2 = np.concatenate([ids_all[off_all[b]:off_all[b + 1]] for b in pick]).astype(np.int32)
+            l2, h2 = WL.tile_box(lo0, hi0, n)
+            return dict(lo=l2, hi=h2, split_off=so2, split_ids=si2, C=C, t=t, relaxed=1, sweeps=cfg["sweeps"])
+        out["cpu_baseline"] = _oracle_rate(cfg, layers, lo0, hi0, 16, mk)
+    net.close()
+    return out
+
+
+def measure_peaks():
+    """The FP32 FMA issue peak (measured here) and the driver's measured HBM / BF16 peaks."""
+    from paper_2512_11087_gb300 import capi
+    fma, ms = capi.cv_fp32_fma_peak()
+    p = dict(fma_lane_gops=fma / 1e9, fma_probe_ms=ms)
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        p.update(hbm_gbs=mp["hbm_gbs"], bf16_tflops=mp["bf16_tflops"], bf16_source="measured")
+    except Exception:
+        p.update(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_source="fallback")
+    return p
+
+
+OTHER = {"mlp5x50": bench_mlp5x50, "cnn3x32": bench_cnn3x32, "mlp784x1024": bench_alpha, "mlp784x512x8": bench_stress}
+
+
+def run_other(args, names, cpu):
+    """The further configurations; returns {name: entry}."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    peaks = measure_peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for n in names:
+        steps = 2 if n == "mlp784x512x8" else max(2, min(args.steps, 5))
+        res[n] = OTHER[n](steps, max(args.warmup, 3), flush, stream, peaks, cpu=cpu)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return res, peaks
+
+
 def main():
     args = parse_args()
     from paper_2512_11087_gb300 import workloads as WL
+    if args.config in OTHER and args.config != "mlp784x512x8" or (args.config == "mlp784x512x8" and args.full_stress):
+        # a further configuration on its own line
+        res, peaks = run_other(args, [args.config], cpu=not args.no_cpu_baseline)
+        e = res[args.config]
+        line = dict(metric=e["metric"], value=e["value"], unit=e["unit"], n_gpus=1, steps=e["steps"],
+                    warmup=e["warmup"], ms_per_step=e.get("ms_per_step", e["value"] / 1e3 if e["unit"] == "us" else None),
+                    higher_is_better=e["higher_is_better"], scaling="weak", vs_baseline=None, dtype="f32",
+                    data="synthetic", config=dict(workload=e["config"]), roofline=e["roofline"], peaks=peaks)
+        for k in ("cpu_baseline", "phase_ms", "subdomains_per_s"):
+            if k in e:
+                line[k] = e[k]
+        print(json.dumps(line), flush=True)
+        return
     cfg = WL.CONFIGS[args.config]
     if args.subdomains > 0:
         cfg = dict(cfg, B=args.subdomains)
@@ -591,13 +986,15 @@ def main():
         del r32
     status = capi.cv_device_status(net.handle)
 
-    # roofline of the dominant kernel (complete clipping, ALU bound)
+    # roofline of the dominant kernel (complete clipping, ALU bound): the benchmark table's count of
+    # about 10 lane operations per coordinate and executed row step, against the measured FP32 issue
+    # peak (lane FMAs per second of the probe kernel)
     ph_mean = [statistics.mean(p[i] for p in phases) for i in range(capi.N_PHASES)]
     n0 = dims[0]
-    alg_ops = steps_cc * n0 * (ALG_OPS_BASE + float(np.log2(n0)))
+    peaks = measure_peaks()
+    alg_ops = steps_cc * n0 * CC_OPS_PER_COORD
     achieved = alg_ops / (ph_mean[2] / 1e3) / 1e9  # Gop/s
-    sm_clock = (clk or {}).get("sm_mhz") or 2070.0
-    peak = 152 * 128 * sm_clock / 1e3  # Gop/s: 152 SMs x 128 FP32/INT32 lanes x clock
+    peak = peaks["fma_lane_gops"]
     if rank == 0:
         line = dict(metric="subdomains bounded+clipped per second", value=value, unit="subdomains/s", n_gpus=world,
                     steps=args.steps, warmup=max(args.warmup, 3), ms_per_step=total_ms / args.steps,
@@ -609,18 +1006,30 @@ def main():
                                 phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
                                                   [round(x, 4) for x in ph_mean]))),
                     roofline=dict(bound="alu", kernel="k_complete", achieved=achieved, peak=peak, unit="Gop/s",
-                                  frac=achieved / peak, traffic=None,
-                                  alg_ops_per_launch=alg_ops, cc_row_steps=steps_cc),
+                                  frac=achieved / peak, traffic=None, alg_ops_per_launch=alg_ops,
+                                  ops_per_coordinate_and_row_step=CC_OPS_PER_COORD, cc_row_steps=steps_cc,
+                                  peak_source="measured: cv_fp32_fma_peak lane FMAs/s"),
                     e2e=dict(value=e2e_value, unit="subdomains/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
-                    gpu_launches=launches, device_status=status, clocks=clk)
+                    gpu_launches=launches, device_status=status, clocks=clk, peaks=peaks)
         if vs_fp32 is not None:
             line["vs_fp32_path"] = vs_fp32
         if world == 1 and not args.no_cpu_baseline:
             n, cores = pick_sample(cfg, 20.0)  # the pick overestimates the cost: about 10-15 s
             rate, dt, cores = oracle_sample_rate(cfg, n, offset=3)
+            n1 = max(4, n // 8)
+            rate1, dt1, _ = oracle_sample_rate(cfg, n1, offset=7, threads=1)
             line["cpu_baseline"] = dict(value=rate, unit="subdomains/s", cores=cores, kind="oracle",
+                                        cpu_model=cpu_model(), single_thread=rate1,
                                         sample=f"{n} subdomains of the benchmark batch (evenly spaced), FP64 C "
-                                               f"oracle ({dt:.1f} s on {cores} threads)")
+                                               f"oracle ({dt:.1f} s on {cores} threads); single thread: {n1} "
+                                               f"subdomains in {dt1:.1f} s")
+        if world == 1 and not args.no_other_configs and args.config == CONFIG and args.subdomains == 0:
+            # the benchmark table's other configurations, each with its own metric and roofline
+            rnd.ws = None
+            del rnd
+            torch.cuda.empty_cache()
+            line["other_configs"], _ = run_other(args, ["mlp5x50", "cnn3x32", "mlp784x1024", "mlp784x512x8"],
+                                                 cpu=not args.no_cpu_baseline)
         print(json.dumps(line), flush=True)
     capi.cv_timer_destroy(timer)
     net.close()

@@ -251,6 +251,18 @@ typedef struct cv_batch_out {
     float* final_c;
 } cv_batch_out;
 
+/* Checks a batch's device inputs before a round.  The round itself reads nothing back to the host
+ * (it never synchronises), so problems in device data reach it only as device status bits; this call
+ * finds them first, with one launch and one read-back (synchronous on `stream`).  Checked: CSR offsets
+ * non-decreasing with per-subdomain counts within max_splits / max_rows; split codes nonzero with
+ * |code| - 1 < n_hidden; target slots in [0, U); every box bound finite with lo <= hi; l_in / u_in
+ * and alpha without NaN, alpha in [0, 1]; G and h (row_off[B] rows), C and t finite.  Returns CV_ENAN
+ * for a non-finite value, CV_EINVAL for any other problem, CV_OK otherwise; code (may be NULL)
+ * receives the bits (1 CSR, 2 split code, 4 non-finite, 8 target slot, 32 lo > hi, 64 slope outside
+ * [0, 1]) and cv_last_error names them.  Nothing is modified.  (The paper has no counterpart: it
+ * defines the inputs, not their validation.) */
+cv_status cv_batch_check(cv_net* net, const cv_cache* cache, const cv_batch_in* in, int* code, void* stream);
+
 /* Bytes of device workspace cv_bound_batch needs for these sizes (in->B, in->m,
  * in->max_splits, in->max_rows; device pointers in `in` are not read). */
 cv_status cv_bound_batch_workspace(const cv_net* net, const cv_cache* cache,
@@ -454,6 +466,14 @@ cv_status cv_select_targets_workspace(int B, int U, size_t* bytes);
 cv_status cv_select_targets(const cv_net* net, const cv_cache* cache, int B, const float* l, const float* u,
                             const int8_t* mask, const float* weight, int k, int* tgt_off, int* tgt_ids,
                             void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Measured FP32 FMA issue rate of the current device, in lane FMAs per second (the roofline
+ * denominator of the ALU-bound complete clipping; the paper has no counterpart).  Times a kernel of
+ * independent FFMA chains (4 blocks of 256 threads per SM) with CUDA events, best of three launches
+ * after a warm-up; ms (may be NULL) receives that launch's time.  Synchronous on `stream`. */
+cv_status cv_fp32_fma_peak(double* lane_fma_per_s, float* ms, void* stream);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 

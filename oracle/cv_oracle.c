@@ -164,6 +164,8 @@ static void backward(const net_t* n, int k, int rows, const double* Lam_k,
                 V[j] = v;
             }
         }
+        /* rows are independent: threads over rows (single-threaded inside the per-subdomain loop) */
+#pragma omp parallel for schedule(static) if (rows >= 64)
         for (int r = 0; r < rows; ++r) {
             const double* lam = cur + (long)r * no;
             double* P = nxt + (long)r * ni;
@@ -174,10 +176,14 @@ static void backward(const net_t* n, int k, int rows, const double* Lam_k,
             }
             bias[r] += bsum;
             if (scale) scale[r] += ssum;
-            for (int q = 0; q < ni; ++q) {
-                double p = 0.0;
-                for (int j = 0; j < no; ++j) p += lam[j] * W[(long)j * ni + q];
-                P[q] = p;
+            /* P_q = sum_j lam_j W_jq, each sum taken over j in increasing order (the j loop outside
+               only makes the reads of W row-wise; every P_q sees the same additions in the same order) */
+            for (int q = 0; q < ni; ++q) P[q] = 0.0;
+            for (int j = 0; j < no; ++j) {
+                const double lj = lam[j];
+                if (lj == 0.0) continue;  /* a zero term adds nothing (inactive neurons, identity starts) */
+                const double* w = W + (long)j * ni;
+                for (int q = 0; q < ni; ++q) P[q] += lj * w[q];
             }
         }
         if (i == 1) {

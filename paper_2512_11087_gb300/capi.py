@@ -27,6 +27,7 @@ CV_RELAX_SEQUENTIAL_ORDERED = 3
 CV_ALPHA_ADAPTIVE = 0
 CV_ALPHA_ONE = 1
 CV_ALPHA_ZERO = 2
+CV_EINVAL, CV_ESHAPE, CV_ENAN, CV_ECUDA, CV_ETIMEOUT, CV_ENOMEM, CV_EUNSUPPORTED, CV_EWORKSPACE, CV_EDEVICE = range(1, 10)
 STATUS_NAMES = {0: "CV_OK", 1: "CV_EINVAL", 2: "CV_ESHAPE", 3: "CV_ENAN", 4: "CV_ECUDA", 5: "CV_ETIMEOUT",
                 6: "CV_ENOMEM", 7: "CV_EUNSUPPORTED", 8: "CV_EWORKSPACE", 9: "CV_EDEVICE"}
 
@@ -91,6 +92,8 @@ def load():
         "cv_cache_destroy": ([P], None),
         "cv_options_default": ([P], None),
         "cv_bound_batch_workspace": ([P, P, P, P, P], I),
+        "cv_batch_check": ([P, P, P, P, P], I),
+        "cv_fp32_fma_peak": ([P, P, P], I),
         "cv_bound_batch": ([P, P, P, P, P, P, ctypes.c_size_t, P], I),
         "cv_timer_create": ([ctypes.POINTER(P)], I),
         "cv_timer_destroy": ([P], None),
@@ -127,7 +130,7 @@ def load():
 def exported_symbols():
     return [n for n in ("cv_last_error", "cv_net_create", "cv_net_destroy", "cv_net_dims", "cv_device_status",
                         "cv_cache_build", "cv_cache_create", "cv_cache_size", "cv_cache_read", "cv_cache_destroy",
-                        "cv_options_default", "cv_bound_batch_workspace", "cv_bound_batch", "cv_timer_create",
+                        "cv_options_default", "cv_bound_batch_workspace", "cv_batch_check", "cv_fp32_fma_peak", "cv_bound_batch", "cv_timer_create",
                         "cv_timer_destroy", "cv_timer_read", "cv_timer_read_cc", "cv_relaxed_clip_static", "cv_alpha_grad_workspace",
                         "cv_alpha_grad", "cv_alpha_adam", "cv_graph_capture", "cv_graph_launch", "cv_graph_destroy",
                         "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc", "cv_input_split_workspace",
@@ -265,6 +268,28 @@ def make_batch_out(lower, lo_clip, hi_clip, l, u, mask, infeasible, verified, er
                         final_c=final_c).items():
         setattr(bo, name, ptr(v))
     return bo
+
+
+def cv_batch_check(net, cache, bi, stream=None):
+    """(status, bits) of the device-side input check; does not raise."""
+    code = ctypes.c_int()
+    st = load().cv_batch_check(net, cache, ctypes.byref(bi), ctypes.byref(code), stream_ptr(stream))
+    return st, code.value
+
+
+def cv_fp32_fma_peak(stream=None):
+    """(lane FMAs per second, ms of the timed launch) of the FFMA probe kernel."""
+    v = ctypes.c_double()
+    ms = ctypes.c_float()
+    _check(load().cv_fp32_fma_peak(ctypes.byref(v), ctypes.byref(ms), stream_ptr(stream)))
+    return v.value, ms.value
+
+
+def cv_device_status_raw(net, stream=None):
+    """(status, raw device status word) without raising."""
+    code = ctypes.c_int()
+    st = load().cv_device_status(net, stream_ptr(stream), ctypes.byref(code))
+    return st, code.value
 
 
 def cv_bound_batch_workspace(net, cache, bi, opt):

@@ -2,6 +2,7 @@
 // validation, workspace layout, and the launch sequence a2..a8 on the caller's stream.
 #include "cv_internal.cuh"
 
+#include <climits>
 #include <string.h>
 
 #include <string>
@@ -67,6 +68,12 @@ static cv_status validate(const cv_net* net, const cv_cache* cache, const cv_bat
     if (cache->net != net) { cv_set_error("cache was built for another network"); return CV_EINVAL; }
     if (in->B < 0 || in->m < 0 || in->max_splits < 0 || in->max_rows < 0) {
         cv_set_error("negative B, m, max_splits or max_rows");
+        return CV_EINVAL;
+    }
+    // sizes the kernels index with 32-bit integers
+    if ((long long)in->max_splits + in->max_rows > INT_MAX || (long long)in->B * in->m > INT_MAX ||
+        (long long)in->B * ((long long)in->max_splits + in->max_rows) > INT_MAX) {
+        cv_set_error("B, m, max_splits + max_rows too large (B x m and B x (max_splits + max_rows) must fit in int)");
         return CV_EINVAL;
     }
     if (opt->relaxed < CV_RELAX_OFF || opt->relaxed > CV_RELAX_SEQUENTIAL_ORDERED || opt->sweeps < 0 ||

@@ -229,8 +229,9 @@ extern "C" cv_status cv_net_create(const cv_layer_desc* layers, int n_layers, cv
         cudaMemcpy(n->W[i], Wp, nw * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(n->b[i], bp, n->dims[i] * sizeof(float), cudaMemcpyHostToDevice);
     }
-    if (dalloc(&n->status, 1)) { cv_net_destroy(n); return CV_ENOMEM; }
-    CV_CUDA(cudaMemset(n->status, 0, sizeof(int)));
+    // the device status word and, after it, cv_batch_check's result word
+    if (dalloc(&n->status, 2)) { cv_net_destroy(n); return CV_ENOMEM; }
+    CV_CUDA(cudaMemset(n->status, 0, 2 * sizeof(int)));
     CV_CUDA(cudaDeviceSynchronize());
     *out = n;
     return CV_OK;

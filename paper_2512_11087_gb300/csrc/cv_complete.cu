@@ -120,6 +120,7 @@ struct CCArgs {
     int* nplaced;                            // positions holding subdomains with work
     int* wide;                               // items of subdomains with more than RTPL rows (first)
     unsigned* ticket;                        // [2] item tickets: wide items, the rest
+    int allwide;                             // 1: the wide launch takes every item (rows too large to stage)
 };
 
 __device__ __forceinline__ int tpi_of(const CCArgs& a, int R) { return a.tpi[R <= 1 ? 0 : (R == 2 ? 1 : 2)]; }
@@ -1362,7 +1363,7 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
     unsigned long long my_steps = 0;
     unsigned my_cs[5] = {0u, 0u, 0u, 0u, 0u};
     const int ibeg = WIDE ? 0 : *a.wide;
-    const int total = WIDE ? *a.wide : a.ioff[B];
+    const int total = (WIDE && !a.allwide) ? *a.wide : a.ioff[B];
     const int np = *a.nplaced;
     int cur_b = -1;
     for (;;) {
@@ -1525,7 +1526,16 @@ cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
 }
 
 template <bool SPEC>
-cv_status launch_cc(const CCArgs& a, int* launches, cudaStream_t st) {
+cv_status launch_cc(const CCArgs& a0, int* launches, cudaStream_t st) {
+    // The main launch stages up to RTPL rows of a subdomain (16 bytes per element) and the box in shared
+    // memory; when that does not fit next to one warp's buffers (large inputs), the wide launch, which
+    // reads the rows from the L2-resident workspace, takes every subdomain.
+    CCArgs a = a0;
+    const size_t n0r = (a.n0 + 31) & ~31;
+    const size_t RsS = a.Rs < RTPL ? a.Rs : RTPL;
+    const size_t main_min = RsS * a.n0 * 16 + (size_t)a.n0 * 8 + n0r * 4 + CAPC * 2 + (size_t)RMAX_CC * 8;
+    a.allwide = main_min > 220 * 1024;
+    if (a.allwide) return launch_cc_one<true, SPEC>(a, launches, st);
     if (a.Rs > RTPL) {
         cv_status s = launch_cc_one<true, SPEC>(a, launches, st);
         if (s) return s;

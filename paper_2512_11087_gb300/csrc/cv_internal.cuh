@@ -45,7 +45,7 @@ struct cv_net {
     int wmax;                    // max width
     float* W[CV_MAX_LAYERS + 1]; // device, W[i]: dims[i] x dims[i-1] row-major (i = 1..L)
     float* b[CV_MAX_LAYERS + 1]; // device, b[i]: dims[i]
-    int* status;                 // device status word
+    int* status;                 // device status word; status[1]: cv_batch_check's result
     int device;
 };
 

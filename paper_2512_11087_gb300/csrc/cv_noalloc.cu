@@ -16,6 +16,7 @@
 // later reads, so nothing needs clearing, and calls whose kernels overlap on the GPU race on it.
 #include "cv_internal.cuh"
 
+#include <climits>
 #include <string.h>
 
 #include <mutex>
@@ -70,6 +71,11 @@ extern "C" cv_status cv_relaxed_clip_static(cv_net* net, const cv_cache* cache, 
     if ((!in->split_off && in->max_splits > 0) || (!in->row_off && in->max_rows > 0) ||
         (in->row_off && (!in->G || !in->h) && in->max_rows > 0)) {
         cv_set_error("cv_relaxed_clip_static: inconsistent split / row arguments");
+        return CV_EINVAL;
+    }
+    if ((long long)in->max_splits + in->max_rows > INT_MAX ||
+        (long long)in->B * ((long long)in->max_splits + in->max_rows) > INT_MAX) {
+        cv_set_error("cv_relaxed_clip_static: B x (max_splits + max_rows) must fit in int");
         return CV_EINVAL;
     }
     if (in->B == 0) return CV_OK;

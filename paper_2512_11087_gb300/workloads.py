@@ -194,6 +194,11 @@ CONFIGS = {
     # alpha optimisation: 784 -> 1024x4 -> 10
     "mlp784x1024": dict(dims=[784] + [1024] * 4 + [10], centre="unit", eps=0.02, clip01=True,
                         B=1024, kmin=0, kmax=12, out_rows=0, sweeps=0, relaxed=1),
+    # CIFAR-style CNN on 3x32x32: conv 16 4x4 s2 p1, conv 32 4x4 s2 p1, conv 32 3x3 s1 p1, FC 100, FC 10;
+    # 2048 subdomains with 1-16 splits; complete clipping on the top-20 targets per hidden layer
+    "cnn3x32": dict(in_shape=(3, 32, 32), convs=[(16, 4, 2, 1), (32, 4, 2, 1), (32, 3, 1, 1)], fcs=[100, 10],
+                    centre="unit", eps=2.0 / 255.0, clip01=True, B=2048, kmin=1, kmax=16, out_rows=0, sweeps=10,
+                    relaxed=1, topk=20),
     # BaB stress: 784 -> 512x8 -> 10, 65536 subdomains
     "mlp784x512x8": dict(dims=[784] + [512] * 8 + [10], centre="unit", eps=0.02, clip01=True,
                          B=65536, kmin=0, kmax=24, out_rows=0, sweeps=10, relaxed=1),

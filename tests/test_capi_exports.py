@@ -34,3 +34,23 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(capi, "_lib", None)
     with pytest.raises(RuntimeError):
         capi.load()
+
+
+def test_null_arguments_are_refused_without_a_launch():
+    # host-side validation runs before any CUDA call, so this needs no GPU (raw calls, NULL stream)
+    from paper_2512_11087_gb300 import capi
+    lib = capi.load()
+    opt = capi.cv_options_default()
+    bi = capi.make_batch_in(4, None, None, 1, None, None)
+    bo = capi.cv_batch_out()
+    assert lib.cv_bound_batch(None, None, ctypes.byref(bi), ctypes.byref(bo), ctypes.byref(opt), None, 0,
+                              None) == capi.CV_EINVAL
+    code = ctypes.c_int(-1)
+    assert lib.cv_batch_check(None, None, ctypes.byref(bi), ctypes.byref(code), None) == capi.CV_EINVAL
+    assert code.value == 0
+    bad = capi.cv_options_default()
+    bad.relaxed = 7
+    n = ctypes.c_size_t()
+    assert lib.cv_bound_batch_workspace(None, None, ctypes.byref(bi), ctypes.byref(bad), ctypes.byref(n)) == \
+        capi.CV_EINVAL
+    assert lib.cv_last_error()

@@ -57,3 +57,77 @@ def test_cnn_uneven_rows_graph_replay_parity():
     assert capi.cv_device_status(net.handle) == 0
     capi.cv_graph_destroy(rnd.graph)
     net.close()
+
+
+def test_cnn3x32_full_size_sampled():
+    """The CIFAR-style CNN of the benchmark table at its full size: 3x32x32 input, 2048 subdomains with
+    1-16 splits, relaxed + complete clipping (10 sweeps) on 80 seeded target slots per subdomain.
+    The GPU bounds all 2048 subdomains (rows too large to stage in shared memory: the wide complete-
+    clipping launch takes every subdomain); the oracle bounds 8 of them, evenly spaced."""
+    from paper_2512_11087_gb300 import workloads as WL
+    cfg = WL.CONFIGS["cnn3x32"]
+    layers = WL.he_cnn(cfg["in_shape"], cfg["convs"], cfg["fcs"], seed=0)
+    case = Case(None, cfg["B"], cfg["kmin"], cfg["kmax"], cfg["eps"], layers=layers, sweeps=cfg["sweeps"], seed=0,
+                targets=80)
+    g = gpu_round(case)
+    sample = (np.arange(8) * case.B) // 8 + 3
+    sub = Case.__new__(Case)
+    sub.__dict__.update(case.__dict__)
+    sub.B = sample.size
+    sub.lo, sub.hi = case.lo[sample], case.hi[sample]
+    so, ids = np.zeros(sample.size + 1, np.int32), []
+    to, tids = np.zeros(sample.size + 1, np.int32), []
+    for i, b in enumerate(sample):
+        seg = case.split_ids[case.split_off[b]:case.split_off[b + 1]]
+        ids.append(seg)
+        so[i + 1] = so[i] + seg.size
+        tseg = case.tgt_ids[case.tgt_off[b]:case.tgt_off[b + 1]]
+        tids.append(tseg)
+        to[i + 1] = to[i] + tseg.size
+    sub.split_off, sub.split_ids = so, np.concatenate(ids).astype(np.int32)
+    sub.tgt_off, sub.tgt_ids = to, np.concatenate(tids).astype(np.int32)
+    o = sub.oracle(nthreads=0)
+    gs = {k: v[sample] for k, v in g.items()}
+    st = compare(sub, gs, o)
+    print("cnn3x32 sampled parity", st)
+
+
+def test_alpha_gradient_config4_full_size_sampled():
+    """Configuration 4's shape at full batch: 784->1024x4->10, 1024 subdomains, slopes per (subdomain,
+    spec row, neuron).  The GPU computes all 1024 bounds and gradients (FP32 CUDA-core contractions:
+    the layers exceed the tensor cores' 512 inputs); 4 subdomains are checked against the oracle's FP64
+    reverse sweep at the bar of tests/test_gpu_alpha.py."""
+    from oracle import oracle as O
+    from paper_2512_11087_gb300 import engine as E
+    from tests.test_gpu_alpha import _full_bounds, _setup, _state
+    s = _setup([784, 1024, 1024, 1024, 1024, 10], 1024, 9, eps=0.02)
+    st = _state(s)
+    lower, grad = st.bound_and_grad(E.to_dev(s["alpha"]))
+    torch.cuda.synchronize()
+    sample = [0, 341, 682, 1023]
+    lower = lower.cpu().numpy()[sample]
+    grad = grad[sample].cpu().numpy()
+    sub = {k: (v[sample] if isinstance(v, np.ndarray) and v.ndim >= 2 and v.shape[0] == s["B"] else v)
+           for k, v in s.items()}
+    o = O.bound_batch(s["onet"], s["cache"] | dict(root_l=s["rl"].astype(np.float64),
+                                                   root_u=s["ru"].astype(np.float64)),
+                      sub["lo"], sub["hi"], l_in=sub["l"], u_in=sub["u"], C=s["C"], t=s["t"],
+                      alpha=sub["alpha"].astype(np.float64), relaxed=0, sweeps=0)
+    worst = 0.0
+    for i in range(len(sample)):
+        hl, hu, hs = _full_bounds(sub, i)
+        f, g = O.alpha_grad(s["onet"], hl, hu, hs, sub["lo"][i], sub["hi"][i], s["C"], s["t"],
+                            sub["alpha"][i].astype(np.float64))
+        sc = o["lower_scale"][i]
+        assert np.all(lower[i] <= f + 1e-12 * sc)
+        assert np.all(np.abs(lower[i] - f) <= 1e-5 * sc)
+        for r in range(s["m"]):
+            gmax = np.max(np.abs(g[r]))
+            if gmax == 0:
+                assert np.all(grad[i, r] == 0)
+                continue
+            err = np.max(np.abs(grad[i, r] - g[r])) / gmax
+            worst = max(worst, err)
+            assert err <= 1e-4, (i, r, err)
+    print("config-4 sampled gradient error / row max", worst)
+    s["net"].close()

@@ -90,3 +90,28 @@ def test_static_scratch_rejects_batches_above_the_limit():
                                                                                   device="cuda"))
     assert ei.value.status == 8
     net.close()
+
+
+def test_static_calls_allocate_no_device_memory():
+    # After a first call (which looks up the array's device address and loads the kernels), further
+    # calls leave the device's free memory unchanged: the entry point itself allocates nothing.
+    from paper_2512_11087_gb300 import capi, engine as E
+    a = Case([40, 64, 64, 6], 64, 1, 4, 0.1, seed=5)
+    net = _net_for(a)
+    d = E.to_dev
+    keep = [d(a.lo), d(a.hi), d(a.split_off), d(a.split_ids)]
+    bi = capi.make_batch_in(a.B, keep[0], keep[1], a.m, None, None, split_off=keep[2], split_ids=keep[3],
+                            max_splits=a.max_splits)
+    lo = torch.empty((a.B, a.n0), device="cuda")
+    hi = torch.empty((a.B, a.n0), device="cuda")
+    inf = torch.empty((a.B,), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    capi.cv_relaxed_clip_static(net.handle, net.cache, bi, lo, hi, inf, relaxed=1, stream=stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        capi.cv_relaxed_clip_static(net.handle, net.cache, bi, lo, hi, inf, relaxed=1, stream=stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    assert capi.cv_device_status(net.handle) == 0
+    net.close()

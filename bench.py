@@ -51,7 +51,7 @@ def parse_args():
     p.add_argument("--precision", default="bf16x8", choices=["fp32", "bf16x8"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--config", default=CONFIG,
-                   choices=["mlp784x256", "mlp5x50", "cnn3x32", "mlp784x1024", "mlp784x512x8"],
+                   choices=["mlp784x256", "mlp5x50", "cnn3x32", "mlp784x1024", "mlp784x512x8", "bab_loop"],
                    help="workload (default: the metric's workload, with the others nested in its line)")
     p.add_argument("--full-stress", action="store_true",
                    help="with --config mlp784x512x8: its own line at the full 65,536 subdomains")
@@ -789,6 +789,123 @@ def bench_stress(steps, warmup, flush, stream, peaks, cpu=True, B=None):
     return out
 
 
+def _bab_instance(cfg, seed=0):
+    """The network, root box and spec rows of a configuration (margin rows e_0 - e_k)."""
+    from paper_2512_11087_gb300 import workloads as WL
+    layers = _layers_of(cfg)
+    lo0, hi0 = WL.box(cfg["dims"][0], cfg["eps"], seed=seed, centre=cfg["centre"], clip01=cfg["clip01"])
+    C, t = WL.margin_spec(cfg["dims"][-1])
+    return layers, lo0, hi0, C, t
+
+
+def bench_bab_loop(steps, warmup, flush, stream, peaks, cpu=True, batch=2048, top_k=20):
+    """The activation-BaB loop of Algorithm 5 (cv_bab_*: pick-out, split with the BaBSR score and weight,
+    top-20 targets, the round, filter, push) on two synthetic instances.
+    (a) Throughput on the 784->256x6->10 network of the headline (eps 0.02 box in [0,1], 9 margin rows):
+        from the root box, untimed iterations until the list holds a full batch of 2048 parents, then
+        `steps` timed iterations of 4096 children each (split-BF16 rounds, 10 sweeps); subdomains bounded
+        per second over the whole iteration (host read-backs included).
+    (b) Domains visited to an answer on the 5->50x6->5 network (box width 0.1, row e_0 - e_1): the
+        threshold clears the least of 65,536 sampled spec values by 5% of its gap to the root bound, and
+        the loop runs until the list is empty (verified) or 200 iterations, for top-k 20, 0 and all."""
+    import numpy as np
+    import torch
+    from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
+    d = E.to_dev
+    res = {}
+    # (a)
+    cfg = WL.CONFIGS["mlp784x256"]
+    layers, lo0, hi0, C, t = _bab_instance(cfg)
+    net = E.Net(layers)
+    U = net.build_cache(lo0, hi0)
+    bab = E.ActivationBaB(net, C, t, batch=batch, top_k=top_k, capacity=1 << 16, max_depth=48, sweeps=cfg["sweeps"],
+                          precision=capi.CV_PREC_BF16X8)
+    st0 = bab.init(lo0[None].astype(np.float32), hi0[None].astype(np.float32), stream)
+    visited, warm = st0["children"], 0
+    while st0["remaining"] > 0:
+        o = bab.step(stream)
+        visited += o["children"]
+        warm += 1
+        if o["remaining"] >= batch or o["picked"] == 0:
+            break
+    for _ in range(max(warmup - 1, 0)):
+        visited += bab.step(stream)["children"]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    tot, iters = bab.run(steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    res["throughput"] = dict(instance="784->256x6->10, eps 0.02 box in [0,1], 9 margin rows, top-20 targets, 10 "
+                                      "sweeps, split-BF16 rounds", cached_neurons=U, batch_parents=batch,
+                             warmup_iterations=warm + max(warmup - 1, 0), timed_iterations=iters,
+                             children_timed=tot["children"], subdomains_per_s=tot["children"] / (ms / 1e3),
+                             ms_per_iteration=ms / max(iters, 1), wall_s=wall,
+                             verified=tot["verified"], infeasible=tot["infeasible"], pushed=tot["pushed"],
+                             list_size=tot["remaining"], domains_visited=visited + tot["children"])
+    bab.close()
+    net.close()
+    torch.cuda.empty_cache()
+    # (b)
+    cfg1 = WL.CONFIGS["mlp5x50"]
+    layers1, lo1, hi1, C1, _ = _bab_instance(cfg1)
+    C1 = C1[:1]
+    net1 = E.Net(layers1)
+    U1 = net1.build_cache(lo1, hi1)
+    r0 = E.Round(net1, 1, 1)
+    f_root = float(r0.run(d(lo1[None]), d(hi1[None]), d(C1), d(np.zeros(1)))["lower"][0, 0].item())
+    rng = np.random.default_rng(5)
+    x = lo1 + (hi1 - lo1) * rng.uniform(size=(65536, lo1.size))
+    for ly in layers1[:-1]:
+        x = np.maximum(x @ np.asarray(ly["W"], np.float64).T + ly["b"], 0.0)
+    y = x @ np.asarray(layers1[-1]["W"], np.float64).T + layers1[-1]["b"]
+    f_samp = float(np.min(y @ C1[0]))
+    t1 = np.array([-f_samp + 0.05 * (f_samp - f_root)])
+    runs = {}
+    for k in (20, 0, -1):
+        b1 = E.ActivationBaB(net1, C1, t1, batch=1024, top_k=k, capacity=1 << 18, max_depth=64, sweeps=10)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s0 = b1.init(lo1[None].astype(np.float32), hi1[None].astype(np.float32), stream)
+        tt, it = b1.run(200, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        dv = s0["children"] + tt["children"]
+        unknown = tt["remaining"] > 0 or tt["stuck"] > 0 or tt["depth_limited"] > 0
+        runs["all" if k < 0 else str(k)] = dict(status="unknown" if unknown else "verified", iterations=it,
+                                                domains_visited=dv, ms=ms1, subdomains_per_s=dv / (ms1 / 1e3),
+                                                stuck=tt["stuck"], depth_limited=tt["depth_limited"],
+                                                remaining=tt["remaining"])
+        b1.close()
+    res["to_answer"] = dict(instance="5->50x6->5, box width 0.1 around U[-1,1]^5, row e_0 - e_1, threshold 5% of "
+                                     "the root gap above the least of 65,536 samples", cached_neurons=U1,
+                            root_lower=f_root, sampled_min=f_samp, threshold=float(t1[0]), by_top_k=runs)
+    net1.close()
+    out = dict(config="activation-BaB loop (Algorithm 5): (a) throughput on 784->256x6->10, 2048 parents per "
+                      "iteration; (b) domains visited to an answer on 5->50x6->5 for top-k 20 / 0 / all",
+               metric="subdomains bounded per second in the activation-BaB loop", value=res["throughput"]
+               ["subdomains_per_s"], unit="subdomains/s", higher_is_better=True,
+               ms_per_step=res["throughput"]["ms_per_iteration"], steps=steps, warmup=warmup,
+               domains_visited=res["to_answer"]["by_top_k"]["20"]["domains_visited"], detail=res)
+    if cpu:
+        from oracle import oracle as O
+        onet = O.Net(layers)
+        cache = O.make_cache(O.root_crown(onet, lo0, hi0))
+        t0 = time.perf_counter()
+        rec = O.activation_bab(onet, cache, lo0[None], hi0[None], C, t, batch=batch, top_k=top_k, capacity=1 << 16,
+                               max_depth=48, max_iters=7, sweeps=cfg["sweeps"])
+        dt = time.perf_counter() - t0
+        n = sum(s["children"] for s in rec["iters"])
+        out["cpu_baseline"] = dict(value=n / dt, unit="subdomains/s", cores=os.cpu_count() or 1, kind="oracle",
+                                   sample=f"the oracle's loop on instance (a): Init and 7 iterations ({n} subdomains, "
+                                          f"{dt:.1f} s)")
+    return out
+
+
 def measure_peaks():
     """The FP32 FMA issue peak (measured here) and the driver's measured HBM / BF16 peaks."""
     from paper_2512_11087_gb300 import capi
@@ -802,7 +919,8 @@ def measure_peaks():
     return p
 
 
-OTHER = {"mlp5x50": bench_mlp5x50, "cnn3x32": bench_cnn3x32, "mlp784x1024": bench_alpha, "mlp784x512x8": bench_stress}
+OTHER = {"mlp5x50": bench_mlp5x50, "cnn3x32": bench_cnn3x32, "mlp784x1024": bench_alpha, "mlp784x512x8": bench_stress,
+         "bab_loop": bench_bab_loop}
 
 
 def run_other(args, names, cpu):
@@ -831,8 +949,8 @@ def main():
         line = dict(metric=e["metric"], value=e["value"], unit=e["unit"], n_gpus=1, steps=e["steps"],
                     warmup=e["warmup"], ms_per_step=e.get("ms_per_step", e["value"] / 1e3 if e["unit"] == "us" else None),
                     higher_is_better=e["higher_is_better"], scaling="weak", vs_baseline=None, dtype="f32",
-                    data="synthetic", config=dict(workload=e["config"]), roofline=e["roofline"], peaks=peaks)
-        for k in ("cpu_baseline", "phase_ms", "subdomains_per_s"):
+                    data="synthetic", config=dict(workload=e["config"]), roofline=e.get("roofline"), peaks=peaks)
+        for k in ("cpu_baseline", "phase_ms", "subdomains_per_s", "domains_visited", "detail"):
             if k in e:
                 line[k] = e[k]
         print(json.dumps(line), flush=True)
@@ -1028,7 +1146,8 @@ def main():
             rnd.ws = None
             del rnd
             torch.cuda.empty_cache()
-            line["other_configs"], _ = run_other(args, ["mlp5x50", "cnn3x32", "mlp784x1024", "mlp784x512x8"],
+            line["other_configs"], _ = run_other(args, ["mlp5x50", "cnn3x32", "mlp784x1024", "mlp784x512x8",
+                                                        "bab_loop"],
                                                  cpu=not args.no_cpu_baseline)
         print(json.dumps(line), flush=True)
     capi.cv_timer_destroy(timer)

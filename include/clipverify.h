@@ -186,10 +186,12 @@ typedef struct cv_options {
     int alpha_mode;     /* CV_ALPHA_*; ignored where batch.alpha is given */
     int enforce_splits; /* 1: clamp split neurons to their side (standard activation BaB) */
     cv_timer* timer;    /* optional phase timing (NULL: none) */
+    int babsr_weight;   /* 1: the round also writes cv_batch_out.babsr_weight (the workspace grows
+                           by B m max_i n_i floats for the layer products) */
 } cv_options;
 
 /* relaxed = 1, sweeps = 0, precision = CV_PREC_FP32, alpha_mode = CV_ALPHA_ADAPTIVE,
- * enforce_splits = 1, timer = NULL. */
+ * enforce_splits = 1, timer = NULL, babsr_weight = 0. */
 void cv_options_default(cv_options* opt);
 
 /* Inputs of one round for B subdomains (all device pointers unless noted).
@@ -236,7 +238,14 @@ typedef struct cv_batch_in {
  *  err_bound  [B x m]      optional: the outward pad included in lower
  *  final_A    [B x m x n_0], final_c [B x m]  optional: the final linear bound
  *             f_r >= final_A_r . x + final_c_r on the clipped box (final_c includes the
- *             pad), e.g. for reuse as output constraints in input BaB (Section 3.3). */
+ *             pad), e.g. for reuse as output constraints in input BaB (Section 3.3).
+ *  babsr_weight [B x U]    written when cv_options.babsr_weight = 1: the weight of the BaBSR score
+ *             (Appendix, neuron selection heuristic) of every cached neuron, the mean over the m
+ *             spec rows of the coefficient of its post-activation in the lower bound, taken in the
+ *             spec back-substitution of this round: for neuron q of hidden layer i, P^(i+1)_{r,q}
+ *             with P^(i+1) = Lam^(i+1) W^(i+1) before layer i's relaxation; summed over the rows in
+ *             increasing order in FP32, then divided by m (0 when m = 0 and for infeasible
+ *             subdomains).  Not a bound: no pad. */
 typedef struct cv_batch_out {
     float* lower;
     float* lo_clip;
@@ -249,6 +258,7 @@ typedef struct cv_batch_out {
     float* err_bound;
     float* final_A;
     float* final_c;
+    float* babsr_weight;
 } cv_batch_out;
 
 /* Checks a batch's device inputs before a round.  The round itself reads nothing back to the host
@@ -466,6 +476,76 @@ cv_status cv_select_targets_workspace(int B, int U, size_t* bytes);
 cv_status cv_select_targets(const cv_net* net, const cv_cache* cache, int B, const float* l, const float* u,
                             const int8_t* mask, const float* weight, int k, int* tgt_off, int* tgt_ids,
                             void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------- the activation-BaB loop */
+
+/* The loop of Algorithm 5 (Clip-and-Verify for activation branch and bound) with every step on the
+ * GPU.  The unknown set D_Unknown is a device-resident stack of domains, each with its split codes,
+ * its clipped box, the bounds / mask / BaBSR weight of its cached neurons from its last round and
+ * its least spec lower bound.  One iteration (cv_bab_step):
+ *   Batch_Pick_Out   the last P = min(batch, |D|, capacity - |D|) domains of the stack (the most
+ *                    recently added: depth first; the cap keeps the children within the capacity)
+ *   Batch_Split      cv_activation_split on them with the BaBSR score and the stored weight; a
+ *                    domain without an unstable cached neuron gives no children (stuck, unknown)
+ *   Top-K_Heuristic  cv_select_targets on the children: their inherited bounds, the parent's mask
+ *                    with the new split fixed (-1 for z <= 0, +1 for z >= 0) and the parent's
+ *                    weight; top_k < 0 takes every unstable cached neuron
+ *   Domain_Clipper / Domain_Update / Solve_Bound   one cv_bound_batch round on the children (the
+ *                    split codes, the inherited box and bounds, the targets; the BaBSR weight on)
+ *   Domain_Filter    verified and infeasible children are dropped; a child that holds max_depth
+ *                    split codes and is not verified is dropped as depth-limited (unknown); the
+ *                    others go back on the stack in child order
+ * The host reads back two small counts per iteration (the children, the survivors) to size the
+ * next launches.  The paper leaves the pick order open; depth first keeps the list compact: only
+ * the picked region of the stack is rewritten. */
+typedef struct cv_bab cv_bab;
+
+typedef struct cv_bab_params {
+    int batch;       /* n of Algorithm 5: parents picked per iteration, >= 1 */
+    int top_k;       /* complete-clipping targets per hidden layer and child; < 0: every unstable one */
+    int capacity;    /* domain-list capacity, >= batch + 1 */
+    int max_depth;   /* split codes a domain may hold, >= 1 */
+    cv_options opt;  /* options of every round (the loop sets opt.babsr_weight = 1) */
+} cv_bab_params;
+
+/* batch 1024, top_k 20, capacity 65536, max_depth 48, opt = cv_options_default with sweeps 10. */
+void cv_bab_params_default(cv_bab_params* p);
+
+typedef struct cv_bab_stats {
+    int picked;         /* parents taken from the list */
+    int stuck;          /* of them without an unstable cached neuron (dropped: unknown) */
+    int children;       /* subdomains bounded by this call's round (the domains it visited) */
+    int verified;       /* children with every spec lower bound > 0 (infeasible ones not counted) */
+    int infeasible;     /* children found infeasible */
+    int depth_limited;  /* children dropped at max_depth split codes, not verified */
+    int pushed;         /* children put back on the list */
+    int remaining;      /* list size after the call */
+    float lower_min;    /* least spec lower bound over the pushed children (+inf when none) */
+} cv_bab_stats;
+
+/* Allocates the list (capacity domains) and the buffers and workspace of one round of 2 batch
+ * subdomains on the current device.  C [m x n_L], t [m]: device spec rows, kept by pointer (they
+ * must outlive the object); m >= 1.  Errors: CV_EINVAL for bad parameters, CV_EUNSUPPORTED where
+ * the round refuses the options, CV_ECUDA when the allocation fails. */
+cv_status cv_bab_create(cv_net* net, const cv_cache* cache, int m, const float* C, const float* t,
+                        const cv_bab_params* params, cv_bab** out);
+/* Init of Algorithm 5: one round on B0 domains without splits (device boxes lo, hi [B0 x n_0],
+ * 1 <= B0 <= min(2 batch, capacity); complete clipping has no rows there), then Domain_Filter; the
+ * list is replaced by the survivors.  stats (host, may be NULL): picked = 0, children = B0. */
+cv_status cv_bab_init(cv_bab* bab, int B0, const float* lo, const float* hi, void* stream,
+                      cv_bab_stats* stats);
+/* One iteration of the while loop.  An empty list returns CV_OK with stats->picked = 0; a full one
+ * (no room for the children of one parent) returns CV_EWORKSPACE and changes nothing. */
+cv_status cv_bab_step(cv_bab* bab, void* stream, cv_bab_stats* stats);
+/* Iterations until the list is empty or max_iters have run (the time-out of Algorithm 5); total
+ * (may be NULL) receives the sums of the iterations' counts (remaining and lower_min of the last
+ * one), iters (may be NULL) the number run.  Stops at the first error. */
+cv_status cv_bab_run(cv_bab* bab, int max_iters, void* stream, cv_bab_stats* total, int* iters);
+/* Host copies of the list (synchronous): count; split_off [count + 1] and split_ids
+ * [split_off[count]] (offsets from 0); lower_min [count]; any may be NULL. */
+cv_status cv_bab_read(const cv_bab* bab, int* count, int* split_off, int* split_ids, float* lower_min,
+                      void* stream);
+void cv_bab_destroy(cv_bab* bab);
 
 /* ---------------------------------------------------------------- measurement */
 

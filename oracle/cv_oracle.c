@@ -698,7 +698,7 @@ static void one_subdomain(const cache_t* cc, int b,
                           double* lower, double* lower_scale, double* lo_c, double* hi_c,
                           double* l_o, double* u_o, double* l_sc, double* u_sc,
                           signed char* mask, unsigned char* infeasible, unsigned char* verified,
-                          double* fA, double* fc) {
+                          double* fA, double* fc, double* bw) {
     const net_t* n = cc->net;
     int n0 = n->dims[0], U = cc->U, L = n->L;
     const double* lo = lo_in + (long)b * n0;
@@ -865,8 +865,26 @@ static void one_subdomain(const cache_t* cc, int b,
         for (int q = 0; q < n0; ++q) xm[q] = fmax(fabs(clo[q]), fabs(chi[q]));
         for (int r = 0; r < m; ++r) { bias[r] = t[r]; sc[r] = fabs(t[r]); }
         memcpy(Lam, C, sizeof(double) * (size_t)m * nL);
+        /* the layer products P^(i) = Lam^(i) W^(i), i = 2..L, for the BaBSR weight */
+        double* keep[64] = {0};
+        if (bw && m > 0)
+            for (int i = 2; i <= L; ++i) keep[i] = (double*)malloc(sizeof(double) * (size_t)m * n->dims[i - 1]);
         backward(n, L, m, Lam, hl, hu, hs, alpha ? alpha + (long)b * m * H : NULL, alpha_mode,
-                 L0, bias, sc, cc->zmag, xm, NULL);
+                 L0, bias, sc, cc->zmag, xm, (bw && m > 0) ? keep : NULL);
+        /* BaBSR weight (Appendix, neuron selection heuristic): the mean over the spec rows of the
+           coefficient of the cached neuron's post-activation in the lower bound, i.e. of column q
+           of P^(h+1) for neuron q of hidden layer h */
+        if (bw && m > 0) {
+            for (int c = 0; c < U; ++c) {
+                int g = cc->ids[c], h = 1;
+                while (h < L - 1 && g >= n->hoff[h + 1]) ++h;
+                int q = g - n->hoff[h], nh = n->dims[h];
+                double sum = 0.0;
+                for (int r = 0; r < m; ++r) sum += keep[h + 1][(long)r * nh + q];
+                bw[(long)b * U + c] = sum / m;
+            }
+            for (int i = 2; i <= L; ++i) free(keep[i]);
+        }
         int ver = 1;
         for (int r = 0; r < m; ++r) {
             double vmin;
@@ -897,7 +915,7 @@ int orc_bound_batch(int L, const int* dims, const double* W, const double* bvec,
                     double* lower, double* lower_scale, double* lo_clip, double* hi_clip,
                     double* l_out, double* u_out, double* l_scale, double* u_scale,
                     signed char* mask, unsigned char* infeasible, unsigned char* verified,
-                    double* final_A, double* final_c, int nthreads) {
+                    double* final_A, double* final_c, double* bab_weight, int nthreads) {
     net_t n;
     if (net_init(&n, L, dims, W, bvec)) return -1;
     cache_t cc;
@@ -916,7 +934,7 @@ int orc_bound_batch(int L, const int* dims, const double* W, const double* bvec,
         one_subdomain(&cc, b, lo, hi, l_in, u_in, split_off, split_ids, row_off, G, h,
                       m, C, t, alpha, alpha_mode, tgt_off, tgt_ids, relaxed, sweeps, enforce_splits,
                       lower, lower_scale, lo_clip, hi_clip, l_out, u_out, l_scale, u_scale,
-                      mask, infeasible, verified, final_A, final_c);
+                      mask, infeasible, verified, final_A, final_c, bab_weight);
     free(slot_of); free(zmag);
     return 0;
 }

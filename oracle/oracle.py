@@ -61,7 +61,7 @@ def _load():
         _lib.orc_bound_batch.argtypes = ([I, P, P, P] + [I, P, P, P, P, P] + [P, P, P] +
                                          [I, P, P, P, P] + [P, P] + [P, P, P] + [I, P, P] +
                                          [P, I] + [P, P] + [I, I, I] +
-                                         [P] * 13 + [I])
+                                         [P] * 14 + [I])
         _lib.orc_bound_batch.restype = I
         _lib.orc_alpha_grad.argtypes = [I, P, P, P, P, P, P, P, P, I, P, P, P, P, P, P]
         _lib.orc_alpha_grad.restype = I
@@ -316,8 +316,10 @@ def dual_value(a, c, G, h, lo, hi, beta):
 def bound_batch(net: Net, cache, lo, hi, *, l_in=None, u_in=None, split_off=None, split_ids=None,
                 row_off=None, G=None, h=None, C, t, alpha=None, alpha_mode=0,
                 tgt_off=None, tgt_ids=None, relaxed=1, sweeps=0, enforce_splits=1, want_final=False,
-                nthreads=0):
-    """One BaB round (a2..a8) for B subdomains.  Returns a dict of outputs."""
+                want_weight=False, nthreads=0):
+    """One BaB round (a2..a8) for B subdomains.  Returns a dict of outputs (with want_weight, also
+    "babsr_weight" [B x U]: the BaBSR weight of every cached neuron from the spec back-substitution;
+    0 for infeasible subdomains)."""
     lib = _load()
     lo, hi = _f64(lo), _f64(hi)
     B, n0 = lo.shape
@@ -352,6 +354,7 @@ def bound_batch(net: Net, cache, lo, hi, *, l_in=None, u_in=None, split_off=None
                mask=np.zeros((B, Uo), np.int8), infeasible=np.zeros(B, np.uint8), verified=np.zeros(B, np.uint8))
     fA = np.zeros((B, m, n0)) if want_final else None
     fc = np.zeros((B, m)) if want_final else None
+    bw = np.zeros((B, Uo)) if want_weight else None
     rc = lib.orc_bound_batch(net.L, _p(net.dims), _p(net.Wflat), _p(net.bflat),
                              U, _p(ids), _p(lA), _p(lc), _p(uA), _p(uc), _p(rl), _p(ru), _p(ps),
                              B, _p(lo), _p(hi), _p(l_in), _p(u_in), _p(so), _p(si), _p(ro), _p(Gx), _p(hx),
@@ -360,13 +363,15 @@ def bound_batch(net: Net, cache, lo, hi, *, l_in=None, u_in=None, split_off=None
                              _p(out["lower"]), _p(out["lower_scale"]), _p(out["lo_clip"]), _p(out["hi_clip"]),
                              _p(out["l"]), _p(out["u"]), _p(out["l_scale"]), _p(out["u_scale"]),
                              _p(out["mask"]), _p(out["infeasible"]), _p(out["verified"]), _p(fA), _p(fc),
-                             int(nthreads))
+                             _p(bw), int(nthreads))
     assert rc == 0
     if U == 0:
         for k in ("l", "u", "l_scale", "u_scale", "mask"):
             out[k] = out[k][:, :0]
     if want_final:
         out["final_A"], out["final_c"] = fA, fc
+    if want_weight:
+        out["babsr_weight"] = bw[:, :U]
     return out
 
 
@@ -393,3 +398,134 @@ def adam_step(alpha, m1, m2, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     g = _f64(g)
     lib.orc_adam_step(alpha.size, _p(alpha), _p(m1), _p(m2), _p(g), int(t), float(lr), float(b1),
                       float(b2), float(eps))
+
+
+def _babsr_scores(l, u, mask, w):
+    """The BaBSR scores as orc_activation_split / orc_select_targets take them (FP32, -1 for stable
+    neurons), for the near-tie margins only."""
+    l, u = np.asarray(l, np.float32), np.asarray(u, np.float32)
+    un = (np.asarray(mask) == 0) & (l < 0) & (u > 0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = (np.maximum(np.float32(0), -l) * np.maximum(np.float32(0), u)) / (u - l)
+    if w is not None:
+        s = s * np.maximum(np.float32(0), -np.asarray(w, np.float32))
+    return np.where(un, s, np.float32(-1)).astype(np.float32)
+
+
+def activation_bab(net: Net, cache, lo0, hi0, C, t, *, batch, top_k, capacity, max_depth, max_iters,
+                   relaxed=1, sweeps=10, enforce_splits=1, alpha_mode=0):
+    """Algorithm 5 (Clip-and-Verify for activation branch and bound) with the oracle's steps, one
+    iteration after another in the paper's order:
+      Init             a round on the B0 initial domains (no splits), Domain_Filter
+      Batch_Pick_Out   the last P = min(batch, |D|, capacity - |D|) domains of the list
+      Batch_Split      activation_split on them (BaBSR score with the stored weight)
+      Top-K_Heuristic  select_targets on the children (parent's bounds, parent's mask with the new
+                       split fixed, parent's weight); top_k < 0: every unstable neuron
+      Domain_Clipper / Domain_Update / Solve_Bound   bound_batch on the children (want_weight)
+      Domain_Filter    drop verified, infeasible and (unverified) max_depth children; push the rest
+    The list is a stack (the pick order is a reading: the paper leaves it open).  Returns a dict:
+      iters [dicts of counts per call, Init first], lists [split-code lists of the list after each
+      call], status ("verified" | "unknown"), and the near-tie margins of every decision taken:
+      branch_gap (relative gap of the best score to the next), topk_gap (at the k-th place of each
+      layer), lower_gap (|lower_min| / its scale for the verified decisions)."""
+    lo0, hi0 = np.atleast_2d(_f64(lo0)), np.atleast_2d(_f64(hi0))
+    ids = np.asarray(cache["ids"])
+    U = ids.size
+    lay = layer_of_slots(net, ids)
+    m = np.asarray(C).shape[0]
+    D = []          # the stack: dicts(codes, lo, hi, l, u, mask, w, lmin)
+    rec = dict(iters=[], lists=[], branch_gap=[], topk_gap=[], lower_gap=[])
+
+    def filter_push(out, codes, lo, hi):
+        st = dict(verified=0, infeasible=0, depth_limited=0, pushed=0, lower_min=np.inf)
+        for k in range(len(codes)):
+            lm = float(np.min(out["lower"][k])) if m else np.inf
+            inf, ver = bool(out["infeasible"][k]), bool(out["verified"][k])
+            if not inf:
+                scale = float(np.max(out["lower_scale"][k]))
+                rec["lower_gap"].append(abs(lm) / max(scale, 1e-300))
+            if inf:
+                st["infeasible"] += 1
+            elif ver:
+                st["verified"] += 1
+            elif len(codes[k]) >= max_depth:
+                st["depth_limited"] += 1
+            else:
+                st["pushed"] += 1
+                st["lower_min"] = min(st["lower_min"], lm)
+                D.append(dict(codes=list(codes[k]), lo=out["lo_clip"][k].copy(), hi=out["hi_clip"][k].copy(),
+                              l=out["l"][k].copy(), u=out["u"][k].copy(), mask=out["mask"][k].copy(),
+                              w=out["babsr_weight"][k].copy(), lmin=lm))
+        return st
+
+    def snapshot(st):
+        st["remaining"] = len(D)
+        rec["iters"].append(st)
+        rec["lists"].append([list(d["codes"]) for d in D])
+
+    out = bound_batch(net, cache, lo0, hi0, C=C, t=t, relaxed=relaxed, sweeps=sweeps,
+                      enforce_splits=enforce_splits, alpha_mode=alpha_mode, want_weight=True)
+    st = filter_push(out, [[] for _ in range(lo0.shape[0])], lo0, hi0)
+    st.update(picked=0, stuck=0, children=lo0.shape[0])
+    snapshot(st)
+    for _ in range(max_iters):
+        if not D:
+            break
+        P = min(batch, len(D), capacity - len(D))
+        if P <= 0:
+            raise RuntimeError("domain list full")
+        parents = D[len(D) - P:]
+        del D[len(D) - P:]
+        st = dict(picked=P, stuck=0, children=0)
+        if U == 0:
+            st.update(stuck=P, verified=0, infeasible=0, depth_limited=0, pushed=0, lower_min=np.inf)
+            snapshot(st)
+            continue
+        so = np.concatenate([[0], np.cumsum([len(p["codes"]) for p in parents])]).astype(np.int32)
+        si = np.array([c for p in parents for c in p["codes"]], np.int32)
+        L_ = np.array([p["l"] for p in parents]); U_ = np.array([p["u"] for p in parents])
+        Mk = np.array([p["mask"] for p in parents]); W_ = np.array([p["w"] for p in parents])
+        sp = activation_split(ids, so, si, np.array([p["lo"] for p in parents]), np.array([p["hi"] for p in parents]),
+                              L_, U_, Mk, W_, np.zeros(P), np.zeros(P))
+        st["stuck"] = int(np.sum(sp["stuck"]))
+        for b in range(P):   # the branching decisions' margins
+            sc = _babsr_scores(L_[b], U_[b], Mk[b], W_[b])
+            top = np.sort(sc)[::-1]
+            if top.size >= 2 and top[0] > 0:      # (ties at a zero weight factor are exact on any side)
+                rec["branch_gap"].append(float((top[0] - top[1]) / top[0]))
+        n = sp["parent"].size
+        st["children"] = n
+        if n == 0:
+            st.update(verified=0, infeasible=0, depth_limited=0, pushed=0, lower_min=np.inf)
+            snapshot(st)
+            continue
+        codes, lo_c, hi_c, l_c, u_c, mk_c, w_c = [], [], [], [], [], [], []
+        for k in range(n):
+            p = parents[sp["parent"][k]]
+            br = int(sp["branched"][k])
+            side = 1 if (k & 1) else -1
+            codes.append(p["codes"] + [side * (int(ids[br]) + 1)])
+            lo_c.append(p["lo"]); hi_c.append(p["hi"]); l_c.append(p["l"]); u_c.append(p["u"])
+            mk = p["mask"].copy(); mk[br] = side
+            mk_c.append(mk); w_c.append(p["w"])
+        l_c, u_c, mk_c, w_c = np.array(l_c), np.array(u_c), np.array(mk_c, np.int8), np.array(w_c)
+        tgt_off = tgt_ids = None
+        if top_k >= 0:
+            tgt_off, tgt_ids = select_targets(lay, l_c, u_c, mk_c, w_c, top_k)
+            for k in range(n):   # the k-th place of every layer
+                sc = _babsr_scores(l_c[k], u_c[k], mk_c[k], w_c[k])
+                for h in np.unique(lay):
+                    v = np.sort(sc[(lay == h) & (sc >= 0)])[::-1]
+                    if v.size > top_k >= 1 and v[top_k - 1] > 0:
+                        rec["topk_gap"].append(float((v[top_k - 1] - v[top_k]) / v[top_k - 1]))
+        so_c = np.concatenate([[0], np.cumsum([len(c) for c in codes])]).astype(np.int32)
+        si_c = np.array([c for cs in codes for c in cs], np.int32)
+        out = bound_batch(net, cache, np.array(lo_c), np.array(hi_c), l_in=l_c, u_in=u_c, split_off=so_c,
+                          split_ids=si_c, C=C, t=t, tgt_off=tgt_off, tgt_ids=tgt_ids, relaxed=relaxed, sweeps=sweeps,
+                          enforce_splits=enforce_splits, alpha_mode=alpha_mode, want_weight=True)
+        st.update(filter_push(out, codes, None, None))
+        snapshot(st)
+    rec["status"] = "verified" if not D and all(s["stuck"] == 0 and s["depth_limited"] == 0
+                                                 for s in rec["iters"]) else "unknown"
+    rec["remaining"] = len(D)
+    return rec

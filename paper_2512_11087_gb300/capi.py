@@ -48,7 +48,7 @@ class cv_layer_desc(ctypes.Structure):
 
 class cv_options(ctypes.Structure):
     _fields_ = [("relaxed", I), ("sweeps", I), ("precision", I), ("alpha_mode", I), ("enforce_splits", I),
-                ("timer", P)]
+                ("timer", P), ("babsr_weight", I)]
 
 
 class cv_batch_in(ctypes.Structure):
@@ -62,9 +62,22 @@ class cv_alpha_in(ctypes.Structure):
                 ("alpha", P), ("grad_f", P)]
 
 
+class cv_bab_params(ctypes.Structure):
+    _fields_ = [("batch", I), ("top_k", I), ("capacity", I), ("max_depth", I), ("opt", cv_options)]
+
+
+class cv_bab_stats(ctypes.Structure):
+    _fields_ = [("picked", I), ("stuck", I), ("children", I), ("verified", I), ("infeasible", I),
+                ("depth_limited", I), ("pushed", I), ("remaining", I), ("lower_min", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class cv_batch_out(ctypes.Structure):
     _fields_ = [("lower", P), ("lo_clip", P), ("hi_clip", P), ("l", P), ("u", P), ("mask", P),
-                ("infeasible", P), ("verified", P), ("err_bound", P), ("final_A", P), ("final_c", P)]
+                ("infeasible", P), ("verified", P), ("err_bound", P), ("final_A", P), ("final_c", P),
+                ("babsr_weight", P)]
 
 
 _lib = None
@@ -116,6 +129,13 @@ def load():
         "cv_activation_split": ([P, P, I] + [P] * 21 + [ctypes.c_size_t, P], I),
         "cv_select_targets_workspace": ([I, I, P], I),
         "cv_select_targets": ([P, P, I, P, P, P, P, I, P, P, P, ctypes.c_size_t, P], I),
+        "cv_bab_params_default": ([P], None),
+        "cv_bab_create": ([P, P, I, P, P, P, ctypes.POINTER(P)], I),
+        "cv_bab_init": ([P, I, P, P, P, P], I),
+        "cv_bab_step": ([P, P, P], I),
+        "cv_bab_run": ([P, I, P, P, P], I),
+        "cv_bab_read": ([P, P, P, P, P, P], I),
+        "cv_bab_destroy": ([P], None),
         "cv_input_split_workspace": ([I, P], I),
         "cv_input_split": ([I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P], I),
     }
@@ -136,7 +156,8 @@ def exported_symbols():
                         "cv_cc_items_set", "cv_cc_items_get", "cv_autotune_cc", "cv_input_split_workspace",
                         "cv_input_split", "cv_spec_clip_workspace", "cv_spec_clip",
                         "cv_activation_split_workspace", "cv_activation_split", "cv_select_targets_workspace",
-                        "cv_select_targets")]
+                        "cv_select_targets", "cv_bab_params_default", "cv_bab_create", "cv_bab_init",
+                        "cv_bab_step", "cv_bab_run", "cv_bab_read", "cv_bab_destroy")]
 
 
 def _check(st):
@@ -261,11 +282,11 @@ def make_batch_in(B, lo, hi, m, C, t, l_in=None, u_in=None, split_off=None, spli
 
 
 def make_batch_out(lower, lo_clip, hi_clip, l, u, mask, infeasible, verified, err_bound=None, final_A=None,
-                   final_c=None):
+                   final_c=None, babsr_weight=None):
     bo = cv_batch_out()
     for name, v in dict(lower=lower, lo_clip=lo_clip, hi_clip=hi_clip, l=l, u=u, mask=mask,
                         infeasible=infeasible, verified=verified, err_bound=err_bound, final_A=final_A,
-                        final_c=final_c).items():
+                        final_c=final_c, babsr_weight=babsr_weight).items():
         setattr(bo, name, ptr(v))
     return bo
 
@@ -374,6 +395,55 @@ def cv_select_targets(net, cache, B, l, u, mask, weight, k, tgt_off, tgt_ids, wo
     _check(load().cv_select_targets(net, cache, int(B), ptr(l), ptr(u), ptr(mask), ptr(weight), int(k),
                                     ptr(tgt_off), ptr(tgt_ids), ptr(workspace), int(workspace_bytes),
                                     stream_ptr(stream)))
+
+
+def cv_bab_params_default():
+    p = cv_bab_params()
+    load().cv_bab_params_default(ctypes.byref(p))
+    return p
+
+
+def cv_bab_create(net, cache, m, C, t, params):
+    h = P()
+    _check(load().cv_bab_create(net, cache, int(m), ptr(C), ptr(t), ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def cv_bab_init(bab, B0, lo, hi, stream=None):
+    st = cv_bab_stats()
+    _check(load().cv_bab_init(bab, int(B0), ptr(lo), ptr(hi), stream_ptr(stream), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def cv_bab_step(bab, stream=None):
+    st = cv_bab_stats()
+    _check(load().cv_bab_step(bab, stream_ptr(stream), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def cv_bab_run(bab, max_iters, stream=None):
+    st = cv_bab_stats()
+    it = ctypes.c_int()
+    _check(load().cv_bab_run(bab, int(max_iters), stream_ptr(stream), ctypes.byref(st), ctypes.byref(it)))
+    return st.as_dict(), it.value
+
+
+def cv_bab_read(bab, stream=None):
+    """(split_off, split_ids, lower_min) of the domain list, host numpy arrays."""
+    lib = load()
+    n = ctypes.c_int()
+    _check(lib.cv_bab_read(bab, ctypes.byref(n), None, None, None, stream_ptr(stream)))
+    off = np.zeros(n.value + 1, np.int32)
+    lm = np.zeros(n.value, np.float32)
+    _check(lib.cv_bab_read(bab, None, off.ctypes.data, None, None, stream_ptr(stream)))
+    ids = np.zeros(max(int(off[-1]), 1), np.int32)
+    _check(lib.cv_bab_read(bab, None, None, ids.ctypes.data, lm.ctypes.data if n.value else None,
+                           stream_ptr(stream)))
+    return off, ids[:int(off[-1])], lm
+
+
+def cv_bab_destroy(bab):
+    load().cv_bab_destroy(bab)
 
 
 def cv_input_split_workspace(B):

@@ -27,10 +27,11 @@ extern "C" void cv_options_default(cv_options* o) {
     o->alpha_mode = CV_ALPHA_ADAPTIVE;
     o->enforce_splits = 1;
     o->timer = nullptr;
+    o->babsr_weight = 0;
 }
 
 cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
-                     int max_rows, int precision, cv_ws_layout* lay) {
+                     int max_rows, int precision, cv_ws_layout* lay, int babsr_weight) {
     memset(lay, 0, sizeof(*lay));
     lay->Rmax = max_splits + max_rows;
     lay->R = B * m;
@@ -58,6 +59,7 @@ cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int
         lay->tc_bexp = take((size_t)B * sizeof(int));
         lay->tc_bsum = take((size_t)B * sizeof(float));
     }
+    if (babsr_weight && m > 0 && cache->U > 0) lay->pbuf = take(R * net->wmax * sizeof(float));
     lay->total = off;
     return CV_OK;
 }
@@ -78,7 +80,8 @@ static cv_status validate(const cv_net* net, const cv_cache* cache, const cv_bat
     }
     if (opt->relaxed < CV_RELAX_OFF || opt->relaxed > CV_RELAX_SEQUENTIAL_ORDERED || opt->sweeps < 0 ||
         opt->alpha_mode < 0 || opt->alpha_mode > 2 ||
-        (opt->precision != CV_PREC_FP32 && opt->precision != CV_PREC_BF16X8)) {
+        (opt->precision != CV_PREC_FP32 && opt->precision != CV_PREC_BF16X8) ||
+        (opt->babsr_weight != 0 && opt->babsr_weight != 1)) {
         cv_set_error("bad options");
         return CV_EINVAL;
     }
@@ -101,7 +104,7 @@ extern "C" cv_status cv_bound_batch_workspace(const cv_net* net, const cv_cache*
     if (s) return s;
     if (!bytes) { cv_set_error("null bytes"); return CV_EINVAL; }
     cv_ws_layout lay;
-    cv_ws_plan(net, cache, in->B, in->m, in->max_splits, in->max_rows, opt->precision, &lay);
+    cv_ws_plan(net, cache, in->B, in->m, in->max_splits, in->max_rows, opt->precision, &lay, opt->babsr_weight);
     *bytes = lay.total;
     return CV_OK;
 }
@@ -131,12 +134,16 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
         cv_set_error("required output pointer is null");
         return CV_EINVAL;
     }
+    if (opt->babsr_weight && U > 0 && !out->babsr_weight) {
+        cv_set_error("cv_options.babsr_weight = 1 needs cv_batch_out.babsr_weight");
+        return CV_EINVAL;
+    }
     if (opt->precision == CV_PREC_BF16X8 && !cv_tc_supported(cache)) {
         cv_set_error("CV_PREC_BF16X8: the tensor-core back-substitution takes layers of at most 512 inputs");
         return CV_EUNSUPPORTED;
     }
     cv_ws_layout lay;
-    cv_ws_plan(net, cache, B, m, in->max_splits, in->max_rows, opt->precision, &lay);
+    cv_ws_plan(net, cache, B, m, in->max_splits, in->max_rows, opt->precision, &lay, opt->babsr_weight);
     if (!workspace || workspace_bytes < lay.total) {
         cv_set_error("workspace too small: need " + std::to_string(lay.total) + " bytes");
         return CV_EWORKSPACE;
@@ -168,6 +175,10 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
                                 out->infeasible, steps, &launches, st)))
         return s;
     if (tm) CV_CUDA(cudaEventRecord(tm->ev[3], st));
+    // BaBSR weight: zero first (m = 0 leaves it so), then one reduction after each hidden layer
+    float* wgt = (opt->babsr_weight && U > 0) ? out->babsr_weight : nullptr;
+    if (wgt) CV_CUDA(cudaMemsetAsync(wgt, 0, (size_t)B * U * sizeof(float), st));
+    if (m == 0) wgt = nullptr;
     if (m > 0 && opt->precision == CV_PREC_BF16X8) {
         s = cv_backward_tc(net, cache, lay.R, m, in->C, in->t, out->l, out->u, out->mask, U, in->alpha,
                            opt->alpha_mode, out->lo_clip, out->hi_clip, out->infeasible, out->lower, out->err_bound,
@@ -175,9 +186,12 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
                            (uint16_t*)(ws + lay.tc_slices), (int*)(ws + lay.tc_exp), (float*)(ws + lay.tc_tab),
                            (double*)(ws + lay.part_bias),
                            (double*)(ws + lay.part_pad), (double*)(ws + lay.part_f), (double*)(ws + lay.part_fmag),
-                           (double*)(ws + lay.acc_bias), (double*)(ws + lay.acc_pad), &launches, st);
+                           (double*)(ws + lay.acc_bias), (double*)(ws + lay.acc_pad), &launches, st,
+                           wgt ? (float*)(ws + lay.pbuf) : nullptr, wgt);
         if (s) return s;
     } else if (m > 0) {
+        float* kpv[CV_MAX_LAYERS + 1];  // every layer's product goes to the one buffer, reduced in turn
+        for (int i = 0; i <= CV_MAX_LAYERS; ++i) kpv[i] = wgt ? (float*)(ws + lay.pbuf) : nullptr;
         s = cv_backward_t<float>(net, lay.R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
                             cache->root_state, cache->slot_of, out->l, out->u, out->mask, U, in->alpha,
                             opt->alpha_mode, cache->V, out->lo_clip, out->hi_clip, out->infeasible, out->lower,
@@ -185,9 +199,9 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
                             (float*)(ws + lay.lam0), (float*)(ws + lay.lam1), (double*)(ws + lay.part_bias),
                             (double*)(ws + lay.part_pad), (double*)(ws + lay.part_f),
                             (double*)(ws + lay.part_fmag), (double*)(ws + lay.acc_bias),
-                            (double*)(ws + lay.acc_pad), nullptr, st);
+                            (double*)(ws + lay.acc_pad), wgt ? kpv : nullptr, st, wgt);
         if (s) return s;
-        launches += 1 + 2 * net->L;
+        launches += 1 + 2 * net->L + (wgt ? net->L - 1 : 0);
     }
     k_verified<<<(B + 255) / 256, 256, 0, st>>>(B, m, out->lower, out->infeasible, out->verified);
     CV_LAUNCH_CHECK("k_verified");

@@ -260,7 +260,30 @@ __global__ void k_bwd_final(int R, int ncb, int rows_per_sub, const double* part
     if (pad_raw) pad_raw[r] = pad;
 }
 
+// BaBSR weight of hidden layer i-1 (Appendix, neuron selection heuristic): thread per (subdomain,
+// neuron) of the layer, the m rows of the subdomain summed in increasing order (coalesced over q)
+__global__ void k_babsr_weight(int nsub, int m, int N, int hoff, const int* slot_of, int U, const float* P,
+                               const uint8_t* skip, float* w) {
+    const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (size_t)nsub * N) return;
+    const int sub = (int)(x / N), q = (int)(x % N);
+    const int slot = slot_of[hoff + q];
+    if (slot < 0 || (skip && skip[sub])) return;  // infeasible subdomains keep the zeros
+    float s = 0.f;
+    for (int r = 0; r < m; ++r) s = __fadd_rn(s, P[((size_t)sub * m + r) * N + q]);
+    w[(size_t)sub * U + slot] = __fdiv_rn(s, (float)m);
+}
+
 }  // namespace
+
+cv_status cv_babsr_weight_layer(int nsub, int m, int N, int hoff, const int* slot_of, int U, const float* P,
+                                const uint8_t* skip, float* w, cudaStream_t st) {
+    const size_t n = (size_t)nsub * N;
+    if (n == 0 || m <= 0 || U <= 0) return CV_OK;
+    k_babsr_weight<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nsub, m, N, hoff, slot_of, U, P, skip, w);
+    CV_LAUNCH_CHECK("k_babsr_weight");
+    return CV_OK;
+}
 
 template <typename T>
 cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
@@ -273,7 +296,7 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         double* bias_raw, double* pad_raw,
                         T* lamA, T* lamB, double* part_bias, double* part_pad,
                         double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                        T* const* keepP, cudaStream_t st) {
+                        T* const* keepP, cudaStream_t st, float* bab_weight) {
     const int nk = net->dims[k];
     {
         dim3 blk(32, 8);
@@ -308,6 +331,13 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
             k_bwd_reduce<<<(R + 255) / 256, 256, 0, st>>>(R, a.ncb, Gam<T>::v, part_bias, part_pad, acc_bias,
                                                           acc_pad);
             CV_LAUNCH_CHECK("k_bwd_reduce");
+            if constexpr (sizeof(T) == sizeof(float)) {
+                if (bab_weight && a.keepP && m > 0 && rows_per_sub == m) {
+                    cv_status s = cv_babsr_weight_layer(R / m, m, a.N, a.hoff, slot_of, U, (const float*)a.keepP,
+                                                        skip, bab_weight, st);
+                    if (s) return s;
+                }
+            }
             T* tmp = cur; cur = nxt; nxt = tmp;
         } else {
             k_bwd_final<<<(R + 255) / 256, 256, 0, st>>>(R, a.ncb, rows_per_sub, part_f, part_fmag,
@@ -325,14 +355,14 @@ template cv_status cv_backward_t<float>(const cv_net*, int, int, int, int, int, 
                                         float* const*, const float*, const float*, const uint8_t*, float*,
                                         double*, float*, float*, float*, double*, double*, float*, float*,
                                         double*, double*, double*, double*, double*, double*, float* const*,
-                                        cudaStream_t);
+                                        cudaStream_t, float*);
 template cv_status cv_backward_t<double>(const cv_net*, int, int, int, int, int, const float*, const float*,
                                          const float*, const double*, const double*, const int8_t*,
                                          const int*, const double*, const double*, const int8_t*, int,
                                          const float*, int, float* const*, const float*, const float*,
                                          const uint8_t*, float*, double*, float*, double*, float*, double*,
                                          double*, double*, double*, double*, double*, double*, double*,
-                                         double*, double*, double* const*, cudaStream_t);
+                                         double*, double*, double* const*, cudaStream_t, float*);
 
 // number of column blocks of the widest layer (sizing of the partial buffers)
 int cv_bwd_ncb_max(const cv_net* net) {

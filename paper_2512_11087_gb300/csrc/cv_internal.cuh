@@ -109,6 +109,7 @@ struct cv_ws_layout {
     size_t rowflag, vmin, lam0, lam1, part_bias, part_pad, part_f, part_fmag, acc_bias, acc_pad, rowdesc, cc, total;
     size_t tc_slices, tc_exp, tc_tab;  // split-BF16 back-substitution scratch (CV_PREC_BF16X8 only)
     size_t tc_box, tc_bexp, tc_bsum;   // split-BF16 re-concretisation scratch (CV_PREC_BF16X8 only)
+    size_t pbuf;                       // layer product P^(i) [R x wmax] for the BaBSR weight (or 0)
     int R, Rmax, ncb;  // rows of the spec backward, max constraint rows, column blocks
 };
 size_t cv_cc_workspace(int B, int Rmax, int n0);  // complete-clipping region (cv_complete.cu)
@@ -118,7 +119,7 @@ cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv
                               const cv_options* opt, const cv_ws_layout* lay, char* ws, float* sscale,
                               unsigned long long* step_counter, int* launches, cudaStream_t st);
 cv_status cv_ws_plan(const cv_net* net, const cv_cache* cache, int B, int m, int max_splits,
-                     int max_rows, int precision, cv_ws_layout* lay);
+                     int max_rows, int precision, cv_ws_layout* lay, int babsr_weight = 0);
 
 // Tensor-core back-substitution (cv_tc.cu).  cv_tc_prepare builds the split weights of every
 // layer once per cache (called by the cache constructors; layers whose shape the path does not
@@ -136,7 +137,8 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                          int alpha_mode, const float* lo, const float* hi, const uint8_t* skip, float* lower,
                          float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
                          int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
-                         double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st);
+                         double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st,
+                         float* pbuf = nullptr, float* bab_weight = nullptr);
 
 // kernels (launch wrappers); each returns CV_OK or a launch error
 cv_status cv_launch_rows(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
@@ -167,7 +169,8 @@ cv_status cv_launch_spec_backward(const cv_net* net, const cv_cache* cache, cons
 // the root arrays.  Outputs (all optional): lower (rounded down), lower64, err (pad), lam0
 // [R x n0], bias_out (bias - pad, rounded down), bias_raw / pad_raw (FP64), keepP[i] [R x n_{i-1}]
 // (the products P^(i), i = 2..k, for the alpha adjoint).  lamA/lamB [R x wmax] and the partial
-// buffers are scratch.
+// buffers are scratch.  bab_weight [nsub x U] (T = float, needs keepP): the BaBSR weight of every
+// cached neuron (cv_babsr_weight_layer after each layer i > 1 on keepP[i]).
 template <typename T>
 cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int init_mode, int m,
                         const float* lam_init, const float* C, const float* t,
@@ -179,7 +182,12 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         double* bias_raw, double* pad_raw,
                         T* lamA, T* lamB, double* part_bias, double* part_pad,
                         double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                        T* const* keepP, cudaStream_t st);
+                        T* const* keepP, cudaStream_t st, float* bab_weight = nullptr);
+// BaBSR weight of the cached neurons of hidden layer i-1 from the layer product P^(i) [R x N]
+// (R = nsub m rows): w[sub, slot_of[hoff + q]] = (sum_{r < m} P[sub m + r, q]) / m, the sum in
+// FP32 in increasing r (cv_backward.cu); subdomains with skip[sub] set are left untouched.
+cv_status cv_babsr_weight_layer(int nsub, int m, int N, int hoff, const int* slot_of, int U, const float* P,
+                                const uint8_t* skip, float* w, cudaStream_t st);
 int cv_bwd_ncb_max(const cv_net* net);
 cv_status cv_bwd_spec_init(int R, int nk, int m, const float* C, const float* t, const float* bk, const float* Vk,
                            float* A, double* acc_bias, double* acc_pad, double gam, cudaStream_t st);

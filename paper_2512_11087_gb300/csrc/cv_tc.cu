@@ -275,6 +275,7 @@ struct TcArgs {
     const float* bnext; const float* Vnext;
     const float* T0; const float* T1; const float* T2;  // relaxation table of layer i-1 [B x N]
     float* Aout;
+    float* keepP;        // optional [R x N]: the product P^(i) (i > 1), for the BaBSR weight
     const float* lo; const float* hi;
     float* lam0;
     double* part_bias; double* part_pad; double* part_f; double* part_fmag; int ncb;
@@ -463,6 +464,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 }
                 const float lam = p * d;
                 a.Aout[(size_t)r * a.N + q] = lam;
+                if (a.keepP) a.keepP[(size_t)r * a.N + q] = p;
                 s1 = fmaf(p, e, s1);
                 s1 = fmaf(lam, s_bn[c], s1);
                 s2 = fmaf(fabsf(lam), s_vn[c], s2);
@@ -537,7 +539,8 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                          int alpha_mode, const float* lo, const float* hi, const uint8_t* skip, float* lower,
                          float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
                          int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
-                         double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st) {
+                         double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st,
+                         float* pbuf, float* bab_weight) {
     if (!cv_tc_supported(cache)) {
         cv_set_error("tensor-core back-substitution: a layer is wider than 512 inputs");
         return CV_EUNSUPPORTED;
@@ -582,6 +585,7 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         a.Vnext = (i > 1) ? cache->V[i - 1] : nullptr;
         a.T0 = tab; a.T1 = tab + tsz; a.T2 = tab + 2 * tsz;
         a.Aout = nxt;
+        a.keepP = (i > 1 && bab_weight && m > 0) ? pbuf : nullptr;
         a.lo = lo; a.hi = hi; a.lam0 = lam0;
         a.part_bias = part_bias; a.part_pad = part_pad; a.part_f = part_f; a.part_fmag = part_fmag;
         a.ncb = (w->N + TBN - 1) / TBN;
@@ -593,6 +597,11 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         if (i > 1) {
             if ((s = cv_bwd_reduce(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad, TC_GAMMA, st))) return s;
             ++*launches;
+            if (a.keepP) {
+                if ((s = cv_babsr_weight_layer(nsub, m, w->N, a.hoff, cache->slot_of, U, pbuf, skip, bab_weight, st)))
+                    return s;
+                ++*launches;
+            }
             float* tmp = cur; cur = nxt; nxt = tmp;
         } else {
             // the concretisation's FP32 products and chains of four: 8 u of its magnitude sum

@@ -70,12 +70,13 @@ class Round:
 
     def __init__(self, net: Net, B, m, max_splits=0, max_rows=0, relaxed=1, sweeps=0,
                  precision=capi.CV_PREC_FP32, alpha_mode=capi.CV_ALPHA_ADAPTIVE, enforce_splits=1,
-                 want_final=False, device="cuda"):
+                 want_final=False, want_weight=False, device="cuda"):
         self.net, self.B, self.m = net, B, m
         self.max_splits, self.max_rows = max_splits, max_rows
         self.opt = capi.cv_options_default()
         self.opt.relaxed, self.opt.sweeps, self.opt.precision = int(relaxed), int(sweeps), int(precision)
         self.opt.alpha_mode, self.opt.enforce_splits = int(alpha_mode), int(enforce_splits)
+        self.opt.babsr_weight = 1 if want_weight else 0
         n0, U = net.n0, max(net.U, 1)
         f32 = dict(dtype=torch.float32, device=device)
         self.out = dict(lower=torch.empty(B, m, **f32), lo_clip=torch.empty(B, n0, **f32),
@@ -87,6 +88,8 @@ class Round:
         if want_final:
             self.out["final_A"] = torch.empty(B, m, n0, **f32)
             self.out["final_c"] = torch.empty(B, m, **f32)
+        if want_weight:
+            self.out["babsr_weight"] = torch.empty(B, U, **f32)
         probe = capi.make_batch_in(B, None, None, m, None, None, max_splits=max_splits, max_rows=max_rows)
         self.ws_bytes = capi.cv_bound_batch_workspace(net.handle, net.cache, probe, self.opt)
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
@@ -278,3 +281,48 @@ def select_targets(net: Net, l, u, mask, k, weight=None, stream=None):
     n = int(off[-1].item())
     return off, ids[:n]
 
+
+
+class ActivationBaB:
+    """The activation-BaB loop of Algorithm 5 on the GPU (cv_bab_*): a device-resident domain list,
+    with every iteration's pick-out, split, top-k targets, round and filter in the library's kernels.
+    C, t: the spec rows (device tensors or host arrays, kept on the device for the loop's lifetime)."""
+
+    def __init__(self, net: Net, C, t, batch=1024, top_k=20, capacity=65536, max_depth=48, relaxed=1, sweeps=10,
+                 precision=capi.CV_PREC_FP32, alpha_mode=capi.CV_ALPHA_ADAPTIVE, enforce_splits=1):
+        self.net = net
+        self.C = to_dev(C, torch.float32)
+        self.t = to_dev(t, torch.float32)
+        p = capi.cv_bab_params_default()
+        p.batch, p.top_k, p.capacity, p.max_depth = int(batch), int(top_k), int(capacity), int(max_depth)
+        p.opt.relaxed, p.opt.sweeps, p.opt.precision = int(relaxed), int(sweeps), int(precision)
+        p.opt.alpha_mode, p.opt.enforce_splits = int(alpha_mode), int(enforce_splits)
+        self.params = p
+        self.handle = capi.cv_bab_create(net.handle, net.cache, self.C.shape[0], self.C, self.t, p)
+
+    def init(self, lo, hi, stream=None):
+        """Init: a round on the initial domains (device boxes [B0 x n0]), the survivors become the list."""
+        self._keep = (to_dev(lo, torch.float32), to_dev(hi, torch.float32))
+        return capi.cv_bab_init(self.handle, self._keep[0].shape[0], self._keep[0], self._keep[1], stream)
+
+    def step(self, stream=None):
+        return capi.cv_bab_step(self.handle, stream)
+
+    def run(self, max_iters, stream=None):
+        """(summed counts, iterations run) until the list is empty or max_iters."""
+        return capi.cv_bab_run(self.handle, max_iters, stream)
+
+    def domains(self, stream=None):
+        """(split_off, split_ids, lower_min) of the list, on the host."""
+        return capi.cv_bab_read(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            capi.cv_bab_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

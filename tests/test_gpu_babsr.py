@@ -108,3 +108,35 @@ def test_one_activation_bab_iteration():
     o1 = kid.oracle(l_in=sp["l"].astype(np.float64), u_in=sp["u"].astype(np.float64))
     compare(kid, g1, o1)
     net.close()
+
+
+def _weight_tol(case, o):
+    # per subdomain and hidden layer: 2e-5 of the layer's largest weight (the FP32 products and the
+    # rounding-level differences of the bounds that choose the relaxations)
+    ids = case.cache["ids"]
+    lay = np.searchsorted(np.cumsum(case.net.dims[1:-1]), ids, side="right")
+    tol = np.zeros_like(o["babsr_weight"])
+    for h in np.unique(lay):
+        sel = lay == h
+        tol[:, sel] = 2e-5 * np.max(np.abs(o["babsr_weight"][:, sel]), axis=1, keepdims=True) + 1e-30
+    return tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("dims,B,seed,sweeps", [([16, 32, 32, 4], 40, 11, 0), ([24, 48, 40, 40, 6], 77, 12, 3),
+                                                ([784, 256, 256, 256, 10], 12, 13, 2)])
+def test_babsr_weight_against_the_oracle(precision, dims, B, seed, sweeps):
+    case = Case(dims, B, 0, 3, 0.05 if dims[0] > 100 else 0.15, seed=seed, sweeps=sweeps)
+    g = gpu_round(case, precision=precision, want_weight=True)
+    o = case.oracle(want_weight=True)
+    compare(case, g, o)
+    fe = ~o["infeasible"].astype(bool)
+    gw, ow = g["babsr_weight"][:, :case.U], o["babsr_weight"]
+    assert np.all(gw[~fe] == 0.0)
+    err = np.abs(gw - ow)[fe]
+    tol = _weight_tol(case, o)[fe]
+    print("weight: max err / tol", float(np.max(err / tol)) if err.size else 0.0)
+    assert np.all(err <= tol)
+    # the sign decides the score factor max(0, -w): equal wherever the oracle's is clear of zero
+    clear = np.abs(ow[fe]) > tol
+    assert np.array_equal(np.sign(gw[fe])[clear], np.sign(ow[fe])[clear])

@@ -23,14 +23,15 @@ SOUND = 1e-12
 LAST_CC_STATS = []  # decision counters of the last gpu_round (complete clipping)
 
 
-def gpu_round(case: Case, precision=0, **kw):
+def gpu_round(case: Case, precision=0, want_weight=False, **kw):
     from paper_2512_11087_gb300 import engine as E
     net = E.Net(case.layers)
     c = case.cache
     net.set_cache(f32(case.lo0), f32(case.hi0), f32(c["root_l"]), f32(c["root_u"]), c["ids"], f32(c["lA"]),
                   f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
     rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, max_rows=case.max_rows, relaxed=case.relaxed,
-                  sweeps=case.sweeps, precision=precision, alpha_mode=case.alpha_mode, enforce_splits=case.enforce)
+                  sweeps=case.sweeps, precision=precision, alpha_mode=case.alpha_mode, enforce_splits=case.enforce,
+                  want_weight=want_weight)
     rnd.enable_timer()
     d = E.to_dev
     out = rnd.run(d(case.lo), d(case.hi), d(case.C), d(case.t), split_off=d(case.split_off),

@@ -95,3 +95,68 @@ def test_top_k_ties_take_the_lowest_slots():
     mask = np.zeros((1, 6), np.int8)
     off, ids = O.select_targets(np.array([1, 1, 1, 2, 2, 2], np.int32), l, u, mask, np.zeros((1, 6)), 2)
     assert ids.tolist() == [0, 1, 3, 4]                # weight 0: every score 0, lowest slots first
+
+
+# ---------------------------------------------------------------- the BaBSR weight
+# The weight of hidden neuron q of layer h is the mean over the spec rows of the coefficient of its
+# post-activation in the lower bound.  With the layers above h all affine on the box (stable
+# neurons only, D = diag(0/1) whatever the coefficient's sign), that coefficient is the plain
+# product C W^(L) D^(L-1) W^(L-1) ... D^(h+1) W^(h+1): closed forms by matrix products.
+
+def _stable_above(seed, dims, on_off):
+    from paper_2512_11087_gb300 import workloads as WL
+    layers = WL.he_mlp(dims, seed=seed)
+    # hidden layer 2 made stable: biases +-50 (active / inactive by on_off)
+    layers[1]["b"] = np.where(on_off, 50.0, -50.0).astype(np.float32)
+    return layers
+
+
+def _weight_case(layers, m_rows, seed):
+    from tests._cases import Case
+    rng = np.random.default_rng(seed)
+    nL = layers[-1]["W"].shape[0]
+    C = rng.normal(size=(m_rows, nL))
+    t = rng.normal(size=m_rows)
+    case = Case(None, 3, 0, 0, 0.2, seed=seed, layers=layers, m_spec=(C, t))
+    o = case.oracle(want_weight=True)
+    return case, o, C
+
+
+def test_weight_of_the_last_hidden_layer_is_the_mean_of_C_W():
+    from paper_2512_11087_gb300 import workloads as WL
+    layers = WL.he_mlp([6, 12, 10, 4], seed=31)
+    case, o, C = _weight_case(layers, 5, 32)
+    ids = case.cache["ids"]
+    W3 = np.asarray(layers[2]["W"], np.float64)
+    expect = (C @ W3).mean(axis=0)            # [n_2]
+    sel = [c for c, g in enumerate(ids) if g >= 12]
+    assert sel, "no cached neuron in hidden layer 2"
+    for b in range(case.B):
+        if o["infeasible"][b]:
+            continue
+        for c in sel:
+            assert abs(o["babsr_weight"][b, c] - expect[ids[c] - 12]) <= 1e-12 * (1 + abs(expect[ids[c] - 12]))
+
+
+def test_weight_through_a_stable_layer_is_the_mean_of_C_W_D_W():
+    on_off = np.array([1, 0, 1, 1, 0, 1, 0, 1, 1, 0], bool)
+    layers = _stable_above(33, [6, 12, 10, 4], on_off)
+    case, o, C = _weight_case(layers, 4, 34)
+    ids = case.cache["ids"]
+    assert all(g < 12 for g in ids), "hidden layer 2 should be stable"
+    W3 = np.asarray(layers[2]["W"], np.float64)
+    W2 = np.asarray(layers[1]["W"], np.float64)
+    expect = (C @ W3 @ np.diag(on_off.astype(float)) @ W2).mean(axis=0)   # [n_1]
+    assert len(ids) > 3
+    for b in range(case.B):
+        for c, g in enumerate(ids):
+            assert abs(o["babsr_weight"][b, c] - expect[g]) <= 1e-12 * (1 + np.abs(C @ W3).sum() * np.abs(W2).max())
+
+
+def test_weight_is_zero_without_spec_rows_and_off_by_default():
+    from paper_2512_11087_gb300 import workloads as WL
+    layers = WL.he_mlp([5, 8, 8, 3], seed=35)
+    case, o, _ = _weight_case(layers, 2, 36)
+    assert "babsr_weight" not in case.oracle()
+    o0 = case.oracle(C=np.zeros((0, 3)), t=np.zeros(0), want_weight=True)
+    assert np.all(o0["babsr_weight"] == 0.0)

@@ -818,7 +818,7 @@ def bench_bab_loop(steps, warmup, flush, stream, peaks, cpu=True, batch=2048, to
     layers, lo0, hi0, C, t = _bab_instance(cfg)
     net = E.Net(layers)
     U = net.build_cache(lo0, hi0)
-    bab = E.ActivationBaB(net, C, t, batch=batch, top_k=top_k, capacity=1 << 16, max_depth=48, sweeps=cfg["sweeps"],
+    bab = E.ActivationBaB(net, C, t, batch=batch, top_k=top_k, capacity=1 << 16, max_depth=32, sweeps=cfg["sweeps"],
                           precision=capi.CV_PREC_BF16X8)
     st0 = bab.init(lo0[None].astype(np.float32), hi0[None].astype(np.float32), stream)
     visited, warm = st0["children"], 0
@@ -866,7 +866,7 @@ def bench_bab_loop(steps, warmup, flush, stream, peaks, cpu=True, batch=2048, to
     t1 = np.array([-f_samp + 0.05 * (f_samp - f_root)])
     runs = {}
     for k in (20, 0, -1):
-        b1 = E.ActivationBaB(net1, C1, t1, batch=1024, top_k=k, capacity=1 << 18, max_depth=64, sweeps=10)
+        b1 = E.ActivationBaB(net1, C1, t1, batch=1024, top_k=k, capacity=1 << 18, max_depth=32, sweeps=10)
         torch.cuda.synchronize()
         e0.record(stream)
         s0 = b1.init(lo1[None].astype(np.float32), hi1[None].astype(np.float32), stream)
@@ -897,7 +897,7 @@ def bench_bab_loop(steps, warmup, flush, stream, peaks, cpu=True, batch=2048, to
         cache = O.make_cache(O.root_crown(onet, lo0, hi0))
         t0 = time.perf_counter()
         rec = O.activation_bab(onet, cache, lo0[None], hi0[None], C, t, batch=batch, top_k=top_k, capacity=1 << 16,
-                               max_depth=48, max_iters=7, sweeps=cfg["sweeps"])
+                               max_depth=32, max_iters=7, sweeps=cfg["sweeps"])
         dt = time.perf_counter() - t0
         n = sum(s["children"] for s in rec["iters"])
         out["cpu_baseline"] = dict(value=n / dt, unit="subdomains/s", cores=os.cpu_count() or 1, kind="oracle",
@@ -1072,6 +1072,8 @@ def main():
         e2e_ms += e0.elapsed_time(e1)
     e2e_ms = job_time_ms(e2e_ms, dist, "cuda")
     e2e_value = job_value(world, B, args.steps, e2e_ms)
+    # the per-round summary every rank contributes (least lower bound, verified / infeasible counts)
+    job_summary = E.reduce_round_summary(*E.round_summary(out, stream), dist)
 
     # the plain FP32 GPU path on the same inputs: its throughput and the agreement of the bounds
     vs_fp32 = None
@@ -1128,7 +1130,8 @@ def main():
                                   ops_per_coordinate_and_row_step=CC_OPS_PER_COORD, cc_row_steps=steps_cc,
                                   peak_source="measured: cv_fp32_fma_peak lane FMAs/s"),
                     e2e=dict(value=e2e_value, unit="subdomains/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
-                    gpu_launches=launches, device_status=status, clocks=clk, peaks=peaks)
+                    gpu_launches=launches, device_status=status, clocks=clk, peaks=peaks,
+                    round_summary=job_summary)
         if vs_fp32 is not None:
             line["vs_fp32_path"] = vs_fp32
         if world == 1 and not args.no_cpu_baseline:

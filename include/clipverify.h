@@ -261,6 +261,16 @@ typedef struct cv_batch_out {
     float* babsr_weight;
 } cv_batch_out;
 
+/* Per-round summary of a round's outputs, the one quantity that ranks exchange when the subdomains
+ * are sharded over GPUs (each rank bounds its own batch; no exchange inside the round): bounds [2]
+ * (device) = the least spec lower bound over the feasible subdomains (Algorithm 5's global bound of
+ * the batch) and over the unverified feasible ones (+inf when there are none), counts [2] (device) =
+ * the verified (feasible) and the infeasible subdomains.  Inputs: lower [B x m], verified [B],
+ * infeasible [B] as cv_bound_batch writes them.  Across ranks the bounds combine by min and the counts
+ * by sum.  One launch; asynchronous on `stream`. */
+cv_status cv_round_summary(int B, int m, const float* lower, const uint8_t* verified, const uint8_t* infeasible,
+                           float* bounds, int* counts, void* stream);
+
 /* Checks a batch's device inputs before a round.  The round itself reads nothing back to the host
  * (it never synchronises), so problems in device data reach it only as device status bits; this call
  * finds them first, with one launch and one read-back (synchronous on `stream`).  Checked: CSR offsets
@@ -504,11 +514,11 @@ typedef struct cv_bab_params {
     int batch;       /* n of Algorithm 5: parents picked per iteration, >= 1 */
     int top_k;       /* complete-clipping targets per hidden layer and child; < 0: every unstable one */
     int capacity;    /* domain-list capacity, >= batch + 1 */
-    int max_depth;   /* split codes a domain may hold, >= 1 */
+    int max_depth;   /* split codes a domain may hold, >= 1 (<= 32 with complete clipping) */
     cv_options opt;  /* options of every round (the loop sets opt.babsr_weight = 1) */
 } cv_bab_params;
 
-/* batch 1024, top_k 20, capacity 65536, max_depth 48, opt = cv_options_default with sweeps 10. */
+/* batch 1024, top_k 20, capacity 65536, max_depth 32, opt = cv_options_default with sweeps 10. */
 void cv_bab_params_default(cv_bab_params* p);
 
 typedef struct cv_bab_stats {

@@ -129,6 +129,7 @@ def load():
         "cv_activation_split": ([P, P, I] + [P] * 21 + [ctypes.c_size_t, P], I),
         "cv_select_targets_workspace": ([I, I, P], I),
         "cv_select_targets": ([P, P, I, P, P, P, P, I, P, P, P, ctypes.c_size_t, P], I),
+        "cv_round_summary": ([I, I, P, P, P, P, P, P], I),
         "cv_bab_params_default": ([P], None),
         "cv_bab_create": ([P, P, I, P, P, P, ctypes.POINTER(P)], I),
         "cv_bab_init": ([P, I, P, P, P, P], I),
@@ -157,7 +158,7 @@ def exported_symbols():
                         "cv_input_split", "cv_spec_clip_workspace", "cv_spec_clip",
                         "cv_activation_split_workspace", "cv_activation_split", "cv_select_targets_workspace",
                         "cv_select_targets", "cv_bab_params_default", "cv_bab_create", "cv_bab_init",
-                        "cv_bab_step", "cv_bab_run", "cv_bab_read", "cv_bab_destroy")]
+                        "cv_bab_step", "cv_bab_run", "cv_bab_read", "cv_bab_destroy", "cv_round_summary")]
 
 
 def _check(st):
@@ -395,6 +396,11 @@ def cv_select_targets(net, cache, B, l, u, mask, weight, k, tgt_off, tgt_ids, wo
     _check(load().cv_select_targets(net, cache, int(B), ptr(l), ptr(u), ptr(mask), ptr(weight), int(k),
                                     ptr(tgt_off), ptr(tgt_ids), ptr(workspace), int(workspace_bytes),
                                     stream_ptr(stream)))
+
+
+def cv_round_summary(B, m, lower, verified, infeasible, bounds, counts, stream=None):
+    _check(load().cv_round_summary(int(B), int(m), ptr(lower), ptr(verified), ptr(infeasible), ptr(bounds),
+                                   ptr(counts), stream_ptr(stream)))
 
 
 def cv_bab_params_default():

@@ -120,7 +120,52 @@ __global__ void k_verified(int B, int m, const float* lower, const uint8_t* infe
     }
     verified[b] = v ? 1 : 0;
 }
+// one block: the least spec lower bound over the feasible subdomains and over the unverified ones,
+// and the verified / infeasible counts (an ordered tree of minima: the result is exact)
+__global__ void __launch_bounds__(1024) k_round_summary(int B, int m, const float* lower, const uint8_t* verified,
+                                                        const uint8_t* infeasible, float* bounds, int* counts) {
+    __shared__ float s0[32], s1[32];
+    __shared__ int c0[32], c1[32];
+    float a = INFINITY, z = INFINITY;
+    int nv = 0, ni = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        if (infeasible[b]) { ++ni; continue; }
+        float v = INFINITY;
+        for (int r = 0; r < m; ++r) v = fminf(v, lower[(size_t)b * m + r]);
+        a = fminf(a, v);
+        if (verified[b]) ++nv;
+        else z = fminf(z, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        z = fminf(z, __shfl_xor_sync(0xffffffffu, z, o));
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        ni += __shfl_xor_sync(0xffffffffu, ni, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s0[warp] = a; s1[warp] = z; c0[warp] = nv; c1[warp] = ni; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a = fminf(a, s0[w]); z = fminf(z, s1[w]); nv += c0[w]; ni += c1[w];
+        }
+        bounds[0] = a; bounds[1] = z;
+        counts[0] = nv; counts[1] = ni;
+    }
+}
 }  // namespace
+
+extern "C" cv_status cv_round_summary(int B, int m, const float* lower, const uint8_t* verified,
+                                      const uint8_t* infeasible, float* bounds, int* counts, void* stream) {
+    if (B < 0 || m < 0 || !bounds || !counts || (B > 0 && (!verified || !infeasible || (m > 0 && !lower)))) {
+        cv_set_error("cv_round_summary: negative size or null pointer");
+        return CV_EINVAL;
+    }
+    k_round_summary<<<1, 1024, 0, (cudaStream_t)stream>>>(B, m, lower, verified, infeasible, bounds, counts);
+    CV_LAUNCH_CHECK("k_round_summary");
+    return CV_OK;
+}
 
 extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv_batch_in* in, cv_batch_out* out,
                                     const cv_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
@@ -139,7 +184,7 @@ extern "C" cv_status cv_bound_batch(cv_net* net, const cv_cache* cache, const cv
         return CV_EINVAL;
     }
     if (opt->precision == CV_PREC_BF16X8 && !cv_tc_supported(cache)) {
-        cv_set_error("CV_PREC_BF16X8: the tensor-core back-substitution takes layers of at most 512 inputs");
+        cv_set_error("CV_PREC_BF16X8: the tensor-core weights of a layer were not prepared (K above 65536)");
         return CV_EUNSUPPORTED;
     }
     cv_ws_layout lay;

@@ -276,7 +276,7 @@ extern "C" void cv_bab_params_default(cv_bab_params* p) {
     p->batch = 1024;
     p->top_k = 20;
     p->capacity = 65536;
-    p->max_depth = 48;
+    p->max_depth = 32;
     cv_options_default(&p->opt);
     p->opt.sweeps = 10;
 }
@@ -291,6 +291,10 @@ extern "C" cv_status cv_bab_create(cv_net* net, const cv_cache* cache, int m, co
         (long long)2 * p->batch * p->max_depth > INT_MAX / 2 || (long long)p->capacity * p->max_depth > INT_MAX) {
         cv_set_error("cv_bab_create: need m >= 1, batch >= 1, max_depth >= 1, capacity > batch (sizes within int)");
         return CV_EINVAL;
+    }
+    if (p->opt.sweeps > 0 && p->max_depth > 32) {
+        cv_set_error("cv_bab_create: complete clipping takes at most 32 rows: max_depth <= 32 when sweeps > 0");
+        return CV_EUNSUPPORTED;
     }
     *out = nullptr;
     cv_bab* b = new cv_bab();

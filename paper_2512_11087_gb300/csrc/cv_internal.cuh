@@ -56,6 +56,7 @@ struct cv_tc_w {
     uint16_t* slices;   // [3][Np][Kp] BF16 bit patterns
     int* fexp;          // [N] column exponents: |W_kq| <= 2^fexp[q]
     double F1, F2;      // sum_q 2^fexp[q] zmag_q and sum_q (sum_k |W_kq|) zmag_q (pad constants)
+    double F3;          // sum_q nnz_q 2^fexp[q] zmag_q, nnz_q the nonzeros of column q (sparse layers)
     int K, N, Kp, Np;
     CUtensorMap tmap;   // 3-D map {Kp, Np, 3}, box {64, 64, 1}, 128-byte swizzle
 };
@@ -65,6 +66,7 @@ struct cv_tc_pc {
     uint16_t* slices;   // [3][Np][Kp] BF16 digits of the rows of PC (row-scaled), zero padded
     int* fexp;          // [2U] row exponents
     float* tsum;        // [2U] sum_k |PC_jk|, rounded up
+    int* nnz;           // [2U] nonzeros of PC_j (its support bounds the quantisation and dropped-level terms)
     int K, N, Kp, Np;
     CUtensorMap tmap;   // 3-D map {Kp, Np, 3}, box {64, 64, 1}, 128-byte swizzle
 };

@@ -12,11 +12,14 @@
 // (3,2)); level 6 (X3 Y3 <= 2^14 per term) is dropped.  For K <= 256 every partial sum of every
 // level is an integer below 2^24 (level 4: 3 K 2^14 <= 1.5 2^23), so the FP32 accumulation in
 // tensor memory is exact in any order; longer K runs in chunks of 256 with an accumulator set
-// per chunk.  The error of P against the exact product of the FP32 operands is therefore
+// per chunk, two sets at a time (a pass of 512 K): the chunk sums are added in FP32 in chunk
+// order, those of every pass but the last through running sums in shared memory while the
+// tensor memory is refilled.  The error of P against the exact product of the FP32 operands is
 //     |dP_rq| <= c 2^-24 (2^f_q S_r + 2^e_r T_q) + 2^(e_r + f_q) K 2^-31,
 //     S_r = sum_k |Lam_rk|,  T_q = sum_k |W_kq|,  c = 1 + 2^-6
 // (quantisation of both operands, the dropped level, and the part of the FP32 level sum that
-// exceeds 3 u sum_k |Lam_rk||W_kq|, which the 24 u gamma |Lam| V pad covers).  Its
+// exceeds 3 u sum_k |Lam_rk||W_kq|, which the gamma |Lam| V pad covers: 24 u, plus one u for
+// every chunk beyond two).  Its
 // effect on the bound, sum_q |dP_rq| zmag_q, is charged to the row's pad by the splitting
 // kernel: 2^-24 c (S_r F1 + 2^e_r F2) + 2^e_r K 2^-31 F1, F1 = sum_q 2^f_q zmag_q,
 // F2 = sum_q T_q zmag_q (per layer, computed with the split weights).
@@ -40,13 +43,15 @@ namespace {
 
 constexpr int TBM = 128, TBN = 64, TBK = 64;  // CTA tile and K step of the TMA boxes
 constexpr int KCH = 256;                       // K rows per exact accumulator set
-constexpr int KMAX = 512;                      // longest K the path takes (two sets)
+constexpr int KMAX = 1 << 16;                  // longest K the path takes (passes of two sets)
 constexpr int NLEV = 4;                        // kept levels 2..5
 constexpr double PAD_C = 1.0 + 1.0 / 64.0;
 // Pad per unit of sum_k |Lam_k| V_k for each contraction (V = |W| zmag + |b|): the FP32 sum of
-// the levels (at most seven roundings with two accumulator sets) and the FP32 relaxation
-// epilogue (15 u, as in the CUDA-core path); the operand splitting is charged separately.
-constexpr double TC_GAMMA = 24.0 * CV_U32;
+// the levels (three roundings per chunk, then one per chunk added: at most nch + 2, budgeted as
+// max(7, nch + 5)) and the FP32 relaxation epilogue (15 u, as in the CUDA-core path), 2 u spare;
+// the operand splitting is charged separately.  nch: the most chunks of any layer.
+inline double tc_gamma(int nch) { return (24.0 + (nch > 2 ? nch - 2 : 0)) * CV_U32; }
+constexpr int TC_RUN_SMEM = TBM * (TBN + 1) * 4;  // running sums of a tile over the passes
 
 // balanced base-256 digits of |n| <= 2^23
 __device__ __forceinline__ void digits3(int n, int& x1, int& x2, int& x3) {
@@ -85,15 +90,18 @@ __global__ void k_tc_wsplit(int K, int N, int Kp, int Np, const float* W, const 
     }
     float mx = 0.f;
     double tsum = 0.0;
+    int nz = 0;
     for (int k = lane; k < K; k += 32) {
         const float w = fabsf(W[(size_t)k * N + q]);
         mx = fmaxf(mx, w);
         tsum += (double)w;
+        nz += w != 0.f;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
         tsum += __shfl_xor_sync(0xffffffffu, tsum, off);
+        nz += __shfl_xor_sync(0xffffffffu, nz, off);
     }
     const int e = pow2_ceil_exp(mx);
     for (int k = lane; k < Kp; k += 32) {
@@ -108,6 +116,7 @@ __global__ void k_tc_wsplit(int K, int N, int Kp, int Np, const float* W, const 
         const double z = (double)zmag[q];
         atomicAdd(&F[0], ldexp(1.0, e) * z);
         atomicAdd(&F[1], tsum * z);
+        atomicAdd(&F[2], (double)nz * ldexp(1.0, e) * z);
     }
 }
 
@@ -174,20 +183,23 @@ struct BoxLd {
 // header).  One warp per row, eight consecutive elements per lane (one 16-byte store per slice).
 template <class Ld>
 __global__ void k_tc_split(int R, int plane_rows, int K, int Kp, Ld ld, uint16_t* S, int* rexp, float* rsum,
-                           double* acc_pad, double F1, double F2) {
+                           int* rnnz, double* acc_pad, double F1, double F2, double F3) {
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= R) return;
     float mx = 0.f, ssum = 0.f;  // ssum: sum of |row| rounded up
+    int nz = 0;
     for (int k = lane; k < K; k += 32) {
         const float v = fabsf(ld(r, k));
         mx = fmaxf(mx, v);
         ssum = __fadd_ru(ssum, v);
+        nz += v != 0.f;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
         ssum = __fadd_ru(ssum, __shfl_xor_sync(0xffffffffu, ssum, off));
+        nz += __shfl_xor_sync(0xffffffffu, nz, off);
     }
     const int e = pow2_ceil_exp(mx);
     const size_t plane = (size_t)plane_rows * Kp;  // slice stride (rows of the tensor map)
@@ -214,9 +226,12 @@ __global__ void k_tc_split(int R, int plane_rows, int K, int Kp, Ld ld, uint16_t
     if (lane == 0) {
         rexp[r] = e;
         if (rsum) rsum[r] = ssum;
+        if (rnnz) rnnz[r] = nz;
         if (acc_pad) {
+            // W's quantisation meets Lam_rk only where W_kq != 0: sum_q min(S_r, nnz_q 2^e) 2^f_q zmag_q
+            // <= min(S_r F1, 2^e F3); the dropped level likewise has nnz_q terms per column
             const double pe = ldexp(1.0, e);
-            acc_pad[r] += (PAD_C * ldexp((double)ssum * F1 + pe * F2, -24) + pe * (double)K * ldexp(F1, -31)) *
+            acc_pad[r] += (PAD_C * ldexp(fmin((double)ssum * F1, pe * F3) + pe * F2, -24) + pe * ldexp(F3, -31)) *
                           (1.0 + 1e-12);
         }
     }
@@ -298,7 +313,13 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
     const int warp = threadIdx.x >> 5;
     const int row0 = blockIdx.y * TBM, col0 = blockIdx.x * TBN;
     const int KT = a.Kp / TBK;
-    const unsigned ncols = (unsigned)(a.nch * NLEV * TBN);  // 256 or 512
+    // K runs in passes of two chunks (two exact accumulator sets); the sums of every pass but the
+    // last are drained into FP32 running sums in shared memory, in chunk order
+    const int nset = a.nch < 2 ? a.nch : 2;
+    const unsigned ncols = (unsigned)(nset * NLEV * TBN);  // 256 or 512
+    const int npass = (a.nch + 1) / 2;
+    constexpr int KTP = 2 * KCH / TBK;                      // K tiles per pass
+    float* s_run = (float*)(sm + NSTAGE * STAGE);           // [TBM][TBN + 1] when npass > 1
     if (threadIdx.x == 0) {
         s_fail = 0;
         for (int s = 0; s < 2; ++s) {
@@ -319,9 +340,12 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
 
+    bool fine = true;
+    for (int pass = 0; pass < npass; ++pass) {
+    const int kt0 = pass * KTP, kt1 = min(KT, kt0 + KTP);
     if (threadIdx.x == 0) {
-        // producer: TMA ring of NSTAGE stages
-        for (int kt = 0; kt < KT; ++kt) {
+        // producer: TMA ring of NSTAGE stages (its phases run on over the passes)
+        for (int kt = kt0; kt < kt1; ++kt) {
             const int s = kt % NSTAGE;
             if (kt >= NSTAGE && !bar_wait(&empty[s], ((kt - NSTAGE) / NSTAGE) & 1)) { s_fail = 1; break; }
             unsigned char* st = sm + s * STAGE;
@@ -339,12 +363,12 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
         const int pi[8] = {0, 0, 1, 0, 1, 2, 1, 2};  // digit of A (slice)
         const int pj[8] = {0, 1, 0, 2, 1, 0, 2, 1};  // digit of B
         bool ok = true;
-        for (int kt = 0; kt < KT && ok; ++kt) {
+        for (int kt = kt0; kt < kt1 && ok; ++kt) {
             const int s = kt % NSTAGE;
             if (!bar_wait(&full[s], (kt / NSTAGE) & 1)) { s_fail = 1; ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned char* st = sm + s * STAGE;
-            const int ch = (kt * TBK) / KCH;
+            const int ch = (kt * TBK) / KCH - 2 * pass;  // accumulator set of the pass
             const bool first_tile = (kt * TBK) % KCH == 0;
             for (int kk = 0; kk < TBK / 16; ++kk) {
 #pragma unroll
@@ -373,9 +397,34 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                          : "memory");
     }
     __syncthreads();
-    const bool fine = !s_fail && bar_wait(&done, 0);
-    if (!fine && threadIdx.x == 0) atomicOr(a.status, CV_DEV_TIMEOUT);
+    fine = __syncthreads_and(fine && !s_fail && bar_wait(&done, pass & 1)) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!fine || pass == npass - 1) break;
+    {
+        // drain both sets of this pass into the running sums, then hand tensor memory back
+        const int dw = warp & 3, dh = warp >> 2;
+        const int dr = dw * 32 + (threadIdx.x & 31);
+        const unsigned dbase = tmem + ((unsigned)(dw * 32) << 16);
+        for (int cc = 0; cc < 32; cc += 8) {
+            const int c0 = dh * 32 + cc;
+            for (int ch = 0; ch < 2; ++ch) {
+                float lv[NLEV][8];
+#pragma unroll
+                for (int v = 0; v < NLEV; ++v) tmem_ld8(dbase + (unsigned)((ch * NLEV + v) * TBN + c0), lv[v]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float* run = s_run + (size_t)dr * (TBN + 1) + c0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float lev = fmaf(lv[0][j], 16777216.f, fmaf(lv[1][j], 65536.f, fmaf(lv[2][j], 256.f, lv[3][j])));
+                    run[j] = (pass == 0 && ch == 0) ? 0.f + lev : run[j] + lev;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    }
+    if (!fine && threadIdx.x == 0) atomicOr(a.status, CV_DEV_TIMEOUT);
     // Epilogue.  Stage what the tile's elements need in the (now idle) stage buffers: per column
     // its exponent, b^(i-1) and V^(i-1); per (subdomain, column) the relaxation table of layer
     // i-1 (i > 1) or the box (i = 1).  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its
@@ -433,9 +482,10 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
     for (int cc = 0; cc < 32 && fine; cc += 8) {
         const int c0 = half * 32 + cc;
         float acc[8];
+        const float* run = s_run + (size_t)tr * (TBN + 1) + c0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-        for (int ch = 0; ch < a.nch; ++ch) {
+        for (int j = 0; j < 8; ++j) acc[j] = npass > 1 ? run[j] : 0.f;
+        for (int ch = 0; ch < a.nch - 2 * (npass - 1); ++ch) {
             float lv[NLEV][8];
 #pragma unroll
             for (int v = 0; v < NLEV; ++v) tmem_ld8(lane_base + (unsigned)((ch * NLEV + v) * TBN + c0), lv[v]);
@@ -542,16 +592,19 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                          double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st,
                          float* pbuf, float* bab_weight) {
     if (!cv_tc_supported(cache)) {
-        cv_set_error("tensor-core back-substitution: a layer is wider than 512 inputs");
+        cv_set_error("tensor-core back-substitution: a layer's weights were not prepared");
         return CV_EUNSUPPORTED;
     }
     if (R == 0) return CV_OK;
     const int L = net->L;
+    int nch_max = 1;
+    for (int i = 1; i <= L; ++i) nch_max = std::max(nch_max, (cache->tcw[i]->Kp + KCH - 1) / KCH);
+    const double gam = tc_gamma(nch_max);
     cv_status s =
-        cv_bwd_spec_init(R, net->dims[L], m, C, t, net->b[L], cache->V[L], lamA, acc_bias, acc_pad, TC_GAMMA, st);
+        cv_bwd_spec_init(R, net->dims[L], m, C, t, net->b[L], cache->V[L], lamA, acc_bias, acc_pad, gam, st);
     if (s) return s;
     ++*launches;
-    CV_CUDA(cudaFuncSetAttribute(k_tc_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    CV_CUDA(cudaFuncSetAttribute(k_tc_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM + TC_RUN_SMEM));
     float* cur = lamA;
     float* nxt = lamB;
     for (int i = L; i >= 1; --i) {
@@ -567,7 +620,7 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
             ++*launches;
         }
         k_tc_split<RowLd><<<(R + 7) / 8, 256, 0, st>>>(R, R, w->K, w->Kp, RowLd{cur, w->K}, slices, rexp, nullptr,
-                                                        acc_pad, w->F1, w->F2);
+                                                        nullptr, acc_pad, w->F1, w->F2, w->F3);
         CV_LAUNCH_CHECK("k_tc_split");
         CUtensorMap tA;
         if ((s = encode_slices(&tA, slices, R, w->Kp, TBM))) return s;
@@ -591,11 +644,11 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         a.ncb = (w->N + TBN - 1) / TBN;
         a.status = net->status;
         dim3 grd(a.ncb, (R + TBM - 1) / TBM);
-        k_tc_layer<<<grd, 256, TC_SMEM, st>>>(tA, w->tmap, a);
+        k_tc_layer<<<grd, 256, TC_SMEM + (a.nch > 2 ? TC_RUN_SMEM : 0), st>>>(tA, w->tmap, a);
         CV_LAUNCH_CHECK("k_tc_layer");
         *launches += 2;
         if (i > 1) {
-            if ((s = cv_bwd_reduce(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad, TC_GAMMA, st))) return s;
+            if ((s = cv_bwd_reduce(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad, gam, st))) return s;
             ++*launches;
             if (a.keepP) {
                 if ((s = cv_babsr_weight_layer(nsub, m, w->N, a.hoff, cache->slot_of, U, pbuf, skip, bab_weight, st)))
@@ -618,9 +671,11 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
 // out[b, j] = [lo_b | hi_b] . PC_j + PCc_j over K = 2 n0, on tensor cores.  Each chunk of 256 K
 // rows accumulates its four levels exactly in one of two tensor-memory sets; eight epilogue warps
 // drain a finished chunk into FP32 running sums (level sum: three roundings; sum over chunks: one
-// rounding per chunk) while the MMA warp fills the other set.  Pad: 12 u pscale_j (the FP32 sums,
-// the intercept, against |value| <= pscale_j over the root box) plus the splitting term of the
-// file header with S_b = sum |box row|, T_j = sum |PC_j|.  A padded value that straddles 0 is
+// rounding per chunk) while the MMA warp fills the other set.  Pad: max(12, nch + 5) u pscale_j
+// (the FP32 sums: three roundings per chunk's levels, one per chunk added, one for the intercept,
+// against |value| <= pscale_j over the root box) plus the splitting term of the file header with
+// S_b = sum |box row| (at most nnz_j 2^e_b on PC_j's support), T_j = sum |PC_j|, and the dropped
+// level over PC_j's nnz_j nonzeros.  A padded value that straddles 0 is
 // recomputed in FP64 from the FP32 operands, as in the CUDA-core kernel.
 namespace {
 
@@ -628,12 +683,13 @@ constexpr int RC_CHUNK_TILES = KCH / TBK;  // K tiles per exact chunk
 constexpr int RC_NSTAGE = 2;
 constexpr int RC_SMEM = RC_NSTAGE * STAGE + 1024;
 constexpr int RC_THREADS = 320;            // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
-constexpr double RC_GAMMA = 12.0 * CV_U32;
 
 struct RcArgs {
     int B, U, N, n0, K, Kp;
     const int* bexp; const float* bsum;   // box rows: exponent, sum |.| (rounded up)
     const int* fexp; const float* tsum;   // PC rows
+    const int* nnz;                       // PC rows' nonzeros
+    float gamma;                          // the FP32 sums' pad per unit of pscale
     const float* PCc; const float* pscale;
     const float* PC; const float* lo; const float* hi;
     const float* rls; const float* rus; const float* l_in; const float* u_in; const uint8_t* infeasible;
@@ -783,11 +839,14 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_tc_reconc(const __grid_consta
                 if (!skip) {
                     const int fj = a.fexp[jj];
                     const float val = ldexpf(acc[j], eb + fj - 38) + a.PCc[jj];
-                    // pad, every operation rounded up
-                    float pad = __fmul_ru((float)RC_GAMMA, a.pscale[jj]);
-                    pad = __fadd_ru(pad, __fmul_ru(c24, __fadd_ru(__fmul_ru(sb, ldexpf(1.f, fj)),
+                    // pad, every operation rounded up; PC's quantisation and the dropped level meet
+                    // the box row only on PC_j's support: min(S_b, nnz_j 2^eb) in place of S_b
+                    const float nzj = (float)a.nnz[jj];
+                    const float sbj = fminf(sb, ldexpf(nzj, eb));
+                    float pad = __fmul_ru(a.gamma, a.pscale[jj]);
+                    pad = __fadd_ru(pad, __fmul_ru(c24, __fadd_ru(__fmul_ru(sbj, ldexpf(1.f, fj)),
                                                                   __fmul_ru(ldexpf(1.f, eb), a.tsum[jj]))));
-                    pad = __fadd_ru(pad, ldexpf((float)a.K, eb + fj - 31));
+                    pad = __fadd_ru(pad, ldexpf(nzj, eb + fj - 31));
                     const float lo_v = __fsub_rd(val, pad), hi_v = __fadd_ru(val, pad);
                     if (lo_v < 0.f && hi_v >= 0.f) straddle |= 1u << j;
                     res = up ? fminf(inh, hi_v) : fmaxf(inh, lo_v);
@@ -841,7 +900,7 @@ cv_status cv_reconc_tc(const cv_cache* cache, int B, const float* lo, const floa
     if (B == 0) return CV_OK;
     const int n0 = cache->n0;
     k_tc_split<BoxLd><<<(B + 7) / 8, 256, 0, st>>>(B, B, pc->K, pc->Kp, BoxLd{lo, hi, n0}, xslices, bexp, bsum,
-                                                    nullptr, 0.0, 0.0);
+                                                    nullptr, nullptr, 0.0, 0.0, 0.0);
     CV_LAUNCH_CHECK("k_tc_split");
     CUtensorMap tX;
     cv_status s = encode_slices(&tX, xslices, B, pc->Kp, TBM);
@@ -849,7 +908,8 @@ cv_status cv_reconc_tc(const cv_cache* cache, int B, const float* lo, const floa
     RcArgs a;
     memset(&a, 0, sizeof(a));
     a.B = B; a.U = cache->U; a.N = pc->N; a.n0 = n0; a.K = pc->K; a.Kp = pc->Kp;
-    a.bexp = bexp; a.bsum = bsum; a.fexp = pc->fexp; a.tsum = pc->tsum;
+    a.bexp = bexp; a.bsum = bsum; a.fexp = pc->fexp; a.tsum = pc->tsum; a.nnz = pc->nnz;
+    a.gamma = (float)(std::max(12, (pc->Kp + KCH - 1) / KCH + 5) * CV_U32 * (1.0 + 1e-6));
     a.PCc = cache->PCc; a.pscale = cache->pscale; a.PC = cache->PC; a.lo = lo; a.hi = hi;
     a.rls = rls; a.rus = rus; a.l_in = l_in; a.u_in = u_in; a.infeasible = infeasible;
     a.l_out = l; a.u_out = u; a.status = status;
@@ -874,6 +934,7 @@ void cv_tc_release(cv_cache* c) {
         cudaFree(c->tcpc->slices);
         cudaFree(c->tcpc->fexp);
         cudaFree(c->tcpc->tsum);
+        cudaFree(c->tcpc->nnz);
         delete c->tcpc;
         c->tcpc = nullptr;
     }
@@ -890,7 +951,7 @@ cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaS
     for (int i = 1; i <= n->L; ++i) {
         const int K = n->dims[i], N = n->dims[i - 1];
         const int Kp = round_up(K, TBK), Np = round_up(N, TBN);
-        if (Kp > KMAX) continue;  // the path takes K <= 512 (two exact accumulator sets)
+        if (Kp > KMAX) continue;  // beyond the path's 32-bit slice indexing
         cv_tc_w* w = new cv_tc_w();
         memset(w, 0, sizeof(*w));
         c->tcw[i] = w;
@@ -898,17 +959,18 @@ cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaS
         double* F = nullptr;
         CV_CUDA(cudaMalloc(&w->slices, (size_t)3 * Np * Kp * sizeof(uint16_t)));
         CV_CUDA(cudaMalloc(&w->fexp, (size_t)N * sizeof(int)));
-        CV_CUDA(cudaMalloc(&F, 2 * sizeof(double)));
-        CV_CUDA(cudaMemsetAsync(F, 0, 2 * sizeof(double), st));
+        CV_CUDA(cudaMalloc(&F, 3 * sizeof(double)));
+        CV_CUDA(cudaMemsetAsync(F, 0, 3 * sizeof(double), st));
         const float* zm = (i == 1) ? xmag : zmag + n->hoff[i - 1];
         k_tc_wsplit<<<(Np + 7) / 8, 256, 0, st>>>(K, N, Kp, Np, n->W[i], zm, w->slices, w->fexp, F);
         CV_LAUNCH_CHECK("k_tc_wsplit");
-        double hF[2];
+        double hF[3];
         CV_CUDA(cudaMemcpyAsync(hF, F, sizeof(hF), cudaMemcpyDeviceToHost, st));
         CV_CUDA(cudaStreamSynchronize(st));
         cudaFree(F);
         w->F1 = hF[0] * (1.0 + 1e-12);
         w->F2 = hF[1] * (1.0 + 1e-12);
+        w->F3 = hF[2] * (1.0 + 1e-12);
         cv_status s = encode_slices(&w->tmap, w->slices, Np, Kp, TBN);
         if (s) return s;
     }
@@ -922,9 +984,11 @@ cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaS
         CV_CUDA(cudaMemsetAsync(pc->slices, 0, (size_t)3 * pc->Np * pc->Kp * sizeof(uint16_t), st));
         CV_CUDA(cudaMalloc(&pc->fexp, (size_t)pc->N * sizeof(int)));
         CV_CUDA(cudaMalloc(&pc->tsum, (size_t)pc->N * sizeof(float)));
+        CV_CUDA(cudaMalloc(&pc->nnz, (size_t)pc->N * sizeof(int)));
         // rows of PC, written into the first N of the Np slice rows (the rest stay zero)
         k_tc_split<RowLd><<<(pc->N + 7) / 8, 256, 0, st>>>(pc->N, pc->Np, pc->K, pc->Kp, RowLd{c->PC, pc->K},
-                                                            pc->slices, pc->fexp, pc->tsum, nullptr, 0.0, 0.0);
+                                                            pc->slices, pc->fexp, pc->tsum, pc->nnz, nullptr, 0.0,
+                                                            0.0, 0.0);
         CV_LAUNCH_CHECK("k_tc_split");
         cv_status s = encode_slices(&pc->tmap, pc->slices, pc->Np, pc->Kp, TBN);
         if (s) return s;

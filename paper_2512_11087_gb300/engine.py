@@ -288,7 +288,7 @@ class ActivationBaB:
     with every iteration's pick-out, split, top-k targets, round and filter in the library's kernels.
     C, t: the spec rows (device tensors or host arrays, kept on the device for the loop's lifetime)."""
 
-    def __init__(self, net: Net, C, t, batch=1024, top_k=20, capacity=65536, max_depth=48, relaxed=1, sweeps=10,
+    def __init__(self, net: Net, C, t, batch=1024, top_k=20, capacity=65536, max_depth=32, relaxed=1, sweeps=10,
                  precision=capi.CV_PREC_FP32, alpha_mode=capi.CV_ALPHA_ADAPTIVE, enforce_splits=1):
         self.net = net
         self.C = to_dev(C, torch.float32)
@@ -326,3 +326,24 @@ class ActivationBaB:
             self.close()
         except Exception:
             pass
+
+
+def round_summary(out, stream=None):
+    """(bounds [2] float32, counts [2] int32) device tensors of a round's outputs (cv_round_summary): the least
+    spec lower bound over the feasible and over the unverified subdomains, the verified and infeasible counts."""
+    B, m = out["lower"].shape
+    bounds = torch.empty(2, dtype=torch.float32, device=out["lower"].device)
+    counts = torch.empty(2, dtype=torch.int32, device=out["lower"].device)
+    capi.cv_round_summary(B, m, out["lower"], out["verified"], out["infeasible"], bounds, counts, stream)
+    return bounds, counts
+
+
+def reduce_round_summary(bounds, counts, dist=None, group=None):
+    """The job's summary over ranks (torch.distributed: min of the bounds, sum of the counts), as a dict.
+    bounds / counts: this rank's (round_summary, or any tensors of that layout on the group's device)."""
+    b, c = bounds.clone(), counts.to(torch.int64)
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(b, op=dist.ReduceOp.MIN, group=group)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM, group=group)
+    b, c = b.cpu().tolist(), c.cpu().tolist()
+    return dict(lower_min=b[0], lower_min_unverified=b[1], verified=int(c[0]), infeasible=int(c[1]))

@@ -59,17 +59,19 @@ def test_cnn_uneven_rows_graph_replay_parity():
     net.close()
 
 
-def test_cnn3x32_full_size_sampled():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cnn3x32_full_size_sampled(precision):
     """The CIFAR-style CNN of the benchmark table at its full size: 3x32x32 input, 2048 subdomains with
-    1-16 splits, relaxed + complete clipping (10 sweeps) on 80 seeded target slots per subdomain.
-    The GPU bounds all 2048 subdomains (rows too large to stage in shared memory: the wide complete-
-    clipping launch takes every subdomain); the oracle bounds 8 of them, evenly spaced."""
+    1-16 splits, relaxed + complete clipping (10 sweeps) on 80 seeded target slots per subdomain, on
+    the FP32 and the split-BF16 tensor-core path (the dense conv layers have up to 4096 outputs: eight
+    passes).  The GPU bounds all 2048 subdomains (rows too large to stage in shared memory: the wide
+    complete-clipping launch takes every subdomain); the oracle bounds 8 of them, evenly spaced."""
     from paper_2512_11087_gb300 import workloads as WL
     cfg = WL.CONFIGS["cnn3x32"]
     layers = WL.he_cnn(cfg["in_shape"], cfg["convs"], cfg["fcs"], seed=0)
     case = Case(None, cfg["B"], cfg["kmin"], cfg["kmax"], cfg["eps"], layers=layers, sweeps=cfg["sweeps"], seed=0,
                 targets=80)
-    g = gpu_round(case)
+    g = gpu_round(case, precision=precision)
     sample = (np.arange(8) * case.B) // 8 + 3
     sub = Case.__new__(Case)
     sub.__dict__.update(case.__dict__)

@@ -183,19 +183,20 @@ def test_round_parity_tensor_core(name, kw):
     compare(case, g, o)
 
 
-def test_tensor_core_refuses_wide_layers():
-    from paper_2512_11087_gb300 import capi, engine as E
-    case = Case([20, 600, 5], 4, 1, 2, 0.1, sweeps=0)
-    net = E.Net(case.layers)
-    c = case.cache
-    net.set_cache(f32(case.lo0), f32(case.hi0), f32(c["root_l"]), f32(c["root_u"]), c["ids"], f32(c["lA"]),
-                  f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
-    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, precision=capi.CV_PREC_BF16X8)
-    d = E.to_dev
-    with pytest.raises(RuntimeError, match="512"):
-        rnd.run(d(case.lo), d(case.hi), d(case.C), d(case.t), split_off=d(case.split_off),
-                split_ids=d(case.split_ids))
-    net.close()
+@pytest.mark.parametrize("name,kw", [
+    ("k600_three_chunks", dict(dims=[20, 600, 5], B=12, kmin=1, kmax=2, eps=0.1, sweeps=2)),
+    ("k1024_two_passes", dict(dims=[64, 1024, 1024, 10], B=10, kmin=1, kmax=3, eps=0.05, sweeps=2)),
+    ("k1300_three_passes", dict(dims=[30, 1300, 200, 7], B=9, kmin=0, kmax=3, eps=0.05, sweeps=3)),
+])
+def test_round_parity_tensor_core_wide_layers(name, kw):
+    """Layers with more than 512 outputs on the tensor cores: K in passes of two exact accumulator
+    sets, the chunk sums of all but the last pass carried in shared memory (one, two and three passes;
+    a last pass with one chunk)."""
+    from paper_2512_11087_gb300 import capi
+    case = Case(**kw)
+    g = gpu_round(case, precision=capi.CV_PREC_BF16X8)
+    o = case.oracle()
+    compare(case, g, o)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -298,13 +299,15 @@ def test_graph_replay_matches_direct_call(precision):
     net.close()
 
 
-def test_cnn_round_parity():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cnn_round_parity(precision):
     """A small CIFAR-shaped CNN (two strided 4x4 convolutions, a 3x3 one, two dense layers): the
-    conv layers are expanded to matrices independently on both sides."""
+    conv layers are expanded to matrices independently on both sides; on both paths (the first
+    layer has 864 outputs: two tensor-core passes)."""
     from paper_2512_11087_gb300 import workloads as WL
     layers = WL.he_cnn((3, 12, 12), [(6, 4, 2, 1), (8, 4, 2, 1), (8, 3, 1, 1)], [20, 10], seed=4)
     case = Case(None, 24, 1, 6, 2.0 / 255.0, layers=layers, sweeps=4, seed=4)
-    g = gpu_round(case)
+    g = gpu_round(case, precision=precision)
     o = case.oracle()
     compare(case, g, o)
 
@@ -335,3 +338,32 @@ def test_bench_workload_full_size_sampled(precision):
     gs = {k: v[sample] for k, v in g.items()}
     st = compare(sub, gs, o)
     print("full-size sampled parity", st)
+
+
+def test_round_summary_of_a_round():
+    # cv_round_summary against its definition on the round's own outputs, and its counts against the oracle's
+    from paper_2512_11087_gb300 import engine as E, workloads as WL
+    C, t = WL.margin_spec(4)
+    # the threshold puts the verified / unverified cut between two of the oracle's bounds 3e-3 apart
+    case = Case([16, 32, 32, 4], 300, 1, 3, 0.12, seed=41, sweeps=2, out_rows=1, m_spec=(C, t + 3.691))
+    net = E.Net(case.layers)
+    c = case.cache
+    net.set_cache(f32(case.lo0), f32(case.hi0), f32(c["root_l"]), f32(c["root_u"]), c["ids"], f32(c["lA"]),
+                  f32(c["lc"]), f32(c["uA"]), f32(c["uc"]))
+    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, max_rows=case.max_rows, sweeps=case.sweeps)
+    d = E.to_dev
+    out = rnd.run(d(case.lo), d(case.hi), d(case.C), d(case.t), split_off=d(case.split_off),
+                  split_ids=d(case.split_ids), row_off=d(case.row_off), G=d(case.G), h=d(case.h))
+    s = E.reduce_round_summary(*E.round_summary(out))
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    feas = g["infeasible"] == 0
+    lm = g["lower"].min(axis=1)
+    assert s["infeasible"] == int((~feas).sum()) and s["verified"] == int((feas & (g["verified"] == 1)).sum())
+    assert s["lower_min"] == (float(lm[feas].min()) if feas.any() else float("inf"))
+    unv = feas & (g["verified"] == 0)
+    assert s["lower_min_unverified"] == (float(lm[unv].min()) if unv.any() else float("inf"))
+    o = case.oracle()
+    ofeas = o["infeasible"] == 0
+    assert s["infeasible"] == int((~ofeas).sum()) and s["verified"] == int((ofeas & (o["verified"] == 1)).sum())
+    assert 0 < s["infeasible"] and 0 < s["verified"] < case.B - s["infeasible"]
+    net.close()

@@ -56,3 +56,30 @@ def test_single_rank_time_is_local():
     import bench
     assert bench.job_time_ms(12.5) == 12.5
     assert bench.job_value(1, 4096, 10, 1000.0) == pytest.approx(40960.0)
+
+
+def _summary_rank(rank, world, port, out_dir):
+    from paper_2512_11087_gb300 import engine as E
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    # the layout cv_round_summary writes: [least lower bound, least unverified lower bound], [verified, infeasible]
+    local = {0: ([-0.5, -0.5], [10, 2]), 1: ([0.25, float("inf")], [30, 0])}[rank]
+    s = E.reduce_round_summary(torch.tensor(local[0], dtype=torch.float32), torch.tensor(local[1], dtype=torch.int32),
+                               dist)
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"sum{rank}.json"), "w") as f:
+        json.dump(s, f)
+
+
+def test_round_summary_reduces_over_two_gloo_ranks(tmp_path):
+    world = 2
+    mp.spawn(_summary_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    r = [json.load(open(tmp_path / f"sum{k}.json")) for k in range(world)]
+    assert r[0] == r[1]
+    assert r[0] == dict(lower_min=-0.5, lower_min_unverified=-0.5, verified=40, infeasible=2)
+
+
+def test_round_summary_without_a_group_is_local():
+    from paper_2512_11087_gb300 import engine as E
+    s = E.reduce_round_summary(torch.tensor([1.0, float("inf")]), torch.tensor([3, 1], dtype=torch.int32))
+    assert s == dict(lower_min=1.0, lower_min_unverified=float("inf"), verified=3, infeasible=1)

@@ -587,9 +587,9 @@ def _phase_roofline(phases, steps_cc, n0, dims, Bm, peaks, prec):
 
 def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
     """Configuration 3: the CIFAR-style CNN on 3x32x32, B = 2048, 1-16 splits, complete clipping (10
-    sweeps) on the top-20 BaBSR targets per hidden layer chosen from a first round's bounds; the timed
-    round is one replay of its captured graph.  Conv layers are dense (Toeplitz) inside the library,
-    whose tensor-core back-substitution takes at most 512 inputs per layer: this one runs the FP32 path."""
+    sweeps) on the top-20 BaBSR targets per hidden layer chosen from a first round's bounds and
+    weights; the timed round is one replay of its captured graph, on the split-BF16 tensor-core path
+    (conv layers are dense Toeplitz matrices inside the library; K up to 4096 runs in passes)."""
     import numpy as np
     import torch
     from paper_2512_11087_gb300 import capi, engine as E, workloads as WL
@@ -607,13 +607,14 @@ def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
     lo, hi = WL.tile_box(lo0, hi0, B)
     d = E.to_dev
     dlo, dhi, dC, dt_, dso, dsi = d(lo), d(hi), d(C), d(t), d(so), d(si)
-    r0 = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=0)
+    prec = capi.CV_PREC_BF16X8
+    r0 = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=0, precision=prec, want_weight=True)
     o0 = r0.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi)
-    toff, tids = E.select_targets(net, o0["l"], o0["u"], o0["mask"], cfg["topk"])
+    toff, tids = E.select_targets(net, o0["l"], o0["u"], o0["mask"], cfg["topk"], weight=o0["babsr_weight"])
     torch.cuda.synchronize()
     ntg = int(toff[-1].item())
     del r0
-    rnd = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=cfg["sweeps"])
+    rnd = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=cfg["sweeps"], precision=prec)
     rnd.enable_timer()
     rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, tgt_off=toff, tgt_ids=tids)
     ph, _, steps_cc = capi.cv_timer_read(rnd.timer)
@@ -624,13 +625,14 @@ def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
     dims = [n0] + [int(np.prod(l["out_shape"])) for l in layers]
     out = dict(config=f"cnn3x32: ReLU CNN 3x32x32 -> conv16 4x4 s2 p1 -> conv32 4x4 s2 p1 -> conv32 3x3 s1 p1 -> "
                       f"FC100 -> FC10, eps=2/255 around U[0,1] clipped to [0,1]; B={B}, 1-16 splits (uneven), "
-                      f"9 margin rows, relaxed + complete clipping (10 sweeps) on the top-20 targets per hidden "
-                      f"layer ({ntg} in all); FP32 path; one captured-graph replay per round",
+                      f"9 margin rows, relaxed + complete clipping (10 sweeps) on the top-20 BaBSR targets per "
+                      f"hidden layer ({ntg} in all); split-BF16 tensor-core path; one captured-graph replay "
+                      f"per round",
                metric="subdomains bounded+clipped per second", value=B / (ms / 1e3), unit="subdomains/s",
                higher_is_better=True, ms_per_step=ms, steps=steps, warmup=warmup, cached_neurons=U,
                phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
                                  [round(x, 3) for x in ph])),
-               roofline=_phase_roofline(ph, steps_cc, n0, dims, B * m, peaks, 0))
+               roofline=_phase_roofline(ph, steps_cc, n0, dims, B * m, peaks, 1))
     if cpu:
         from oracle import oracle as O
         onet = O.Net(layers)
@@ -640,9 +642,10 @@ def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
             so2, si2 = WL.draw_splits(cache["ids"], n, cfg["kmin"], cfg["kmax"], seed=1)
             l2, h2 = WL.tile_box(lo0, hi0, n)
             o = O.bound_batch(onet, cache, l2, h2, split_off=so2, split_ids=si2, C=C, t=t, relaxed=1, sweeps=0,
-                              nthreads=os.cpu_count() or 1)
+                              want_weight=True, nthreads=os.cpu_count() or 1)
             mask = np.where(o["l"] >= 0, 1, np.where(o["u"] <= 0, -1, 0)).astype(np.int8)
-            to, ti = O.select_targets(O.layer_of_slots(onet, cache["ids"]), o["l"], o["u"], mask, None, cfg["topk"])
+            to, ti = O.select_targets(O.layer_of_slots(onet, cache["ids"]), o["l"], o["u"], mask, o["babsr_weight"],
+                                      cfg["topk"])
             return dict(lo=l2, hi=h2, split_off=so2, split_ids=si2, C=C, t=t, relaxed=1, sweeps=cfg["sweeps"],
                         tgt_off=to, tgt_ids=ti)
         out["cpu_baseline"] = _oracle_rate(cfg, layers, lo0, hi0, 4, mk)

@@ -387,6 +387,7 @@ struct CertState {
 // gs / rk / wk the staged rows, bh / bl the multipliers' leading and trailing parts (shared slots).
 // Once more than 64 candidates' breakpoints are written over the key buffer, keys are recomputed from
 // the target plane.
+template <bool WIDE>
 __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const float* gs, const float* rk,
                                         const long long* wk, unsigned* keys, unsigned short* cidx, const float* ap,
                                         float sa, const float* bh, const float* bl, float amx, long long T,
@@ -395,11 +396,15 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
     const float tu = 1.1933e-07f;   // >= 2 * 2^-24 * 1.001
     float smx = amx;
     int nnz = 0;
+    // rows p != k whose terms are formed: in the wide launch those with a nonzero multiplier (the
+    // others add exactly nothing), in the main launch all of them
+    unsigned nzm = 0u;
     for (int p = 0; p < R; ++p) {
         if (p == k) continue;
         const float b = bh[p];
         smx = __fmaf_ru(fabsf(b), cc_Gm[p], smx);
         nnz += b != 0.f;
+        if (!WIDE || b != 0.f) nzm |= 1u << p;
     }
     const float Ru = nnz ? __fmul_ru((float)(nnz + 1), cu1) : 0.f;
     const float c1 = __fmul_ru(Ru, smx);
@@ -411,8 +416,15 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
     // the FP32 key of element j exactly as the key pass forms it
     auto key_calc = [&](int j) -> float {
         float x = sa * __ldg(ap + j);
-        for (int p = 0; p < R; ++p)
-            if (p != k) x = fmaf(bh[p], gs[p * n0 + j], x);
+        if constexpr (WIDE) {
+            for (unsigned mm = nzm; mm; mm &= mm - 1u) {
+                const int p = __ffs(mm) - 1;
+                x = fmaf(bh[p], gs[p * n0 + j], x);
+            }
+        } else {
+            for (int p = 0; p < R; ++p)
+                if (p != k) x = fmaf(bh[p], gs[p * n0 + j], x);
+        }
         return (-x) * rk[j];
     };
     bool keys_ok = true;  // the key buffer holds every element's key
@@ -421,8 +433,15 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
         const float r = rk[j];
         if (r == 0.f) return 0;  // g_kj = 0: no breakpoint (weight 0)
         float S = fabsf(av);
-        for (int p = 0; p < R; ++p)
-            if (p != k) S = __fmaf_ru(fabsf(bh[p]), fabsf(gs[p * n0 + j]), S);
+        if constexpr (WIDE) {
+            for (unsigned mm = nzm; mm; mm &= mm - 1u) {
+                const int p = __ffs(mm) - 1;
+                S = __fmaf_ru(fabsf(bh[p]), fabsf(gs[p * n0 + j]), S);
+            }
+        } else {
+            for (int p = 0; p < R; ++p)
+                if (p != k) S = __fmaf_ru(fabsf(bh[p]), fabsf(gs[p * n0 + j]), S);
+        }
         if (S == 0.f) return 0.f < Lw ? 1 : (0.f <= Hw ? 3 : 0);
         const float E = __fmaf_ru(__fmul_ru(Ru, S), fabsf(r), __fmul_ru(tu, fabsf(q)));
         if (__fadd_ru(q, E) < Lw) return 1;
@@ -432,8 +451,7 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
     // refined once: qh from fl(1/g), the remainder qh g + sh by fma, the correction from it.
     auto ff_key = [&](int j, float av, float& kh, float& kl) {
         float sh = sa * av, sl = 0.f;
-        for (int p = 0; p < R; ++p) {
-            if (p == k) continue;
+        auto term = [&](int p) {
             const float b1 = bh[p], b2 = bl[p], g = gs[p * n0 + j];
             const float pr = __fmul_rn(b1, g);
             float pe = __fmaf_rn(b1, g, -pr);  // exact error of the product
@@ -443,6 +461,12 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
             const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(pr, bb));
             sh = t;
             sl = __fadd_rn(sl, __fadd_rn(er, pe));
+        };
+        if constexpr (WIDE) {  // (a zero leading part has a zero trailing part: those rows add nothing)
+            for (unsigned mm = nzm; mm; mm &= mm - 1u) term(__ffs(mm) - 1);
+        } else {
+            for (int p = 0; p < R; ++p)
+                if (p != k) term(p);
         }
         const float t = __fadd_rn(sh, sl);
         sl = __fsub_rn(sl, __fsub_rn(t, sh));
@@ -814,15 +838,28 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     if (p == k) { bk = beta[p]; jp = jprev[p]; }
             }
             if (CERT) blk = blsm[k];
-            // q_j from a' = a + sum_{p != k} beta_p g_p (fma chain in increasing p)
+            // q_j from a' = a + sum_{p != k} beta_p g_p (fma chain in increasing p).  The wide launch
+            // skips the rows whose multiplier is 0: fma(0, g, x) = x (up to the sign of a zero, which
+            // is never a breakpoint), so the keys are the same and only the nonzero rows are read.
+            unsigned nzm = 0u;
+            if constexpr (WIDE) {
+                for (int p = 0; p < R; ++p)
+                    if (p != k && bsm[p] != 0.f) nzm |= 1u << p;
+            }
             auto q_of = [&](float av, int j) -> float {
                 float apr = sa * av;
+                if constexpr (WIDE) {
+                    for (unsigned mm = nzm; mm; mm &= mm - 1u) {
+                        const int p = __ffs(mm) - 1;
+                        apr = fmaf(bsm[p], rw.gs[p * n0 + j], apr);
+                    }
+                } else {
 #pragma unroll
-                for (int p = 0; p < RC; ++p) {
-                    if (WIDE && p >= R) break;
-                    if (RC > 1) {
-                        const float t = fmaf(bget(p), rw.gs[p * n0 + j], apr);
-                        apr = (p != k) ? t : apr;
+                    for (int p = 0; p < RC; ++p) {
+                        if (RC > 1) {
+                            const float t = fmaf(bget(p), rw.gs[p * n0 + j], apr);
+                            apr = (p != k) ? t : apr;
+                        }
                     }
                 }
                 return (-apr) * rk[j];
@@ -1179,15 +1216,15 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     cst.bn = bn; cst.bln = 0.f; cst.jn = jn;
                     const float amx = SPEC ? a.samax[o] : __ldg(a.amax + (side ? a.U + c : c));
                     if constexpr (WIDE) {
-                        cc_certify(n0, R, k, lane, rw.gs, rk, wk, keys, cidx, ap, sa, bsm, blsm, amx, T, Fdec, dec,
-                                   &cst);
+                        cc_certify<true>(n0, R, k, lane, rw.gs, rk, wk, keys, cidx, ap, sa, bsm, blsm, amx, T,
+                                         Fdec, dec, &cst);
                     } else {
                         // the leading parts in the warp's shared slots after the trailing ones
 #pragma unroll
                         for (int p = 0; p < RC; ++p) blsm[RMAX_CC + p] = beta[p];
                         __syncwarp();
-                        cc_certify(n0, R, k, lane, rw.gs, rk, wk, keys, cidx, ap, sa, blsm + RMAX_CC, blsm, amx, T,
-                                   Fdec, dec, &cst);
+                        cc_certify<false>(n0, R, k, lane, rw.gs, rk, wk, keys, cidx, ap, sa, blsm + RMAX_CC, blsm,
+                                          amx, T, Fdec, dec, &cst);
                     }
                     bn = cst.bn; bln = cst.bln; jn = cst.jn;
 #pragma unroll
@@ -1229,6 +1266,11 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
     const float psc = SPEC ? a.sscale[o] : __ldg(a.pscale + (side ? a.U + c : c));
     const float cur = SPEC ? a.slower[o] : (side == 0 ? a.l[o] : -a.u[o]);
     float part = 0.f;
+    unsigned nzv = 0u;  // rows with a nonzero multiplier (wide launch)
+    if constexpr (WIDE) {
+        for (int p = 0; p < R; ++p)
+            if (bsm[p] != 0.f) nzv |= 1u << p;
+    }
     if (!WIDE && (n0 & 1) == 0) {
         // two adjacent elements per lane, packed FP32: each lane sums at most ceil(n0/64) terms per
         // component and one more to combine them, within the ceil(n0/32) the rounding bound allows
@@ -1276,10 +1318,14 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             for (int u = 0; u < PF; ++u) {
                 const int jj = min(j0 + 32 * u, n0 - 1);
                 float v = sa * av[u];
+                if constexpr (WIDE) {
+                    for (unsigned mm = nzv; mm; mm &= mm - 1u) {  // zero multipliers add nothing
+                        const int p = __ffs(mm) - 1;
+                        v = fmaf(bsm[p], rw.gs[p * n0 + jj], v);
+                    }
+                } else {
 #pragma unroll
-                for (int p = 0; p < RC; ++p) {
-                    if (WIDE && p >= R) break;
-                    v = fmaf(bget(p), rw.gs[p * n0 + jj], v);
+                    for (int p = 0; p < RC; ++p) v = fmaf(bget(p), rw.gs[p * n0 + jj], v);
                 }
                 part += fminf(v * lv[u], v * hv[u]);  // 0 past n0 (lv = hv = 0)
             }

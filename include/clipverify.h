@@ -342,7 +342,8 @@ cv_status cv_cc_items_get(const cv_cache* cache, int items[3]);
 
 /* Autotuner of the item sizes for a batch: runs cv_bound_batch on (in, out, opt, workspace)
  * repeatedly on `stream` and times its complete-clipping phase with CUDA events: one row class
- * at a time, the candidates 128/256/512 (one row), 32/64/128 (two), 8/16/32/64 (three or more),
+ * at a time, the candidates 128/256/512/1024 (one row), 32/64/128/256 (two), 8/16/32/64/128 (three
+ * or more),
  * each round twice, the faster time counting; the fastest sizes stay in the cache.
  * best (may be NULL) receives them, best_ms (may be NULL) their phase time in milliseconds.
  * Host-synchronous (it reads the events), so it cannot be captured in a CUDA graph; `out`

@@ -372,7 +372,7 @@ extern "C" cv_status cv_autotune_cc(cv_net* net, cv_cache* cache, const cv_batch
                                     int best[3], float* best_ms) {
     if (!net || !cache || !in || !out || !opt) { cv_set_error("cv_autotune_cc: null argument"); return CV_EINVAL; }
     if (opt->sweeps <= 0) { cv_set_error("cv_autotune_cc: sweeps = 0, no complete clipping to tune"); return CV_EINVAL; }
-    static const int cand[3][4] = {{128, 256, 512, 0}, {32, 64, 128, 0}, {8, 16, 32, 64}};
+    static const int cand[3][5] = {{128, 256, 512, 1024, 0}, {32, 64, 128, 256, 0}, {8, 16, 32, 64, 128}};
     cv_timer* timer = nullptr;
     cv_status s = cv_timer_create(&timer);
     if (s) return s;
@@ -401,7 +401,7 @@ extern "C" cv_status cv_autotune_cc(cv_net* net, cv_cache* cache, const cv_batch
     if (!s) s = time_it(cur, &t0);
     if (!s) { best_t = t0; have = true; }
     for (int c = 0; c < 3 && !s; ++c) {
-        for (int i = 0; i < 4 && !s; ++i) {
+        for (int i = 0; i < 5 && !s; ++i) {
             const int v = cand[c][i];
             if (v == 0 || v == cur[c]) continue;
             int trial[3] = {cur[0], cur[1], cur[2]};

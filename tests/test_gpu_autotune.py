@@ -10,7 +10,7 @@ from tests._cases import Case, f32  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-GRID = ({128, 256, 512}, {32, 64, 128}, {8, 16, 32, 64})
+GRID = ({128, 256, 512, 1024}, {32, 64, 128, 256}, {8, 16, 32, 64, 128})
 
 
 def _setup(case):

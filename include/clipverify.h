@@ -381,7 +381,9 @@ void      cv_graph_destroy(cv_graph* graph);
  *              cv_bound_batch); the other hidden neurons use their root state
  *  C, t        spec rows [m x n_L], thresholds [m]
  *  alpha       [B x m x n_hidden] lower slopes of unstable neurons, in [0, 1]
- *  grad_f      [B x m] upstream gradient of the bounds; NULL = ones */
+ *  grad_f      [B x m] upstream gradient of the bounds; NULL = ones
+ *  precision   CV_PREC_FP32 (CUDA-core contractions) or CV_PREC_BF16X8 (the forward and the reverse
+ *              sweep's contractions on tensor cores, split-BF16 as in cv_bound_batch) */
 typedef struct cv_alpha_in {
     int B, m;
     const float* lo;
@@ -393,6 +395,7 @@ typedef struct cv_alpha_in {
     const float* t;
     const float* alpha;
     const float* grad_f;
+    int precision;
 } cv_alpha_in;
 
 /* Bytes of workspace cv_alpha_grad needs for B subdomains and m spec rows. */

@@ -59,7 +59,7 @@ class cv_batch_in(ctypes.Structure):
 
 class cv_alpha_in(ctypes.Structure):
     _fields_ = [("B", I), ("m", I), ("lo", P), ("hi", P), ("l", P), ("u", P), ("mask", P), ("C", P), ("t", P),
-                ("alpha", P), ("grad_f", P)]
+                ("alpha", P), ("grad_f", P), ("precision", I)]
 
 
 class cv_bab_params(ctypes.Structure):
@@ -499,9 +499,9 @@ def cv_relaxed_clip_static(net, cache, bi, lo_clip, hi_clip, infeasible, relaxed
                                          int(relaxed), stream_ptr(stream)))
 
 
-def make_alpha_in(B, m, lo, hi, l, u, mask, C, t, alpha, grad_f=None):
+def make_alpha_in(B, m, lo, hi, l, u, mask, C, t, alpha, grad_f=None, precision=0):
     ai = cv_alpha_in()
-    ai.B, ai.m = int(B), int(m)
+    ai.B, ai.m, ai.precision = int(B), int(m), int(precision)
     for name, v in dict(lo=lo, hi=hi, l=l, u=u, mask=mask, C=C, t=t, alpha=alpha, grad_f=grad_f).items():
         setattr(ai, name, ptr(v))
     return ai

@@ -134,7 +134,8 @@ __global__ void k_adam(long long n, float* alpha, float* m1, float* m2, const fl
 }
 
 struct AlphaLayout {
-    size_t lamA, lamB, pb, pp, pf, pm, ab, ap, lam0, keep[CV_MAX_LAYERS + 1], gA, gB, total;
+    size_t lamA, lamB, pb, pp, pf, pm, ab, ap, lam0, keep[CV_MAX_LAYERS + 1], gA, gB;
+    size_t tc_slices, tc_exp, tc_tab, total;  // tensor-core path
 };
 
 void alpha_plan(const cv_net* net, int B, int m, AlphaLayout* L) {
@@ -155,6 +156,11 @@ void alpha_plan(const cv_net* net, int B, int m, AlphaLayout* L) {
     for (int i = 2; i <= net->L; ++i) L->keep[i] = take(R * net->dims[i - 1] * 4);
     L->gA = take(R * net->wmax * 4);
     L->gB = take(R * net->wmax * 4);
+    // digit slices of R rows for the forward (K = n_i, i >= 1) and the reverse sweep (K = n_{h-1},
+    // down to n_0): every width of the network, rounded up to the 64-wide K tile
+    L->tc_slices = take((size_t)3 * R * (size_t)((net->wmax + 63) / 64 * 64) * sizeof(uint16_t));
+    L->tc_exp = take(R * sizeof(int));
+    L->tc_tab = take((size_t)3 * B * net->wmax * sizeof(float));
     L->total = off;
 }
 
@@ -180,6 +186,14 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
         cv_set_error("cv_alpha_grad: missing input");
         return CV_EINVAL;
     }
+    if (in->precision != CV_PREC_FP32 && in->precision != CV_PREC_BF16X8) {
+        cv_set_error("cv_alpha_grad: unknown precision");
+        return CV_EINVAL;
+    }
+    if (in->precision == CV_PREC_BF16X8 && !cv_tc_supported(cache)) {
+        cv_set_error("cv_alpha_grad: the tensor-core weights of a layer were not prepared");
+        return CV_EUNSUPPORTED;
+    }
     if (B == 0) return CV_OK;
     AlphaLayout L;
     alpha_plan(net, B, m, &L);
@@ -193,13 +207,27 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
     float* keep[CV_MAX_LAYERS + 1] = {nullptr};
     for (int i = 2; i <= net->L; ++i) keep[i] = (float*)(ws + L.keep[i]);
     float* lam0 = (float*)(ws + L.lam0);
-    cv_status s = cv_backward_t<float>(net, R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
-                                       cache->root_state, cache->slot_of, in->l, in->u, in->mask, U, in->alpha,
-                                       CV_ALPHA_ADAPTIVE, cache->V, in->lo, in->hi, nullptr, lower, nullptr,
-                                       nullptr, lam0, nullptr, nullptr, nullptr, (float*)(ws + L.lamA),
-                                       (float*)(ws + L.lamB), (double*)(ws + L.pb), (double*)(ws + L.pp),
-                                       (double*)(ws + L.pf), (double*)(ws + L.pm), (double*)(ws + L.ab),
-                                       (double*)(ws + L.ap), keep, st);
+    const bool tc = in->precision == CV_PREC_BF16X8;
+    cv_status s;
+    int launches = 0;
+    if (tc) {
+        // the forward on tensor cores (the bound of cv_bound_batch's split-BF16 path), keeping P^(i)
+        // and Lam_0; lower is written unless NULL
+        s = cv_backward_tc(net, cache, R, m, in->C, in->t, in->l, in->u, in->mask, U, in->alpha, CV_ALPHA_ADAPTIVE,
+                           in->lo, in->hi, nullptr, lower, nullptr, lam0, nullptr, (float*)(ws + L.lamA),
+                           (float*)(ws + L.lamB), (uint16_t*)(ws + L.tc_slices), (int*)(ws + L.tc_exp),
+                           (float*)(ws + L.tc_tab), (double*)(ws + L.pb), (double*)(ws + L.pp),
+                           (double*)(ws + L.pf), (double*)(ws + L.pm), (double*)(ws + L.ab), (double*)(ws + L.ap),
+                           &launches, st, nullptr, nullptr, keep);
+    } else {
+        s = cv_backward_t<float>(net, R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
+                                 cache->root_state, cache->slot_of, in->l, in->u, in->mask, U, in->alpha,
+                                 CV_ALPHA_ADAPTIVE, cache->V, in->lo, in->hi, nullptr, lower, nullptr,
+                                 nullptr, lam0, nullptr, nullptr, nullptr, (float*)(ws + L.lamA),
+                                 (float*)(ws + L.lamB), (double*)(ws + L.pb), (double*)(ws + L.pp),
+                                 (double*)(ws + L.pf), (double*)(ws + L.pm), (double*)(ws + L.ab),
+                                 (double*)(ws + L.ap), keep, st);
+    }
     if (s) return s;
     CV_CUDA(cudaMemsetAsync(grad_alpha, 0, (size_t)B * m * H * sizeof(float), st));
     float* gA = (float*)(ws + L.gA);
@@ -209,6 +237,9 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
         k_adj_start<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(R, n0, m, lam0, in->lo, in->hi, in->grad_f, gA);
         CV_LAUNCH_CHECK("k_adj_start");
     }
+    if (tc)
+        return cv_alpha_reverse_tc(net, cache, R, m, in->l, in->u, in->mask, in->alpha, in->grad_f, keep, gA, gB,
+                                   (uint16_t*)(ws + L.tc_slices), (int*)(ws + L.tc_exp), grad_alpha, &launches, st);
     for (int h = 1; h <= net->L - 1; ++h) {
         AdjArgs a;
         a.A = gA; a.W = net->W[h]; a.b = net->b[h];

@@ -91,6 +91,7 @@ struct cv_cache {
     float* root_lo;    // [n0]
     float* root_hi;    // [n0]
     cv_tc_w* tcw[CV_MAX_LAYERS + 1]; // tensor-core weights per layer (host objects), or null
+    cv_tc_w* tcwT[CV_MAX_LAYERS + 1];// rows of W^(i) split for the slope adjoint's W^T contraction, or null
     cv_tc_pc* tcpc;                  // tensor-core re-concretisation operand, or null
     int cc_items[3];   // complete clipping: tasks per work item for 1, 2 and more active rows
 };
@@ -140,7 +141,14 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                          float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
                          int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
                          double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st,
-                         float* pbuf = nullptr, float* bab_weight = nullptr);
+                         float* pbuf = nullptr, float* bab_weight = nullptr, float* const* keepP_layers = nullptr);
+// Reverse sweep of the slope adjoint on tensor cores (cv_tc.cu): g0 = dLam_0 [R x n0] in, the
+// layer products P^(h+1) of the forward in keepP[h + 1]; gA / gB [R x wmax] scratch (gA holds g0);
+// slices / rexp as for cv_backward_tc.  Writes grad_alpha (zeroed by the caller).
+cv_status cv_alpha_reverse_tc(const cv_net* net, const cv_cache* cache, int R, int m, const float* l, const float* u,
+                              const int8_t* mask, const float* alpha, const float* grad_f, float* const* keepP,
+                              float* gA, float* gB, uint16_t* slices, int* rexp, float* grad_alpha, int* launches,
+                              cudaStream_t st);
 
 // kernels (launch wrappers); each returns CV_OK or a launch error
 cv_status cv_launch_rows(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,

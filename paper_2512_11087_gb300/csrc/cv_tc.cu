@@ -290,7 +290,14 @@ struct TcArgs {
     const float* bnext; const float* Vnext;
     const float* T0; const float* T1; const float* T2;  // relaxation table of layer i-1 [B x N]
     float* Aout;
-    float* keepP;        // optional [R x N]: the product P^(i) (i > 1), for the BaBSR weight
+    float* keepP;        // optional [R x N]: the product P^(i) (i > 1), for the BaBSR weight or the adjoint
+    // slope adjoint (adj = 1): P is dLam^(h) = dP^(h) W^(h)^T with W^(h)'s rows as the B operand;
+    // the epilogue applies the fixed relaxation of the forward (its products Pfwd = P^(h+1))
+    int adj, last;
+    const float* bvec;   // b^(h) [N]
+    const float* Pfwd;   // P^(h+1) [R x N]
+    const float* grad_f; // [R] or NULL
+    float* grad_alpha;   // [B x m x H]
     const float* lo; const float* hi;
     float* lam0;
     double* part_bias; double* part_pad; double* part_f; double* part_fmag; int ncb;
@@ -425,6 +432,74 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
     }
     }
     if (!fine && threadIdx.x == 0) atomicOr(a.status, CV_DEV_TIMEOUT);
+    if (a.adj) {
+        // Slope adjoint: dLam^(h)_q = (dP W^T)_q + g_f b_q; with the forward's relaxation choice
+        // (P^(h+1) >= 0 selects the lower line): d alpha = dLam P^(h+1) for unstable neurons on
+        // the lower line; dP^(h+1)_q = dLam d_q + g_f e_q (unless h is the last hidden layer).
+        const int wq = warp & 3, half = warp >> 2;
+        const int tr = wq * 32 + (threadIdx.x & 31);
+        const int r = row0 + tr;
+        const bool rok = fine && r < a.R;
+        const int er = rok ? a.rexp[r] : 0;
+        const int sub = rok ? r / a.m : 0;
+        const float gf = (rok && a.grad_f) ? a.grad_f[r] : 1.f;
+        const unsigned lane_base = tmem + ((unsigned)(wq * 32) << 16);
+        for (int cc = 0; cc < 32 && fine; cc += 8) {
+            const int c0 = half * 32 + cc;
+            float acc[8];
+            const float* run = s_run + (size_t)tr * (TBN + 1) + c0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = npass > 1 ? run[j] : 0.f;
+            for (int ch = 0; ch < a.nch - 2 * (npass - 1); ++ch) {
+                float lv[NLEV][8];
+#pragma unroll
+                for (int v = 0; v < NLEV; ++v) tmem_ld8(lane_base + (unsigned)((ch * NLEV + v) * TBN + c0), lv[v]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[j] += fmaf(lv[0][j], 16777216.f, fmaf(lv[1][j], 65536.f, fmaf(lv[2][j], 256.f, lv[3][j])));
+            }
+            if (!rok) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int q = col0 + c0 + j;
+                if (q >= a.N) continue;
+                const float dl = ldexpf(acc[j], er + a.fexp[q] - 38) + gf * a.bvec[q];
+                const int g = a.hoff + q;
+                const int slot = a.slot_of[g];
+                float lb, ub;
+                int st;
+                if (slot >= 0) {
+                    const size_t o = (size_t)sub * a.U + slot;
+                    lb = a.l[o]; ub = a.u[o]; st = a.mask[o];
+                } else {
+                    lb = a.root_l[g]; ub = a.root_u[g]; st = a.root_state[g];
+                }
+                const float pf = a.Pfwd[(size_t)r * a.N + q];
+                float d, e;
+                const size_t ga = ((size_t)sub * a.m + (r % a.m)) * a.H + g;
+                if (st > 0) { d = 1.f; e = 0.f; }
+                else if (st < 0) { d = 0.f; e = 0.f; }
+                else if (pf >= 0.f) {
+                    d = a.alpha[ga];
+                    e = 0.f;
+                    a.grad_alpha[ga] = dl * pf;
+                } else {
+                    const float s = ub / (ub - lb);
+                    d = s;
+                    e = -s * lb;
+                }
+                if (!a.last) a.Aout[(size_t)r * a.N + q] = dl * d + gf * e;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+        }
+        return;
+    }
     // Epilogue.  Stage what the tile's elements need in the (now idle) stage buffers: per column
     // its exponent, b^(i-1) and V^(i-1); per (subdomain, column) the relaxation table of layer
     // i-1 (i > 1) or the box (i = 1).  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its
@@ -590,7 +665,7 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                          float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
                          int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
                          double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st,
-                         float* pbuf, float* bab_weight) {
+                         float* pbuf, float* bab_weight, float* const* keepP_layers) {
     if (!cv_tc_supported(cache)) {
         cv_set_error("tensor-core back-substitution: a layer's weights were not prepared");
         return CV_EUNSUPPORTED;
@@ -638,7 +713,7 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         a.Vnext = (i > 1) ? cache->V[i - 1] : nullptr;
         a.T0 = tab; a.T1 = tab + tsz; a.T2 = tab + 2 * tsz;
         a.Aout = nxt;
-        a.keepP = (i > 1 && bab_weight && m > 0) ? pbuf : nullptr;
+        a.keepP = (i > 1 && keepP_layers) ? keepP_layers[i] : ((i > 1 && bab_weight && m > 0) ? pbuf : nullptr);
         a.lo = lo; a.hi = hi; a.lam0 = lam0;
         a.part_bias = part_bias; a.part_pad = part_pad; a.part_f = part_f; a.part_fmag = part_fmag;
         a.ncb = (w->N + TBN - 1) / TBN;
@@ -650,7 +725,7 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         if (i > 1) {
             if ((s = cv_bwd_reduce(R, a.ncb, part_bias, part_pad, acc_bias, acc_pad, gam, st))) return s;
             ++*launches;
-            if (a.keepP) {
+            if (a.keepP && bab_weight && !keepP_layers) {
                 if ((s = cv_babsr_weight_layer(nsub, m, w->N, a.hoff, cache->slot_of, U, pbuf, skip, bab_weight, st)))
                     return s;
                 ++*launches;
@@ -663,6 +738,55 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                 return s;
             ++*launches;
         }
+    }
+    return CV_OK;
+}
+
+cv_status cv_alpha_reverse_tc(const cv_net* net, const cv_cache* cache, int R, int m, const float* l, const float* u,
+                              const int8_t* mask, const float* alpha, const float* grad_f, float* const* keepP,
+                              float* gA, float* gB, uint16_t* slices, int* rexp, float* grad_alpha, int* launches,
+                              cudaStream_t st) {
+    const int L = net->L;
+    for (int h = 1; h < L; ++h)
+        if (!cache->tcwT[h]) {
+            cv_set_error("tensor-core slope adjoint: a layer's weights were not prepared");
+            return CV_EUNSUPPORTED;
+        }
+    if (R == 0) return CV_OK;
+    CV_CUDA(cudaFuncSetAttribute(k_tc_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM + TC_RUN_SMEM));
+    for (int h = 1; h < L; ++h) {
+        const cv_tc_w* w = cache->tcwT[h];
+        // dP^(h) rows to digit slices (no pad: the gradient is not a bound)
+        k_tc_split<RowLd><<<(R + 7) / 8, 256, 0, st>>>(R, R, w->K, w->Kp, RowLd{gA, w->K}, slices, rexp, nullptr,
+                                                        nullptr, nullptr, 0.0, 0.0, 0.0);
+        CV_LAUNCH_CHECK("k_tc_split");
+        CUtensorMap tA;
+        cv_status s = encode_slices(&tA, slices, R, w->Kp, TBM);
+        if (s) return s;
+        TcArgs a;
+        memset(&a, 0, sizeof(a));
+        a.adj = 1;
+        a.last = (h == L - 1);
+        a.R = R; a.K = w->K; a.N = w->N; a.i = h; a.Kp = w->Kp; a.nch = (w->Kp + KCH - 1) / KCH;
+        a.rows_per_sub = m; a.m = m;
+        a.hoff = net->hoff[h];
+        a.H = net->H;
+        a.rexp = rexp; a.fexp = w->fexp;
+        a.root_l = cache->root_l; a.root_u = cache->root_u; a.root_state = cache->root_state;
+        a.slot_of = cache->slot_of; a.l = l; a.u = u; a.mask = mask; a.U = cache->U;
+        a.alpha = alpha;
+        a.bvec = net->b[h];
+        a.Pfwd = keepP[h + 1];
+        a.grad_f = grad_f;
+        a.grad_alpha = grad_alpha;
+        a.Aout = gB;
+        a.ncb = (w->N + TBN - 1) / TBN;
+        a.status = net->status;
+        dim3 grd(a.ncb, (R + TBM - 1) / TBM);
+        k_tc_layer<<<grd, 256, TC_SMEM + (a.nch > 2 ? TC_RUN_SMEM : 0), st>>>(tA, w->tmap, a);
+        CV_LAUNCH_CHECK("k_tc_layer");
+        *launches += 2;
+        float* t = gA; gA = gB; gB = t;
     }
     return CV_OK;
 }
@@ -923,12 +1047,14 @@ cv_status cv_reconc_tc(const cv_cache* cache, int B, const float* lo, const floa
 void cv_tc_release(cv_cache* c) {
     if (!c) return;
     for (int i = 0; i <= CV_MAX_LAYERS; ++i) {
-        cv_tc_w* w = c->tcw[i];
-        if (!w) continue;
-        cudaFree(w->slices);
-        cudaFree(w->fexp);
-        delete w;
-        c->tcw[i] = nullptr;
+        for (cv_tc_w** slot : {&c->tcw[i], &c->tcwT[i]}) {
+            cv_tc_w* w = *slot;
+            if (!w) continue;
+            cudaFree(w->slices);
+            cudaFree(w->fexp);
+            delete w;
+            *slot = nullptr;
+        }
     }
     if (c->tcpc) {
         cudaFree(c->tcpc->slices);
@@ -971,6 +1097,24 @@ cv_status cv_tc_prepare(cv_cache* c, const float* xmag, const float* zmag, cudaS
         w->F1 = hF[0] * (1.0 + 1e-12);
         w->F2 = hF[1] * (1.0 + 1e-12);
         w->F3 = hF[2] * (1.0 + 1e-12);
+        cv_status s = encode_slices(&w->tmap, w->slices, Np, Kp, TBN);
+        if (s) return s;
+    }
+    // the rows of W^(h), h < L, for the slope adjoint's contraction dP^(h) W^(h)^T (K = n_{h-1})
+    for (int h = 1; h < n->L; ++h) {
+        const int K = n->dims[h - 1], N = n->dims[h];
+        const int Kp = round_up(K, TBK), Np = round_up(N, TBN);
+        if (Kp > KMAX) continue;
+        cv_tc_w* w = new cv_tc_w();
+        memset(w, 0, sizeof(*w));
+        c->tcwT[h] = w;
+        w->K = K; w->N = N; w->Kp = Kp; w->Np = Np;
+        CV_CUDA(cudaMalloc(&w->slices, (size_t)3 * Np * Kp * sizeof(uint16_t)));
+        CV_CUDA(cudaMemsetAsync(w->slices, 0, (size_t)3 * Np * Kp * sizeof(uint16_t), st));
+        CV_CUDA(cudaMalloc(&w->fexp, (size_t)N * sizeof(int)));
+        k_tc_split<RowLd><<<(N + 7) / 8, 256, 0, st>>>(N, Np, K, Kp, RowLd{n->W[h], K}, w->slices, w->fexp, nullptr,
+                                                        nullptr, nullptr, 0.0, 0.0, 0.0);
+        CV_LAUNCH_CHECK("k_tc_split");
         cv_status s = encode_slices(&w->tmap, w->slices, Np, Kp, TBN);
         if (s) return s;
     }

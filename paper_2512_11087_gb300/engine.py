@@ -187,8 +187,9 @@ class AlphaBound(torch.autograd.Function):
 class AlphaState:
     """Inputs that stay fixed during slope optimisation, plus the workspace."""
 
-    def __init__(self, net: Net, lo, hi, l, u, mask, C, t):
+    def __init__(self, net: Net, lo, hi, l, u, mask, C, t, precision=capi.CV_PREC_FP32):
         self.net = net
+        self.precision = int(precision)
         self.B, self.n0 = lo.shape
         self.m = C.shape[0]
         self.lo, self.hi, self.l, self.u, self.mask, self.C, self.t = lo, hi, l, u, mask, C, t
@@ -199,7 +200,7 @@ class AlphaState:
         lower = torch.empty(self.B, self.m, dtype=torch.float32, device=alpha.device)
         grad = torch.empty_like(alpha)
         ai = capi.make_alpha_in(self.B, self.m, self.lo, self.hi, self.l, self.u, self.mask, self.C, self.t,
-                                alpha.detach().contiguous(), grad_f)
+                                alpha.detach().contiguous(), grad_f, precision=self.precision)
         capi.cv_alpha_grad(self.net.handle, self.net.cache, ai, lower, grad, self.ws, self.ws_bytes)
         return lower, grad
 

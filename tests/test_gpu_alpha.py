@@ -58,18 +58,22 @@ def _full_bounds(s, b):
     return hl, hu, hs
 
 
-def _state(s):
+def _state(s, precision=0):
     from paper_2512_11087_gb300 import engine as E
     d = E.to_dev
-    return E.AlphaState(s["net"], d(s["lo"]), d(s["hi"]), d(s["l"]), d(s["u"]), d(s["mask"]), d(s["C"]), d(s["t"]))
+    return E.AlphaState(s["net"], d(s["lo"]), d(s["hi"]), d(s["l"]), d(s["u"]), d(s["mask"]), d(s["C"]), d(s["t"]),
+                        precision=precision)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("dims,B,seed", [([30, 40, 40, 40, 5], 6, 1), ([784, 96, 96, 10], 5, 2),
-                                         ([5] + [50] * 6 + [5], 4, 3)])
-def test_alpha_gradient_parity(dims, B, seed):
+                                         ([5] + [50] * 6 + [5], 4, 3), ([40, 600, 300, 6], 5, 4)])
+def test_alpha_gradient_parity(dims, B, seed, precision):
+    """FP32 CUDA-core contractions and the split-BF16 tensor-core forward and reverse sweep (the
+    last network has a 600-wide layer: several K passes both ways)."""
     from paper_2512_11087_gb300 import engine as E
     s = _setup(dims, B, seed, eps=0.05 if dims[0] > 5 else 0.1)
-    st = _state(s)
+    st = _state(s, precision)
     rng = np.random.default_rng(seed + 10)
     gf = rng.uniform(0.5, 1.5, size=(B, s["m"])).astype(np.float32)
     lower, grad = st.bound_and_grad(E.to_dev(s["alpha"]), E.to_dev(gf))

@@ -94,16 +94,17 @@ def test_cnn3x32_full_size_sampled(precision):
     print("cnn3x32 sampled parity", st)
 
 
-def test_alpha_gradient_config4_full_size_sampled():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_alpha_gradient_config4_full_size_sampled(precision):
     """Configuration 4's shape at full batch: 784->1024x4->10, 1024 subdomains, slopes per (subdomain,
-    spec row, neuron).  The GPU computes all 1024 bounds and gradients (FP32 CUDA-core contractions:
-    the layers exceed the tensor cores' 512 inputs); 4 subdomains are checked against the oracle's FP64
-    reverse sweep at the bar of tests/test_gpu_alpha.py."""
+    spec row, neuron).  The GPU computes all 1024 bounds and gradients (FP32 CUDA-core contractions,
+    or the split-BF16 tensor cores with 1024-wide layers in two K passes); 4 subdomains are checked
+    against the oracle's FP64 reverse sweep at the bar of tests/test_gpu_alpha.py."""
     from oracle import oracle as O
     from paper_2512_11087_gb300 import engine as E
     from tests.test_gpu_alpha import _full_bounds, _setup, _state
     s = _setup([784, 1024, 1024, 1024, 1024, 10], 1024, 9, eps=0.02)
-    st = _state(s)
+    st = _state(s, precision)
     lower, grad = st.bound_and_grad(E.to_dev(s["alpha"]))
     torch.cuda.synchronize()
     sample = [0, 341, 682, 1023]

@@ -517,59 +517,24 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
             return cls;
         };
         if (it == 0) {
-            // With E_j <= c1 max|1/g_k| + tu |q_j|, an element can meet the window only if
-            // |q_j - q*| <= X = (c1 max|1/g_k| + tu |q*| + E*) / (1 - tu): a range of key bits when it
-            // lies in one sign (one subtraction and one comparison per key), |q| <= X around 0 for
-            // dec = 0; otherwise the float test of the screen bound.
-            const float X = __fmul_ru(__fadd_ru(__fmaf_ru(c1, cc_Rm[k], __fmul_ru(tu, fabsf(qs))), Es), 1.0000002f);
-            int mode = 2;  // 0: positive range [klo, klo + span]; 1: |q| <= X; 2: float test
-            unsigned klo = 0u, span = 0u;
-            if (dec == 0) {
-                mode = 1;
-                span = __float_as_uint(X);
-            } else {
-                const float lo_ = __fsub_rd(qs, X);
-                if (lo_ > 0.f && X < INFINITY) {
-                    mode = 0;
-                    klo = __float_as_uint(lo_);
-                    span = __float_as_uint(__fadd_ru(qs, X)) - klo;
-                }
-            }
-            const bool vec = ((n0 & 3) == 0) && (((size_t)keys & 15u) == 0u);
+            // With E_j <= c1 |1/g_kj| + tu |q_j| (c1 bounds Ru S_j for every j), an element can meet the
+            // window only if |q_j - q*| <= c1 |1/g_kj| + tu |q_j| + E*: the screen tests that (1% above,
+            // for its own roundings) with each element's own |1/g_kj|, 32 elements a lane at a time.
 #pragma unroll 1
             for (int cb = 0; cb < n0; cb += 1024) {
-                unsigned msk = 0u;  // bit i: element cb + 4 (32 (i / 4) + lane) + i % 4 (vec) or cb + 32 i + lane
-                if (vec && mode != 2) {
-#pragma unroll 2
-                    for (int i = 0; i < 8; ++i) {
-                        const int j = cb + 4 * (32 * i + lane);
-                        const bool v = j < n0;
-                        const uint4 kk = *(const uint4*)(keys + (v ? j : 0));
-                        const unsigned t[4] = {kk.x, kk.y, kk.z, kk.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const bool in = v && (mode == 0 ? (t[e] - klo) <= span : (t[e] & 0x7fffffffu) <= span);
-                            msk |= (unsigned)in << (4 * i + e);
-                        }
-                    }
-                } else {
+                unsigned msk = 0u;  // bit i: element cb + 32 i + lane
 #pragma unroll 8
-                    for (int i = 0; i < 32; ++i) {
-                        const int j = cb + 32 * i + lane;
-                        const int jj = j < n0 ? j : n0 - 1;
-                        const unsigned kb = keys[jj];
-                        const float q = __uint_as_float(kb);
-                        bool scr;
-                        if (mode == 0) scr = (kb - klo) <= span;
-                        else if (mode == 1) scr = (kb & 0x7fffffffu) <= span;
-                        else scr = fabsf(q - qs) <= fmaf(sc1, fabsf(rk[jj]), fmaf(stu, fabsf(q), sEs));
-                        msk |= (unsigned)(j < n0 && scr) << i;
-                    }
+                for (int i = 0; i < 32; ++i) {
+                    const int j = cb + 32 * i + lane;
+                    const int jj = j < n0 ? j : n0 - 1;
+                    const float q = __uint_as_float(keys[jj]);
+                    const bool scr = fabsf(q - qs) <= fmaf(sc1, fabsf(rk[jj]), fmaf(stu, fabsf(q), sEs));
+                    msk |= (unsigned)(j < n0 && scr) << i;
                 }
                 while (msk) {
                     const int i = __ffs(msk) - 1;
                     msk &= msk - 1u;
-                    const int j = (vec && mode != 2) ? cb + 4 * (32 * (i >> 2) + lane) + (i & 3) : cb + 32 * i + lane;
+                    const int j = cb + 32 * i + lane;
                     take(j, __uint_as_float(keys[j]), j == jn0 ? a_jn : __ldg(ap + j));
                 }
             }

@@ -39,7 +39,7 @@
 // single-block scan turns the per-subdomain task counts into work items (by default 256 (target,
 // side) tasks for one row, 64 for two, 16 for more: longer tasks, smaller items; the cache holds
 // the sizes, which cv_cc_items_set and the autotuner change), subdomains with more rows first; a
-// persistent k_complete grid (two blocks of 14 warps per SM) takes items from an atomic ticket,
+// persistent k_complete grid (two blocks of 12 warps per SM) takes items from an atomic ticket,
 // stages the item's rows in shared memory, and its warps take the item's tasks one at a time from
 // a shared counter.  The task body is compiled for each row count (multipliers in registers);
 // subdomains with more than four rows run in a separate launch of one block per SM (more
@@ -57,9 +57,9 @@ constexpr int RMAX_CC = 32;  // rows per subdomain handled by complete clipping
 constexpr int RTPL = 4;     // row counts up to this run in the main launch (two blocks per SM)
 // (target, side) tasks per work item: fewer for subdomains with more rows (longer tasks)
 #ifndef CV_CC_NWARP
-#define CV_CC_NWARP 14
+#define CV_CC_NWARP 12
 #endif
-constexpr int NWARP = CV_CC_NWARP;  // warps per block at most (two blocks per SM of 14 leave 72 registers a thread)
+constexpr int NWARP = CV_CC_NWARP;  // warps per block at most (two blocks per SM of 12 leave 84 registers a thread)
 constexpr int CAPC = 256;   // breakpoints a warp's compacted list holds
 constexpr int SAMP_MIN = 64;     // brackets with more breakpoints start from sampled pivots
 constexpr float SAMP_D = 0.10f;  // rank margin of the sampled pivots around the target fraction
@@ -523,7 +523,7 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
 #pragma unroll 1
             for (int cb = 0; cb < n0; cb += 1024) {
                 unsigned msk = 0u;  // bit i: element cb + 32 i + lane
-#pragma unroll 8
+#pragma unroll 2
                 for (int i = 0; i < 32; ++i) {
                     const int j = cb + 32 * i + lane;
                     const int jj = j < n0 ? j : n0 - 1;
@@ -866,7 +866,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 const float2* ap2 = (const float2*)keys;  // the plane, overwritten pair by pair
                 constexpr int P2 = 1;  // pairs per lane per iteration
                 if (warm) {
-#pragma unroll 2
+#pragma unroll 1
                     for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
                         float2 av[P2];
                         av[0] = ap2[min(j0, n0 - 2) >> 1];
@@ -889,7 +889,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     fle += flt;
                 } else {
                     ext = false;
-#pragma unroll 2
+#pragma unroll 1
                     for (int j0 = 2 * lane; j0 < n0; j0 += 64 * P2) {
                         float2 av[P2];
                         av[0] = ap2[min(j0, n0 - 2) >> 1];
@@ -970,7 +970,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     const unsigned kp = __float_as_uint(qp);
                     if (Fle < T) { lo = kp; Flo = Fle; }
                     else { hi = kp - 1u; Fhi = Flt; }
-#pragma unroll 4
+#pragma unroll 1
                     for (int j = lane; j < n0; j += 32) {
                         const unsigned kk = keys[j];
                         const unsigned long long w = (unsigned long long)wk[j];

@@ -137,12 +137,32 @@ static double alpha_rule(int mode, double l, double u) {
 /* state the tolerance of the CUDA comparison).  If keepP != NULL, the        */
 /* products P^(i) = Lam^(i) W^(i) for i = 2..k are saved (for the adjoint).   */
 /* ------------------------------------------------------------------------- */
+static void backward_beta(const net_t* n, int k, int rows, const double* Lam_k,
+                          const double* hl, const double* hu, const signed char* hstate,
+                          const double* alpha, int alpha_mode,
+                          double* Lam0, double* bias,
+                          double* scale, const double* zmag, const double* xmag,
+                          double** keepP, const double* beta, const signed char* bsign);
 static void backward(const net_t* n, int k, int rows, const double* Lam_k,
                      const double* hl, const double* hu, const signed char* hstate,
                      const double* alpha, int alpha_mode,
                      double* Lam0, double* bias,
                      double* scale, const double* zmag, const double* xmag,
                      double** keepP) {
+    backward_beta(n, k, rows, Lam_k, hl, hu, hstate, alpha, alpha_mode, Lam0, bias, scale, zmag, xmag, keepP,
+                  NULL, NULL);
+}
+
+/* The same with split multipliers (the beta-CROWN form of the split constraints of Section 3.4):  */
+/* beta [rows x H] >= 0 and bsign [H] (+1: split z_g >= 0, -1: z_g <= 0, 0: none).  A split holds   */
+/* the constraint -bsign_g z_g <= 0, so adding beta_g (-bsign_g z_g) to the bound keeps it a lower   */
+/* bound on the subdomain: after hidden layer i-1's relaxation, Lam_g -= bsign_g beta_g.            */
+static void backward_beta(const net_t* n, int k, int rows, const double* Lam_k,
+                          const double* hl, const double* hu, const signed char* hstate,
+                          const double* alpha, int alpha_mode,
+                          double* Lam0, double* bias,
+                          double* scale, const double* zmag, const double* xmag,
+                          double** keepP, const double* beta, const signed char* bsign) {
     const int* d = n->dims;
     int wmax = 0;
     for (int i = 0; i <= n->L; ++i) if (d[i] > wmax) wmax = d[i];
@@ -203,6 +223,7 @@ static void backward(const net_t* n, int k, int rows, const double* Lam_k,
                 double dd, ee;
                 relu_relax(P[q], hl[g], hu[g], hstate[g], a, &dd, &ee);
                 out[q] = P[q] * dd;
+                if (beta && bsign[g]) out[q] -= (double)bsign[g] * beta[(long)r * n->H + g];
                 bsum += P[q] * ee;
             }
             bias[r] += bsum;
@@ -952,7 +973,8 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
                    const double* hl, const double* hu, const signed char* hs,
                    const double* lo, const double* hi,
                    int m, const double* C, const double* t, const double* alpha,
-                   const double* grad_f, double* f_out, double* grad_alpha) {
+                   const double* grad_f, double* f_out, double* grad_alpha,
+                   const double* beta, const signed char* bsign, double* grad_beta) {
     net_t n;
     if (net_init(&n, L, dims, W, bvec)) return -1;
     int n0 = dims[0], H = n.H;
@@ -963,7 +985,7 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
     double* L0 = (double*)malloc(sizeof(double) * (size_t)m * n0);
     memcpy(Lam, C, sizeof(double) * (size_t)m * dims[L]);
     for (int r = 0; r < m; ++r) bias[r] = t[r];
-    backward(&n, L, m, Lam, hl, hu, hs, alpha, 0, L0, bias, NULL, NULL, NULL, keepP);
+    backward_beta(&n, L, m, Lam, hl, hu, hs, alpha, 0, L0, bias, NULL, NULL, NULL, keepP, beta, bsign);
     int wmax = 0;
     for (int i = 0; i <= L; ++i) if (dims[i] > wmax) wmax = dims[i];
     double* gl = (double*)malloc(sizeof(double) * wmax);   /* adjoint of Lam^(i) */
@@ -974,6 +996,8 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
         f_out[r] = vmin;
         double gf = grad_f ? grad_f[r] : 1.0;
         for (int g = 0; g < H; ++g) grad_alpha[(long)r * H + g] = 0.0;
+        if (grad_beta)
+            for (int g = 0; g < H; ++g) grad_beta[(long)r * H + g] = 0.0;
         /* d f / d Lam0_q = xhat_q - sign(Lam0_q) eps_q */
         double* gx = (double*)malloc(sizeof(double) * n0);
         for (int q = 0; q < n0; ++q) {
@@ -1001,6 +1025,8 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
                 double dd, ee;
                 relu_relax(P[j], hl[g], hu[g], hs[g], a, &dd, &ee);
                 if (hs[g] == 0 && P[j] >= 0.0) grad_alpha[(long)r * H + g] = gl[j] * P[j];
+                /* Lam^(i)_j = P_j d_j - bsign_j beta_j: d f / d beta_j = -bsign_j dLam^(i)_j */
+                if (grad_beta && bsign && bsign[g]) grad_beta[(long)r * H + g] = -(double)bsign[g] * gl[j];
                 gp[j] = gl[j] * dd + gf * ee;
             }
             /* P^(i+1) = Lam^(i+1) W^(i+1), bias += Lam^(i+1) b^(i+1) */
@@ -1017,16 +1043,21 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
     return 0;
 }
 
-/* Adam ascent step on alpha with clamp to [0, 1] (Kingma & Ba; the paper's   */
-/* SDP-FO setting: lr 0.1 decayed by 0.98 per iteration).  t is 1-based.     */
-void orc_adam_step(long n, double* alpha, double* m1, double* m2, const double* g,
-                   int t, double lr, double b1, double b2, double eps) {
+/* Adam ascent step with clamp to [lo, hi] (Kingma & Ba); beta uses [0, inf).  */
+void orc_adam_step_range(long n, double* x, double* m1, double* m2, const double* g, int t, double lr,
+                         double b1, double b2, double eps, double lo, double hi) {
     double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
     for (long i = 0; i < n; ++i) {
         m1[i] = b1 * m1[i] + (1.0 - b1) * g[i];
         m2[i] = b2 * m2[i] + (1.0 - b2) * g[i] * g[i];
-        double mh = m1[i] / c1, vh = m2[i] / c2;
-        double a = alpha[i] + lr * mh / (sqrt(vh) + eps);
-        alpha[i] = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+        double step = lr * (m1[i] / c1) / (sqrt(m2[i] / c2) + eps);
+        x[i] = fmin(fmax(x[i] + step, lo), hi);
     }
+}
+
+/* Adam ascent step on alpha with clamp to [0, 1] (Kingma & Ba; the paper's   */
+/* SDP-FO setting: lr 0.1 decayed by 0.98 per iteration).  t is 1-based.     */
+void orc_adam_step(long n, double* alpha, double* m1, double* m2, const double* g,
+                   int t, double lr, double b1, double b2, double eps) {
+    orc_adam_step_range(n, alpha, m1, m2, g, t, lr, b1, b2, eps, 0.0, 1.0);
 }

@@ -383,7 +383,15 @@ void      cv_graph_destroy(cv_graph* graph);
  *  alpha       [B x m x n_hidden] lower slopes of unstable neurons, in [0, 1]
  *  grad_f      [B x m] upstream gradient of the bounds; NULL = ones
  *  precision   CV_PREC_FP32 (CUDA-core contractions) or CV_PREC_BF16X8 (the forward and the reverse
- *              sweep's contractions on tensor cores, split-BF16 as in cv_bound_batch) */
+ *              sweep's contractions on tensor cores, split-BF16 as in cv_bound_batch)
+ *  beta        [B x m x n_hidden] split multipliers >= 0, or NULL (none): the beta-CROWN form of the
+ *              split constraints of Section 3.4.  A split z_g >= 0 (z_g <= 0) holds -z_g <= 0 (z_g <= 0)
+ *              on the subdomain, so beta_g times it is added to the bound, which stays a lower bound
+ *              for any beta >= 0 (after hidden layer h's relaxation, Lam_g -= sign_g beta_g, rounded
+ *              so that the multiplier in effect is >= beta_g)
+ *  split_sign  [B x n_hidden] +1 for a split z_g >= 0, -1 for z_g <= 0, 0 for none (cv_split_signs);
+ *              required with beta
+ *  grad_beta   [B x m x n_hidden] output (with beta): d sum_r grad_f f_r / d beta, 0 where no split */
 typedef struct cv_alpha_in {
     int B, m;
     const float* lo;
@@ -396,6 +404,9 @@ typedef struct cv_alpha_in {
     const float* alpha;
     const float* grad_f;
     int precision;
+    const float* beta;
+    const int8_t* split_sign;
+    float* grad_beta;
 } cv_alpha_in;
 
 /* Bytes of workspace cv_alpha_grad needs for B subdomains and m spec rows. */
@@ -410,6 +421,17 @@ cv_status cv_alpha_grad_workspace(const cv_net* net, int B, int m, size_t* bytes
  * The gradient is FP32 and carries no pad. */
 cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_alpha_in* in, float* lower,
                         float* grad_alpha, void* workspace, size_t workspace_bytes, void* stream);
+
+/* The split signs [B x n_hidden] of a batch's CSR split lists (device; split_off NULL: no splits):
+ * +1 for a code +(g+1) (z_g >= 0), -1 for -(g+1) (z_g <= 0), 0 elsewhere.  Codes out of range are
+ * skipped (and flagged in the network's status word, as in cv_bound_batch). */
+cv_status cv_split_signs(cv_net* net, int B, const int* split_off, const int* split_ids, int8_t* sign,
+                         void* stream);
+
+/* One Adam ascent step on n values clamped to [lo, hi] (the split multipliers: [0, inf)); as
+ * cv_alpha_adam otherwise. */
+cv_status cv_adam_range(float* x, float* m1, float* m2, const float* grad, long long n, int t, float lr,
+                        float beta1, float beta2, float eps, float lo, float hi, void* stream);
 
 /* One Adam ascent step on n slopes (device arrays alpha, m1, m2, grad), t >= 1 the step count,
  * followed by clamping alpha to [0, 1] (the paper's alpha optimisation uses Adam with learning

@@ -974,10 +974,24 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
                    const double* lo, const double* hi,
                    int m, const double* C, const double* t, const double* alpha,
                    const double* grad_f, double* f_out, double* grad_alpha,
-                   const double* beta, const signed char* bsign, double* grad_beta) {
+                   const double* beta, const signed char* bsign, double* grad_beta,
+                   const double* zmag, double* scale_out) {
     net_t n;
     if (net_init(&n, L, dims, W, bvec)) return -1;
     int n0 = dims[0], H = n.H;
+    /* with scale_out: the magnitude scale of every bound (as orc_bound_batch's lower_scale), with the
+       hidden neurons' magnitudes zmag (max(|hl|, |hu|) when NULL) */
+    double* sc = NULL;
+    double* zm = NULL;
+    double* xm = NULL;
+    if (scale_out) {
+        sc = scale_out;
+        for (int r = 0; r < m; ++r) sc[r] = fabs(t[r]);
+        zm = (double*)malloc(sizeof(double) * (H > 0 ? H : 1));
+        for (int g = 0; g < H; ++g) zm[g] = zmag ? zmag[g] : fmax(fabs(hl[g]), fabs(hu[g]));
+        xm = (double*)malloc(sizeof(double) * n0);
+        for (int q = 0; q < n0; ++q) xm[q] = fmax(fabs(lo[q]), fabs(hi[q]));
+    }
     double** keepP = (double**)calloc(L + 1, sizeof(double*));
     for (int i = 2; i <= L; ++i) keepP[i] = (double*)malloc(sizeof(double) * (size_t)m * dims[i - 1]);
     double* Lam = (double*)malloc(sizeof(double) * (size_t)m * dims[L]);
@@ -985,7 +999,7 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
     double* L0 = (double*)malloc(sizeof(double) * (size_t)m * n0);
     memcpy(Lam, C, sizeof(double) * (size_t)m * dims[L]);
     for (int r = 0; r < m; ++r) bias[r] = t[r];
-    backward_beta(&n, L, m, Lam, hl, hu, hs, alpha, 0, L0, bias, NULL, NULL, NULL, keepP, beta, bsign);
+    backward_beta(&n, L, m, Lam, hl, hu, hs, alpha, 0, L0, bias, sc, zm, xm, keepP, beta, bsign);
     int wmax = 0;
     for (int i = 0; i <= L; ++i) if (dims[i] > wmax) wmax = dims[i];
     double* gl = (double*)malloc(sizeof(double) * wmax);   /* adjoint of Lam^(i) */
@@ -994,6 +1008,8 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
         double vmin;
         orc_concretize(n0, L0 + (long)r * n0, bias[r], lo, hi, &vmin, NULL);
         f_out[r] = vmin;
+        if (sc)
+            for (int q = 0; q < n0; ++q) sc[r] += fabs(L0[(long)r * n0 + q]) * xm[q];
         double gf = grad_f ? grad_f[r] : 1.0;
         for (int g = 0; g < H; ++g) grad_alpha[(long)r * H + g] = 0.0;
         if (grad_beta)
@@ -1039,7 +1055,7 @@ int orc_alpha_grad(int L, const int* dims, const double* W, const double* bvec,
         }
     }
     for (int i = 2; i <= L; ++i) free(keepP[i]);
-    free(keepP); free(Lam); free(bias); free(L0); free(gl); free(gp);
+    free(keepP); free(Lam); free(bias); free(L0); free(gl); free(gp); free(zm); free(xm);
     return 0;
 }
 

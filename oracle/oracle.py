@@ -63,7 +63,7 @@ def _load():
                                          [P, I] + [P, P] + [I, I, I] +
                                          [P] * 14 + [I])
         _lib.orc_bound_batch.restype = I
-        _lib.orc_alpha_grad.argtypes = [I, P, P, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P]
+        _lib.orc_alpha_grad.argtypes = [I, P, P, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_adam_step_range.argtypes = [ctypes.c_long, P, P, P, P, I, D, D, D, D, D, D]
         _lib.orc_alpha_grad.restype = I
         _lib.orc_adam_step.argtypes = [ctypes.c_long, P, P, P, P, I, D, D, D, D]
@@ -376,9 +376,11 @@ def bound_batch(net: Net, cache, lo, hi, *, l_in=None, u_in=None, split_off=None
     return out
 
 
-def alpha_grad(net: Net, hl, hu, hs, lo, hi, C, t, alpha, grad_f=None, beta=None, bsign=None):
+def alpha_grad(net: Net, hl, hu, hs, lo, hi, C, t, alpha, grad_f=None, beta=None, bsign=None, zmag=None,
+               want_scale=False):
     """f [m] and d(sum grad_f*f)/d alpha [m x H] for one subdomain; with split multipliers beta [m x H]
-    and split signs bsign [H] (+1: z >= 0, -1: z <= 0, 0: none) also d/d beta [m x H]."""
+    and split signs bsign [H] (+1: z >= 0, -1: z <= 0, 0: none) also d/d beta [m x H]; with want_scale,
+    last, the bounds' magnitude scales [m] (hidden magnitudes zmag, default max(|hl|, |hu|))."""
     lib = _load()
     m = int(np.asarray(C).shape[0])
     hl, hu, lo, hi, Cx, tx, al = _f64(hl), _f64(hu), _f64(lo), _f64(hi), _f64(C), _f64(t), _f64(alpha)
@@ -389,10 +391,14 @@ def alpha_grad(net: Net, hl, hu, hs, lo, hi, C, t, alpha, grad_f=None, beta=None
     bt = None if beta is None else _f64(beta)
     bs = None if beta is None else np.ascontiguousarray(np.asarray(bsign, np.int8))
     gb = None if beta is None else np.zeros((m, net.H))
+    zm = None if zmag is None else _f64(zmag)
+    sc = np.zeros(m) if want_scale else None
     rc = lib.orc_alpha_grad(net.L, _p(net.dims), _p(net.Wflat), _p(net.bflat), _p(hl), _p(hu), _p(hs),
-                            _p(lo), _p(hi), m, _p(Cx), _p(tx), _p(al), _p(gf), _p(f), _p(g), _p(bt), _p(bs), _p(gb))
+                            _p(lo), _p(hi), m, _p(Cx), _p(tx), _p(al), _p(gf), _p(f), _p(g), _p(bt), _p(bs), _p(gb),
+                            _p(zm), _p(sc))
     assert rc == 0
-    return (f, g) if beta is None else (f, g, gb)
+    out = (f, g) if beta is None else (f, g, gb)
+    return out + (sc,) if want_scale else out
 
 
 def adam_step_range(x, m1, m2, g, t, lr, lo, hi, b1=0.9, b2=0.999, eps=1e-8):

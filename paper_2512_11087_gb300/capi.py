@@ -59,7 +59,7 @@ class cv_batch_in(ctypes.Structure):
 
 class cv_alpha_in(ctypes.Structure):
     _fields_ = [("B", I), ("m", I), ("lo", P), ("hi", P), ("l", P), ("u", P), ("mask", P), ("C", P), ("t", P),
-                ("alpha", P), ("grad_f", P), ("precision", I)]
+                ("alpha", P), ("grad_f", P), ("precision", I), ("beta", P), ("split_sign", P), ("grad_beta", P)]
 
 
 class cv_bab_params(ctypes.Structure):
@@ -130,6 +130,9 @@ def load():
         "cv_select_targets_workspace": ([I, I, P], I),
         "cv_select_targets": ([P, P, I, P, P, P, P, I, P, P, P, ctypes.c_size_t, P], I),
         "cv_round_summary": ([I, I, P, P, P, P, P, P], I),
+        "cv_split_signs": ([P, I, P, P, P, P], I),
+        "cv_adam_range": ([P, P, P, P, ctypes.c_longlong, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, ctypes.c_float, ctypes.c_float, P], I),
         "cv_bab_params_default": ([P], None),
         "cv_bab_create": ([P, P, I, P, P, P, ctypes.POINTER(P)], I),
         "cv_bab_init": ([P, I, P, P, P, P], I),
@@ -158,7 +161,8 @@ def exported_symbols():
                         "cv_input_split", "cv_spec_clip_workspace", "cv_spec_clip",
                         "cv_activation_split_workspace", "cv_activation_split", "cv_select_targets_workspace",
                         "cv_select_targets", "cv_bab_params_default", "cv_bab_create", "cv_bab_init",
-                        "cv_bab_step", "cv_bab_run", "cv_bab_read", "cv_bab_destroy", "cv_round_summary")]
+                        "cv_bab_step", "cv_bab_run", "cv_bab_read", "cv_bab_destroy", "cv_round_summary",
+                        "cv_split_signs", "cv_adam_range")]
 
 
 def _check(st):
@@ -398,6 +402,15 @@ def cv_select_targets(net, cache, B, l, u, mask, weight, k, tgt_off, tgt_ids, wo
                                     stream_ptr(stream)))
 
 
+def cv_split_signs(net, B, split_off, split_ids, sign, stream=None):
+    _check(load().cv_split_signs(net, int(B), ptr(split_off), ptr(split_ids), ptr(sign), stream_ptr(stream)))
+
+
+def cv_adam_range(x, m1, m2, grad, t, lr, lo, hi, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().cv_adam_range(ptr(x), ptr(m1), ptr(m2), ptr(grad), int(x.numel()), int(t), float(lr), float(beta1),
+                                float(beta2), float(eps), float(lo), float(hi), stream_ptr(stream)))
+
+
 def cv_round_summary(B, m, lower, verified, infeasible, bounds, counts, stream=None):
     _check(load().cv_round_summary(int(B), int(m), ptr(lower), ptr(verified), ptr(infeasible), ptr(bounds),
                                    ptr(counts), stream_ptr(stream)))
@@ -499,10 +512,12 @@ def cv_relaxed_clip_static(net, cache, bi, lo_clip, hi_clip, infeasible, relaxed
                                          int(relaxed), stream_ptr(stream)))
 
 
-def make_alpha_in(B, m, lo, hi, l, u, mask, C, t, alpha, grad_f=None, precision=0):
+def make_alpha_in(B, m, lo, hi, l, u, mask, C, t, alpha, grad_f=None, precision=0, beta=None, split_sign=None,
+                  grad_beta=None):
     ai = cv_alpha_in()
     ai.B, ai.m, ai.precision = int(B), int(m), int(precision)
-    for name, v in dict(lo=lo, hi=hi, l=l, u=u, mask=mask, C=C, t=t, alpha=alpha, grad_f=grad_f).items():
+    for name, v in dict(lo=lo, hi=hi, l=l, u=u, mask=mask, C=C, t=t, alpha=alpha, grad_f=grad_f, beta=beta,
+                        split_sign=split_sign, grad_beta=grad_beta).items():
         setattr(ai, name, ptr(v))
     return ai
 

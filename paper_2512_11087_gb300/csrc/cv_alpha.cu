@@ -45,6 +45,8 @@ struct AdjArgs {
     const float* grad_f; // [R] or NULL
     float* out;          // dP^(h+1) [R x N] (unless last)
     float* grad_alpha;   // [B x m x H]
+    const int8_t* bsign; // [B x H] split signs, or NULL (no split multipliers)
+    float* grad_beta;    // [B x m x H]: d / d beta = -sign dLam^(h) at split neurons
 };
 
 __global__ void __launch_bounds__(256) k_adj_layer(AdjArgs a) {
@@ -114,6 +116,10 @@ __global__ void __launch_bounds__(256) k_adj_layer(AdjArgs a) {
                 const float s = ub / (ub - lb);
                 d = s;
                 e = -s * lb;
+            }
+            if (a.bsign) {
+                const int sg = a.bsign[(size_t)sub * a.H + g];
+                if (sg) a.grad_beta[ga] = (float)(-sg) * dl;
             }
             if (!a.last) a.out[(size_t)r * a.N + q] = dl * d + gf * e;
         }
@@ -190,6 +196,10 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
         cv_set_error("cv_alpha_grad: unknown precision");
         return CV_EINVAL;
     }
+    if (in->beta && (!in->split_sign || !in->grad_beta)) {
+        cv_set_error("cv_alpha_grad: beta needs split_sign and grad_beta");
+        return CV_EINVAL;
+    }
     if (in->precision == CV_PREC_BF16X8 && !cv_tc_supported(cache)) {
         cv_set_error("cv_alpha_grad: the tensor-core weights of a layer were not prepared");
         return CV_EUNSUPPORTED;
@@ -218,7 +228,7 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
                            (float*)(ws + L.lamB), (uint16_t*)(ws + L.tc_slices), (int*)(ws + L.tc_exp),
                            (float*)(ws + L.tc_tab), (double*)(ws + L.pb), (double*)(ws + L.pp),
                            (double*)(ws + L.pf), (double*)(ws + L.pm), (double*)(ws + L.ab), (double*)(ws + L.ap),
-                           &launches, st, nullptr, nullptr, keep);
+                           &launches, st, nullptr, nullptr, keep, in->beta, in->split_sign);
     } else {
         s = cv_backward_t<float>(net, R, m, net->L, 1, m, nullptr, in->C, in->t, cache->root_l, cache->root_u,
                                  cache->root_state, cache->slot_of, in->l, in->u, in->mask, U, in->alpha,
@@ -226,9 +236,11 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
                                  nullptr, lam0, nullptr, nullptr, nullptr, (float*)(ws + L.lamA),
                                  (float*)(ws + L.lamB), (double*)(ws + L.pb), (double*)(ws + L.pp),
                                  (double*)(ws + L.pf), (double*)(ws + L.pm), (double*)(ws + L.ab),
-                                 (double*)(ws + L.ap), keep, st);
+                                 (double*)(ws + L.ap), keep, st, nullptr, in->beta, in->split_sign);
     }
     if (s) return s;
+    const int8_t* bsign = in->beta ? in->split_sign : nullptr;
+    if (bsign) CV_CUDA(cudaMemsetAsync(in->grad_beta, 0, (size_t)B * m * H * sizeof(float), st));
     CV_CUDA(cudaMemsetAsync(grad_alpha, 0, (size_t)B * m * H * sizeof(float), st));
     float* gA = (float*)(ws + L.gA);
     float* gB = (float*)(ws + L.gB);
@@ -239,7 +251,8 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
     }
     if (tc)
         return cv_alpha_reverse_tc(net, cache, R, m, in->l, in->u, in->mask, in->alpha, in->grad_f, keep, gA, gB,
-                                   (uint16_t*)(ws + L.tc_slices), (int*)(ws + L.tc_exp), grad_alpha, &launches, st);
+                                   (uint16_t*)(ws + L.tc_slices), (int*)(ws + L.tc_exp), grad_alpha, &launches, st,
+                                   bsign, in->grad_beta);
     for (int h = 1; h <= net->L - 1; ++h) {
         AdjArgs a;
         a.A = gA; a.W = net->W[h]; a.b = net->b[h];
@@ -250,11 +263,72 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
         a.root_l = cache->root_l; a.root_u = cache->root_u; a.root_state = cache->root_state;
         a.alpha = in->alpha; a.grad_f = in->grad_f;
         a.out = gB; a.grad_alpha = grad_alpha;
+        a.bsign = bsign; a.grad_beta = in->grad_beta;
         dim3 grd((a.N + BN - 1) / BN, (R + BM - 1) / BM);
         k_adj_layer<<<grd, 256, 0, st>>>(a);
         CV_LAUNCH_CHECK("k_adj_layer");
         float* t = gA; gA = gB; gB = t;
     }
+    return CV_OK;
+}
+
+namespace {
+
+__global__ void k_adam_range(long long n, float* x, float* m1, float* m2, const float* g, float lr, float b1,
+                             float b2, float c1, float c2, float eps, float lo, float hi) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a1 = b1 * m1[i] + (1.f - b1) * gi;
+    const float a2 = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a1;
+    m2[i] = a2;
+    const float step = lr * (a1 / c1) / (sqrtf(a2 / c2) + eps);
+    x[i] = fminf(fmaxf(x[i] + step, lo), hi);
+}
+
+// thread per split code: +(g+1) -> +1, -(g+1) -> -1 at [b, g]
+__global__ void k_split_signs(int B, int H, const int* split_off, const int* split_ids, int8_t* sign, int* status) {
+    const int b = blockIdx.x;
+    if (b >= B) return;
+    const int k0 = split_off[b], k1 = split_off[b + 1];
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const int code = split_ids[k];
+        const int g = (code > 0 ? code : -code) - 1;
+        if (code == 0 || g >= H) { atomicOr(status, CV_DEV_SPLIT_RANGE); continue; }
+        sign[(size_t)b * H + g] = code > 0 ? (int8_t)1 : (int8_t)-1;
+    }
+}
+
+}  // namespace
+
+extern "C" cv_status cv_split_signs(cv_net* net, int B, const int* split_off, const int* split_ids, int8_t* sign,
+                                    void* stream) {
+    if (!net || B < 0 || (B > 0 && !sign) || (split_off && !split_ids)) {
+        cv_set_error("cv_split_signs: bad arguments");
+        return CV_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int H = net->H;
+    if (B == 0 || H == 0) return CV_OK;
+    CV_CUDA(cudaMemsetAsync(sign, 0, (size_t)B * H, st));
+    if (!split_off) return CV_OK;
+    k_split_signs<<<B, 64, 0, st>>>(B, H, split_off, split_ids, sign, net->status);
+    CV_LAUNCH_CHECK("k_split_signs");
+    return CV_OK;
+}
+
+extern "C" cv_status cv_adam_range(float* x, float* m1, float* m2, const float* grad, long long n, int t, float lr,
+                                   float beta1, float beta2, float eps, float lo, float hi, void* stream) {
+    if (!x || !m1 || !m2 || !grad || n < 0 || t < 1 || !(lo <= hi)) {
+        cv_set_error("cv_adam_range: bad arguments");
+        return CV_EINVAL;
+    }
+    if (n == 0) return CV_OK;
+    const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
+    k_adam_range<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, m1, m2, grad, lr, beta1, beta2,
+                                                                              c1, c2, eps, lo, hi);
+    CV_LAUNCH_CHECK("k_adam_range");
     return CV_OK;
 }
 

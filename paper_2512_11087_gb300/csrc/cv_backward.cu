@@ -44,6 +44,8 @@ struct LayerArgs {
     const float* lo; const float* hi;  // [nsub x N] (i == 1)
     T* lam0;              // optional [R x N]
     T* keepP;             // optional [R x N]: the product P^(i) (i > 1), kept for the alpha adjoint
+    const float* beta;    // optional [nsub x m x H] split multipliers (with bsign [nsub x H])
+    const int8_t* bsign;
     double* part_bias; double* part_pad; double* part_f; double* part_fmag; int ncb;
 };
 
@@ -55,6 +57,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+// lam - sign beta, rounded away from lam (down for sign +1, up for -1): the multiplier in effect,
+// |result - lam|, is then at least beta >= 0, so the bound stays valid
+__device__ __forceinline__ float beta_shift(float lam, int sg, float bt) {
+    return sg > 0 ? __fsub_rd(lam, bt) : __fadd_ru(lam, bt);
+}
+__device__ __forceinline__ double beta_shift(double lam, int sg, float bt) {
+    return sg > 0 ? __dsub_rd(lam, (double)bt) : __dadd_ru(lam, (double)bt);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs<T> a) {
@@ -159,7 +170,11 @@ __global__ void __launch_bounds__(256) k_bwd_layer(LayerArgs<T> a) {
                     d = s;
                     e = -s * l;
                 }
-                const T lam = p * d;
+                T lam = p * d;
+                if (a.bsign) {  // split multiplier: Lam_g -= sign_g beta_g
+                    const int sg = a.bsign[(size_t)sub * a.H + g];
+                    if (sg) lam = beta_shift(lam, sg, a.beta[((size_t)sub * a.m + (r % a.m)) * a.H + g]);
+                }
                 a.Aout[(size_t)r * a.N + q] = lam;
                 if (a.keepP) a.keepP[(size_t)r * a.N + q] = p;
                 bsum = fma(p, e, bsum);
@@ -296,7 +311,8 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         double* bias_raw, double* pad_raw,
                         T* lamA, T* lamB, double* part_bias, double* part_pad,
                         double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                        T* const* keepP, cudaStream_t st, float* bab_weight) {
+                        T* const* keepP, cudaStream_t st, float* bab_weight, const float* beta,
+                        const int8_t* bsign) {
     const int nk = net->dims[k];
     {
         dim3 blk(32, 8);
@@ -322,6 +338,8 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
         a.Aout = nxt;
         a.lo = lo; a.hi = hi; a.lam0 = lam0;
         a.keepP = (keepP && i > 1) ? keepP[i] : nullptr;
+        a.beta = (i > 1) ? beta : nullptr;
+        a.bsign = (i > 1 && beta) ? bsign : nullptr;
         a.ncb = (a.N + BN - 1) / BN;
         a.part_bias = part_bias; a.part_pad = part_pad; a.part_f = part_f; a.part_fmag = part_fmag;
         dim3 grd(a.ncb, (R + BM - 1) / BM);
@@ -355,14 +373,15 @@ template cv_status cv_backward_t<float>(const cv_net*, int, int, int, int, int, 
                                         float* const*, const float*, const float*, const uint8_t*, float*,
                                         double*, float*, float*, float*, double*, double*, float*, float*,
                                         double*, double*, double*, double*, double*, double*, float* const*,
-                                        cudaStream_t, float*);
+                                        cudaStream_t, float*, const float*, const int8_t*);
 template cv_status cv_backward_t<double>(const cv_net*, int, int, int, int, int, const float*, const float*,
                                          const float*, const double*, const double*, const int8_t*,
                                          const int*, const double*, const double*, const int8_t*, int,
                                          const float*, int, float* const*, const float*, const float*,
                                          const uint8_t*, float*, double*, float*, double*, float*, double*,
                                          double*, double*, double*, double*, double*, double*, double*,
-                                         double*, double*, double* const*, cudaStream_t, float*);
+                                         double*, double*, double* const*, cudaStream_t, float*, const float*,
+                                         const int8_t*);
 
 // number of column blocks of the widest layer (sizing of the partial buffers)
 int cv_bwd_ncb_max(const cv_net* net) {

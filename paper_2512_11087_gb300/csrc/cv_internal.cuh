@@ -141,14 +141,15 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                          float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
                          int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
                          double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st,
-                         float* pbuf = nullptr, float* bab_weight = nullptr, float* const* keepP_layers = nullptr);
+                         float* pbuf = nullptr, float* bab_weight = nullptr, float* const* keepP_layers = nullptr,
+                         const float* beta = nullptr, const int8_t* bsign = nullptr);
 // Reverse sweep of the slope adjoint on tensor cores (cv_tc.cu): g0 = dLam_0 [R x n0] in, the
 // layer products P^(h+1) of the forward in keepP[h + 1]; gA / gB [R x wmax] scratch (gA holds g0);
 // slices / rexp as for cv_backward_tc.  Writes grad_alpha (zeroed by the caller).
 cv_status cv_alpha_reverse_tc(const cv_net* net, const cv_cache* cache, int R, int m, const float* l, const float* u,
                               const int8_t* mask, const float* alpha, const float* grad_f, float* const* keepP,
                               float* gA, float* gB, uint16_t* slices, int* rexp, float* grad_alpha, int* launches,
-                              cudaStream_t st);
+                              cudaStream_t st, const int8_t* bsign = nullptr, float* grad_beta = nullptr);
 
 // kernels (launch wrappers); each returns CV_OK or a launch error
 cv_status cv_launch_rows(const cv_net* net, const cv_cache* cache, const cv_batch_in* in,
@@ -192,7 +193,8 @@ cv_status cv_backward_t(const cv_net* net, int R, int rows_per_sub, int k, int i
                         double* bias_raw, double* pad_raw,
                         T* lamA, T* lamB, double* part_bias, double* part_pad,
                         double* part_f, double* part_fmag, double* acc_bias, double* acc_pad,
-                        T* const* keepP, cudaStream_t st, float* bab_weight = nullptr);
+                        T* const* keepP, cudaStream_t st, float* bab_weight = nullptr,
+                        const float* beta = nullptr, const int8_t* bsign = nullptr);
 // BaBSR weight of the cached neurons of hidden layer i-1 from the layer product P^(i) [R x N]
 // (R = nsub m rows): w[sub, slot_of[hoff + q]] = (sum_{r < m} P[sub m + r, q]) / m, the sum in
 // FP32 in increasing r (cv_backward.cu); subdomains with skip[sub] set are left untouched.

@@ -298,6 +298,9 @@ struct TcArgs {
     const float* Pfwd;   // P^(h+1) [R x N]
     const float* grad_f; // [R] or NULL
     float* grad_alpha;   // [B x m x H]
+    const float* beta;   // split multipliers [B x m x H] with their signs bsign [B x H], or NULL
+    const int8_t* bsign;
+    float* grad_beta;    // adjoint: [B x m x H]
     const float* lo; const float* hi;
     float* lam0;
     double* part_bias; double* part_pad; double* part_f; double* part_fmag; int ncb;
@@ -489,6 +492,10 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                     d = s;
                     e = -s * lb;
                 }
+                if (a.bsign) {
+                    const int sg = a.bsign[(size_t)sub * a.H + g];
+                    if (sg) a.grad_beta[ga] = (float)(-sg) * dl;
+                }
                 if (!a.last) a.Aout[(size_t)r * a.N + q] = dl * d + gf * e;
             }
         }
@@ -587,7 +594,15 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                     d = t1[c];
                     e = t2[c];
                 }
-                const float lam = p * d;
+                float lam = p * d;
+                if (a.bsign) {  // split multiplier: Lam_g -= sign_g beta_g, rounded away from lam
+                    const int g = a.hoff + q;
+                    const int sg = a.bsign[(size_t)(sub0 + sb) * a.H + g];
+                    if (sg) {
+                        const float bt = a.beta[((size_t)(sub0 + sb) * a.m + (r % a.m)) * a.H + g];
+                        lam = sg > 0 ? __fsub_rd(lam, bt) : __fadd_ru(lam, bt);
+                    }
+                }
                 a.Aout[(size_t)r * a.N + q] = lam;
                 if (a.keepP) a.keepP[(size_t)r * a.N + q] = p;
                 s1 = fmaf(p, e, s1);
@@ -665,7 +680,8 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
                          float* err, float* lam0, float* bias_out, float* lamA, float* lamB, uint16_t* slices,
                          int* rexp, float* tab, double* part_bias, double* part_pad, double* part_f,
                          double* part_fmag, double* acc_bias, double* acc_pad, int* launches, cudaStream_t st,
-                         float* pbuf, float* bab_weight, float* const* keepP_layers) {
+                         float* pbuf, float* bab_weight, float* const* keepP_layers, const float* beta,
+                         const int8_t* bsign) {
     if (!cv_tc_supported(cache)) {
         cv_set_error("tensor-core back-substitution: a layer's weights were not prepared");
         return CV_EUNSUPPORTED;
@@ -714,6 +730,8 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
         a.T0 = tab; a.T1 = tab + tsz; a.T2 = tab + 2 * tsz;
         a.Aout = nxt;
         a.keepP = (i > 1 && keepP_layers) ? keepP_layers[i] : ((i > 1 && bab_weight && m > 0) ? pbuf : nullptr);
+        a.beta = (i > 1) ? beta : nullptr;
+        a.bsign = (i > 1 && beta) ? bsign : nullptr;
         a.lo = lo; a.hi = hi; a.lam0 = lam0;
         a.part_bias = part_bias; a.part_pad = part_pad; a.part_f = part_f; a.part_fmag = part_fmag;
         a.ncb = (w->N + TBN - 1) / TBN;
@@ -745,7 +763,7 @@ cv_status cv_backward_tc(const cv_net* net, const cv_cache* cache, int R, int m,
 cv_status cv_alpha_reverse_tc(const cv_net* net, const cv_cache* cache, int R, int m, const float* l, const float* u,
                               const int8_t* mask, const float* alpha, const float* grad_f, float* const* keepP,
                               float* gA, float* gB, uint16_t* slices, int* rexp, float* grad_alpha, int* launches,
-                              cudaStream_t st) {
+                              cudaStream_t st, const int8_t* bsign, float* grad_beta) {
     const int L = net->L;
     for (int h = 1; h < L; ++h)
         if (!cache->tcwT[h]) {
@@ -779,6 +797,8 @@ cv_status cv_alpha_reverse_tc(const cv_net* net, const cv_cache* cache, int R, i
         a.Pfwd = keepP[h + 1];
         a.grad_f = grad_f;
         a.grad_alpha = grad_alpha;
+        a.bsign = bsign;
+        a.grad_beta = grad_beta;
         a.Aout = gB;
         a.ncb = (w->N + TBN - 1) / TBN;
         a.status = net->status;

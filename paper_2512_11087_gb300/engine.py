@@ -187,38 +187,61 @@ class AlphaBound(torch.autograd.Function):
 class AlphaState:
     """Inputs that stay fixed during slope optimisation, plus the workspace."""
 
-    def __init__(self, net: Net, lo, hi, l, u, mask, C, t, precision=capi.CV_PREC_FP32):
+    def __init__(self, net: Net, lo, hi, l, u, mask, C, t, precision=capi.CV_PREC_FP32, split_sign=None):
+        """split_sign [B x H] int8 (split_signs()) enables split multipliers beta in bound_and_grad."""
         self.net = net
         self.precision = int(precision)
+        self.split_sign = split_sign
         self.B, self.n0 = lo.shape
         self.m = C.shape[0]
         self.lo, self.hi, self.l, self.u, self.mask, self.C, self.t = lo, hi, l, u, mask, C, t
         self.ws_bytes = capi.cv_alpha_grad_workspace(net.handle, self.B, self.m)
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=lo.device)
 
-    def bound_and_grad(self, alpha, grad_f=None):
+    def bound_and_grad(self, alpha, grad_f=None, beta=None):
+        """(lower, d/d alpha), and d/d beta as a third entry when split multipliers beta [B x m x H] are given."""
         lower = torch.empty(self.B, self.m, dtype=torch.float32, device=alpha.device)
         grad = torch.empty_like(alpha)
+        gb = None
+        if beta is not None:
+            if self.split_sign is None:
+                raise ValueError("split multipliers need the state's split_sign")
+            beta = beta.detach().contiguous()
+            gb = torch.empty_like(beta)
         ai = capi.make_alpha_in(self.B, self.m, self.lo, self.hi, self.l, self.u, self.mask, self.C, self.t,
-                                alpha.detach().contiguous(), grad_f, precision=self.precision)
+                                alpha.detach().contiguous(), grad_f, precision=self.precision, beta=beta,
+                                split_sign=self.split_sign if beta is not None else None, grad_beta=gb)
         capi.cv_alpha_grad(self.net.handle, self.net.cache, ai, lower, grad, self.ws, self.ws_bytes)
-        return lower, grad
+        return (lower, grad) if beta is None else (lower, grad, gb)
 
 
-def optimize_alpha(state: AlphaState, alpha, steps=20, lr=0.1, decay=0.98):
-    """Adam ascent on the slopes (the paper's SDP-FO setting: 20 steps, lr 0.1, x0.98 per step).
-    Returns the final slopes and the bound after each step (every step runs in library kernels)."""
+def optimize_alpha(state: AlphaState, alpha, steps=20, lr=0.1, decay=0.98, beta=None, beta_lr=None):
+    """Adam ascent on the slopes (the paper's SDP-FO setting: 20 steps, lr 0.1, x0.98 per step), and on
+    the split multipliers when beta is given (clamped to [0, inf), learning rate beta_lr or lr).
+    Returns the final slopes (and multipliers) and the bound after each step (every step runs in
+    library kernels)."""
     alpha = alpha.detach().clone().contiguous()
     m1 = torch.zeros_like(alpha)
     m2 = torch.zeros_like(alpha)
+    if beta is not None:
+        beta = beta.detach().clone().contiguous()
+        n1, n2 = torch.zeros_like(beta), torch.zeros_like(beta)
     history = []
     for it in range(1, steps + 1):
-        lower, grad = state.bound_and_grad(alpha)
-        history.append(lower)
-        capi.cv_alpha_adam(alpha, m1, m2, grad, it, lr * decay ** (it - 1))
-    lower, _ = state.bound_and_grad(alpha)
-    history.append(lower)
-    return alpha, history
+        res = state.bound_and_grad(alpha, beta=beta)
+        history.append(res[0])
+        capi.cv_alpha_adam(alpha, m1, m2, res[1], it, lr * decay ** (it - 1))
+        if beta is not None:
+            capi.cv_adam_range(beta, n1, n2, res[2], it, (beta_lr or lr) * decay ** (it - 1), 0.0, float("inf"))
+    history.append(state.bound_and_grad(alpha, beta=beta)[0])
+    return (alpha, history) if beta is None else (alpha, beta, history)
+
+
+def split_signs(net: Net, split_off, split_ids, B, stream=None):
+    """[B x H] int8 split signs of a CSR split list (cv_split_signs): +1 for z >= 0, -1 for z <= 0."""
+    sign = torch.empty(max(B, 1), max(net.H, 1), dtype=torch.int8, device="cuda")
+    capi.cv_split_signs(net.handle, B, split_off, split_ids, sign, stream)
+    return sign[:B, :net.H]
 
 
 def input_split(lo, hi, final_A, final_c, lower, verified, infeasible, stream=None):

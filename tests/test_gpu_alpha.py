@@ -151,3 +151,88 @@ def test_adam_step_matches_oracle_and_optimisation_improves():
     print("mean bound before / after 20 Adam steps:", first.mean(), last.mean())
     assert last.mean() > first.mean()
     s["net"].close()
+
+
+def _split_setup(dims, B, seed, eps=0.05):
+    """A batch whose subdomains hold 1-3 splits each, enforced on the split neurons' bounds, with
+    random split multipliers beta >= 0."""
+    s = _setup(dims, B, seed, eps=eps)
+    so, si = WL.draw_splits(s["ids"], B, 1, 3, seed=seed + 5)
+    H = s["onet"].H
+    bsign = np.zeros((B, H), np.int8)
+    slot = {int(g): c for c, g in enumerate(s["ids"])}
+    for b in range(B):
+        for code in si[so[b]:so[b + 1]]:
+            g = abs(int(code)) - 1
+            bsign[b, g] = 1 if code > 0 else -1
+            c = slot[g]
+            if code > 0: s["l"][b, c] = max(s["l"][b, c], 0.0)
+            else: s["u"][b, c] = min(s["u"][b, c], 0.0)
+    s["mask"] = np.where(s["l"] >= 0, 1, np.where(s["u"] <= 0, -1, 0)).astype(np.int8)
+    rng = np.random.default_rng(seed + 6)
+    s["beta"] = (rng.uniform(0, 0.5, size=(B, s["m"], H)) * (bsign[:, None, :] != 0)).astype(np.float32)
+    s["bsign"], s["so"], s["si"] = bsign, so, si
+    return s
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("dims,B,seed", [([30, 40, 40, 40, 5], 6, 21), ([784, 96, 96, 10], 5, 22)])
+def test_split_multiplier_bound_and_gradient_parity(dims, B, seed, precision):
+    """Split multipliers (beta-CROWN form of the split constraints): the bound and d/d beta against the
+    oracle's FP64 back-substitution and reverse sweep; the split signs from the CSR exactly."""
+    from paper_2512_11087_gb300 import engine as E
+    s = _split_setup(dims, B, seed)
+    d = E.to_dev
+    sign = E.split_signs(s["net"], d(s["so"]), d(s["si"]), B)
+    torch.cuda.synchronize()
+    assert np.array_equal(sign.cpu().numpy(), s["bsign"])
+    st = E.AlphaState(s["net"], d(s["lo"]), d(s["hi"]), d(s["l"]), d(s["u"]), d(s["mask"]), d(s["C"]), d(s["t"]),
+                      precision=precision, split_sign=sign)
+    lower, grad, gb = st.bound_and_grad(d(s["alpha"]), beta=d(s["beta"]))
+    lower, grad, gb = lower.cpu().numpy(), grad.cpu().numpy(), gb.cpu().numpy()
+    worst = 0.0
+    for b in range(B):
+        hl, hu, hs = _full_bounds(s, b)
+        # the magnitude scale of the bounds with the multipliers, over the root magnitudes (as the
+        # round's lower_scale)
+        zm = np.maximum(np.abs(s["rl"]), np.abs(s["ru"])).astype(np.float64)
+        f, g, gbo, sc = O.alpha_grad(s["onet"], hl, hu, hs, s["lo"][b], s["hi"][b], s["C"], s["t"],
+                                     s["alpha"][b].astype(np.float64), beta=s["beta"][b].astype(np.float64),
+                                     bsign=s["bsign"][b], zmag=zm, want_scale=True)
+        assert np.all(lower[b] <= f + 1e-12 * sc)
+        assert np.all(np.abs(lower[b] - f) <= 1e-5 * sc), (b, lower[b] - f, sc)
+        assert np.all(gb[b][:, s["bsign"][b] == 0] == 0)
+        for r in range(s["m"]):
+            gmax = np.max(np.abs(gbo[r]))
+            if gmax == 0:
+                continue
+            err = np.max(np.abs(gb[b, r] - gbo[r])) / gmax
+            worst = max(worst, err)
+            assert err <= 1e-4, (b, r, err)
+    print("max d/d beta error / row max", worst)
+    s["net"].close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_split_multipliers_raise_the_bound_and_stay_sound(precision):
+    from paper_2512_11087_gb300 import engine as E
+    s = _split_setup([30, 40, 40, 40, 5], 8, 23)
+    d = E.to_dev
+    sign = E.split_signs(s["net"], d(s["so"]), d(s["si"]), s["B"])
+    st = E.AlphaState(s["net"], d(s["lo"]), d(s["hi"]), d(s["l"]), d(s["u"]), d(s["mask"]), d(s["C"]), d(s["t"]),
+                      precision=precision, split_sign=sign)
+    a0 = d(s["alpha"])
+    b0 = torch.zeros(s["B"], s["m"], s["onet"].H, dtype=torch.float32, device="cuda")
+    al, bt, hist = E.optimize_alpha(st, a0, steps=15, beta=b0, beta_lr=0.05)
+    torch.cuda.synchronize()
+    first, last = hist[0].cpu().numpy(), hist[-1].cpu().numpy()
+    assert np.mean(last) > np.mean(first)
+    bt = bt.cpu().numpy()
+    assert np.all(bt >= 0) and np.any(bt > 0)
+    al = al.cpu().numpy()
+    for b in range(s["B"]):
+        hl, hu, hs = _full_bounds(s, b)
+        f = O.alpha_grad(s["onet"], hl, hu, hs, s["lo"][b], s["hi"][b], s["C"], s["t"], al[b].astype(np.float64),
+                         beta=bt[b].astype(np.float64), bsign=s["bsign"][b])[0]
+        assert np.all(last[b] <= f + 1e-9 * (1 + np.abs(f)))
+    s["net"].close()

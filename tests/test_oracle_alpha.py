@@ -50,6 +50,10 @@ def test_alpha_gradient_consistent_with_batch_bound():
     hs = np.where(root["l"] >= 0, 1, np.where(root["u"] <= 0, -1, 0)).astype(np.int8)
     f, _ = O.alpha_grad(net, root["l"], root["u"], hs, lo, hi, C, t, alpha[0])
     assert np.allclose(f, out["lower"][0], rtol=1e-12, atol=1e-12)
+    # the magnitude scale it reports is the round's lower_scale (root magnitudes)
+    zm = np.maximum(np.abs(cache["root_l"]), np.abs(cache["root_u"]))
+    _, _, sc = O.alpha_grad(net, root["l"], root["u"], hs, lo, hi, C, t, alpha[0], zmag=zm, want_scale=True)
+    assert np.allclose(sc, out["lower_scale"][0], rtol=1e-12, atol=0)
 
 
 def test_adam_first_step_and_clamp():

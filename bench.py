@@ -704,6 +704,28 @@ def bench_alpha(steps, warmup, flush, stream, peaks, cpu=True, adam_steps=20):
         capi.cv_alpha_grad(net.handle, net.cache, ai, lower, grad, st.ws, st.ws_bytes, stream)
         f1 = float(lower[torch.isfinite(lower)].double().mean())
         res[prec] = (statistics.mean(ts), f0, f1)
+    # the slopes and the split multipliers together (beta-CROWN form of the splits), tensor cores
+    sign = E.split_signs(net, d(so), d(si), B)
+    beta = torch.zeros_like(alpha)
+    n1, n2 = torch.zeros_like(alpha), torch.zeros_like(alpha)
+    gbeta = torch.empty_like(alpha)
+    aib = capi.make_alpha_in(B, m, st.lo, st.hi, st.l, st.u, st.mask, st.C, st.t, alpha, None,
+                             precision=capi.CV_PREC_BF16X8, beta=beta, split_sign=sign, grad_beta=gbeta)
+
+    def step_b():
+        alpha.copy_(a0)
+        m1.zero_(); m2.zero_()
+        beta.zero_(); n1.zero_(); n2.zero_()
+        for it in range(1, adam_steps + 1):
+            capi.cv_alpha_grad(net.handle, net.cache, aib, lower, grad, st.ws, st.ws_bytes, stream)
+            lr_it = 0.1 * 0.98 ** (it - 1)
+            capi.cv_alpha_adam(alpha, m1, m2, grad, it, lr_it, stream=stream)
+            capi.cv_adam_range(beta, n1, n2, gbeta, it, lr_it, 0.0, float("inf"), stream=stream)
+
+    tsb = _timed(step_b, steps, warmup, flush, stream)
+    capi.cv_alpha_grad(net.handle, net.cache, aib, lower, grad, st.ws, st.ws_bytes, stream)
+    fb1 = float(lower[torch.isfinite(lower)].double().mean())
+    msb = statistics.mean(tsb)
     ms, f0, f1 = res[capi.CV_PREC_BF16X8]
     ms32, f032, f132 = res[capi.CV_PREC_FP32]
     # forward and reverse sweep: two contractions of B m rows through the layers per iteration
@@ -716,6 +738,8 @@ def bench_alpha(steps, warmup, flush, stream, peaks, cpu=True, adam_steps=20):
                unit="subdomains/s", higher_is_better=True, ms_per_step=ms, steps=steps, warmup=warmup,
                cached_neurons=U, mean_bound_before=f0, mean_bound_after=f1,
                fp32_path=dict(value=B / (ms32 / 1e3), ms_per_step=ms32, mean_bound_after=f132),
+               with_split_multipliers=dict(value=B / (msb / 1e3), ms_per_step=msb, mean_bound_after=fb1,
+                                           note="slopes and split multipliers optimised together"),
                roofline=dict(bound="tensor", kernel="cv_alpha_grad (k_tc_layer forward + adjoint contractions)",
                              achieved=fl, peak=pk, unit="TFLOP/s", frac=fl / pk, traffic=None,
                              peak_source="MEASURED_PEAKS bf16 burst / 8 digit products (FP32-equivalent flops)"))
@@ -969,7 +993,7 @@ def main():
                     higher_is_better=e["higher_is_better"], scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic", config=dict(workload=e["config"]), roofline=e.get("roofline"), peaks=peaks)
         for k in ("cpu_baseline", "phase_ms", "subdomains_per_s", "domains_visited", "detail", "fp32_path",
-                  "cc_items"):
+                  "cc_items", "with_split_multipliers"):
             if k in e:
                 line[k] = e[k]
         print(json.dumps(line), flush=True)

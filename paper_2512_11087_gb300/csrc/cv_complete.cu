@@ -345,6 +345,51 @@ __device__ __forceinline__ void cc_plane_to_smem(unsigned* dst, const float* src
     __syncwarp();
 }
 
+// Wide launch: a' = sa a + sum over the rows p of msk (increasing p) of beta_p g_p, formed over the
+// plane in the warp's buffer buf, two rows per pass over the elements.  Each element gets the same fma
+// chain, in the same order, as forming it element by element, so the bits are the same.  The loads
+// of a pass do not depend on one another, so one L2 round trip covers PWA elements a lane, instead of
+// one per row and element.  Returns the factor still to apply to the buffer: sa when msk is empty,
+// else 1.  Lanes write only their own elements; the warp is synchronised on return.
+constexpr int PWA = 4;
+__device__ __forceinline__ float cc_accum_rows(float* buf, const float* gs, const float* bsm, unsigned msk,
+                                               int n0, float sa, int lane) {
+    float s0 = sa;
+    while (msk) {
+        const int p1 = __ffs(msk) - 1;
+        msk &= msk - 1u;
+        const bool two = msk != 0u;
+        const int p2 = two ? __ffs(msk) - 1 : p1;
+        if (two) msk &= msk - 1u;
+        const float b1 = bsm[p1], b2 = bsm[p2];
+        const float* g1 = gs + (size_t)p1 * n0;
+        const float* g2 = gs + (size_t)p2 * n0;
+#pragma unroll 1
+        for (int j0 = lane; j0 < n0; j0 += 32 * PWA) {
+            float x[PWA], y1[PWA], y2[PWA];
+#pragma unroll
+            for (int u = 0; u < PWA; ++u) {
+                const int j = j0 + 32 * u;
+                const int jj = min(j, n0 - 1);
+                x[u] = j < n0 ? buf[j] : 0.f;
+                y1[u] = __ldg(g1 + jj);
+                y2[u] = __ldg(g2 + jj);
+            }
+#pragma unroll
+            for (int u = 0; u < PWA; ++u) {
+                const int j = j0 + 32 * u;
+                float v = fmaf(b1, y1[u], s0 * x[u]);
+                const float v2 = fmaf(b2, y2[u], v);
+                v = two ? v2 : v;
+                if (j < n0) buf[j] = v;
+            }
+        }
+        s0 = 1.f;
+    }
+    __syncwarp();
+    return s0;
+}
+
 // Rows of the task's subdomain: staged in shared memory (main launch) or read from the
 // workspace (subdomains with more rows than the main launch stages).
 struct CCRows {
@@ -523,7 +568,8 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
 #pragma unroll 1
             for (int cb = 0; cb < n0; cb += 1024) {
                 unsigned msk = 0u;  // bit i: element cb + 32 i + lane
-#pragma unroll 2
+                constexpr int SCRU = WIDE ? 8 : 2;  // (the wide launch reads 1/g from L2)
+#pragma unroll SCRU
                 for (int i = 0; i < 32; ++i) {
                     const int j = cb + 32 * i + lane;
                     const int jj = j < n0 ? j : n0 - 1;
@@ -754,6 +800,10 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                                         unsigned (&my_cs)[5]) {
     // with two or more rows the FP32 decisions are certified (see cc_certify below)
     constexpr bool CERT = WIDE || RC >= 2;
+    // elements a lane loads ahead in the scalar key pass (the wide launch reads its rows from L2)
+    constexpr int PFK = WIDE ? 8 : PF;
+    // and in the search passes over keys and weights
+    constexpr int PFS = WIDE ? 4 : 1;
     const int n0 = a.n0;
     const int R = WIDE ? Rn : RC;
     // the target plane a.x + c0 (lower side; the upper side is the negated upper plane), or in
@@ -835,6 +885,14 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             float qp = 0.f;
             if (jp >= 0) qp = q_of(__uint_as_float(keys[jp]), jp);
             __syncwarp();
+            // wide launch: a' formed over the plane in the buffer first (the same bits as q_of forms),
+            // so that the key pass below only scales it
+            float skey = sa;
+            if constexpr (WIDE) skey = cc_accum_rows((float*)keys, rw.gs, bsm, nzm, n0, sa, lane);
+            auto qk_of = [&](float av, int j) -> float {
+                if constexpr (WIDE) return (-(skey * av)) * rk[j];
+                else return q_of(av, j);
+            };
             const bool warm = qp > 0.f;
             const long long T = cc_T64[k];
             const long long W = cc_W64[k];
@@ -909,16 +967,16 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             } else {
                 if (warm) {
 #pragma unroll 1
-                    for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
-                        float av[PF];
+                    for (int j0 = lane; j0 < n0; j0 += 32 * PFK) {
+                        float av[PFK];
 #pragma unroll
-                        for (int u = 0; u < PF; ++u) av[u] = __uint_as_float(keys[min(j0 + 32 * u, n0 - 1)]);
+                        for (int u = 0; u < PFK; ++u) av[u] = __uint_as_float(keys[min(j0 + 32 * u, n0 - 1)]);
 #pragma unroll
-                        for (int u = 0; u < PF; ++u) {
+                        for (int u = 0; u < PFK; ++u) {
                             const int j = j0 + 32 * u;
                             const bool v = j < n0;
                             const int jj = v ? j : n0 - 1;
-                            const float q = q_of(av[u], jj);
+                            const float q = qk_of(av[u], jj);
                             if (v) keys[j] = __float_as_uint(q);
                             const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
                             flt += (q < qp) ? w : 0ull;
@@ -927,16 +985,16 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     }
                 } else {
 #pragma unroll 1
-                    for (int j0 = lane; j0 < n0; j0 += 32 * PF) {
-                        float av[PF];
+                    for (int j0 = lane; j0 < n0; j0 += 32 * PFK) {
+                        float av[PFK];
 #pragma unroll
-                        for (int u = 0; u < PF; ++u) av[u] = __uint_as_float(keys[min(j0 + 32 * u, n0 - 1)]);
+                        for (int u = 0; u < PFK; ++u) av[u] = __uint_as_float(keys[min(j0 + 32 * u, n0 - 1)]);
 #pragma unroll
-                        for (int u = 0; u < PF; ++u) {
+                        for (int u = 0; u < PFK; ++u) {
                             const int j = j0 + 32 * u;
                             const bool v = j < n0;
                             const int jj = v ? j : n0 - 1;
-                            const float q = q_of(av[u], jj);
+                            const float q = qk_of(av[u], jj);
                             const unsigned kk = __float_as_uint(q);
                             if (v) keys[j] = kk;
                             const unsigned long long w = v ? (unsigned long long)wk[jj] : 0ull;
@@ -971,14 +1029,26 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     if (Fle < T) { lo = kp; Flo = Fle; }
                     else { hi = kp - 1u; Fhi = Flt; }
 #pragma unroll 1
-                    for (int j = lane; j < n0; j += 32) {
-                        const unsigned kk = keys[j];
-                        const unsigned long long w = (unsigned long long)wk[j];
-                        f0 += (__uint_as_float(kk) <= 0.f) ? w : 0ull;
-                        const bool in = kk > lo && kk <= hi;
-                        mn = min(mn, in ? kk : 0xffffffffu);
-                        mx = max(mx, in ? kk : 0u);
-                        cnt += in ? 1u : 0u;
+                    for (int j0 = lane; j0 < n0; j0 += 32 * PFS) {
+                        unsigned kq[PFS];
+                        unsigned long long wq[PFS];
+#pragma unroll
+                        for (int u = 0; u < PFS; ++u) {
+                            const int j = j0 + 32 * u;
+                            const int jj = min(j, n0 - 1);
+                            kq[u] = keys[jj];
+                            wq[u] = j < n0 ? (unsigned long long)wk[jj] : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < PFS; ++u) {
+                            const unsigned kk = kq[u];
+                            const unsigned long long w = wq[u];
+                            f0 += (__uint_as_float(kk) <= 0.f) ? w : 0ull;
+                            const bool in = j0 + 32 * u < n0 && kk > lo && kk <= hi;
+                            mn = min(mn, in ? kk : 0xffffffffu);
+                            mx = max(mx, in ? kk : 0u);
+                            cnt += in ? 1u : 0u;
+                        }
                     }
                     const long long F0 = warp_sum64(f0);
                     if (lo == 0u) Flo = F0;
@@ -1055,12 +1125,22 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                         unsigned c1 = 0u, emn = 0xffffffffu, emx = 0u;
                         int wpos = 0;
 #pragma unroll 1
-                        for (int j0 = 0; j0 < n0; j0 += 32) {
-                            const int j = j0 + lane;
+                        for (int j00 = 0; j00 < n0; j00 += 32 * PFS) {
+                          unsigned kq[PFS];
+                          unsigned long long wq[PFS];
+#pragma unroll
+                          for (int u = 0; u < PFS; ++u) {
+                              const int j = j00 + 32 * u + lane;
+                              const int jj = j < n0 ? j : 0;
+                              kq[u] = keys[jj];
+                              wq[u] = (unsigned long long)wk[jj];
+                          }
+#pragma unroll
+                          for (int u = 0; u < PFS; ++u) {
+                            const int j = j00 + 32 * u + lane;
                             const bool v = j < n0;
-                            const int jj = v ? j : 0;
-                            const unsigned kk = keys[jj];
-                            const unsigned long long w = (unsigned long long)wk[jj];
+                            const unsigned kk = kq[u];
+                            const unsigned long long w = wq[u];
                             const unsigned d = v ? kk - cmin : 0xffffffffu;
                             const bool L1 = d < e1;
                             const bool M = !L1 && d < e2;
@@ -1072,6 +1152,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                             if (M) fM += w;
                             emn = min(emn, d);
                             emx = max(emx, d <= span ? d : 0u);
+                          }
                         }
                         __syncwarp();
                         const long long F1 = Flo + warp_sum64(f1);
@@ -1119,12 +1200,29 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                     unsigned mxL = 0u, mnR = 0xffffffffu, cl = 0u;
                     int wpos = 0;
 #pragma unroll 1
-                    for (int j0 = 0; j0 < m; j0 += 32) {
-                        const int j = j0 + lane;
+                    for (int j00 = 0; j00 < m; j00 += 32 * PFS) {
+                      // (in-place compaction writes only at or before the positions this chunk read)
+                      int eq[PFS];
+                      unsigned kq[PFS];
+                      unsigned long long wq[PFS];
+#pragma unroll
+                      for (int u = 0; u < PFS; ++u) {
+                          const int j = j00 + 32 * u + lane;
+                          const bool v = j < m;
+                          const int jj = v ? j : 0;
+                          eq[u] = v ? (listed ? (int)cidx[jj] : jj) : 0;
+                      }
+#pragma unroll
+                      for (int u = 0; u < PFS; ++u) {
+                          kq[u] = keys[eq[u]];
+                          wq[u] = (unsigned long long)wk[eq[u]];
+                      }
+#pragma unroll
+                      for (int u = 0; u < PFS; ++u) {
+                        const int j = j00 + 32 * u + lane;
                         const bool v = j < m;
-                        const int jj = v ? j : 0;
-                        const int e = v ? (listed ? (int)cidx[jj] : jj) : 0;
-                        const unsigned kk = keys[e];
+                        const int e = eq[u];
+                        const unsigned kk = kq[u];
                         const unsigned d = v ? kk - cmin : 0xffffffffu;
                         const bool in = d <= span;
                         if (wr) {
@@ -1134,11 +1232,12 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                             if (in) cidx[q] = (unsigned short)e;
                             wpos += __popc(bal);
                         }
-                        const unsigned long long w = (unsigned long long)wk[e];
+                        const unsigned long long w = wq[u];
                         const bool L = d <= dm;
                         if (L) { fm += w; ++cl; }
                         mxL = max(mxL, L ? d : 0u);
                         mnR = min(mnR, d - dm1);
+                      }
                     }
                     __syncwarp();
                     if (wr) { listed = true; m = wpos; }
@@ -1225,16 +1324,19 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
     // are no longer needed), the box as staged for the work item
     __syncwarp();
     cc_plane_to_smem(keys, ap, n0, lane);
-    const float* apl = (const float*)keys;
+    float* keys_f = (float*)keys;
+    const float* apl = keys_f;
     const float* slo = blo;
     const float* shi = bhi;
     const float psc = SPEC ? a.sscale[o] : __ldg(a.pscale + (side ? a.U + c : c));
     const float cur = SPEC ? a.slower[o] : (side == 0 ? a.l[o] : -a.u[o]);
     float part = 0.f;
     unsigned nzv = 0u;  // rows with a nonzero multiplier (wide launch)
+    float sval = sa;    // factor of the buffer: 1 once the wide launch has formed a' over it
     if constexpr (WIDE) {
         for (int p = 0; p < R; ++p)
             if (bsm[p] != 0.f) nzv |= 1u << p;
+        sval = cc_accum_rows(keys_f, rw.gs, bsm, nzv, n0, sa, lane);
     }
     if (!WIDE && (n0 & 1) == 0) {
         // two adjacent elements per lane, packed FP32: each lane sums at most ceil(n0/64) terms per
@@ -1282,12 +1384,9 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
 #pragma unroll
             for (int u = 0; u < PF; ++u) {
                 const int jj = min(j0 + 32 * u, n0 - 1);
-                float v = sa * av[u];
+                float v = sval * av[u];
                 if constexpr (WIDE) {
-                    for (unsigned mm = nzv; mm; mm &= mm - 1u) {  // zero multipliers add nothing
-                        const int p = __ffs(mm) - 1;
-                        v = fmaf(bsm[p], rw.gs[p * n0 + jj], v);
-                    }
+                    // a' already formed over the buffer (zero multipliers add nothing)
                 } else {
 #pragma unroll
                     for (int p = 0; p < RC; ++p) v = fmaf(bget(p), rw.gs[p * n0 + jj], v);
@@ -1324,7 +1423,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
         // the stability decision is uncertain in FP32: evaluate D(beta) in FP64
         double d = 0.0;
         for (int j = lane; j < n0; j += 32) {
-            double v = (double)(sa * apl[j]);
+            double v = (double)(sa * __ldg(ap + j));  // (the wide launch's buffer holds a', not a)
 #pragma unroll
             for (int p = 0; p < RC; ++p) {
                 if (WIDE && p >= R) break;

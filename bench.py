@@ -615,8 +615,6 @@ def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
     ntg = int(toff[-1].item())
     del r0
     rnd = E.Round(net, B, m, max_splits=cfg["kmax"], relaxed=1, sweeps=cfg["sweeps"], precision=prec)
-    # complete clipping's item sizes, tuned on this batch before the graph is captured (untimed)
-    items, _ = rnd.autotune(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, tgt_off=toff, tgt_ids=tids)
     rnd.enable_timer()
     rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, tgt_off=toff, tgt_ids=tids)
     ph, _, steps_cc = capi.cv_timer_read(rnd.timer)
@@ -633,7 +631,7 @@ def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
                metric="subdomains bounded+clipped per second", value=B / (ms / 1e3), unit="subdomains/s",
                higher_is_better=True, ms_per_step=ms, steps=steps, warmup=warmup, cached_neurons=U,
                phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
-                                 [round(x, 3) for x in ph])), cc_items=dict(sizes=items, tuned=True),
+                                 [round(x, 3) for x in ph])),
                roofline=_phase_roofline(ph, steps_cc, n0, dims, B * m, peaks, 1))
     if cpu:
         from oracle import oracle as O

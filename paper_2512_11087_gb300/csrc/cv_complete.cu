@@ -117,9 +117,11 @@ struct CCArgs {
     int* wcnt;                               // [B] work items
     int* order;                              // [B] positions -> subdomains, more rows first
     int* ioff;                               // [B+1] first item of every position; [B] = total
+    int* toff;                               // [B+1] first task of every position (wide launch)
     int* nplaced;                            // positions holding subdomains with work
     int* wide;                               // items of subdomains with more than RTPL rows (first)
-    unsigned* ticket;                        // [2] item tickets: wide items, the rest
+    int* nwpos;                              // positions of subdomains with more than RTPL rows
+    unsigned* ticket;                        // [2] tickets: wide-launch tasks, main-launch items
     int allwide;                             // 1: the wide launch takes every item (rows too large to stage)
 };
 
@@ -211,37 +213,43 @@ __global__ void __launch_bounds__(256) k_cc_prep(CCArgs a) {
 
 // Work-item offsets with the subdomains ordered by decreasing row count (longest tasks first).
 __global__ void __launch_bounds__(1024) k_cc_scan(CCArgs a) {
-    __shared__ int sc[1024], si[1024];
-    __shared__ int placed, carry;
+    __shared__ int sc[1024], si[1024], sk[1024];
+    __shared__ int placed, carry, tcarry;
     const int B = a.B, tid = threadIdx.x, nt = blockDim.x;
     const int per = (B + nt - 1) / nt;
-    if (tid == 0) { placed = 0; carry = 0; *a.wide = 0; }
+    if (tid == 0) { placed = 0; carry = 0; tcarry = 0; *a.wide = 0; *a.nwpos = 0; }
     __syncthreads();
     for (int v = a.Rs; v >= 1; --v) {
-        int c = 0, s = 0;
+        int c = 0, s = 0, k = 0;
         for (int i = 0; i < per; ++i) {
             const int b = tid * per + i;
-            if (b < B && a.wR[b] == v) { ++c; s += a.wcnt[b]; }
+            if (b < B && a.wR[b] == v) { ++c; s += a.wcnt[b]; k += ntasks(a, b); }
         }
         sc[tid] = c;
         si[tid] = s;
+        sk[tid] = k;
         __syncthreads();
         for (int off = 1; off < nt; off <<= 1) {  // inclusive scans
             const int tc = tid >= off ? sc[tid - off] : 0;
             const int ts = tid >= off ? si[tid - off] : 0;
+            const int tk = tid >= off ? sk[tid - off] : 0;
             __syncthreads();
             sc[tid] += tc;
             si[tid] += ts;
+            sk[tid] += tk;
             __syncthreads();
         }
         int pos = placed + sc[tid] - c;
         int ib = carry + si[tid] - s;
+        int tb = tcarry + sk[tid] - k;
         for (int i = 0; i < per; ++i) {
             const int b = tid * per + i;
             if (b < B && a.wR[b] == v) {
                 a.order[pos] = b;
                 a.ioff[pos] = ib;
+                a.toff[pos] = tb;
                 ib += a.wcnt[b];
+                tb += ntasks(a, b);
                 ++pos;
             }
         }
@@ -249,13 +257,15 @@ __global__ void __launch_bounds__(1024) k_cc_scan(CCArgs a) {
         if (tid == 0) {
             placed += sc[nt - 1];
             carry += si[nt - 1];
-            if (v == RTPL + 1) *a.wide = carry;
+            tcarry += sk[nt - 1];
+            if (v == RTPL + 1) { *a.wide = carry; *a.nwpos = placed; }
         }
         __syncthreads();
     }
-    for (int i = placed + tid; i < B; i += nt) { a.ioff[i] = carry; a.order[i] = -1; }
+    for (int i = placed + tid; i < B; i += nt) { a.ioff[i] = carry; a.toff[i] = tcarry; a.order[i] = -1; }
     if (tid == 0) {
         a.ioff[B] = carry;
+        a.toff[B] = tcarry;
         *a.nplaced = placed;
         a.ticket[0] = 0u;
         a.ticket[1] = 0u;
@@ -275,6 +285,29 @@ __shared__ double cc_Sg[RMAX_CC];      // magnitude of g against the root box
 __shared__ float cc_SgH[RMAX_CC];      // Sg + |h| rounded up
 __shared__ float cc_Gm[RMAX_CC];       // max |g| of every row
 __shared__ float cc_Rm[RMAX_CC];       // max |fl(1/g)| of every row
+// The wide launch's warps take tasks independently: each holds its subdomain's row constants itself.
+__shared__ long long cc_wT64[NWARP][RMAX_CC];
+__shared__ long long cc_wW64[NWARP][RMAX_CC];
+__shared__ float cc_whrow[NWARP][RMAX_CC];
+__shared__ float cc_wSgH[NWARP][RMAX_CC];
+__shared__ float cc_wGm[NWARP][RMAX_CC];
+constexpr size_t CC_WCONST = (size_t)NWARP * RMAX_CC * (8 + 8 + 4 + 4 + 4);  // their bytes
+// row p's constants for the calling thread: the block's (main launch) or its warp's (wide launch)
+template <bool WIDE> __device__ __forceinline__ long long ccT(int p) {
+    if constexpr (WIDE) return cc_wT64[threadIdx.x >> 5][p]; else return cc_T64[p];
+}
+template <bool WIDE> __device__ __forceinline__ long long ccW(int p) {
+    if constexpr (WIDE) return cc_wW64[threadIdx.x >> 5][p]; else return cc_W64[p];
+}
+template <bool WIDE> __device__ __forceinline__ float cch(int p) {
+    if constexpr (WIDE) return cc_whrow[threadIdx.x >> 5][p]; else return cc_hrow[p];
+}
+template <bool WIDE> __device__ __forceinline__ float ccSgH(int p) {
+    if constexpr (WIDE) return cc_wSgH[threadIdx.x >> 5][p]; else return cc_SgH[p];
+}
+template <bool WIDE> __device__ __forceinline__ float ccGm(int p) {
+    if constexpr (WIDE) return cc_wGm[threadIdx.x >> 5][p]; else return cc_Gm[p];
+}
 
 struct CCView {
     float* blo;            // the staged subdomain's clipped box [n0] (lower ends)
@@ -292,7 +325,8 @@ struct CCView {
 // Main launch: keys [nw][n0r] | w64 [RsS][n0] | g [RsS][n0] | 1/g [RsS][n0] | list [nw][CAPC] |
 // multipliers' trailing parts and a copy of their leading parts [nw][2 RMAX_CC] | box [2][n0].
 // Wide launch: keys [nw][n0r] | list [nw][CAPC] | multipliers [nw][RMAX_CC] | elements [nw][RMAX_CC] |
-// multipliers' trailing parts [nw][RMAX_CC] | box [2][n0].
+// multipliers' trailing parts [nw][RMAX_CC] (its warps read the box from global memory; blo / bhi
+// are not used there).
 __device__ __forceinline__ CCView cc_view(int n0, int RsS, bool wide) {
     const int n0r = (n0 + 31) & ~31;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -447,7 +481,7 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
     for (int p = 0; p < R; ++p) {
         if (p == k) continue;
         const float b = bh[p];
-        smx = __fmaf_ru(fabsf(b), cc_Gm[p], smx);
+        smx = __fmaf_ru(fabsf(b), ccGm<WIDE>(p), smx);
         nnz += b != 0.f;
         if (!WIDE || b != 0.f) nzm |= 1u << p;
     }
@@ -894,8 +928,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
                 else return q_of(av, j);
             };
             const bool warm = qp > 0.f;
-            const long long T = cc_T64[k];
-            const long long W = cc_W64[k];
+            const long long T = ccT<WIDE>(k);
+            const long long W = ccW<WIDE>(k);
             // One pass over all n0 elements keeps the keys in the warp's buffer.  Without a previous
             // breakpoint it takes F(0) = sum_{q <= 0} w (the paired pass: W minus the weight of q > 0,
             // leaving the extent and size of the search range to the search); with one, F just below
@@ -1412,8 +1446,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
 #pragma unroll
     for (int p = 0; p < RC; ++p) {
         if (WIDE && p >= R) break;
-        cst = fmaf(bget(p), cc_hrow[p], cst);
-        scale = __fmaf_ru(bget(p), cc_SgH[p], scale);
+        cst = fmaf(bget(p), cch<WIDE>(p), cst);
+        scale = __fmaf_ru(bget(p), ccSgH<WIDE>(p), scale);
     }
     const float gam = __fmul_ru((float)(R + (n0 + 31) / 32 + 12), 5.9611e-08f);  // >= 2^-24 * 1.0001
     const float pad = __fmul_ru(__fmul_ru(gam, scale), 1.0001f);
@@ -1437,7 +1471,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
 #pragma unroll
         for (int p = 0; p < RC; ++p) {
             if (WIDE && p >= R) break;
-            d += (double)bget(p) * (double)cc_hrow[p];
+            d += (double)bget(p) * (double)cch<WIDE>(p);
         }
         // D at the leading parts differs from D at the full multipliers (the ascent's point) by at most
         // sum_p |beta_lo,p| (sum_j |g_pj| max(|lo_j|, |hi_j|) + |h_p|); charged so that the bound never
@@ -1447,7 +1481,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
 #pragma unroll
             for (int p = 0; p < RC; ++p) {
                 if (WIDE && p >= R) break;
-                tpad = __fmaf_ru(fabsf(blsm[p]), cc_SgH[p], tpad);
+                tpad = __fmaf_ru(fabsf(blsm[p]), ccSgH<WIDE>(p), tpad);
             }
         }
         val = __double2float_rd(d - ldexp((double)scale, -40) - (double)tpad);
@@ -1459,8 +1493,8 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
     }
 }
 
-// WIDE: the items of subdomains with more than RTPL rows (one block per SM, more registers);
-// otherwise the rest.
+// WIDE: the tasks of subdomains with more than RTPL rows, taken by each warp on its own (one block
+// per SM, more registers); otherwise the rest, in work items shared by a block's warps.
 template <bool WIDE, bool SPEC>
 __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a) {
     const int n0 = a.n0, Rs = a.Rs, B = a.B;
@@ -1472,106 +1506,172 @@ __global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a)
     if (threadIdx.x == 0) { nsteps = 0; ncs[0] = ncs[1] = ncs[2] = ncs[3] = ncs[4] = 0; }
     unsigned long long my_steps = 0;
     unsigned my_cs[5] = {0u, 0u, 0u, 0u, 0u};
-    const int ibeg = WIDE ? 0 : *a.wide;
-    const int total = (WIDE && !a.allwide) ? *a.wide : a.ioff[B];
     const int np = *a.nplaced;
-    int cur_b = -1;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int it = ibeg + (int)atomicAdd(&a.ticket[WIDE ? 0 : 1], 1u);
-            s_item = it;
-            if (it < total) {
-                int lo = 0, hi = np - 1;  // last position whose first item is <= it
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (a.ioff[mid] <= it) lo = mid; else hi = mid - 1;
-                }
-                s_pos = lo;
-            }
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total) break;
-        const int pos = s_pos;
-        const int b = a.order[pos];
-        if (b != cur_b) {
-            // stage the subdomain's row constants (and, in the main launch, its rows)
-            if (threadIdx.x == 0) s_R = a.wR[b];
-            __syncthreads();
-            const int R = s_R;
-            if (!WIDE) {
-                const size_t base = (size_t)b * Rs * n0;
-                for (int i = threadIdx.x; i < R * n0; i += blockDim.x) {
-                    sv.w64[i] = a.ww[base + i];
-                    sv.gs[i] = a.wg[base + i];
-                    sv.rg[i] = a.wrg[base + i];
-                }
-            }
-            for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-                sv.blo[i] = a.lo[(size_t)b * n0 + i];
-                sv.bhi[i] = a.hi[(size_t)b * n0 + i];
-            }
-            if (threadIdx.x < R) {
-                cc_T64[threadIdx.x] = a.wT[(size_t)b * Rs + threadIdx.x];
-                cc_W64[threadIdx.x] = a.wW[(size_t)b * Rs + threadIdx.x];
-                cc_hrow[threadIdx.x] = a.wh[(size_t)b * Rs + threadIdx.x];
-                cc_Sg[threadIdx.x] = a.wSg[(size_t)b * Rs + threadIdx.x];
-                cc_SgH[threadIdx.x] = __double2float_ru(cc_Sg[threadIdx.x] + fabs((double)cc_hrow[threadIdx.x]));
-                cc_Gm[threadIdx.x] = a.wGm[(size_t)b * Rs + threadIdx.x];
-                cc_Rm[threadIdx.x] = a.wRm[(size_t)b * Rs + threadIdx.x];
-            }
-            cur_b = b;
-        }
-        const int R = s_R;
-        CCRows rw;
-        if (WIDE) {
-            const size_t base = (size_t)b * Rs * n0;
-            rw.gs = a.wg + base; rw.rg = a.wrg + base; rw.w64 = a.ww + base;
-        } else {
-            rw.gs = sv.gs; rw.rg = sv.rg; rw.w64 = sv.w64;
-        }
+    if constexpr (WIDE) {
+        // Each warp takes (target, side) tasks one at a time from the wide launch's ticket, over the
+        // subdomains in order of decreasing row count, holding its subdomain's row constants in its
+        // own slots: no block barrier between tasks.  The rows and the box are read from L2.
+        __syncthreads();  // the block's counters are initialised
+        const int warp = threadIdx.x >> 5;
+        const int npw = a.allwide ? np : *a.nwpos;
+        const int total = a.toff[npw];
         const bool have_list = a.tgt_off != nullptr;
-        const int t0 = have_list ? a.tgt_off[b] : 0;
-        const int ntask = SPEC ? a.m : 2 * ntargets(a, b);
-        const int first = (item - a.ioff[pos]) * tpi_of(a, R);
-        const int last = min(first + tpi_of(a, R), ntask);
-        if (threadIdx.x == 0) s_next = first;
-        __syncthreads();
-        // the warps take the item's tasks one at a time from its counter
+        int cb = -1, R = 0, tbeg = 0, tend = 0, t0 = 0;
+        CCRows rw;
+        rw.gs = nullptr; rw.rg = nullptr; rw.w64 = nullptr;
+        const float* blo = nullptr;
+        const float* bhi = nullptr;
         for (;;) {
             int t = 0;
-            if (lane == 0) t = atomicAdd(&s_next, 1);
+            if (lane == 0) t = (int)atomicAdd(&a.ticket[0], 1u);
             t = __shfl_sync(0xffffffffu, t, 0);
-            if (t >= last) break;
+            if (t >= total) break;
+            if (t < tbeg || t >= tend) {
+                int pos = 0;
+                if (lane == 0) {
+                    int lo = 0, hi = npw - 1;  // the last position whose first task is <= t
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (a.toff[mid] <= t) lo = mid; else hi = mid - 1;
+                    }
+                    pos = lo;
+                }
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                tbeg = a.toff[pos];
+                tend = a.toff[pos + 1];
+                const int b = a.order[pos];
+                if (b != cb) {
+                    R = a.wR[b];
+                    if (lane < R) {
+                        const size_t q = (size_t)b * Rs + lane;
+                        cc_wT64[warp][lane] = a.wT[q];
+                        cc_wW64[warp][lane] = a.wW[q];
+                        cc_whrow[warp][lane] = a.wh[q];
+                        cc_wSgH[warp][lane] = __double2float_ru(a.wSg[q] + fabs((double)a.wh[q]));
+                        cc_wGm[warp][lane] = a.wGm[q];
+                    }
+                    __syncwarp();
+                    cb = b;
+                    const size_t base = (size_t)b * Rs * n0;
+                    rw.gs = a.wg + base; rw.rg = a.wrg + base; rw.w64 = a.ww + base;
+                    blo = a.lo + (size_t)b * n0;
+                    bhi = a.hi + (size_t)b * n0;
+                    t0 = have_list ? a.tgt_off[b] : 0;
+                }
+            }
+            const int tl = t - tbeg;  // the task's index within its subdomain
             int c, side;
             if (SPEC) {
-                c = t;
+                c = tl;
                 side = 0;
-                if (a.slower[(size_t)b * a.m + c] > 0.f) continue;  // proven already
+                if (a.slower[(size_t)cb * a.m + c] > 0.f) continue;  // proven already
             } else {
-                const int ti = t >> 1;
-                side = t & 1;
+                const int ti = tl >> 1;
+                side = tl & 1;
                 c = have_list ? a.tgt_ids[t0 + ti] : ti;
                 if (c < 0 || c >= a.U) {
                     if (lane == 0) atomicOr(a.status, CV_DEV_TARGET);
                     continue;
                 }
-                if (a.mask[(size_t)b * a.U + c] != 0) continue;
+                if (a.mask[(size_t)cb * a.U + c] != 0) continue;
             }
-            if (WIDE) {
-                if (R <= 8) cc_task<8, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, sv.blo, sv.bhi, R, b, c, side, lane, my_steps, my_cs);
-                else if (R <= 16) cc_task<16, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, sv.blo, sv.bhi, R, b, c, side, lane, my_steps, my_cs);
-                else cc_task<32, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, sv.blo, sv.bhi, R, b, c, side, lane, my_steps, my_cs);
-            } else {
-                switch (R) {
-                    case 1: cc_task<1, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 1, b, c, side, lane, my_steps, my_cs); break;
-                    case 2: cc_task<2, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 2, b, c, side, lane, my_steps, my_cs); break;
-                    case 3: cc_task<3, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 3, b, c, side, lane, my_steps, my_cs); break;
-                    default: cc_task<4, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 4, b, c, side, lane, my_steps, my_cs); break;
+            if (R <= 8) cc_task<8, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, blo, bhi, R, cb, c, side, lane, my_steps, my_cs);
+            else if (R <= 16) cc_task<16, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, blo, bhi, R, cb, c, side, lane, my_steps, my_cs);
+            else cc_task<32, true, SPEC>(a, rw, sv.keys, sv.cidx, sv.bsm, sv.blsm, sv.jsm, blo, bhi, R, cb, c, side, lane, my_steps, my_cs);
+            __syncwarp();
+        }
+    } else {
+        const int ibeg = *a.wide;
+        const int total = a.ioff[B];
+        int cur_b = -1;
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int it = ibeg + (int)atomicAdd(&a.ticket[1], 1u);
+                s_item = it;
+                if (it < total) {
+                    int lo = 0, hi = np - 1;  // last position whose first item is <= it
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (a.ioff[mid] <= it) lo = mid; else hi = mid - 1;
+                    }
+                    s_pos = lo;
                 }
             }
-            __syncwarp();
+            __syncthreads();
+            const int item = s_item;
+            if (item >= total) break;
+            const int pos = s_pos;
+            const int b = a.order[pos];
+            if (b != cur_b) {
+                // stage the subdomain's row constants (and, in the main launch, its rows)
+                if (threadIdx.x == 0) s_R = a.wR[b];
+                __syncthreads();
+                const int R = s_R;
+                {
+                    const size_t base = (size_t)b * Rs * n0;
+                    for (int i = threadIdx.x; i < R * n0; i += blockDim.x) {
+                        sv.w64[i] = a.ww[base + i];
+                        sv.gs[i] = a.wg[base + i];
+                        sv.rg[i] = a.wrg[base + i];
+                    }
+                }
+                for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+                    sv.blo[i] = a.lo[(size_t)b * n0 + i];
+                    sv.bhi[i] = a.hi[(size_t)b * n0 + i];
+                }
+                if (threadIdx.x < R) {
+                    cc_T64[threadIdx.x] = a.wT[(size_t)b * Rs + threadIdx.x];
+                    cc_W64[threadIdx.x] = a.wW[(size_t)b * Rs + threadIdx.x];
+                    cc_hrow[threadIdx.x] = a.wh[(size_t)b * Rs + threadIdx.x];
+                    cc_Sg[threadIdx.x] = a.wSg[(size_t)b * Rs + threadIdx.x];
+                    cc_SgH[threadIdx.x] = __double2float_ru(cc_Sg[threadIdx.x] + fabs((double)cc_hrow[threadIdx.x]));
+                    cc_Gm[threadIdx.x] = a.wGm[(size_t)b * Rs + threadIdx.x];
+                    cc_Rm[threadIdx.x] = a.wRm[(size_t)b * Rs + threadIdx.x];
+                }
+                cur_b = b;
+            }
+            const int R = s_R;
+            CCRows rw;
+            rw.gs = sv.gs; rw.rg = sv.rg; rw.w64 = sv.w64;
+            const bool have_list = a.tgt_off != nullptr;
+            const int t0 = have_list ? a.tgt_off[b] : 0;
+            const int ntask = SPEC ? a.m : 2 * ntargets(a, b);
+            const int first = (item - a.ioff[pos]) * tpi_of(a, R);
+            const int last = min(first + tpi_of(a, R), ntask);
+            if (threadIdx.x == 0) s_next = first;
+            __syncthreads();
+            // the warps take the item's tasks one at a time from its counter
+            for (;;) {
+                int t = 0;
+                if (lane == 0) t = atomicAdd(&s_next, 1);
+                t = __shfl_sync(0xffffffffu, t, 0);
+                if (t >= last) break;
+                int c, side;
+                if (SPEC) {
+                    c = t;
+                    side = 0;
+                    if (a.slower[(size_t)b * a.m + c] > 0.f) continue;  // proven already
+                } else {
+                    const int ti = t >> 1;
+                    side = t & 1;
+                    c = have_list ? a.tgt_ids[t0 + ti] : ti;
+                    if (c < 0 || c >= a.U) {
+                        if (lane == 0) atomicOr(a.status, CV_DEV_TARGET);
+                        continue;
+                    }
+                    if (a.mask[(size_t)b * a.U + c] != 0) continue;
+                }
+                {
+                    switch (R) {
+                        case 1: cc_task<1, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 1, b, c, side, lane, my_steps, my_cs); break;
+                        case 2: cc_task<2, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 2, b, c, side, lane, my_steps, my_cs); break;
+                        case 3: cc_task<3, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 3, b, c, side, lane, my_steps, my_cs); break;
+                        default: cc_task<4, false, SPEC>(a, rw, sv.keys, sv.cidx, nullptr, sv.blsm, nullptr, sv.blo, sv.bhi, 4, b, c, side, lane, my_steps, my_cs); break;
+                    }
+                }
+                __syncwarp();
+            }
         }
     }
     if (a.steps && lane == 0) {
@@ -1612,10 +1712,11 @@ template <bool WIDE, bool SPEC>
 cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
     const size_t n0r = (a.n0 + 31) & ~31;
     const size_t RsS = a.Rs < RTPL ? a.Rs : RTPL;
-    // main: staged rows + per warp keys and list; wide: per warp keys, list and multiplier slots
-    const size_t fixed = (WIDE ? 0 : RsS * a.n0 * (8 + 4 + 4)) + (size_t)a.n0 * 8;  // rows, box
+    // main: staged rows and box + per warp keys and list; wide: per warp keys, list and multiplier
+    // slots (its row constants are static shared memory, CC_WCONST bytes)
+    const size_t fixed = WIDE ? 0 : RsS * a.n0 * (8 + 4 + 4) + (size_t)a.n0 * 8;  // rows, box
     const size_t per_warp = n0r * 4 + CAPC * 2 + (WIDE ? (size_t)RMAX_CC * 12 : (size_t)RMAX_CC * 8);
-    const size_t limit = 220 * 1024;
+    const size_t limit = 220 * 1024 - (WIDE ? CC_WCONST : 0);
     int nw = NWARP;
     while (nw > 1 && fixed + nw * per_warp > limit) --nw;
     const size_t smem = fixed + nw * per_warp;
@@ -1693,8 +1794,8 @@ size_t cv_cc_workspace(int B, int Rmax, int n0) {
     s += cv_align256(b * Rs * 8) * 3;       // wT, wW, wSg
     s += cv_align256(b * Rs * 4) * 3;       // wh, wGm, wRm
     s += cv_align256(b * 4) * 3;            // wR, wcnt, order
-    s += cv_align256((b + 1) * 4);          // ioff
-    s += 256 * 2;                           // nplaced, ticket
+    s += cv_align256((b + 1) * 4) * 2;      // ioff, toff
+    s += 256 * 2;                           // nplaced / wide / nwpos, ticket
     return s;
 }
 
@@ -1740,8 +1841,10 @@ cv_status cv_launch_complete(const cv_net* net, const cv_cache* cache, const cv_
     a.wcnt = (int*)p; p += cv_align256(B * 4);
     a.order = (int*)p; p += cv_align256(B * 4);
     a.ioff = (int*)p; p += cv_align256((B + 1) * 4);
+    a.toff = (int*)p; p += cv_align256((B + 1) * 4);
     a.nplaced = (int*)p;
     a.wide = a.nplaced + 1;
+    a.nwpos = a.nplaced + 2;
     p += 256;
     a.ticket = (unsigned*)p;
     k_cc_prep<<<in->B, 256, 0, st>>>(a);
@@ -1799,8 +1902,10 @@ cv_status cv_launch_spec_clip(const cv_net* net, const cv_cache* cache, const cv
     a.wcnt = (int*)p; p += cv_align256(B * 4);
     a.order = (int*)p; p += cv_align256(B * 4);
     a.ioff = (int*)p; p += cv_align256((B + 1) * 4);
+    a.toff = (int*)p; p += cv_align256((B + 1) * 4);
     a.nplaced = (int*)p;
     a.wide = a.nplaced + 1;
+    a.nwpos = a.nplaced + 2;
     p += 256;
     a.ticket = (unsigned*)p;
     k_spec_scale<<<(unsigned)(B * in->m), 256, 0, st>>>(in->m, (int)n0, out->final_A, out->final_c, out->lo_clip,

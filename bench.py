@@ -618,6 +618,8 @@ def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
     rnd.enable_timer()
     rnd.run(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, tgt_off=toff, tgt_ids=tids)
     ph, _, steps_cc = capi.cv_timer_read(rnd.timer)
+    cc_counts = dict(zip(["row_steps", "certified", "several_candidates", "widened", "fp32_decision_kept",
+                          "over_candidate_limit"], rnd.cc_stats()))
     rnd.opt.timer = None
     rnd.capture(dlo, dhi, dC, dt_, split_off=dso, split_ids=dsi, tgt_off=toff, tgt_ids=tids)
     ts = _timed(lambda: rnd.replay(stream), steps, warmup, flush, stream)
@@ -631,7 +633,7 @@ def bench_cnn3x32(steps, warmup, flush, stream, peaks, cpu=True):
                metric="subdomains bounded+clipped per second", value=B / (ms / 1e3), unit="subdomains/s",
                higher_is_better=True, ms_per_step=ms, steps=steps, warmup=warmup, cached_neurons=U,
                phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
-                                 [round(x, 3) for x in ph])),
+                                 [round(x, 3) for x in ph])), cc_counters=cc_counts,
                roofline=_phase_roofline(ph, steps_cc, n0, dims, B * m, peaks, 1))
     if cpu:
         from oracle import oracle as O
@@ -993,7 +995,7 @@ def main():
                     higher_is_better=e["higher_is_better"], scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic", config=dict(workload=e["config"]), roofline=e.get("roofline"), peaks=peaks)
         for k in ("cpu_baseline", "phase_ms", "subdomains_per_s", "domains_visited", "detail", "fp32_path",
-                  "cc_items", "with_split_multipliers"):
+                  "cc_items", "cc_counters", "with_split_multipliers"):
             if k in e:
                 line[k] = e[k]
         print(json.dumps(line), flush=True)

@@ -326,11 +326,14 @@ cv_status cv_spec_clip(cv_net* net, const cv_cache* cache, const cv_batch_in* in
 
 /* ---------------------------------------------------------------- scheduler tuning */
 
-/* Complete clipping runs as one persistent launch over uneven work: each subdomain's
- * (target, side) tasks are cut into work items that thread blocks take from an atomic ticket
- * (the paper's Algorithm 1 per task; the split into items is this library's scheduling, with
- * no counterpart in the paper).  items[c] is the number of tasks per item for subdomains with
- * c + 1 active rows (c = 2: three or more).  The item size changes no result, only the time.
+/* Complete clipping runs as persistent launches over uneven work (the paper's Algorithm 1 per
+ * (target, side) task; the scheduling is this library's, with no counterpart in the paper).  In
+ * the main launch, which stages a subdomain's rows in shared memory, each subdomain's tasks are
+ * cut into work items that thread blocks take from an atomic ticket; items[c] is the number of
+ * tasks per item for subdomains with c + 1 active rows (c = 2: three or more).  The wide launch
+ * (subdomains with more than four rows, or every subdomain when the rows do not fit in shared
+ * memory) hands out single tasks to warps and does not use the item sizes.  The item size
+ * changes no result, only the time.
  * A cache starts with CV_CC_ITEMS_1/2/3.  cv_cc_items_set: each value in [1, 4096] (else
  * CV_EINVAL); it affects rounds run and graphs captured after the call (a graph captured before
  * keeps the sizes it was captured with). */

@@ -60,6 +60,7 @@ constexpr int RTPL = 4;     // row counts up to this run in the main launch (two
 #define CV_CC_NWARP 12
 #endif
 constexpr int NWARP = CV_CC_NWARP;  // warps per block at most (two blocks per SM of 12 leave 84 registers a thread)
+constexpr int NWARPW = 16;  // warps per block at most in the wide launch (one block per SM, 128 registers a thread)
 constexpr int CAPC = 256;   // breakpoints a warp's compacted list holds
 constexpr int SAMP_MIN = 64;     // brackets with more breakpoints start from sampled pivots
 constexpr float SAMP_D = 0.10f;  // rank margin of the sampled pivots around the target fraction
@@ -286,12 +287,12 @@ __shared__ float cc_SgH[RMAX_CC];      // Sg + |h| rounded up
 __shared__ float cc_Gm[RMAX_CC];       // max |g| of every row
 __shared__ float cc_Rm[RMAX_CC];       // max |fl(1/g)| of every row
 // The wide launch's warps take tasks independently: each holds its subdomain's row constants itself.
-__shared__ long long cc_wT64[NWARP][RMAX_CC];
-__shared__ long long cc_wW64[NWARP][RMAX_CC];
-__shared__ float cc_whrow[NWARP][RMAX_CC];
-__shared__ float cc_wSgH[NWARP][RMAX_CC];
-__shared__ float cc_wGm[NWARP][RMAX_CC];
-constexpr size_t CC_WCONST = (size_t)NWARP * RMAX_CC * (8 + 8 + 4 + 4 + 4);  // their bytes
+__shared__ long long cc_wT64[NWARPW][RMAX_CC];
+__shared__ long long cc_wW64[NWARPW][RMAX_CC];
+__shared__ float cc_whrow[NWARPW][RMAX_CC];
+__shared__ float cc_wSgH[NWARPW][RMAX_CC];
+__shared__ float cc_wGm[NWARPW][RMAX_CC];
+constexpr size_t CC_WCONST = (size_t)NWARPW * RMAX_CC * (8 + 8 + 4 + 4 + 4);  // their bytes
 // row p's constants for the calling thread: the block's (main launch) or its warp's (wide launch)
 template <bool WIDE> __device__ __forceinline__ long long ccT(int p) {
     if constexpr (WIDE) return cc_wT64[threadIdx.x >> 5][p]; else return cc_T64[p];
@@ -917,7 +918,21 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
             cc_plane_to_smem(keys, ap, n0, lane);
             // previous breakpoint of this row (same value for every lane)
             float qp = 0.f;
-            if (jp >= 0) qp = q_of(__uint_as_float(keys[jp]), jp);
+            if (jp >= 0) {
+                if constexpr (WIDE) {
+                    // q_of at one element with the rows' coefficients loaded by one lane each (all in
+                    // flight at once) and passed along the fma chain by shuffles: the same bits
+                    const float gl = lane < R ? __ldg(rw.gs + (size_t)lane * n0 + jp) : 0.f;
+                    float apr = sa * __uint_as_float(keys[jp]);
+                    for (unsigned mm = nzm; mm; mm &= mm - 1u) {
+                        const int p = __ffs(mm) - 1;
+                        apr = fmaf(bsm[p], __shfl_sync(0xffffffffu, gl, p), apr);
+                    }
+                    qp = (-apr) * rk[jp];
+                } else {
+                    qp = q_of(__uint_as_float(keys[jp]), jp);
+                }
+            }
             __syncwarp();
             // wide launch: a' formed over the plane in the buffer first (the same bits as q_of forms),
             // so that the key pass below only scales it
@@ -1496,7 +1511,7 @@ __device__ __forceinline__ void cc_task(const CCArgs& a, const CCRows& rw, unsig
 // WIDE: the tasks of subdomains with more than RTPL rows, taken by each warp on its own (one block
 // per SM, more registers); otherwise the rest, in work items shared by a block's warps.
 template <bool WIDE, bool SPEC>
-__global__ void __launch_bounds__(NWARP * 32, WIDE ? 1 : 2) k_complete(CCArgs a) {
+__global__ void __launch_bounds__((WIDE ? NWARPW : NWARP) * 32, WIDE ? 1 : 2) k_complete(CCArgs a) {
     const int n0 = a.n0, Rs = a.Rs, B = a.B;
     const int RsS = Rs < RTPL ? Rs : RTPL;  // rows staged by the main launch
     const int lane = threadIdx.x & 31;
@@ -1717,7 +1732,7 @@ cv_status launch_cc_one(const CCArgs& a, int* launches, cudaStream_t st) {
     const size_t fixed = WIDE ? 0 : RsS * a.n0 * (8 + 4 + 4) + (size_t)a.n0 * 8;  // rows, box
     const size_t per_warp = n0r * 4 + CAPC * 2 + (WIDE ? (size_t)RMAX_CC * 12 : (size_t)RMAX_CC * 8);
     const size_t limit = 220 * 1024 - (WIDE ? CC_WCONST : 0);
-    int nw = NWARP;
+    int nw = WIDE ? NWARPW : NWARP;
     while (nw > 1 && fixed + nw * per_warp > limit) --nw;
     const size_t smem = fixed + nw * per_warp;
     if (smem > limit || a.n0 > 65535) {

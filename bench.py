@@ -27,6 +27,10 @@ CONFIG = "mlp784x256"
 # lane operations per coordinate and row step of Algorithm 1 (a' and the breakpoint 3, the weight 1,
 # the slope update 3, the crossing test and bookkeeping 3): the count of the benchmark table
 CC_OPS_PER_COORD = 10
+# DRAM bytes (read + write) of complete clipping's main launch per executed row step, from one ncu
+# capture of the kernel on this workload at B = 1024 (19.675 MB over 1,717,951 row steps); the
+# launch's traffic grows with its row steps, so the timed launch's is this times its row steps
+CC_DRAM_BYTES_PER_ROW_STEP = 19.675e6 / 1717951
 
 
 def workload_desc(cfg, name=CONFIG):
@@ -1171,7 +1175,10 @@ def main():
                                 phase_ms=dict(zip(["rows+relaxed", "reconcretize", "complete_clip", "backsubst"],
                                                   [round(x, 4) for x in ph_mean]))),
                     roofline=dict(bound="alu", kernel="k_complete", achieved=achieved, peak=peak, unit="Gop/s",
-                                  frac=achieved / peak, traffic=None, alg_ops_per_launch=alg_ops,
+                                  frac=achieved / peak,
+                                  traffic=(CC_DRAM_BYTES_PER_ROW_STEP * steps_cc if args.config == CONFIG else None),
+                                  traffic_source="ncu capture at B = 1024, scaled by the row steps",
+                                  alg_ops_per_launch=alg_ops,
                                   ops_per_coordinate_and_row_step=CC_OPS_PER_COORD, cc_row_steps=steps_cc,
                                   peak_source="measured: cv_fp32_fma_peak lane FMAs/s"),
                     e2e=dict(value=e2e_value, unit="subdomains/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),

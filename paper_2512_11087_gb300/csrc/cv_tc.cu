@@ -463,28 +463,48 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                     acc[j] += fmaf(lv[0][j], 16777216.f, fmaf(lv[1][j], 65536.f, fmaf(lv[2][j], 256.f, lv[3][j])));
             }
             if (!rok) continue;
+            // the eight columns' independent loads are issued together (one round trip each stage
+            // instead of one per column): slot, exponent, bias, kept product, slope; then the bounds
+            int slotv[8], fev[8];
+            float bvv[8], pfv[8], alv[8], lbv[8], ubv[8];
+            int stv[8];
+            const size_t gar = ((size_t)sub * a.m + (r % a.m)) * a.H + a.hoff;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int q = col0 + c0 + j;
+                const bool qv = q < a.N;
+                slotv[j] = qv ? a.slot_of[a.hoff + q] : -1;
+                fev[j] = qv ? a.fexp[q] : 0;
+                bvv[j] = qv ? a.bvec[q] : 0.f;
+                pfv[j] = qv ? a.Pfwd[(size_t)r * a.N + q] : 0.f;
+                alv[j] = qv ? a.alpha[gar + q] : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int g = a.hoff + col0 + c0 + j;
+                if (col0 + c0 + j >= a.N) { lbv[j] = 0.f; ubv[j] = 0.f; stv[j] = 0; continue; }
+                if (slotv[j] >= 0) {
+                    const size_t o = (size_t)sub * a.U + slotv[j];
+                    lbv[j] = a.l[o]; ubv[j] = a.u[o]; stv[j] = a.mask[o];
+                } else {
+                    lbv[j] = a.root_l[g]; ubv[j] = a.root_u[g]; stv[j] = a.root_state[g];
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int q = col0 + c0 + j;
                 if (q >= a.N) continue;
-                const float dl = ldexpf(acc[j], er + a.fexp[q] - 38) + gf * a.bvec[q];
+                const float dl = ldexpf(acc[j], er + fev[j] - 38) + gf * bvv[j];
                 const int g = a.hoff + q;
-                const int slot = a.slot_of[g];
-                float lb, ub;
-                int st;
-                if (slot >= 0) {
-                    const size_t o = (size_t)sub * a.U + slot;
-                    lb = a.l[o]; ub = a.u[o]; st = a.mask[o];
-                } else {
-                    lb = a.root_l[g]; ub = a.root_u[g]; st = a.root_state[g];
-                }
-                const float pf = a.Pfwd[(size_t)r * a.N + q];
+                const float lb = lbv[j], ub = ubv[j];
+                const int st = stv[j];
+                const float pf = pfv[j];
                 float d, e;
-                const size_t ga = ((size_t)sub * a.m + (r % a.m)) * a.H + g;
+                const size_t ga = gar + q;
                 if (st > 0) { d = 1.f; e = 0.f; }
                 else if (st < 0) { d = 0.f; e = 0.f; }
                 else if (pf >= 0.f) {
-                    d = a.alpha[ga];
+                    d = alv[j];
                     e = 0.f;
                     a.grad_alpha[ga] = dl * pf;
                 } else {
@@ -579,27 +599,39 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
         }
         if (!rok) continue;
         float s1 = 0.f, s2 = 0.f;
+        // products and relaxation of the eight columns first, so that their global loads (slopes
+        // given per row, split signs and multipliers) are issued together, not one column at a time
+        float pv[8], dv[8], ev[8], btv[8];
+        int sgv[8];
+        if (a.i > 1) {
+            const size_t arow = ((size_t)(sub0 + sb) * a.m + (r % a.m)) * a.H + a.hoff;
+            const size_t srow = (size_t)(sub0 + sb) * a.H + a.hoff;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + j;
+                const bool qv = col0 + c < a.N;
+                pv[j] = ldexpf(acc[j], er + s_fexp[c] - 38);  // 2^(e + f - 46) times the 2^8 level unit
+                // relaxation of neuron q by the sign of p (table of layer i-1; NaN: slope from alpha)
+                if (pv[j] >= 0.f) { dv[j] = qv ? t0[c] : 0.f; ev[j] = 0.f; }
+                else { dv[j] = qv ? t1[c] : 0.f; ev[j] = qv ? t2[c] : 0.f; }
+                sgv[j] = (qv && a.bsign) ? (int)a.bsign[srow + col0 + c] : 0;
+                btv[j] = (qv && a.bsign) ? a.beta[arow + col0 + c] : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (col0 + c0 + j < a.N && dv[j] != dv[j]) dv[j] = a.alpha[arow + col0 + c0 + j];
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int c = c0 + j, q = col0 + c;
             if (q >= a.N) continue;
-            const float p = ldexpf(acc[j], er + s_fexp[c] - 38);  // 2^(e + f - 46) times the 2^8 level unit
             if (a.i > 1) {
-                // relaxation of neuron q by the sign of p (table of layer i-1; NaN: slope from alpha)
-                float d, e = 0.f;
-                if (p >= 0.f) {
-                    d = t0[c];
-                    if (d != d) d = a.alpha[((size_t)(sub0 + sb) * a.m + (r % a.m)) * a.H + a.hoff + q];
-                } else {
-                    d = t1[c];
-                    e = t2[c];
-                }
+                const float p = pv[j], d = dv[j], e = ev[j];
                 float lam = p * d;
                 if (a.bsign) {  // split multiplier: Lam_g -= sign_g beta_g, rounded away from lam
-                    const int g = a.hoff + q;
-                    const int sg = a.bsign[(size_t)(sub0 + sb) * a.H + g];
+                    const int sg = sgv[j];
                     if (sg) {
-                        const float bt = a.beta[((size_t)(sub0 + sb) * a.m + (r % a.m)) * a.H + g];
+                        const float bt = btv[j];
                         lam = sg > 0 ? __fsub_rd(lam, bt) : __fadd_ru(lam, bt);
                     }
                 }
@@ -611,6 +643,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
             } else {
                 // FP32 terms in chains of four (charged 8 u of the magnitude sum in the final pad);
                 // the magnitude sum itself is rounded up
+                const float p = ldexpf(acc[j], er + s_fexp[c] - 38);
                 const float lo = t0[c], hi = t1[c];
                 s1 += fminf(p * lo, p * hi);
                 s2 = __fadd_ru(s2, __fmul_ru(fabsf(p), fmaxf(fabsf(lo), fabsf(hi))));

@@ -412,7 +412,8 @@ typedef struct cv_alpha_in {
     float* grad_beta;
 } cv_alpha_in;
 
-/* Bytes of workspace cv_alpha_grad needs for B subdomains and m spec rows. */
+/* Bytes of workspace cv_alpha_grad needs for B subdomains and m spec rows (the workspace passed
+ * to cv_alpha_grad must be 256-byte aligned, else CV_EINVAL). */
 cv_status cv_alpha_grad_workspace(const cv_net* net, int B, int m, size_t* bytes);
 
 /* The spec lower bounds f [B x m] (as cv_bound_batch's back-substitution with these slopes,

@@ -211,6 +211,10 @@ extern "C" cv_status cv_alpha_grad(cv_net* net, const cv_cache* cache, const cv_
         cv_set_error("cv_alpha_grad: workspace too small: need " + std::to_string(L.total) + " bytes");
         return CV_EWORKSPACE;
     }
+    if (((uintptr_t)workspace & 255) != 0) {
+        cv_set_error("cv_alpha_grad: workspace must be 256-byte aligned");
+        return CV_EINVAL;
+    }
     char* ws = (char*)workspace;
     cudaStream_t st = (cudaStream_t)stream;
     const int R = B * m, n0 = net->dims[0];

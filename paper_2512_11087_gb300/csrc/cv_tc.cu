@@ -469,6 +469,16 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
             float bvv[8], pfv[8], alv[8], lbv[8], ubv[8];
             int stv[8];
             const size_t gar = ((size_t)sub * a.m + (r % a.m)) * a.H + a.hoff;
+            // all eight columns inside the layer and 16-byte aligned: kept products in and the next
+            // dP out as 16-byte accesses
+            const bool vq = (a.N & 3) == 0 && col0 + c0 + 8 <= a.N;
+            float aov[8];
+            if (vq) {
+                const float4* pf4 = (const float4*)(a.Pfwd + (size_t)r * a.N + col0 + c0);
+                const float4 x0 = pf4[0], x1 = pf4[1];
+                pfv[0] = x0.x; pfv[1] = x0.y; pfv[2] = x0.z; pfv[3] = x0.w;
+                pfv[4] = x1.x; pfv[5] = x1.y; pfv[6] = x1.z; pfv[7] = x1.w;
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int q = col0 + c0 + j;
@@ -476,7 +486,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 slotv[j] = qv ? a.slot_of[a.hoff + q] : -1;
                 fev[j] = qv ? a.fexp[q] : 0;
                 bvv[j] = qv ? a.bvec[q] : 0.f;
-                pfv[j] = qv ? a.Pfwd[(size_t)r * a.N + q] : 0.f;
+                if (!vq) pfv[j] = qv ? a.Pfwd[(size_t)r * a.N + q] : 0.f;
                 alv[j] = qv ? a.alpha[gar + q] : 0.f;
             }
 #pragma unroll
@@ -516,7 +526,15 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                     const int sg = a.bsign[(size_t)sub * a.H + g];
                     if (sg) a.grad_beta[ga] = (float)(-sg) * dl;
                 }
-                if (!a.last) a.Aout[(size_t)r * a.N + q] = dl * d + gf * e;
+                if (!a.last) {
+                    if (vq) aov[j] = dl * d + gf * e;
+                    else a.Aout[(size_t)r * a.N + q] = dl * d + gf * e;
+                }
+            }
+            if (vq && !a.last) {
+                float4* ao = (float4*)(a.Aout + (size_t)r * a.N + col0 + c0);
+                ao[0] = make_float4(aov[0], aov[1], aov[2], aov[3]);
+                ao[1] = make_float4(aov[4], aov[5], aov[6], aov[7]);
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -601,8 +619,11 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
         float s1 = 0.f, s2 = 0.f;
         // products and relaxation of the eight columns first, so that their global loads (slopes
         // given per row, split signs and multipliers) are issued together, not one column at a time
-        float pv[8], dv[8], ev[8], btv[8];
+        float pv[8], dv[8], ev[8], btv[8], lamv[8];
         int sgv[8];
+        // all eight columns inside the layer and 16-byte aligned: the outputs leave as two 16-byte
+        // stores per lane (a quarter of the sector writes of eight 4-byte ones)
+        const bool vec8 = a.i > 1 && (a.N & 3) == 0 && col0 + c0 + 8 <= a.N;
         if (a.i > 1) {
             const size_t arow = ((size_t)(sub0 + sb) * a.m + (r % a.m)) * a.H + a.hoff;
             const size_t srow = (size_t)(sub0 + sb) * a.H + a.hoff;
@@ -635,8 +656,11 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                         lam = sg > 0 ? __fsub_rd(lam, bt) : __fadd_ru(lam, bt);
                     }
                 }
-                a.Aout[(size_t)r * a.N + q] = lam;
-                if (a.keepP) a.keepP[(size_t)r * a.N + q] = p;
+                if (vec8) lamv[j] = lam;
+                else {
+                    a.Aout[(size_t)r * a.N + q] = lam;
+                    if (a.keepP) a.keepP[(size_t)r * a.N + q] = p;
+                }
                 s1 = fmaf(p, e, s1);
                 s1 = fmaf(lam, s_bn[c], s1);
                 s2 = fmaf(fabsf(lam), s_vn[c], s2);
@@ -650,6 +674,16 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 if (a.lam0) a.lam0[(size_t)r * a.N + q] = p;
             }
             if ((j & 3) == 3) { pb += (double)s1; pp += (double)s2; s1 = 0.f; s2 = 0.f; }
+        }
+        if (vec8) {
+            float4* ao = (float4*)(a.Aout + (size_t)r * a.N + col0 + c0);
+            ao[0] = make_float4(lamv[0], lamv[1], lamv[2], lamv[3]);
+            ao[1] = make_float4(lamv[4], lamv[5], lamv[6], lamv[7]);
+            if (a.keepP) {
+                float4* ko = (float4*)(a.keepP + (size_t)r * a.N + col0 + c0);
+                ko[0] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+                ko[1] = make_float4(pv[4], pv[5], pv[6], pv[7]);
+            }
         }
         pb += (double)s1;
         pp += (double)s2;

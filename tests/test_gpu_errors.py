@@ -168,3 +168,33 @@ def test_host_checks_before_any_launch(setup):
         capi.cv_bound_batch(net.handle, net.cache, bi, rnd.bo, rnd.opt, rnd.ws, rnd.ws_bytes - 256)
     assert e.value.status == capi.CV_EWORKSPACE
     assert _status(net) == (capi.CV_OK, 0)
+
+
+def test_misaligned_workspace_is_refused_before_any_launch(setup):
+    """cv_bound_batch and cv_alpha_grad take a 256-byte aligned workspace (their kernels use 16-byte
+    vector accesses and TMA into it); a misaligned one is refused with CV_EINVAL and nothing runs."""
+    from paper_2512_11087_gb300 import capi, engine as E
+    case, net = setup
+    ref = _round(case, net)
+    d = E.to_dev
+    rnd = E.Round(net, case.B, case.m, max_splits=case.max_splits, sweeps=case.sweeps)
+    keep = [d(case.lo), d(case.hi), d(case.C), d(case.t), d(case.split_off), d(case.split_ids)]
+    bi = capi.make_batch_in(case.B, keep[0], keep[1], case.m, keep[2], keep[3], split_off=keep[4],
+                            split_ids=keep[5], max_splits=case.max_splits)
+    bad = torch.empty(rnd.ws_bytes + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.CVError) as e:
+        capi.cv_bound_batch(net.handle, net.cache, bi, rnd.bo, rnd.opt, bad[4:], rnd.ws_bytes)
+    assert e.value.status == capi.CV_EINVAL
+    # the slope gradient, on this round's bounds and masks
+    st = E.AlphaState(net, d(case.lo), d(case.hi), d(ref["l"]), d(ref["u"]), d(ref["mask"]), d(case.C), d(case.t))
+    alpha = torch.full((case.B, case.m, net.H), 0.5, dtype=torch.float32, device="cuda")
+    lower = torch.empty(case.B, case.m, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(alpha)
+    ai = capi.make_alpha_in(st.B, st.m, st.lo, st.hi, st.l, st.u, st.mask, st.C, st.t, alpha, None)
+    bad = torch.empty(st.ws_bytes + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.CVError) as e:
+        capi.cv_alpha_grad(net.handle, net.cache, ai, lower, grad, bad[4:], st.ws_bytes)
+    assert e.value.status == capi.CV_EINVAL
+    torch.cuda.synchronize()
+    assert _status(net) == (capi.CV_OK, 0)
+    _clean_round_unchanged(case, net, ref)

@@ -472,12 +472,31 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
             // all eight columns inside the layer and 16-byte aligned: kept products in and the next
             // dP out as 16-byte accesses
             const bool vq = (a.N & 3) == 0 && col0 + c0 + 8 <= a.N;
-            float aov[8];
+            float aov[8], gav[8], gbv[8];
+            int sgv[8];
             if (vq) {
                 const float4* pf4 = (const float4*)(a.Pfwd + (size_t)r * a.N + col0 + c0);
                 const float4 x0 = pf4[0], x1 = pf4[1];
                 pfv[0] = x0.x; pfv[1] = x0.y; pfv[2] = x0.z; pfv[3] = x0.w;
                 pfv[4] = x1.x; pfv[5] = x1.y; pfv[6] = x1.z; pfv[7] = x1.w;
+            }
+            // the slopes and their gradient (and the multipliers' gradient) as 16-byte accesses when
+            // their addresses allow; every entry of the eight is then written (0 where nothing enters:
+            // the buffers were cleared before the sweep)
+            const bool vg = vq && ((uintptr_t)(a.alpha + gar + col0 + c0) & 15) == 0 &&
+                            ((uintptr_t)(a.grad_alpha + gar + col0 + c0) & 15) == 0 &&
+                            (!a.bsign || ((uintptr_t)(a.grad_beta + gar + col0 + c0) & 15) == 0);
+            if (vg) {
+                const float4* al4 = (const float4*)(a.alpha + gar + col0 + c0);
+                const float4 x0 = al4[0], x1 = al4[1];
+                alv[0] = x0.x; alv[1] = x0.y; alv[2] = x0.z; alv[3] = x0.w;
+                alv[4] = x1.x; alv[5] = x1.y; alv[6] = x1.z; alv[7] = x1.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                gav[j] = 0.f;
+                gbv[j] = 0.f;
+                sgv[j] = (a.bsign && col0 + c0 + j < a.N) ? (int)a.bsign[(size_t)sub * a.H + a.hoff + col0 + c0 + j] : 0;
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -487,7 +506,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 fev[j] = qv ? a.fexp[q] : 0;
                 bvv[j] = qv ? a.bvec[q] : 0.f;
                 if (!vq) pfv[j] = qv ? a.Pfwd[(size_t)r * a.N + q] : 0.f;
-                alv[j] = qv ? a.alpha[gar + q] : 0.f;
+                if (!vg) alv[j] = qv ? a.alpha[gar + q] : 0.f;
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -505,7 +524,6 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 const int q = col0 + c0 + j;
                 if (q >= a.N) continue;
                 const float dl = ldexpf(acc[j], er + fev[j] - 38) + gf * bvv[j];
-                const int g = a.hoff + q;
                 const float lb = lbv[j], ub = ubv[j];
                 const int st = stv[j];
                 const float pf = pfv[j];
@@ -516,15 +534,19 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 else if (pf >= 0.f) {
                     d = alv[j];
                     e = 0.f;
-                    a.grad_alpha[ga] = dl * pf;
+                    if (vg) gav[j] = dl * pf;
+                    else a.grad_alpha[ga] = dl * pf;
                 } else {
                     const float s = ub / (ub - lb);
                     d = s;
                     e = -s * lb;
                 }
                 if (a.bsign) {
-                    const int sg = a.bsign[(size_t)sub * a.H + g];
-                    if (sg) a.grad_beta[ga] = (float)(-sg) * dl;
+                    const int sg = sgv[j];
+                    if (sg) {
+                        if (vg) gbv[j] = (float)(-sg) * dl;
+                        else a.grad_beta[ga] = (float)(-sg) * dl;
+                    }
                 }
                 if (!a.last) {
                     if (vq) aov[j] = dl * d + gf * e;
@@ -535,6 +557,16 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 float4* ao = (float4*)(a.Aout + (size_t)r * a.N + col0 + c0);
                 ao[0] = make_float4(aov[0], aov[1], aov[2], aov[3]);
                 ao[1] = make_float4(aov[4], aov[5], aov[6], aov[7]);
+            }
+            if (vg) {
+                float4* go = (float4*)(a.grad_alpha + gar + col0 + c0);
+                go[0] = make_float4(gav[0], gav[1], gav[2], gav[3]);
+                go[1] = make_float4(gav[4], gav[5], gav[6], gav[7]);
+                if (a.bsign) {
+                    float4* bo = (float4*)(a.grad_beta + gar + col0 + c0);
+                    bo[0] = make_float4(gbv[0], gbv[1], gbv[2], gbv[3]);
+                    bo[1] = make_float4(gbv[4], gbv[5], gbv[6], gbv[7]);
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -638,9 +670,22 @@ __global__ void __launch_bounds__(256, 2) k_tc_layer(const __grid_constant__ CUt
                 sgv[j] = (qv && a.bsign) ? (int)a.bsign[srow + col0 + c] : 0;
                 btv[j] = (qv && a.bsign) ? a.beta[arow + col0 + c] : 0.f;
             }
+            bool need = false;  // the table says NaN only when slopes are given per row (alpha set)
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (col0 + c0 + j < a.N && dv[j] != dv[j]) dv[j] = a.alpha[arow + col0 + c0 + j];
+            for (int j = 0; j < 8; ++j) need |= dv[j] != dv[j];
+            if (need && vec8 && a.alpha && ((uintptr_t)(a.alpha + arow + col0 + c0) & 15) == 0) {
+                // slopes given per row: all eight as two 16-byte loads, used where the table says NaN
+                const float4* al4 = (const float4*)(a.alpha + arow + col0 + c0);
+                const float4 x0 = al4[0], x1 = al4[1];
+                const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (dv[j] != dv[j]) dv[j] = xs[j];
+            } else if (need) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (col0 + c0 + j < a.N && dv[j] != dv[j]) dv[j] = a.alpha[arow + col0 + c0 + j];
+            }
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {

@@ -508,6 +508,16 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
         return (-x) * rk[j];
     };
     bool keys_ok = true;  // the key buffer holds every element's key
+    // With E' = c1 |1/g_kj| + tu |q_j| (every operation rounded up) >= E_j, an element whose interval
+    // with E' lies wholly below the window is below it (class 1) and one wholly above is outside it
+    // (class 0), exactly as classify finds with its own E_j <= E'; -1: the element needs its own test.
+    // (g_kj = 0 gives weight 0: either class leaves the sums unchanged.)
+    auto preclass = [&](int j, float q) -> int {
+        const float Ep = __fmaf_ru(c1, fabsf(rk[j]), __fmul_ru(tu, fabsf(q)));
+        if (__fadd_ru(q, Ep) < Lw) return 1;
+        if (__fsub_rd(q, Ep) > Hw) return 0;
+        return -1;
+    };
     // the element's own interval against the window: 1 below, 2 candidate, 3 exact zero inside, 0 else
     auto classify = [&](int j, float q, float av) -> int {
         const float r = rk[j];
@@ -620,10 +630,15 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
                 }
             }
         } else {
+            // a widened window: every element, most of them settled by the global bound
 #pragma unroll 1
             for (int j0 = 0; j0 < n0; j0 += 32) {
                 const int j = j0 + lane;
-                if (j < n0) take(j, keys_ok ? __uint_as_float(keys[j]) : key_calc(j), __ldg(ap + j));
+                if (j >= n0) continue;
+                const float q = keys_ok ? __uint_as_float(keys[j]) : key_calc(j);
+                const int pc = preclass(j, q);
+                if (pc == 1) fb += (unsigned long long)wk[j];
+                else if (pc < 0) take(j, q, __ldg(ap + j));
             }
         }
         nc = __reduce_add_sync(0xffffffffu, (unsigned)nloc);
@@ -639,8 +654,11 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
                 const int jj = v ? j : n0 - 1;
                 const float q = keys_ok ? __uint_as_float(keys[jj]) : key_calc(jj);
                 bool look = v;
+                int pc = -1;
                 if (it == 0) look = v && fabsf(q - qs) <= fmaf(sc1, fabsf(rk[jj]), fmaf(stu, fabsf(q), sEs));
-                const int cls = look ? take(jj, q, __ldg(ap + jj)) : 0;
+                else if (v) pc = preclass(jj, q);
+                if (pc == 1) fb += (unsigned long long)wk[jj];
+                const int cls = (look && pc < 0) ? take(jj, q, __ldg(ap + jj)) : (pc == 1 ? 1 : 0);
                 const unsigned bal = __ballot_sync(0xffffffffu, cls == 2);
                 const int pos = ncl + __popc(bal & below_lanes);
                 if (cls == 2 && pos < CAPC) cidx[pos] = (unsigned short)jj;
@@ -674,6 +692,7 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
                     if (j >= n0) continue;
                     const float q = keys_ok ? __uint_as_float(keys[j]) : key_calc(j);
                     if (it0 && !(fabsf(q - qs) <= fmaf(sc1, fabsf(rk[j]), fmaf(stu, fabsf(q), sEs)))) continue;
+                    if (!it0 && preclass(j, q) >= 0) continue;  // settled by the global bound: not a candidate
                     const float av = __ldg(ap + j);
                     if (classify(j, q, av) != 2) continue;
                     float kh, kl;
@@ -691,21 +710,120 @@ __device__ __forceinline__ void cc_certify(int n0, int R, int k, int lane, const
                 found = true;
                 rh = -INFINITY; rl = 0.f; rj = -1;
             } else {
+                // The same bisections, with each count taken from stored ordinals.  One pass computes
+                // every candidate's exact breakpoint once and keeps the ordinal of its leading part over
+                // the key buffer (NONC, above every pivot, for the other elements), so the first bisection
+                // reads ordinals; the candidates tied at its result then get their trailing parts in the
+                // list buffer for the other two.  Every count equals count_le's at the same point.
+                constexpr unsigned NONC = 0xffffffffu;  // no finite breakpoint has this ordinal
+                const unsigned z = ordf(0.f);           // the exact zeros' point (0, 0, -1)
+#pragma unroll 1
+                for (int j0 = 0; j0 < n0; j0 += 32) {
+                    const int j = j0 + lane;
+                    if (j >= n0) continue;
+                    const float q = keys_ok ? __uint_as_float(keys[j]) : key_calc(j);
+                    bool cand;
+                    if (it0) cand = fabsf(q - qs) <= fmaf(sc1, fabsf(rk[j]), fmaf(stu, fabsf(q), sEs));
+                    else cand = preclass(j, q) < 0;
+                    unsigned o = NONC;
+                    if (cand) {
+                        const float av = __ldg(ap + j);
+                        if (classify(j, q, av) == 2) {
+                            float kh, kl;
+                            ff_key(j, av, kh, kl);
+                            o = ordf(kh);
+                        }
+                    }
+                    keys[j] = o;  // (each lane rewrites only the elements it read)
+                }
+                keys_ok = false;
+                __syncwarp();
+                // weight of the candidates whose leading ordinal is at or below X1 (the count at
+                // (X1, max, max)), plus Fb and the zeros
+                auto count1 = [&](unsigned X1) -> long long {
+                    unsigned long long f = 0ull;
+#pragma unroll 1
+                    for (int j0 = 0; j0 < n0; j0 += 32 * 4) {
+                        unsigned kq[4];
+                        unsigned long long wq[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = min(j0 + 32 * u + lane, n0 - 1);
+                            kq[u] = keys[j];
+                            wq[u] = (unsigned long long)wk[j];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (j0 + 32 * u + lane < n0 && kq[u] <= X1) f += wq[u];
+                    }
+                    long long F2 = Fb + warp_sum64(f);
+                    if (z <= X1) F2 += Fz;
+                    return F2;
+                };
                 // invariants F(<= low end) < T <= F(<= high end); ordinal 0 lies below every key
                 unsigned l1 = 0u, h1 = 0xffffffffu;
                 while (h1 - l1 > 1u) {
                     const unsigned m1 = l1 + ((h1 - l1) >> 1);
-                    if (count_le(m1, 0xffffffffu, INT_MAX) >= T) h1 = m1; else l1 = m1;
+                    if (count1(m1) >= T) h1 = m1; else l1 = m1;
                 }
+                // the candidates tied at h1: listed (at most CAPC), their trailing ordinals over their key
+                // slots; the weight strictly below h1 summed on the way
+                unsigned long long fl = 0ull;
+                int ntie = 0;
+#pragma unroll 1
+                for (int j0 = 0; j0 < n0; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool v = j < n0;
+                    const unsigned o = v ? keys[j] : NONC;
+                    if (v && o < h1) fl += (unsigned long long)wk[j];
+                    const bool tie = v && o == h1 && o != NONC;
+                    const unsigned bal = __ballot_sync(0xffffffffu, tie);
+                    const int pos = ntie + __popc(bal & below_lanes);
+                    if (tie && pos < CAPC) cidx[pos] = (unsigned short)j;
+                    ntie += __popc(bal);
+                }
+                __syncwarp();
+                const long long Flow = Fb + warp_sum64(fl);
                 unsigned l2 = 0u, h2 = 0xffffffffu;
-                while (h2 - l2 > 1u) {
-                    const unsigned m2 = l2 + ((h2 - l2) >> 1);
-                    if (count_le(h1, m2, INT_MAX) >= T) h2 = m2; else l2 = m2;
-                }
                 int l3 = -2, h3 = n0;
-                while (h3 - l3 > 1) {
-                    const int m3 = l3 + ((h3 - l3) >> 1);
-                    if (count_le(h1, h2, m3) >= T) h3 = m3; else l3 = m3;
+                if (ntie <= CAPC) {
+                    for (int t = lane; t < ntie; t += 32) {
+                        const int j = cidx[t];
+                        float kh, kl;
+                        ff_key(j, __ldg(ap + j), kh, kl);
+                        keys[j] = ordf(kl);
+                    }
+                    __syncwarp();
+                    // weight at or below (h1, X2, X3) from the list
+                    auto count23 = [&](unsigned X2, int X3) -> long long {
+                        unsigned long long f = 0ull;
+                        for (int t = lane; t < ntie; t += 32) {
+                            const int j = cidx[t];
+                            const unsigned o2 = keys[j];
+                            if (o2 < X2 || (o2 == X2 && j <= X3)) f += (unsigned long long)wk[j];
+                        }
+                        long long F2 = Flow + warp_sum64(f);
+                        if (z < h1 || (z == h1 && (z < X2 || (z == X2 && -1 <= X3)))) F2 += Fz;
+                        return F2;
+                    };
+                    while (h2 - l2 > 1u) {
+                        const unsigned m2 = l2 + ((h2 - l2) >> 1);
+                        if (count23(m2, INT_MAX) >= T) h2 = m2; else l2 = m2;
+                    }
+                    while (h3 - l3 > 1) {
+                        const int m3 = l3 + ((h3 - l3) >> 1);
+                        if (count23(h2, m3) >= T) h3 = m3; else l3 = m3;
+                    }
+                } else {
+                    // more ties than the list holds: the counts recomputed from the rows
+                    while (h2 - l2 > 1u) {
+                        const unsigned m2 = l2 + ((h2 - l2) >> 1);
+                        if (count_le(h1, m2, INT_MAX) >= T) h2 = m2; else l2 = m2;
+                    }
+                    while (h3 - l3 > 1) {
+                        const int m3 = l3 + ((h3 - l3) >> 1);
+                        if (count_le(h1, h2, m3) >= T) h3 = m3; else l3 = m3;
+                    }
                 }
                 found = true;
                 rh = unord(h1); rl = unord(h2); rj = h3;

@@ -367,3 +367,39 @@ def test_round_summary_of_a_round():
     assert s["infeasible"] == int((~ofeas).sum()) and s["verified"] == int((ofeas & (o["verified"] == 1)).sum())
     assert 0 < s["infeasible"] and 0 < s["verified"] < case.B - s["infeasible"]
     net.close()
+
+
+@pytest.mark.parametrize("n0,extra", [(200, 1), (600, 1), (200, 4), (600, 4)])
+def test_complete_clipping_exact_ties_over_the_candidate_limit(n0, extra):
+    """Every breakpoint of a row step exactly tied.
+
+    The first hidden neuron's plane is all ones and the first row is g = -1 (sum x >= the box
+    centre's sum, less a slack), so on that row's first step every element's breakpoint is exactly
+    1: every element is a candidate of the certification, more than its list holds. The over-limit
+    search bisects on the candidates' stored ordinals. Their ties fit the list (n0 = 200) or exceed
+    it (n0 = 600: the counts recomputed from the rows). With 1 random row besides, the main launch
+    runs; with 4, the wide launch. Against the oracle's FP64 Algorithm 1; the search must have run."""
+    from paper_2512_11087_gb300 import workloads as WL
+    dims = [n0, 4, 3]
+    layers = WL.he_mlp(dims, seed=41)
+    lo0, hi0 = WL.box(n0, 0.05, seed=41, centre="unit", clip01=True)
+    xh = 0.5 * (lo0.astype(np.float64) + hi0.astype(np.float64))
+    ep = 0.5 * (hi0.astype(np.float64) - lo0.astype(np.float64))
+    layers[0]["W"][0, :] = 1.0
+    layers[0]["b"][0] = np.float32(-xh.sum())
+    case = Case(dims, 2, 0, 0, 0.05, seed=41, layers=layers, sweeps=3, relaxed=0)
+    assert np.array_equal(case.lo0, lo0) and np.array_equal(case.hi0, hi0)
+    off, Gr, hr = WL.random_cut_rows(case.lo, case.hi, case.B, extra, extra, seed=43)
+    G = np.empty((case.B * (extra + 1), n0), np.float32)
+    h = np.empty(case.B * (extra + 1), np.float32)
+    for b in range(case.B):
+        G[b * (extra + 1)] = -1.0
+        h[b * (extra + 1)] = np.float32(xh.sum() - 0.3 * ep.sum())
+        G[b * (extra + 1) + 1:(b + 1) * (extra + 1)] = Gr[off[b]:off[b + 1]]
+        h[b * (extra + 1) + 1:(b + 1) * (extra + 1)] = hr[off[b]:off[b + 1]]
+    case.row_off = np.arange(0, case.B * (extra + 1) + 1, extra + 1, dtype=np.int32)
+    case.G, case.h, case.max_rows = G, h, extra + 1
+    g = gpu_round(case)
+    o = case.oracle()
+    compare(case, g, o)
+    assert LAST_CC_STATS[5] > 0, LAST_CC_STATS  # the over-limit search ran

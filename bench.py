@@ -953,7 +953,7 @@ def bench_bab_loop(steps, warmup, flush, stream, peaks, cpu=True, batch=2048, to
                                           f"{dt:.1f} s)")
     return out
 
-
+    """The FP32 FMA issue peak (measured here) and the HBM / BF16 peaks measured on this GPU type (MEASURED_PEAKS.json)."""
 def measure_peaks():
     """The FP32 FMA issue peak (measured here) and the driver's measured HBM / BF16 peaks."""
     from paper_2512_11087_gb300 import capi

@@ -953,9 +953,10 @@ def bench_bab_loop(steps, warmup, flush, stream, peaks, cpu=True, batch=2048, to
                                           f"{dt:.1f} s)")
     return out
 
-    """The FP32 FMA issue peak (measured here) and the HBM / BF16 peaks measured on this GPU type (MEASURED_PEAKS.json)."""
+
 def measure_peaks():
-    """The FP32 FMA issue peak (measured here) and the driver's measured HBM / BF16 peaks."""
+    """The FP32 FMA issue peak (measured here) and the HBM / BF16 peaks measured on this GPU type
+    (MEASURED_PEAKS.json)."""
     from paper_2512_11087_gb300 import capi
     fma, ms = capi.cv_fp32_fma_peak()
     p = dict(fma_lane_gops=fma / 1e9, fma_probe_ms=ms)

@@ -3,7 +3,8 @@
 Pins: Lemma A.1 (box extremes at vertices), Theorem 1 (one-row complete clipping
 is the exact LP optimum; equals the fractional-knapsack greedy), Theorem 2
 (one-row relaxed clipping is component-wise tight), weak duality and monotone
-ascent for Algorithm 1 with several rows, the a-priori infeasibility test, the
+ascent for Algorithm 1 with several rows, its exactness when the rows' supports are disjoint (a
+separable dual), the a-priori infeasibility test, the
 order-dependency example of the Appendix (Algorithm 3 vs Algorithm 2), the constraint
 importance order (hyperplane distances by least squares), and the batch round's relaxed
 modes (parallel, sequential, sequential in importance order) on a hand-derived example and
@@ -92,6 +93,37 @@ def test_multi_row_weak_duality_and_monotone_ascent():
             assert v >= prev - 1e-12 * (1 + abs(prev))      # ascent never decreases the dual
             assert O.dual_value(a, c, G, h, lo, hi, beta) == pytest.approx(v, abs=1e-12 * (1 + abs(v)))
             prev = v
+
+
+def test_multi_row_disjoint_supports_is_exact_lp():
+    """Rows on disjoint sets of coordinates make the dual separable: D(beta) is a constant plus one
+    concave 1-D dual per row, and each row step of Algorithm 1 maximises its own exactly (Theorem 1),
+    whatever the other multipliers. So one sweep reaches the dual optimum, and by LP duality the value
+    is the exact LP optimum over the box and all rows (vertex enumeration)."""
+    rng = np.random.default_rng(8)
+    for _ in range(80):
+        R = int(rng.integers(2, 4))
+        sizes = rng.integers(1, 3, size=R)
+        while sizes.sum() > 4:
+            sizes[int(np.argmax(sizes))] -= 1
+        n = int(sizes.sum()) + int(rng.integers(0, 2))  # plus at most one coordinate in no row
+        lo, hi = rand_box(rng, n)
+        xh, ep = (lo + hi) / 2, (hi - lo) / 2
+        perm = rng.permutation(n)
+        G = np.zeros((R, n))
+        h = np.zeros(R)
+        start = 0
+        for p in range(R):
+            idx = perm[start:start + sizes[p]]
+            start += sizes[p]
+            G[p, idx] = rng.normal(size=idx.size)
+            h[p] = -(G[p] @ xh) + rng.uniform(-0.6, 0.6) * (np.abs(G[p]) @ ep)  # cuts its own coordinates
+        a, c = rng.normal(size=n), rng.normal()
+        lp = lp_vertex(a, c, G, h, lo, hi)
+        for sweeps in (1, 3):
+            v, beta, _ = O.complete_clip(a, c, G, h, lo, hi, sweeps=sweeps)
+            assert np.all(beta >= 0.0)
+            assert v == pytest.approx(lp, abs=1e-9 * (1 + abs(lp))), (sweeps, v, lp)
 
 
 def test_infeasibility_precheck_matches_lp():

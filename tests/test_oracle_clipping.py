@@ -2,7 +2,8 @@
 
 Pins: Lemma A.1 (box extremes at vertices), Theorem 1 (one-row complete clipping
 is the exact LP optimum; equals the fractional-knapsack greedy), Theorem 2
-(one-row relaxed clipping is component-wise tight), weak duality and monotone
+(one-row relaxed clipping is component-wise tight; with several rows, the tightest row per
+coordinate), weak duality and monotone
 ascent for Algorithm 1 with several rows, its exactness when the rows' supports are disjoint (a
 separable dual), the a-priori infeasibility test, the
 order-dependency example of the Appendix (Algorithm 3 vs Algorithm 2), the constraint
@@ -70,6 +71,33 @@ def test_one_row_relaxed_clip_is_componentwise_tight():
             e = np.eye(n)[i]
             assert lo2[i] == pytest.approx(lp_vertex(e, 0.0, [g], [h], lo, hi, "min"), abs=1e-9)
             assert hi2[i] == pytest.approx(lp_vertex(e, 0.0, [g], [h], lo, hi, "max"), abs=1e-9)
+
+
+def test_multi_row_relaxed_clip_is_the_tightest_row_on_the_same_box():
+    """Algorithm 2 clips the box with every row against the same (unclipped) box and keeps the
+    tightest end per coordinate: each end is the best of the rows' one-row LP optima (Theorem 2),
+    computed here by vertex enumeration for each row alone."""
+    rng = np.random.default_rng(9)
+    for _ in range(60):
+        n = int(rng.integers(1, 5))
+        R = int(rng.integers(2, 4))
+        lo, hi = rand_box(rng, n)
+        rows = [cutting_row(rng, lo, hi, spread=0.5) for _ in range(R)]
+        G = [g for g, _ in rows]
+        h = [hh for _, hh in rows]
+        lo2, hi2, inf = O.relaxed_clip(G, h, lo, hi)
+        want_lo = np.array([max(lp_vertex(np.eye(n)[i], 0.0, [g], [hh], lo, hi, "min") for g, hh in rows)
+                            for i in range(n)])
+        want_hi = np.array([min(lp_vertex(np.eye(n)[i], 0.0, [g], [hh], lo, hi, "max") for g, hh in rows)
+                            for i in range(n)])
+        gap = np.max(want_lo - want_hi)
+        if abs(gap) <= 1e-9:
+            continue  # an interval closing to a point: the decision is a tie
+        # the rows' intervals fail to meet in some coordinate exactly when the batch is infeasible
+        assert inf == (gap > 0), (gap, inf)
+        if not inf:
+            assert np.allclose(lo2, want_lo, rtol=0, atol=1e-9)
+            assert np.allclose(hi2, want_hi, rtol=0, atol=1e-9)
 
 
 def test_multi_row_weak_duality_and_monotone_ascent():
